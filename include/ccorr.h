@@ -1,0 +1,271 @@
+/*
+ * ccorr -- point-to-point correlation measures between ensemble member
+ * vectors at pairs of 3D grid points, on one GB300 GPU (sm_103a).
+ *
+ * Method: arxiv 2309.03308, "Adaptive Sampling of 3D Spatial Correlations for
+ * Focus+Context Visualization". The library evaluates Pearson (PPMCC),
+ * Spearman, joint-histogram mutual information and the Kraskov (KSG) k-NN
+ * mutual-information estimator (Section 3.2) on batches of point pairs, all
+ * pairs between two regions ("bricks", Section 3), and reduces them to the
+ * per-region-pair maximum (Section 3: the brick-pair indicator).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns cc_status (0 = CC_OK, negative = error) and never
+ *     throws or aborts across the ABI. cc_last_error() gives a message.
+ *   - Work is queued on the context's CUDA stream. Functions that return data
+ *     in HOST memory synchronise that stream before they return; functions
+ *     writing only DEVICE memory are asynchronous. cc_sync() waits and reports
+ *     any error a kernel recorded in the context's device status word.
+ *   - Caller buffers stay owned by the caller. Flags named *_is_device / *_on_device
+ *     say whether a pointer is device memory (e.g. a PyTorch CUDA tensor's
+ *     data pointer) or host memory.
+ *   - A field is an ensemble on an X x Y x Z grid with n members, fp32, given
+ *     in layout [n][Z][Y][X] (member-major, x fastest). Grid point ids are
+ *     linear: id = x + X * (y + Y * z).
+ *   - Regions are half-open axis-aligned boxes of one field. The points of a
+ *     region are enumerated x fastest, then y, then z; a region-local index
+ *     is a position in that enumeration.
+ *   - Measures with identical results on both GPUs are bit-exact: average
+ *     ranks, bin ids and KSG neighbour counts (from the same fp32 input).
+ *   - One context may be used by one host thread at a time.
+ */
+#ifndef CCORR_H
+#define CCORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_ctx cc_ctx;
+typedef int32_t cc_status;
+
+#define CC_OK 0
+#define CC_ERR_INVALID_ARG (-1)  /* bad pointer, size, id or parameter */
+#define CC_ERR_OOM (-2)          /* device or host allocation failed */
+#define CC_ERR_CUDA (-3)         /* a CUDA call failed (message has the CUDA error) */
+#define CC_ERR_NONFINITE (-4)    /* NaN or Inf in a loaded field */
+#define CC_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define CC_ERR_UNSUPPORTED (-6)  /* valid request this build or device cannot run */
+
+/* Measures (Section 3.2; Spearman is a project addition). */
+#define CC_PEARSON 0   /* PPMCC of the member vectors */
+#define CC_SPEARMAN 1  /* PPMCC of the average (tie-averaged) ranks */
+#define CC_MI_BINNED 2 /* MI of the joint histogram, bins equal-width over each point's [min,max] */
+#define CC_MI_KSG 3    /* Kraskov estimator, Chebyshev k-NN in the joint space */
+
+/* Arithmetic of Pearson/Spearman (other measures ignore it). */
+#define CC_FP32 0       /* fp32 values and accumulation */
+#define CC_BF16 1       /* bf16 tensor-core contraction, fp32 accumulation */
+#define CC_FP8_E4M3 2   /* fp8 e4m3 (per-point scale) tensor-core contraction, fp32 accumulation */
+#define CC_FP32_DOT2 3  /* compensated fp32 (Dot2: TwoProduct/TwoSum) */
+
+/*
+ * Measure parameters.
+ *   measure   CC_PEARSON .. CC_MI_KSG
+ *   k         KSG neighbour count, 1 <= k <= min(n-1, 32); k = -1 selects the
+ *             paper's rule k = ceil(3n/100) (Section 3.2). Ignored otherwise.
+ *   bins      histogram bins per variable for CC_MI_BINNED, 2..16.
+ *   precision CC_FP32 .. CC_FP32_DOT2 (Pearson/Spearman only).
+ *   flags     reserved, must be 0.
+ */
+typedef struct {
+    int32_t measure;
+    int32_t k;
+    int32_t bins;
+    int32_t precision;
+    int32_t flags;
+} cc_params;
+
+/* Half-open voxel box [x0,x1) x [y0,y1) x [z0,z1). */
+typedef struct {
+    int32_t x0, y0, z0, x1, y1, z1;
+} cc_box;
+
+/*
+ * Extremes of one region pair (Section 3: maximum over point pairs; Section
+ * 5.3 also uses the minimum). argmax/argmin are pair indices whose meaning is
+ * given by the producing call; ties resolve to the smallest index. count is
+ * the number of pairs reduced; with count == 0, max = -inf and min = +inf.
+ */
+typedef struct {
+    float max;
+    float min;
+    uint64_t argmax;
+    uint64_t argmin;
+    uint64_t count;
+} cc_rp_result;
+
+/* ------------------------------------------------------------------------ context */
+
+/*
+ * Create a context on CUDA device `device`. `stream` is a cudaStream_t to
+ * queue work on (e.g. a PyTorch stream handle) or NULL for a stream the
+ * context creates and owns. *out receives the context.
+ */
+cc_status cc_create(int device, void* stream, cc_ctx** out);
+
+/* Release every device buffer of the context (fields, regions, scratch). */
+cc_status cc_destroy(cc_ctx* ctx);
+
+/* Message of the last failing call on this context; owned by the context. */
+const char* cc_last_error(const cc_ctx* ctx);
+
+/* Wait for the context's stream; returns a device-recorded error if any. */
+cc_status cc_sync(cc_ctx* ctx);
+
+/* --------------------------------------------------------------- field ingest */
+
+/*
+ * Load an ensemble field and precompute its per-point planes (Section 3: an
+ * ensemble of n members on an X x Y x Z grid; Section 3.2: PPMCC needs only
+ * the means and variances). data is fp32 [n][Z][Y][X]; data_is_device says
+ * where it lives. The library copies it; the caller keeps ownership.
+ * Per grid point the library computes, on the GPU: FP64 mean and sum of
+ * squared deviations, the unit-norm centred vector used by Pearson, the
+ * doubled average ranks and unit-norm centred ranks used by Spearman, the
+ * member values in ascending order with their stable argsort (KSG).
+ * Requires 2 <= n <= 1024. A NaN or Inf anywhere returns CC_ERR_NONFINITE and
+ * loads nothing. *field_id receives the new field's id.
+ */
+cc_status cc_load_field(cc_ctx* ctx, const float* data, int data_is_device, int X, int Y, int Z,
+                        int n, int32_t* field_id);
+
+/*
+ * Replace the member values of an already loaded field (same X, Y, Z, n) and
+ * recompute every per-point plane in place, reusing the field's buffers (an
+ * update from host memory stages through a device buffer of the field's size,
+ * allocated on the first such call and kept with the field). Planes of the
+ * field's regions and bin planes are rebuilt on their next use. Asynchronous:
+ * a NaN or Inf is reported as CC_ERR_NONFINITE by cc_sync or by the next call
+ * that returns host data.
+ */
+cc_status cc_update_field(cc_ctx* ctx, int32_t field_id, const float* data, int data_is_device);
+
+/* Drop a field and its regions' device planes. */
+cc_status cc_free_field(cc_ctx* ctx, int32_t field_id);
+
+/*
+ * Read back per-point planes for inspection (bit-exact tests). plane:
+ *   CC_PLANE_RANK2   int32 [count][n]  doubled average rank 2*rank (1-based)
+ *   CC_PLANE_BINS    uint8 [count][n]  bin ids for `bins` bins
+ *   CC_PLANE_SORTED  float [count][n]  ascending member values
+ *   CC_PLANE_ZHAT    float [count][n]  (v - mean) / sqrt(sum of squared deviations)
+ * pts are `count` grid point ids (host); out is host memory.
+ */
+#define CC_PLANE_RANK2 0
+#define CC_PLANE_BINS 1
+#define CC_PLANE_SORTED 2
+#define CC_PLANE_ZHAT 3
+cc_status cc_get_plane(cc_ctx* ctx, int32_t field_id, int plane, int bins, const uint32_t* pts,
+                       int64_t count, void* out);
+
+/* --------------------------------------------------------------------- regions */
+
+/*
+ * Define `count` regions (bricks, Section 3) of field `field_id` from boxes
+ * (host array). region_ids (host, `count` entries) receives their ids.
+ */
+cc_status cc_define_regions(cc_ctx* ctx, int32_t field_id, const cc_box* boxes, int count,
+                            int32_t* region_ids);
+
+/*
+ * Partition the field into axis-aligned boxes of bx x by x bz voxels
+ * (Section 3: bricks; boxes at the high boundary are smaller when the grid
+ * size is not a multiple). Boxes are enumerated x fastest, then y, then z.
+ * Up to `cap` ids go to region_ids; *count receives the number of regions.
+ * Returns CC_ERR_INVALID_ARG (and defines nothing) if cap is too small.
+ */
+cc_status cc_partition_regular(cc_ctx* ctx, int32_t field_id, int bx, int by, int bz,
+                               int32_t* region_ids, int cap, int* count);
+
+/* Number of points of a region (*npoints) and its box (*box, may be NULL). */
+cc_status cc_region_info(cc_ctx* ctx, int32_t region_id, int64_t* npoints, cc_box* box);
+
+/* ------------------------------------------------------------------- sampling */
+
+/*
+ * Uniform random point pairs between two regions (Section 3.1: random
+ * samples in the 6D space of a brick pair). Pair t uses one Philox4x64-10
+ * block (Salmon et al., SC 2011) at counter {first + t, 0, 0, 0} with key
+ * {seed, stream}; with outputs w0, w1:
+ *   region_a != region_b: a = floor(w0 * |A| / 2^64), b = floor(w1 * |B| / 2^64)
+ *   region_a == region_b: a = floor(w0 * |A| / 2^64), b' = floor(w1 * (|A|-1) / 2^64),
+ *                         b = b' + (b' >= a), then ordered so that a < b.
+ * pa[t], pb[t] receive the grid point ids of the region-local indices a, b.
+ * pa/pb are device or host memory (out_is_device).
+ */
+cc_status cc_sample_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, uint64_t seed,
+                          uint64_t stream, uint64_t first, int64_t n_pairs, uint32_t* pa,
+                          uint32_t* pb, int out_is_device);
+
+/* ------------------------------------------------------------------ evaluation */
+
+/*
+ * Evaluate one measure on a batch of point pairs (Section 3.2): out[t] =
+ * measure(field_a point pa[t], field_b point pb[t]). The fields must have the
+ * same member count. pa/pb are grid point ids (pairs_on_device says where
+ * they live), out is float[n_pairs] (out_on_device). Pearson/Spearman use
+ * fp32 here regardless of params->precision. MI is in nats. An out-of-range
+ * point id returns CC_ERR_INVALID_ARG (device-side check, reported by this
+ * call when out is host memory, else by cc_sync).
+ */
+cc_status cc_eval_pairs(cc_ctx* ctx, int32_t field_a, int32_t field_b, const cc_params* params,
+                        const uint32_t* pa, const uint32_t* pb, int64_t n_pairs,
+                        int pairs_on_device, float* out, int out_on_device);
+
+/*
+ * KSG with its per-sample neighbour counts, for bit-exact verification
+ * (Section 3.2). nx, ny are int32 [n_pairs][n] in the fields' member order
+ * (n_x,i = 1 + #{j != i : |x_i - x_j| < eps_i}); eps is float [n_pairs][n]
+ * (k-th smallest Chebyshev distance) or NULL. All outputs are host memory;
+ * pa/pb are host memory.
+ */
+cc_status cc_ksg_counts(cc_ctx* ctx, int32_t field_a, int32_t field_b, int32_t k,
+                        const uint32_t* pa, const uint32_t* pb, int64_t n_pairs, float* out,
+                        int32_t* nx, int32_t* ny, float* eps);
+
+/*
+ * Per-region-pair extremes of a measure over candidate pair batches
+ * (Section 3: max of point-to-point correlations per brick pair; Section 3.1:
+ * batched evaluation across brick pairs). Segment s covers pairs
+ * seg_offsets[s] .. seg_offsets[s+1]-1 of pa/pb (grid point ids of one field),
+ * seg_offsets has n_seg + 1 host entries. out[s] (host) gets max/min and
+ * argmax/argmin as batch indices t. values (float[n_pairs], device, or NULL)
+ * receives every evaluated value.
+ */
+cc_status cc_segment_extremes(cc_ctx* ctx, int32_t field_id, const cc_params* params,
+                              const uint32_t* pa, const uint32_t* pb, int pairs_on_device,
+                              const int64_t* seg_offsets, int n_seg, float* values,
+                              cc_rp_result* out);
+
+/*
+ * All pairs between two regions (Section 4.2: exhaustive focus refinement of
+ * a brick pair; Section 3: maximum per brick pair). Pair (a, b) has linear
+ * index a * |B| + b with a, b region-local indices. When region_a ==
+ * region_b only a < b is reduced (each unordered pair once, no self pairs).
+ *   values  device float matrix [|A|][ld] (ld >= |B|) receiving every value
+ *           (for a self pair the full square, diagonal included), or NULL.
+ *   out     host cc_rp_result of the reduced pairs.
+ * Measures: CC_PEARSON and CC_SPEARMAN (params->precision CC_FP32). The
+ * regions may belong to different fields with the same n (inter-variable
+ * correlation, Section 4.3).
+ */
+cc_status cc_all_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, const cc_params* params,
+                       float* values, int64_t ld, cc_rp_result* out);
+
+/* ------------------------------------------------------------------ instrumentation */
+
+/*
+ * Number of kernels this library has launched in the process so far (all
+ * contexts). Lets a caller count the library's launches inside a timed
+ * region. Not part of the method.
+ */
+cc_status cc_launch_count(uint64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCORR_H */

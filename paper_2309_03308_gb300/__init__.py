@@ -1,0 +1,209 @@
+"""GB300-native point-to-point correlation measures for 3D ensemble fields.
+
+A thin Python view of the C ABI in ``include/ccorr.h`` (arxiv 2309.03308,
+Section 3 and 3.2): every method marshals arguments and calls one entry point
+of ``libccorr.so``; all arithmetic runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams. Arrays may be torch tensors (CUDA
+or CPU) or numpy arrays; CPU arrays are passed as host memory.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import (CC_BF16, CC_FP8_E4M3, CC_FP32, CC_FP32_DOT2, CC_MI_BINNED, CC_MI_KSG,
+                   CC_PEARSON, CC_PLANE_BINS, CC_PLANE_RANK2, CC_PLANE_SORTED, CC_PLANE_ZHAT,
+                   CC_SPEARMAN, CCError)
+
+__all__ = ["Context", "Params", "CCError", "CC_PEARSON", "CC_SPEARMAN", "CC_MI_BINNED",
+           "CC_MI_KSG", "CC_FP32", "CC_BF16", "CC_FP8_E4M3", "CC_FP32_DOT2"]
+
+
+@dataclass
+class Params:
+    """cc_params: measure, KSG k (-1 = paper rule ceil(3n/100)), bins, precision."""
+    measure: int = CC_PEARSON
+    k: int = 10
+    bins: int = 16
+    precision: int = CC_FP32
+
+    def c(self) -> _lib.cc_params:
+        return _lib.cc_params(self.measure, self.k, self.bins, self.precision, 0)
+
+
+def _ptr(a):
+    """(pointer, is_device) of a torch tensor or numpy array (must be contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Context:
+    """One cc_ctx: a device, a stream, loaded fields and regions."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        s = int(stream) if stream is not None else None
+        self._check(self.lib.cc_create(device, s, ctypes.byref(h)), ctx=None)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, status, ctx="self"):
+        if status != 0:
+            msg = ""
+            if ctx == "self" and self.h:
+                m = self.lib.cc_last_error(self.h)
+                msg = m.decode() if m else ""
+            raise CCError(status, msg)
+
+    # --------------------------------------------------------------- fields
+    def cc_load_field(self, data, X: int, Y: int, Z: int, n: int) -> int:
+        p, dev = _ptr(data)
+        fid = ctypes.c_int32()
+        self._check(self.lib.cc_load_field(self.h, p, dev, X, Y, Z, n, ctypes.byref(fid)))
+        return fid.value
+
+    def load_field(self, data) -> int:
+        """Load an fp32 [n][Z][Y][X] array (torch or numpy)."""
+        n, Z, Y, X = data.shape
+        return self.cc_load_field(data, X, Y, Z, n)
+
+    def update_field(self, fid: int, data):
+        """Replace a loaded field's values (same shape) and recompute its planes in place."""
+        p, dev = _ptr(data)
+        self._check(self.lib.cc_update_field(self.h, fid, p, dev))
+
+    def free_field(self, fid: int):
+        self._check(self.lib.cc_free_field(self.h, fid))
+
+    def get_plane(self, fid: int, plane: int, pts, n: int, bins: int = 0) -> np.ndarray:
+        pts = np.ascontiguousarray(pts, dtype=np.uint32)
+        dt = {CC_PLANE_RANK2: np.int32, CC_PLANE_BINS: np.uint8, CC_PLANE_SORTED: np.float32,
+              CC_PLANE_ZHAT: np.float32}[plane]
+        out = np.empty((pts.shape[0], n), dtype=dt)
+        self._check(self.lib.cc_get_plane(self.h, fid, plane, bins, pts.ctypes.data,
+                                          pts.shape[0], out.ctypes.data))
+        return out
+
+    # --------------------------------------------------------------- regions
+    def define_regions(self, fid: int, boxes) -> list:
+        arr = (_lib.cc_box * len(boxes))(*[_lib.cc_box(*b) for b in boxes])
+        ids = (ctypes.c_int32 * len(boxes))()
+        self._check(self.lib.cc_define_regions(self.h, fid, arr, len(boxes), ids))
+        return list(ids)
+
+    def partition_regular(self, fid: int, bx: int, by: int, bz: int, cap: int = 1 << 20) -> list:
+        ids = (ctypes.c_int32 * cap)()
+        cnt = ctypes.c_int()
+        self._check(self.lib.cc_partition_regular(self.h, fid, bx, by, bz, ids, cap,
+                                                  ctypes.byref(cnt)))
+        return list(ids[:cnt.value])
+
+    def region_info(self, rid: int):
+        npts = ctypes.c_int64()
+        box = _lib.cc_box()
+        self._check(self.lib.cc_region_info(self.h, rid, ctypes.byref(npts), ctypes.byref(box)))
+        return npts.value, (box.x0, box.y0, box.z0, box.x1, box.y1, box.z1)
+
+    # --------------------------------------------------------------- sampling / evaluation
+    def sample_pairs(self, ra: int, rb: int, seed: int, n_pairs: int, stream: int = 0,
+                     first: int = 0, pa=None, pb=None):
+        """Seeded uniform pairs; fills pa/pb (allocated as numpy when None)."""
+        if pa is None:
+            pa = np.empty(n_pairs, np.uint32)
+            pb = np.empty(n_pairs, np.uint32)
+        a, dev = _ptr(pa)
+        b, _ = _ptr(pb)
+        self._check(self.lib.cc_sample_pairs(self.h, ra, rb, seed, stream, first, n_pairs, a, b,
+                                             dev))
+        return pa, pb
+
+    def eval_pairs(self, fa: int, fb: int, params: Params, pa, pb, out=None):
+        n_pairs = int(pa.shape[0])
+        a, pdev = _ptr(pa)
+        b, _ = _ptr(pb)
+        if out is None:
+            out = np.empty(n_pairs, np.float32)
+        o, odev = _ptr(out)
+        prm = params.c()
+        self._check(self.lib.cc_eval_pairs(self.h, fa, fb, ctypes.byref(prm), a, b, n_pairs, pdev,
+                                           o, odev))
+        return out
+
+    def ksg_counts(self, fa: int, fb: int, k: int, pa, pb, n: int):
+        pa = np.ascontiguousarray(pa, np.uint32)
+        pb = np.ascontiguousarray(pb, np.uint32)
+        N = pa.shape[0]
+        out = np.empty(N, np.float32)
+        nx = np.empty((N, n), np.int32)
+        ny = np.empty((N, n), np.int32)
+        eps = np.empty((N, n), np.float32)
+        self._check(self.lib.cc_ksg_counts(self.h, fa, fb, k, pa.ctypes.data, pb.ctypes.data, N,
+                                           out.ctypes.data, nx.ctypes.data, ny.ctypes.data,
+                                           eps.ctypes.data))
+        return out, nx, ny, eps
+
+    def segment_extremes(self, fid: int, params: Params, pa, pb, seg_offsets, values=None):
+        offs = np.ascontiguousarray(seg_offsets, np.int64)
+        n_seg = offs.shape[0] - 1
+        a, pdev = _ptr(pa)
+        b, _ = _ptr(pb)
+        v = _ptr(values)[0] if values is not None else None
+        res = (_lib.cc_rp_result * max(n_seg, 1))()
+        prm = params.c()
+        self._check(self.lib.cc_segment_extremes(self.h, fid, ctypes.byref(prm), a, b, pdev,
+                                                 offs.ctypes.data, n_seg, v, res))
+        return [_res(r) for r in res[:n_seg]]
+
+    def all_pairs(self, ra: int, rb: int, params: Params, values=None, ld: int = 0):
+        v = None
+        if values is not None:
+            v, dev = _ptr(values)
+            if not dev:
+                raise ValueError("values must be device memory")
+            ld = ld or int(values.shape[-1])
+        res = _lib.cc_rp_result()
+        prm = params.c()
+        self._check(self.lib.cc_all_pairs(self.h, ra, rb, ctypes.byref(prm), v, ld,
+                                          ctypes.byref(res)))
+        return _res(res)
+
+    def sync(self):
+        self._check(self.lib.cc_sync(self.h))
+
+
+def launch_count() -> int:
+    """Kernels launched by libccorr.so in this process so far."""
+    c = ctypes.c_uint64()
+    _lib.load().cc_launch_count(ctypes.byref(c))
+    return c.value
+
+
+def _res(r) -> dict:
+    return dict(max=r.max, min=r.min, argmax=r.argmax, argmin=r.argmin, count=r.count)

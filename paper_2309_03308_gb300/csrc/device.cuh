@@ -1,0 +1,86 @@
+// Device-side helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace cc {
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// (value, index) extremes with the smallest index winning ties.
+struct Ext {
+    float vmax, vmin;
+    unsigned long long imax, imin, count;
+};
+
+__device__ __forceinline__ Ext ext_empty() {
+    Ext e;
+    e.vmax = -CUDART_INF_F;
+    e.vmin = CUDART_INF_F;
+    e.imax = ~0ull;
+    e.imin = ~0ull;
+    e.count = 0;
+    return e;
+}
+
+__device__ __forceinline__ void ext_add(Ext& e, float v, unsigned long long idx) {
+    if (v > e.vmax || (v == e.vmax && idx < e.imax)) {
+        e.vmax = v;
+        e.imax = idx;
+    }
+    if (v < e.vmin || (v == e.vmin && idx < e.imin)) {
+        e.vmin = v;
+        e.imin = idx;
+    }
+    e.count++;
+}
+
+__device__ __forceinline__ void ext_merge(Ext& e, float vmax, unsigned long long imax, float vmin,
+                                          unsigned long long imin, unsigned long long count) {
+    if (vmax > e.vmax || (vmax == e.vmax && imax < e.imax)) {
+        e.vmax = vmax;
+        e.imax = imax;
+    }
+    if (vmin < e.vmin || (vmin == e.vmin && imin < e.imin)) {
+        e.vmin = vmin;
+        e.imin = imin;
+    }
+    e.count += count;
+}
+
+__device__ __forceinline__ Ext warp_ext(Ext e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float vmax = __shfl_xor_sync(0xffffffffu, e.vmax, o);
+        float vmin = __shfl_xor_sync(0xffffffffu, e.vmin, o);
+        unsigned long long imax = __shfl_xor_sync(0xffffffffu, e.imax, o);
+        unsigned long long imin = __shfl_xor_sync(0xffffffffu, e.imin, o);
+        unsigned long long c = __shfl_xor_sync(0xffffffffu, e.count, o);
+        ext_merge(e, vmax, imax, vmin, imin, c);
+    }
+    return e;
+}
+
+}  // namespace cc

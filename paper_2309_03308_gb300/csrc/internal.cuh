@@ -1,0 +1,143 @@
+// Internal types and helpers of the ccorr library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ccorr.h"
+
+namespace cc {
+
+// Device status word values written by kernels (first error wins).
+enum : int { DEV_OK = 0, DEV_BAD_INDEX = 1, DEV_NONFINITE = 2, DEV_TIMEOUT = 3 };
+
+// Fixed-point scale for order-independent sums of digamma and c*ln(c) terms:
+// each table entry is round(value * 2^40) as int64.
+constexpr double kFixScale = 1099511627776.0;  // 2^40
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    ~DevMem() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t n) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        else p = nullptr;
+        return e;
+    }
+    // Grow-only reallocation (contents are not kept).
+    cudaError_t ensure(size_t n) { return n <= bytes ? cudaSuccess : alloc(n); }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+// Per-point planes of one field, point-major [P][n_pad].
+struct Field {
+    int X = 0, Y = 0, Z = 0, n = 0, n_pad = 0;
+    int64_t P = 0;
+    DevMem vals;    // float    member values in member order
+    DevMem sorted;  // float    ascending values (+inf padding)
+    DevMem perm;    // uint16   stable argsort: sorted[t] = vals[perm[t]]
+    DevMem rank2;   // int16    doubled average rank (1-based)
+    DevMem zhat;    // float    (v - mean) / sqrt(sum of squared deviations)
+    DevMem rhat;    // float    centred doubled ranks, unit norm
+    DevMem mean;    // double   [P]
+    DevMem ss;      // double   [P] sum of squared deviations
+    std::map<int, std::unique_ptr<DevMem>> bins;   // B -> uint8 [P][n_pad]
+    std::map<int, std::unique_ptr<DevMem>> hmarg;  // B -> int64 [P] fixed-point sum c ln c
+    std::map<int, uint64_t> bins_version;          // B -> version the bins were built from
+    uint64_t version = 0;                          // bumped by every value update
+    DevMem staging;                                // host-update staging [n][P]
+};
+
+// A box of one field, with its point list and lazily built member-major
+// compact planes ([nk][np_pad]) for the all-pairs contraction.
+struct Region {
+    int field = -1;
+    cc_box box{};
+    int64_t np = 0;
+    std::vector<uint32_t> pts_host;
+    DevMem pts;  // uint32 [np]
+    int nk = 0;
+    int64_t np_pad = 0;
+    DevMem zT;  // float [nk][np_pad]
+    DevMem rT;  // float [nk][np_pad]
+    uint64_t planes_version = ~0ull;  // field version the planes were built from
+};
+
+struct Partial {  // per-CTA extremes, reduced by a finishing kernel
+    float max, min;
+    unsigned long long argmax, argmin, count;
+};
+
+}  // namespace cc
+
+struct cc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<std::unique_ptr<cc::Field>> fields;
+    std::vector<std::unique_ptr<cc::Region>> regions;
+    cc::DevMem status;  // int device status word
+    // scratch
+    cc::DevMem pair_a, pair_b, vals_out, partials, rp_out, ksg_nx, ksg_ny, ksg_eps;
+    std::map<int, std::unique_ptr<cc::DevMem>> psi_fix;   // n -> int64 [n+1]
+    std::map<int, std::unique_ptr<cc::DevMem>> clogc_fix; // n -> int64 [n+1]
+};
+
+namespace cc {
+
+// Counts kernel launches of the library (cc_launch_count).
+void note_launch(int kernels = 1);
+
+// Kernel launchers (defined in the .cu files), all on `st`.
+cudaError_t launch_ingest(const float* in, int n, int64_t P, int n_pad, float* vals, int* status,
+                          cudaStream_t st);
+cudaError_t launch_point_prep(const Field& f, cudaStream_t st);
+cudaError_t launch_bins(const Field& f, int B, const int64_t* clogc_fix, uint8_t* bins,
+                        int64_t* hmarg, cudaStream_t st);
+cudaError_t launch_region_planes(const Field& f, const Region& r, cudaStream_t st);
+
+cudaError_t launch_pearson_pairs(const float* plane_a, int64_t Pa, const float* plane_b,
+                                 int64_t Pb, int n_pad, const uint32_t* pa, const uint32_t* pb,
+                                 int64_t N, float* out, int* status, cudaStream_t st);
+cudaError_t launch_hist_pairs(const uint8_t* bins_a, const int64_t* hm_a, int64_t Pa,
+                              const uint8_t* bins_b, const int64_t* hm_b, int64_t Pb, int n,
+                              int n_pad, int B, const int64_t* clogc_fix, const uint32_t* pa,
+                              const uint32_t* pb, int64_t N, float* out, int* status,
+                              cudaStream_t st);
+cudaError_t launch_ksg_pairs(const Field& fa, const Field& fb, int k, const int64_t* psi_fix,
+                             const uint32_t* pa, const uint32_t* pb, int64_t N, float* out,
+                             int32_t* nx, int32_t* ny, float* eps, int* status, cudaStream_t st);
+cudaError_t launch_sample_pairs(const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
+                                int64_t nb, int self, uint64_t seed, uint64_t stream,
+                                uint64_t first, int64_t N, uint32_t* pa, uint32_t* pb,
+                                cudaStream_t st);
+constexpr int64_t kSegChunk = 8192;  // values per CTA in the segment reduction
+cudaError_t launch_segment_extremes(const float* values, const int64_t* chunk_bounds,
+                                    int64_t n_chunks, const int64_t* seg_first_chunk, int n_seg,
+                                    Partial* chunk_part, Partial* out, cudaStream_t st);
+cudaError_t launch_allpairs_f32(const float* A, int64_t lda, const float* B, int64_t ldb, int nk,
+                                int64_t PA, int64_t PB, int self, float* C, int64_t ldc,
+                                Partial* partials, Partial* result, cudaStream_t st);
+size_t allpairs_partials(int64_t PA, int64_t PB);
+
+}  // namespace cc

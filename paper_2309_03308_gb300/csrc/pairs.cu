@@ -1,0 +1,249 @@
+// Pearson/Spearman and binned MI on batches of point pairs (Section 3.2), the seeded pair sampler
+// (Section 3.1) and per-segment extremes (Section 3, brick-pair maximum).
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace cc {
+
+constexpr int kWarpsPerBlock = 8;
+
+static unsigned pair_grid(int64_t N, int warps_per_block) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = (N + warps_per_block - 1) / warps_per_block;
+    int64_t cap = (int64_t)sms * 16;
+    return (unsigned)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+// ----------------------------------------------------------------------------
+// Pearson / Spearman on a pair batch: r = sum_m zhat_a[m] * zhat_b[m] with
+// zhat the unit-norm centred vector (PPMCC, Section 3.2); on the rank plane
+// this is Spearman. One warp per pair; VEC = 4 reads each row as float4.
+template <int VEC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_pearson_pairs(const float* __restrict__ A, int64_t Pa, const float* __restrict__ B,
+                    int64_t Pb, int n_pad, const uint32_t* __restrict__ pa,
+                    const uint32_t* __restrict__ pb, int64_t N, float* __restrict__ out,
+                    int* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t t = w0; t < N; t += stride) {
+        const uint32_t p = pa[t], q = pb[t];
+        if (p >= Pa || q >= Pb) {
+            if (lane == 0) {
+                out[t] = CUDART_NAN_F;
+                set_status(status, DEV_BAD_INDEX);
+            }
+            continue;
+        }
+        const float* a = A + (int64_t)p * n_pad;
+        const float* b = B + (int64_t)q * n_pad;
+        float acc = 0.f;
+        if (VEC == 4) {
+            for (int m = lane * 4; m < n_pad; m += 128) {
+                const float4 u = __ldg(reinterpret_cast<const float4*>(a + m));
+                const float4 v = __ldg(reinterpret_cast<const float4*>(b + m));
+                acc = fmaf(u.x, v.x, acc);
+                acc = fmaf(u.y, v.y, acc);
+                acc = fmaf(u.z, v.z, acc);
+                acc = fmaf(u.w, v.w, acc);
+            }
+        } else {
+            for (int m = lane; m < n_pad; m += 32) acc = fmaf(__ldg(a + m), __ldg(b + m), acc);
+        }
+        acc = warp_sum_f32(acc);
+        if (lane == 0) out[t] = acc;
+    }
+}
+
+cudaError_t launch_pearson_pairs(const float* plane_a, int64_t Pa, const float* plane_b,
+                                 int64_t Pb, int n_pad, const uint32_t* pa, const uint32_t* pb,
+                                 int64_t N, float* out, int* status, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const unsigned g = pair_grid(N, kWarpsPerBlock);
+    note_launch();
+    if (n_pad % 128 == 0)
+        k_pearson_pairs<4><<<g, kWarpsPerBlock * 32, 0, st>>>(plane_a, Pa, plane_b, Pb, n_pad, pa,
+                                                             pb, N, out, status);
+    else
+        k_pearson_pairs<1><<<g, kWarpsPerBlock * 32, 0, st>>>(plane_a, Pa, plane_b, Pb, n_pad, pa,
+                                                             pb, N, out, status);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Joint-histogram MI (Section 3.2, binning; Eq. 1 on the empirical
+// distribution): with joint counts c_xy and marginals c_x, c_y,
+//   MI = ln n + (1/n) [sum c_xy ln c_xy - sum c_x ln c_x - sum c_y ln c_y].
+// The marginal sums are precomputed per point; c ln c comes from a
+// fixed-point table so the sum is exact and order independent.
+// One warp per pair; the B x B histogram lives in shared memory.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_hist_pairs(const uint8_t* __restrict__ bins_a, const long long* __restrict__ hm_a,
+                 int64_t Pa, const uint8_t* __restrict__ bins_b,
+                 const long long* __restrict__ hm_b, int64_t Pb, int n, int n_pad, int B,
+                 const long long* __restrict__ clogc_fix, const uint32_t* __restrict__ pa,
+                 const uint32_t* __restrict__ pb, int64_t N, float* __restrict__ out,
+                 int* status) {
+    __shared__ int hist[kWarpsPerBlock][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* h = hist[warp];
+    const int cells = B * B;
+    const double logn = log((double)n);
+    const int64_t w0 = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int c = lane; c < cells; c += 32) h[c] = 0;
+    __syncwarp();
+    for (int64_t t = w0; t < N; t += stride) {
+        const uint32_t p = pa[t], q = pb[t];
+        if (p >= Pa || q >= Pb) {
+            if (lane == 0) {
+                out[t] = CUDART_NAN_F;
+                set_status(status, DEV_BAD_INDEX);
+            }
+            continue;
+        }
+        const uint8_t* ba = bins_a + (int64_t)p * n_pad;
+        const uint8_t* bb = bins_b + (int64_t)q * n_pad;
+        for (int m = lane; m < n; m += 32) atomicAdd(&h[ba[m] * B + bb[m]], 1);
+        __syncwarp();
+        long long s = 0;
+        for (int c = lane; c < cells; c += 32) {
+            s += clogc_fix[h[c]];
+            h[c] = 0;
+        }
+        s = warp_sum_i64(s);
+        if (lane == 0) {
+            const long long d = s - hm_a[p] - hm_b[q];
+            out[t] = (float)(logn + ((double)d / kFixScale) / (double)n);
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_hist_pairs(const uint8_t* bins_a, const int64_t* hm_a, int64_t Pa,
+                              const uint8_t* bins_b, const int64_t* hm_b, int64_t Pb, int n,
+                              int n_pad, int B, const int64_t* clogc_fix, const uint32_t* pa,
+                              const uint32_t* pb, int64_t N, float* out, int* status,
+                              cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const unsigned g = pair_grid(N, kWarpsPerBlock);
+    note_launch();
+    k_hist_pairs<<<g, kWarpsPerBlock * 32, 0, st>>>(
+        bins_a, (const long long*)hm_a, Pa, bins_b, (const long long*)hm_b, Pb, n, n_pad, B,
+        (const long long*)clogc_fix, pa, pb, N, out, status);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Uniform pair sampler (Section 3.1). Philox4x64-10 (Salmon, Moraes, Dror,
+// Shaw, SC 2011) from its published definition: 10 rounds of two 64x64->128
+// multiplies with the Weyl key schedule.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t lo0 = 0xD2E7470EE14C6C93ull * c[0];
+        const uint64_t hi0 = __umul64hi(0xD2E7470EE14C6C93ull, c[0]);
+        const uint64_t lo1 = 0xCA5A826395121157ull * c[2];
+        const uint64_t hi1 = __umul64hi(0xCA5A826395121157ull, c[2]);
+        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B97F4A7C15ull;
+        k1 += 0xBB67AE8584CAA73Bull;
+    }
+}
+
+__global__ void k_sample_pairs(const uint32_t* __restrict__ pts_a, int64_t na,
+                               const uint32_t* __restrict__ pts_b, int64_t nb, int self,
+                               uint64_t seed, uint64_t sstream, uint64_t first, int64_t N,
+                               uint32_t* __restrict__ pa, uint32_t* __restrict__ pb) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t c[4] = {first + (uint64_t)t, 0, 0, 0};
+        philox4x64_10(c, seed, sstream);
+        uint64_t a = __umul64hi(c[0], (uint64_t)na), b;
+        if (self) {
+            b = __umul64hi(c[1], (uint64_t)na - 1);
+            b += (b >= a);
+            if (b < a) {
+                const uint64_t tmp = a;
+                a = b;
+                b = tmp;
+            }
+        } else {
+            b = __umul64hi(c[1], (uint64_t)nb);
+        }
+        pa[t] = pts_a[a];
+        pb[t] = pts_b[b];
+    }
+}
+
+cudaError_t launch_sample_pairs(const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
+                                int64_t nb, int self, uint64_t seed, uint64_t stream,
+                                uint64_t first, int64_t N, uint32_t* pa, uint32_t* pb,
+                                cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    int64_t blocks = (N + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    note_launch();
+    k_sample_pairs<<<(unsigned)blocks, 256, 0, st>>>(pts_a, na, pts_b, nb, self, seed, stream,
+                                                     first, N, pa, pb);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Extremes per segment of a value batch (Section 3: brick-pair maximum over
+// its evaluated point pairs; minimum too, Section 5.3). Two levels: one CTA
+// per chunk of at most kChunk values, then one warp per segment folds its
+// chunks. Ties resolve to the smallest batch index.
+__global__ void __launch_bounds__(256)
+    k_chunk_extremes(const float* __restrict__ v, const int64_t* __restrict__ bounds,
+                     Partial* __restrict__ part) {
+    __shared__ Ext red[8];
+    const int64_t lo = bounds[2 * blockIdx.x], hi = bounds[2 * blockIdx.x + 1];
+    Ext e = ext_empty();
+    for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) ext_add(e, v[t], (unsigned long long)t);
+    e = warp_ext(e);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Ext r = red[0];
+        for (int w = 1; w < 8; ++w)
+            ext_merge(r, red[w].vmax, red[w].imax, red[w].vmin, red[w].imin, red[w].count);
+        part[blockIdx.x] = Partial{r.vmax, r.vmin, r.imax, r.imin, r.count};
+    }
+}
+
+__global__ void k_fold_segments(const Partial* __restrict__ part, const int64_t* __restrict__ first,
+                                int n_seg, Partial* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= n_seg) return;
+    Ext e = ext_empty();
+    for (int64_t c = first[s] + lane; c < first[s + 1]; c += 32)
+        ext_merge(e, part[c].max, part[c].argmax, part[c].min, part[c].argmin, part[c].count);
+    e = warp_ext(e);
+    if (lane == 0) out[s] = Partial{e.vmax, e.vmin, e.imax, e.imin, e.count};
+}
+
+cudaError_t launch_segment_extremes(const float* values, const int64_t* chunk_bounds,
+                                    int64_t n_chunks, const int64_t* seg_first_chunk, int n_seg,
+                                    Partial* chunk_part, Partial* out, cudaStream_t st) {
+    if (n_chunks > 0) {
+        note_launch();
+        k_chunk_extremes<<<(unsigned)n_chunks, 256, 0, st>>>(values, chunk_bounds, chunk_part);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (n_seg <= 0) return cudaSuccess;
+    note_launch();
+    k_fold_segments<<<(n_seg + 7) / 8, 256, 0, st>>>(chunk_part, seg_first_chunk, n_seg, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cc

@@ -1,0 +1,328 @@
+// Field ingest and per-point planes (Section 3: an ensemble of n members on
+// a 3D grid; Section 3.2: PPMCC needs only means and variances, KSG needs the
+// per-sample neighbour structure, binned MI needs per-point bins).
+//
+// Every plane is point-major [P][n_pad] so a pair kernel reads each point's
+// member vector as one contiguous, aligned row.
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace cc {
+
+// ----------------------------------------------------------------------------
+// [n][P] member-major input -> [P][n_pad] point-major values, via a 32x32
+// shared-memory tile (both global sides coalesced). Padding members are 0.
+// Non-finite inputs set DEV_NONFINITE.
+__global__ void k_ingest(const float* __restrict__ in, int n, int64_t P, int n_pad,
+                         float* __restrict__ vals, int* status) {
+    __shared__ float tile[32][33];
+    const int64_t p0 = (int64_t)blockIdx.x * 32;
+    const int m0 = blockIdx.y * 32;
+    bool bad = false;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int m = m0 + r;
+        const int64_t p = p0 + threadIdx.x;
+        float v = 0.f;
+        if (m < n && p < P) {
+            v = __ldcs(in + (int64_t)m * P + p);
+            bad |= !isfinite(v);
+        }
+        tile[r][threadIdx.x] = v;
+    }
+    if (bad) set_status(status, DEV_NONFINITE);
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t p = p0 + r;
+        const int m = m0 + threadIdx.x;
+        if (p < P && m < n_pad) vals[p * n_pad + m] = tile[threadIdx.x][r];
+    }
+}
+
+cudaError_t launch_ingest(const float* in, int n, int64_t P, int n_pad, float* vals, int* status,
+                          cudaStream_t st) {
+    dim3 grid((unsigned)((P + 31) / 32), (unsigned)(n_pad / 32));
+    note_launch();
+    k_ingest<<<grid, dim3(32, 8), 0, st>>>(in, n, P, n_pad, vals, status);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// One warp per grid point, member vector in registers in blocked layout
+// (lane l holds members l*E .. l*E+E-1, E = n_pad / 32):
+//   mean, ss      FP64 (sum, then sum of squared deviations about the mean)
+//   zhat          (v - mean) / sqrt(ss) rounded to fp32 (0 when ss == 0)
+//   sorted, perm  ascending order, stable: a warp bitonic sort of the unique
+//                 64-bit keys (order-preserving bits of v + 0.0f, member index),
+//                 so -0.0 and +0.0 tie and equal values keep member order
+//   rank2         2 * average rank (ties averaged): for a run of equal values
+//                 at sorted positions a..b, every member gets a + b + 2
+//                 (= 2L + E + 1 with L values below and E equal)
+//   rhat          c / sqrt(sum c^2) with c = rank2 - (n + 1) (exact integers)
+constexpr int kPrepWarps = 4;
+
+__device__ __forceinline__ unsigned order_bits(float v) {
+    const unsigned b = __float_as_uint(v + 0.0f);  // -0.0 -> +0.0
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float unorder_bits(unsigned o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+template <int E>
+__global__ void __launch_bounds__(kPrepWarps * 32)
+    k_point_prep(const float* __restrict__ vals, int64_t P, int n, double inv_n,
+                 float* __restrict__ sorted,
+                 uint16_t* __restrict__ perm, int16_t* __restrict__ rank2,
+                 float* __restrict__ zhat, float* __restrict__ rhat,
+                 double* __restrict__ mean_out, double* __restrict__ ss_out) {
+    constexpr int NP = 32 * E;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * kPrepWarps + warp;
+    if (p >= P) return;
+    const int64_t row = p * NP;
+    const int g0 = lane * E;
+
+    unsigned long long key[E];
+    double s = 0.0;
+    {
+        float v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = vals[row + g0 + e];
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (g0 + e < n) s += (double)v[e];
+        const double mean = warp_sum_f64(s) * inv_n;
+        double q = 0.0;
+        float dev[E];  // v - mean, centred in FP64, then rounded to fp32
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const double d = (double)v[e] - mean;
+            dev[e] = (float)d;
+            if (g0 + e < n) q = fma(d, d, q);
+        }
+        const double ss = warp_sum_f64(q);
+        // one FP64 reciprocal square root per point; the per-member scaling
+        // is an fp32 multiply (relative error <= 3 fp32 roundings)
+        const float inv = ss > 0.0 ? (float)rsqrt(ss) : 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int g = g0 + e;
+            zhat[row + g] = g < n ? dev[e] * inv : 0.f;
+            key[e] = g < n ? ((unsigned long long)order_bits(v[e]) << 32) | (unsigned)g
+                           : (0xffffffffull << 32) | (unsigned)g;
+        }
+        if (lane == 0) {
+            mean_out[p] = mean;
+            ss_out[p] = ss;
+        }
+    }
+
+    // bitonic sort, ascending, over NP keys
+#pragma unroll
+    for (int size = 2; size <= NP; size <<= 1) {
+#pragma unroll
+        for (int d = size >> 1; d > 0; d >>= 1) {
+            if (d >= E) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int g = g0 + e;
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[e], d / E);
+                    const bool keep_min = ((g & d) == 0) == ((g & size) == 0);
+                    key[e] = keep_min ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int e2 = e ^ d;
+                    if (e2 > e) {
+                        const bool asc = ((g0 + e) & size) == 0;
+                        const unsigned long long lo = key[e] < key[e2] ? key[e] : key[e2];
+                        const unsigned long long hi = key[e] < key[e2] ? key[e2] : key[e];
+                        key[e] = asc ? lo : hi;
+                        key[e2] = asc ? hi : lo;
+                    }
+                }
+            }
+        }
+    }
+
+    // sorted values, permutation, and runs of equal values
+    float sv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int g = g0 + e;
+        sv[e] = unorder_bits((unsigned)(key[e] >> 32));
+        sorted[row + g] = g < n ? sv[e] : CUDART_INF_F;
+        perm[row + g] = (uint16_t)(key[e] & 0xffffu);
+    }
+    // run start a: prefix max of (start ? g : 0); run end b: suffix min of (end ? g : NP)
+    const float prev_last = __shfl_up_sync(0xffffffffu, sv[E - 1], 1);
+    const float next_first = __shfl_down_sync(0xffffffffu, sv[0], 1);
+    int a[E], b[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int g = g0 + e;
+        const float pv = e > 0 ? sv[e - 1] : prev_last;
+        const bool start = g == 0 || g >= n || !(pv == sv[e]);
+        a[e] = start ? g : 0;
+        if (e > 0) a[e] = max(a[e], a[e - 1]);
+    }
+#pragma unroll
+    for (int e = E - 1; e >= 0; --e) {
+        const int g = g0 + e;
+        const float nv = e < E - 1 ? sv[e + 1] : next_first;
+        const bool end = g >= n - 1 || !(nv == sv[e]);
+        b[e] = end ? g : NP;
+        if (e < E - 1) b[e] = min(b[e], b[e + 1]);
+    }
+    int carry_a = a[E - 1], carry_b = b[0];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ta = __shfl_up_sync(0xffffffffu, carry_a, o);
+        const int tb = __shfl_down_sync(0xffffffffu, carry_b, o);
+        if (lane >= o) carry_a = max(carry_a, ta);
+        if (lane + o < 32) carry_b = min(carry_b, tb);
+    }
+    const int before_a = __shfl_up_sync(0xffffffffu, carry_a, 1);
+    const int after_b = __shfl_down_sync(0xffffffffu, carry_b, 1);
+    long long c2 = 0;
+    int r2[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int g = g0 + e;
+        const int aa = lane > 0 ? max(a[e], before_a) : a[e];
+        const int bb = lane < 31 ? min(b[e], after_b) : b[e];
+        r2[e] = aa + bb + 2;
+        if (g < n) {
+            const long long c = r2[e] - (n + 1);
+            c2 += c * c;
+        }
+    }
+    c2 = warp_sum_i64(c2);
+    const float rinv = c2 > 0 ? (float)rsqrt((double)c2) : 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int g = g0 + e;
+        const int m = (int)(key[e] & 0xffffu);  // member at sorted position g
+        if (g < n) {
+            rank2[row + m] = (int16_t)r2[e];
+            rhat[row + m] = (float)(r2[e] - (n + 1)) * rinv;  // exact integer times fp32 scale
+        } else {
+            rank2[row + g] = 0;
+            rhat[row + g] = 0.f;
+        }
+    }
+}
+
+cudaError_t launch_point_prep(const Field& f, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((f.P + kPrepWarps - 1) / kPrepWarps);
+    note_launch();
+#define CC_PREP(E)                                                                               \
+    k_point_prep<E><<<blocks, kPrepWarps * 32, 0, st>>>(                                         \
+        f.vals.as<float>(), f.P, f.n, 1.0 / f.n, f.sorted.as<float>(), f.perm.as<uint16_t>(),   \
+        f.rank2.as<int16_t>(), f.zhat.as<float>(), f.rhat.as<float>(), f.mean.as<double>(),      \
+        f.ss.as<double>())
+    switch (f.n_pad / 32) {  // n_pad is a power of two >= 32
+        case 1: CC_PREP(1); break;
+        case 2: CC_PREP(2); break;
+        case 4: CC_PREP(4); break;
+        case 8: CC_PREP(8); break;
+        case 16: CC_PREP(16); break;
+        case 32: CC_PREP(32); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef CC_PREP
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Bins for B bins per variable (Section 3.2, binning): over the point's own
+// [lo, hi] = [min, max], b = floor(((v - lo) / (hi - lo)) * B) with each step
+// an IEEE fp32 operation, clamped to [0, B-1]; hi == lo gives bin 0.
+// Also the marginal term sum_b c_b ln c_b of the point (fixed point, 2^-40).
+__global__ void __launch_bounds__(128)
+    k_bins(const float* __restrict__ vals, const float* __restrict__ sorted, int64_t P, int n,
+           int n_pad, int B, const long long* __restrict__ clogc_fix, uint8_t* __restrict__ bins,
+           long long* __restrict__ hmarg) {
+    __shared__ int hist[4][16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * 4 + warp;
+    if (p >= P) return;
+    if (lane < 16) hist[warp][lane] = 0;
+    __syncwarp();
+    const float lo = sorted[p * n_pad];
+    const float hi = sorted[p * n_pad + n - 1];
+    const bool flat = !(hi > lo);
+    const float w = __fsub_rn(hi, lo);
+    for (int m = lane; m < n_pad; m += 32) {
+        int b = 0;
+        if (m < n && !flat) {
+            const float v = vals[p * n_pad + m];
+            const float t = __fsub_rn(v, lo);
+            const float r = __fdiv_rn(t, w);
+            const float sc = __fmul_rn(r, (float)B);
+            b = (int)floorf(sc);
+            b = b < 0 ? 0 : (b > B - 1 ? B - 1 : b);
+        }
+        bins[p * n_pad + m] = (uint8_t)b;
+        if (m < n) atomicAdd(&hist[warp][b], 1);
+    }
+    __syncwarp();
+    long long s = lane < B ? clogc_fix[hist[warp][lane]] : 0;
+    s = warp_sum_i64(s);
+    if (lane == 0) hmarg[p] = s;
+}
+
+cudaError_t launch_bins(const Field& f, int B, const int64_t* clogc_fix, uint8_t* bins,
+                        int64_t* hmarg, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((f.P + 3) / 4);
+    note_launch();
+    k_bins<<<blocks, 128, 0, st>>>(f.vals.as<float>(), f.sorted.as<float>(), f.P, f.n, f.n_pad,
+                                   B, (const long long*)clogc_fix, bins, (long long*)hmarg);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Member-major compact planes of a region for the all-pairs contraction:
+// zT[k][a] = zhat[pts[a]][k] for k < n, a < np; zero elsewhere (k < nk,
+// a < np_pad). Same for the rank plane.
+__global__ void k_region_planes(const float* __restrict__ zhat, const float* __restrict__ rhat,
+                                int n, int n_pad, const uint32_t* __restrict__ pts, int64_t np,
+                                int nk, int64_t np_pad, float* __restrict__ zT,
+                                float* __restrict__ rT) {
+    __shared__ float tz[32][33], tr[32][33];
+    const int64_t a0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t a = a0 + r;
+        const int k = k0 + threadIdx.x;
+        float z = 0.f, q = 0.f;
+        if (a < np && k < n) {
+            const int64_t off = (int64_t)pts[a] * n_pad + k;
+            z = zhat[off];
+            q = rhat[off];
+        }
+        tz[r][threadIdx.x] = z;
+        tr[r][threadIdx.x] = q;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int k = k0 + r;
+        const int64_t a = a0 + threadIdx.x;
+        if (k < nk && a < np_pad) {
+            zT[(int64_t)k * np_pad + a] = tz[threadIdx.x][r];
+            rT[(int64_t)k * np_pad + a] = tr[threadIdx.x][r];
+        }
+    }
+}
+
+cudaError_t launch_region_planes(const Field& f, const Region& r, cudaStream_t st) {
+    dim3 grid((unsigned)(r.np_pad / 32), (unsigned)((r.nk + 31) / 32));
+    note_launch();
+    k_region_planes<<<grid, dim3(32, 8), 0, st>>>(f.zhat.as<float>(), f.rhat.as<float>(), f.n,
+                                                  f.n_pad, r.pts.as<uint32_t>(), r.np, r.nk,
+                                                  r.np_pad, r.zT.as<float>(), r.rT.as<float>());
+    return cudaGetLastError();
+}
+
+}  // namespace cc
