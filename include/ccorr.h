@@ -256,6 +256,45 @@ cc_status cc_segment_extremes(cc_ctx* ctx, int32_t field_id, const cc_params* pa
 cc_status cc_all_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, const cc_params* params,
                        float* values, int64_t ld, cc_rp_result* out);
 
+/* ------------------------------------------------------------ allocation-free form */
+
+/*
+ * All-pairs extremes without any device allocation. The paper has no
+ * counterpart: this exists for callers that must not allocate device memory
+ * while they run -- e.g. an interactive viewer's per-frame loop, or a host
+ * application that owns all device memory in its own pool -- because
+ * cudaMalloc may synchronise the whole device and fragments such pools.
+ *
+ * Same arithmetic as cc_all_pairs with measure CC_PEARSON/CC_SPEARMAN and
+ * CC_FP32, but the caller supplies the standardized planes, so no context or
+ * loaded field is needed:
+ *   za, zb  device, member-major fp32 planes [nk][lda] / [nk][ldb]: column a
+ *           holds the unit-norm centred member vector of point a (for
+ *           Spearman: of its average ranks), rows n..nk-1 zero. 16-byte
+ *           aligned; lda >= 128 * ceil(na / 128) and ldb >= 128 * ceil(nb /
+ *           128), both multiples of 4, padding columns readable.
+ *   nk      member count rounded up to a multiple of 8.
+ *   na, nb  points per plane. self != 0 reduces only pairs a < b and needs
+ *           za == zb, na == nb, lda == ldb.
+ *   values  optional device matrix [na][ldv] (ldv >= nb) of every value.
+ *   out     DEVICE pointer to one cc_rp_result (linear index a * nb + b).
+ *   stream  cudaStream_t to run on (NULL: the default stream). Asynchronous.
+ * Scratch is a file-scope device array of 65,536 tile partials (2.5 MiB,
+ * held by every GPU that loads the library until the process exits), so at
+ * most 65,536 tiles of 128 x 128 pairs: ceil(na/128) * ceil(nb/128) beyond
+ * that returns CC_ERR_INVALID_ARG before any work is queued. The first call
+ * on a device resolves the array's device address with that device current
+ * (once per device); make that first call before any stream capture. Every
+ * call shares the array: each call overwrites all partials it reads, so
+ * nothing needs clearing, but calls whose work overlaps on the GPU race and
+ * must be ordered (same stream, or events). Calls no cudaMalloc or cudaFree.
+ * Returns CC_ERR_INVALID_ARG for bad sizes or alignment, CC_ERR_CUDA if a
+ * launch fails.
+ */
+cc_status cc_all_pairs_static(const float* za, int64_t lda, const float* zb, int64_t ldb, int nk,
+                              int64_t na, int64_t nb, int self, float* values, int64_t ldv,
+                              cc_rp_result* out, void* stream);
+
 /* ------------------------------------------------------------------ instrumentation */
 
 /*

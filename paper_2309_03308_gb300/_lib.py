@@ -66,6 +66,7 @@ SIGNATURES = {
     "cc_segment_extremes": (_S, [_P, _I32, ctypes.POINTER(cc_params), _P, _P, _I, _P, _I, _P,
                                  _P]),
     "cc_all_pairs": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _P, _I64, _P]),
+    "cc_all_pairs_static": (_S, [_P, _I64, _P, _I64, _I, _I64, _I64, _I, _P, _I64, _P, _P]),
     "cc_launch_count": (_S, [ctypes.POINTER(_U64)]),
 }
 

@@ -183,3 +183,66 @@ cudaError_t launch_allpairs_f32(const float* A, int64_t lda, const float* B, int
 }
 
 }  // namespace cc
+
+// ----------------------------------------------------------------------------
+// Allocation-free variant of the all-pairs extremes (cc_all_pairs_static).
+// The per-tile partials live in a file-scope device array instead of context
+// scratch; the caller passes the standardized planes and the output.
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kStaticTiles = 1 << 16;  // 65,536 tiles of 128 x 128 pairs (2.5 MiB)
+__device__ __align__(256) cc::Partial g_static_partials[kStaticTiles];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+cc::Partial* g_static_addr[kMaxDevices] = {};
+
+static_assert(sizeof(cc::Partial) == sizeof(cc_rp_result), "result layout");
+static_assert(offsetof(cc::Partial, argmax) == offsetof(cc_rp_result, argmax), "result layout");
+static_assert(offsetof(cc::Partial, count) == offsetof(cc_rp_result, count), "result layout");
+
+// Device address of the static partials on the current device; resolved
+// once per device with that device current.
+cudaError_t static_partials(cc::Partial** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = static_cast<cc::Partial*>(p);
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" cc_status cc_all_pairs_static(const float* za, int64_t lda, const float* zb, int64_t ldb,
+                                         int nk, int64_t na, int64_t nb, int self, float* values,
+                                         int64_t ldv, cc_rp_result* out, void* stream) {
+    if (!za || !zb || !out || nk < 8 || nk % 8 != 0 || na < 1 || nb < 1)
+        return CC_ERR_INVALID_ARG;
+    const int64_t ta = (na + cc::BM - 1) / cc::BM, tb = (nb + cc::BN - 1) / cc::BN;
+    if (lda < ta * cc::BM || ldb < tb * cc::BN || lda % 4 || ldb % 4 ||
+        ((uintptr_t)za & 15) || ((uintptr_t)zb & 15))
+        return CC_ERR_INVALID_ARG;
+    if (self && (za != zb || na != nb || lda != ldb)) return CC_ERR_INVALID_ARG;
+    if (values && ldv < nb) return CC_ERR_INVALID_ARG;
+    if (ta * tb > kStaticTiles || ta > 65535) return CC_ERR_INVALID_ARG;  // beyond the static scratch
+    cc::Partial* parts = nullptr;
+    cudaError_t e = static_partials(&parts);
+    if (e == cudaSuccess)
+        e = cc::launch_allpairs_f32(za, lda, zb, ldb, nk, na, nb, self, values, ldv, parts,
+                                    reinterpret_cast<cc::Partial*>(out), (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CC_ERR_CUDA;
+    }
+    return CC_OK;
+}
