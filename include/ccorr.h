@@ -208,7 +208,8 @@ cc_status cc_sample_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, uint6
  * measure(field_a point pa[t], field_b point pb[t]). The fields must have the
  * same member count. pa/pb are grid point ids (pairs_on_device says where
  * they live), out is float[n_pairs] (out_on_device). Pearson/Spearman use
- * fp32 here regardless of params->precision. MI is in nats. An out-of-range
+ * fp32 (CC_FP32, CC_BF16, CC_FP8_E4M3) or the compensated Dot2 product
+ * (CC_FP32_DOT2) of the fp32 planes. MI is in nats. An out-of-range
  * point id returns CC_ERR_INVALID_ARG (device-side check, reported by this
  * call when out is host memory, else by cc_sync).
  */
@@ -249,12 +250,54 @@ cc_status cc_segment_extremes(cc_ctx* ctx, int32_t field_id, const cc_params* pa
  *   values  device float matrix [|A|][ld] (ld >= |B|) receiving every value
  *           (for a self pair the full square, diagonal included), or NULL.
  *   out     host cc_rp_result of the reduced pairs.
- * Measures: CC_PEARSON and CC_SPEARMAN (params->precision CC_FP32). The
- * regions may belong to different fields with the same n (inter-variable
- * correlation, Section 4.3).
+ * Measures: CC_PEARSON and CC_SPEARMAN. params->precision CC_FP32 runs the
+ * FP32 SIMT contraction; CC_BF16 / CC_FP8_E4M3 run cc_all_pairs_topk with
+ * topk = 0 (values must then be NULL). The regions may belong to different
+ * fields with the same n (inter-variable correlation, Section 4.3).
  */
 cc_status cc_all_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, const cc_params* params,
                        float* values, int64_t ld, cc_rp_result* out);
+
+/*
+ * Certificate of a reduced-precision all-pairs evaluation.
+ *   bound          stated |approximate - refined| bound for every pair:
+ *                  2e + e^2 + (1 + e)^2 2^-12 + 2^-20 with e the largest
+ *                  per-point quantization error norm of the two regions
+ *   threshold_max  pairs were re-evaluated when their approximate value could
+ *                  reach this (= refined max - bound after the second pass)
+ *   threshold_min  the same for the minimum (refined min + bound)
+ *   certified_max  1 when every pair that could exceed out->max was re-evaluated,
+ *                  so out->max is the exact maximum of the fp32 planes
+ *   certified_min  likewise for out->min
+ *   refined_pairs  pairs re-evaluated in compensated fp32 (Dot2)
+ */
+typedef struct {
+    float bound;
+    float threshold_max;
+    float threshold_min;
+    int32_t certified_max;
+    int32_t certified_min;
+    int64_t refined_pairs;
+} cc_mixed_info;
+
+/*
+ * All pairs between two regions in reduced precision with exact extremes and
+ * the top-`topk` list (project addition to Section 4.2's focus refinement).
+ * params->precision CC_BF16 or CC_FP8_E4M3 (per-point scale 448/max|z|):
+ * the contraction runs on the tensor cores with FP32 accumulation and yields
+ * per-(row, 32-column chunk) approximate extremes; the top chunks and then
+ * every chunk that could beat the best re-evaluated value within `bound` are
+ * re-evaluated in compensated fp32 (Dot2, Ogita-Rump-Oishi 2005). out gets the
+ * refined max/min (same index convention and self-pair rule as cc_all_pairs);
+ * ids/vals (host, topk entries, may be NULL when topk == 0) the topk largest
+ * refined values in descending order with their linear pair indices (missing
+ * entries: value -inf, id UINT64_MAX). 0 <= topk <= 4096. info (host, may be
+ * NULL) receives the certificate. Requires |A| * |B| < 2^32.
+ * cc_all_pairs with precision CC_BF16 / CC_FP8_E4M3 is this call with topk = 0.
+ */
+cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t region_b,
+                            const cc_params* params, int topk, uint64_t* ids, float* vals,
+                            cc_rp_result* out, cc_mixed_info* info);
 
 /* ------------------------------------------------------------ allocation-free form */
 

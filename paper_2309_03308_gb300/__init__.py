@@ -194,6 +194,19 @@ class Context:
                                           ctypes.byref(res)))
         return _res(res)
 
+    def all_pairs_topk(self, ra: int, rb: int, params: Params, topk: int = 0):
+        """Reduced-precision all-pairs: (extremes, top ids, top values, certificate)."""
+        ids = np.empty(max(topk, 1), np.uint64)
+        vals = np.empty(max(topk, 1), np.float32)
+        res = _lib.cc_rp_result()
+        info = _lib.cc_mixed_info()
+        prm = params.c()
+        self._check(self.lib.cc_all_pairs_topk(self.h, ra, rb, ctypes.byref(prm), topk,
+                                               ids.ctypes.data, vals.ctypes.data,
+                                               ctypes.byref(res), ctypes.byref(info)))
+        cert = {f: getattr(info, f) for f, _ in _lib.cc_mixed_info._fields_}
+        return _res(res), ids[:topk], vals[:topk], cert
+
     def sync(self):
         self._check(self.lib.cc_sync(self.h))
 

@@ -40,6 +40,12 @@ class cc_rp_result(ctypes.Structure):
                 ("argmin", ctypes.c_uint64), ("count", ctypes.c_uint64)]
 
 
+class cc_mixed_info(ctypes.Structure):
+    _fields_ = [("bound", ctypes.c_float), ("threshold_max", ctypes.c_float),
+                ("threshold_min", ctypes.c_float), ("certified_max", ctypes.c_int32),
+                ("certified_min", ctypes.c_int32), ("refined_pairs", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I32 = ctypes.c_int32
@@ -66,6 +72,7 @@ SIGNATURES = {
     "cc_segment_extremes": (_S, [_P, _I32, ctypes.POINTER(cc_params), _P, _P, _I, _P, _I, _P,
                                  _P]),
     "cc_all_pairs": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _P, _I64, _P]),
+    "cc_all_pairs_topk": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _I, _P, _P, _P, _P]),
     "cc_all_pairs_static": (_S, [_P, _I64, _P, _I64, _I, _I64, _I64, _I, _P, _I64, _P, _P]),
     "cc_launch_count": (_S, [ctypes.POINTER(_U64)]),
 }

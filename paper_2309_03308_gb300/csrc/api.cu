@@ -147,6 +147,8 @@ cc_status check_params(cc_ctx* ctx, const cc_params* p, int n, int* k_out) {
     if (p->flags != 0) return fail(ctx, CC_ERR_INVALID_ARG, "params.flags must be 0");
     if (p->measure < CC_PEARSON || p->measure > CC_MI_KSG)
         return fail(ctx, CC_ERR_INVALID_ARG, "unknown measure %d", p->measure);
+    if (p->precision < CC_FP32 || p->precision > CC_FP32_DOT2)
+        return fail(ctx, CC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
     if (p->measure == CC_MI_BINNED && (p->bins < 2 || p->bins > 16))
         return fail(ctx, CC_ERR_INVALID_ARG, "bins must be in [2, 16], got %d", p->bins);
     if (p->measure == CC_MI_KSG) {
@@ -162,15 +164,21 @@ cc_status check_params(cc_ctx* ctx, const cc_params* p, int n, int* k_out) {
 cc_status eval_device(cc_ctx* ctx, Field& fa, Field& fb, const cc_params* p, int k,
                       const uint32_t* pa, const uint32_t* pb, int64_t N, float* out) {
     int* st = ctx->status.as<int>();
+    const bool dot2 = p->precision == CC_FP32_DOT2;
     switch (p->measure) {
         case CC_PEARSON:
-            CK(launch_pearson_pairs(fa.zhat.as<float>(), fa.P, fb.zhat.as<float>(), fb.P, fa.n_pad,
-                                    pa, pb, N, out, st, ctx->stream));
+        case CC_SPEARMAN: {
+            const bool sp = p->measure == CC_SPEARMAN;
+            const float* A = sp ? fa.rhat.as<float>() : fa.zhat.as<float>();
+            const float* B = sp ? fb.rhat.as<float>() : fb.zhat.as<float>();
+            if (dot2)
+                CK(launch_dot2_pairs(A, fa.P, B, fb.P, fa.n_pad, fa.n, pa, pb, N, out, st,
+                                     ctx->stream));
+            else
+                CK(launch_pearson_pairs(A, fa.P, B, fb.P, fa.n_pad, pa, pb, N, out, st,
+                                        ctx->stream));
             break;
-        case CC_SPEARMAN:
-            CK(launch_pearson_pairs(fa.rhat.as<float>(), fa.P, fb.rhat.as<float>(), fb.P, fa.n_pad,
-                                    pa, pb, N, out, st, ctx->stream));
-            break;
+        }
         case CC_MI_BINNED: {
             cc_status s = ensure_bins(ctx, fa, p->bins);
             if (!s && &fb != &fa) s = ensure_bins(ctx, fb, p->bins);
@@ -609,6 +617,11 @@ cc_status cc_all_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, const cc
     if (s) return s;
     if (params->measure != CC_PEARSON && params->measure != CC_SPEARMAN)
         return fail(ctx, CC_ERR_UNSUPPORTED, "all-pairs supports Pearson and Spearman");
+    if (params->precision == CC_BF16 || params->precision == CC_FP8_E4M3) {
+        if (values) return fail(ctx, CC_ERR_INVALID_ARG, "reduced precision stores no values");
+        return cc_all_pairs_topk(ctx, region_a, region_b, params, 0, nullptr, nullptr, out,
+                                 nullptr);
+    }
     if (params->precision != CC_FP32)
         return fail(ctx, CC_ERR_UNSUPPORTED, "all-pairs precision %d not built",
                     params->precision);
@@ -632,3 +645,174 @@ cc_status cc_all_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, const cc
 }
 
 }  // extern "C"
+
+namespace {
+
+// Reduced-precision plane of a region (rows padded to 256, K to 128 bytes).
+cc_status ensure_qplane(cc_ctx* ctx, Region& r, bool sp, bool fp8, Region::QPlane** out) {
+    Field& f = *ctx->fields[r.field];
+    auto& slot = r.qplanes[(sp ? 2 : 0) + (fp8 ? 1 : 0)];
+    if (!slot) slot = std::make_unique<Region::QPlane>();
+    Region::QPlane& qp = *slot;
+    *out = &qp;
+    if (qp.version == f.version) return CC_OK;
+    if (!qp.q.p) {
+        qp.rows_pad = (r.np + 255) / 256 * 256;
+        qp.kbytes = fp8 ? round_up(f.n, 128) : round_up(f.n, 64) * 2;
+        CK(qp.q.alloc((size_t)qp.rows_pad * qp.kbytes));
+        CK(qp.inv.alloc(sizeof(float) * qp.rows_pad));
+        CK(qp.emax.alloc(sizeof(unsigned)));
+    }
+    CK(cudaMemsetAsync(qp.emax.p, 0, sizeof(unsigned), ctx->stream));
+    CK(launch_quantize(fp8, sp ? f.rhat.as<float>() : f.zhat.as<float>(), f.n_pad, f.n,
+                       r.pts.as<uint32_t>(), r.np, qp.rows_pad, qp.kbytes, qp.q.p,
+                       qp.inv.as<float>(), qp.emax.as<unsigned>(), ctx->stream));
+    unsigned bits = 0;
+    CK(cudaMemcpyAsync(&bits, qp.emax.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    memcpy(&qp.emax_host, &bits, sizeof(float));
+    qp.version = f.version;
+    return CC_OK;
+}
+
+float unorder_key(unsigned o) {
+    unsigned b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    float v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+}  // namespace
+
+extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t region_b,
+                                       const cc_params* params, int topk, uint64_t* ids,
+                                       float* vals, cc_rp_result* out, cc_mixed_info* info) {
+    if (!ctx) return CC_ERR_INVALID_ARG;
+    Region* ra = get_region(ctx, region_a);
+    Region* rb = get_region(ctx, region_b);
+    if (!ra || !rb || !out) return fail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    Field& fa = *ctx->fields[ra->field];
+    Field& fb = *ctx->fields[rb->field];
+    if (fa.n != fb.n) return fail(ctx, CC_ERR_INVALID_ARG, "fields differ in member count");
+    cc_status s = check_params(ctx, params, fa.n, nullptr);
+    if (s) return s;
+    if (params->measure != CC_PEARSON && params->measure != CC_SPEARMAN)
+        return fail(ctx, CC_ERR_UNSUPPORTED, "reduced precision supports Pearson and Spearman");
+    if (params->precision != CC_BF16 && params->precision != CC_FP8_E4M3)
+        return fail(ctx, CC_ERR_INVALID_ARG, "precision must be CC_BF16 or CC_FP8_E4M3");
+    if (topk < 0 || topk > 4096 || (topk > 0 && (!ids || !vals)))
+        return fail(ctx, CC_ERR_INVALID_ARG, "topk in [0, 4096] with ids and vals");
+    if ((uint64_t)ra->np * (uint64_t)rb->np >= (1ull << 32))
+        return fail(ctx, CC_ERR_INVALID_ARG, "|A| * |B| must be below 2^32");
+    const bool fp8 = params->precision == CC_FP8_E4M3, sp = params->measure == CC_SPEARMAN;
+    const int self = region_a == region_b;
+    Region::QPlane *qa = nullptr, *qb = nullptr;
+    if ((s = ensure_qplane(ctx, *ra, sp, fp8, &qa))) return s;
+    if ((s = ensure_qplane(ctx, *rb, sp, fp8, &qb))) return s;
+    const int64_t na = ra->np, nb = rb->np, na_pad = qa->rows_pad, nb_pad = qb->rows_pad;
+    const int64_t N = (nb_pad / 32) * na_pad;  // chunks
+    const unsigned cap = 1u << 18;             // candidate chunks per extreme
+    // scratch arena
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t o_cmax = take(4 * N), o_cmin = take(4 * N), o_hist = take(4 * 4096),
+                 o_sel = take(sizeof(Select) * 2), o_cnt = take(16), o_best = take(8),
+                 o_thr = take(8), o_ids = take(4ull * cap), o_vals = take(4ull * cap * 32),
+                 o_pids = take(8ull * cap * 32), o_sidx = take(4 * 8192), o_tv = take(4 * 4096),
+                 o_ti = take(8 * 4096);
+    CK(ctx->mixed.ensure(off));
+    unsigned char* base = ctx->mixed.as<unsigned char>();
+    float* cmax = (float*)(base + o_cmax);
+    float* cmin = (float*)(base + o_cmin);
+    unsigned* hist = (unsigned*)(base + o_hist);
+    Select* sel = (Select*)(base + o_sel);
+    unsigned* cnt2 = (unsigned*)(base + o_cnt);  // [count, overflow] of the second pass
+    unsigned long long* best = (unsigned long long*)(base + o_best);
+    float* thr = (float*)(base + o_thr);  // [threshold, bound]
+    uint32_t* cids = (uint32_t*)(base + o_ids);
+    float* rvals = (float*)(base + o_vals);
+    unsigned long long* rpids = (unsigned long long*)(base + o_pids);
+    uint32_t* sidx = (uint32_t*)(base + o_sidx);
+    float* tvals = (float*)(base + o_tv);
+    unsigned long long* tids = (unsigned long long*)(base + o_ti);
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(hist, 0, 4 * 4096, st));
+    CK(launch_tc_chunk_extremes(fp8, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad, qa->kbytes, self,
+                                qa->inv.as<float>(), qb->inv.as<float>(), cmax, cmin,
+                                ctx->status.as<int>(), st));
+    const float emax = std::max(qa->emax_host, qb->emax_host);
+    const float* plane_a = sp ? fa.rhat.as<float>() : fa.zhat.as<float>();
+    const float* plane_b = sp ? fb.rhat.as<float>() : fb.zhat.as<float>();
+    cc_mixed_info inf{};
+    float ext_val[2] = {-INFINITY, -INFINITY};
+    uint64_t ext_id[2] = {~0ull, ~0ull};
+    for (int side = 0; side < 2; ++side) {
+        const float sign = side == 0 ? 1.f : -1.f;
+        const float* v = side == 0 ? cmax : cmin;
+        CK(cudaMemsetAsync(sel, 0, sizeof(Select) * 2, st));
+        CK(cudaMemsetAsync(cnt2, 0, 16, st));
+        CK(cudaMemsetAsync(best, 0, 8, st));
+        const unsigned want = side == 0 ? (unsigned)std::max(topk, 256) : 256u;
+        CK(launch_select_top(v, N, sign, want, hist, sel, cids, cap, st));
+        CK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
+                                rb->pts.as<uint32_t>(), nb, self, na_pad, cids, &sel->count, cap,
+                                sign, rvals, rpids, best, st));
+        Select h1;
+        CK(cudaMemcpyAsync(&h1, sel, sizeof h1, cudaMemcpyDeviceToHost, st));
+        CK(launch_second_threshold(best, emax, 1.f / 4096.f, thr, thr + 1, st));
+        CK(cudaStreamSynchronize(st));
+        const unsigned c1 = std::min(h1.count, cap);
+        bool certified = h1.overflow == 0;
+        unsigned c2 = 0;
+        if (certified && h1.threshold != 0 && c1 < cap) {
+            CK(launch_compact_range(v, N, sign, thr, &sel->threshold, cids + c1, cap - c1, cnt2,
+                                    cnt2 + 1, st));
+            CK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
+                                    rb->pts.as<uint32_t>(), nb, self, na_pad, cids + c1, cnt2,
+                                    cap - c1, sign, rvals + (size_t)c1 * 32,
+                                    rpids + (size_t)c1 * 32, best, st));
+            unsigned h2[2];
+            CK(cudaMemcpyAsync(h2, cnt2, sizeof h2, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            c2 = std::min(h2[0], cap - c1);
+            certified = h2[1] == 0;
+        } else if (h1.threshold != 0) {
+            certified = false;
+        }
+        unsigned long long hb = 0;
+        float ht[2];
+        CK(cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ht, thr, 8, cudaMemcpyDeviceToHost, st));
+        if (side == 0 && topk > 0) {
+            const int64_t n2 = (int64_t)(c1 + c2) * 32;
+            CK(cudaMemsetAsync(sel + 1, 0, sizeof(Select), st));
+            CK(launch_select_top(rvals, n2, 1.f, (unsigned)topk, hist, sel + 1, sidx, 8192, st));
+            CK(launch_sort_top(rvals, rpids, sidx, &sel[1].count, 8192, 1.f, topk, tvals, tids,
+                               st));
+            CK(cudaMemcpyAsync(vals, tvals, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(ids, tids, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
+        }
+        if ((s = take_status(ctx))) return s;
+        if (hb != 0) {
+            ext_val[side] = unorder_key((unsigned)(hb >> 32));
+            ext_id[side] = 0xffffffffull - (hb & 0xffffffffull);
+        }
+        inf.bound = ht[1];
+        if (side == 0) {
+            inf.threshold_max = ht[0];
+            inf.certified_max = certified;
+        } else {
+            inf.threshold_min = -ht[0];
+            inf.certified_min = certified;
+        }
+        inf.refined_pairs += (int64_t)(c1 + c2) * 32;
+    }
+    const uint64_t count = self ? (uint64_t)na * (na - 1) / 2 : (uint64_t)na * nb;
+    *out = cc_rp_result{ext_val[0], -ext_val[1], ext_id[0], ext_id[1], count};
+    if (info) *info = inf;
+    return CC_OK;
+}

@@ -80,6 +80,16 @@ struct Region {
     DevMem zT;  // float [nk][np_pad]
     DevMem rT;  // float [nk][np_pad]
     uint64_t planes_version = ~0ull;  // field version the planes were built from
+    // reduced-precision K-major planes [rows_pad][kbytes] for the tensor-core
+    // contraction, keyed by (plane: 0 zhat / 1 rhat) * 2 + fp8
+    struct QPlane {
+        DevMem q, inv, emax;
+        int64_t rows_pad = 0;
+        int kbytes = 0;
+        float emax_host = 0.f;
+        uint64_t version = ~0ull;
+    };
+    std::map<int, std::unique_ptr<QPlane>> qplanes;
 };
 
 struct Partial {  // per-CTA extremes, reduced by a finishing kernel
@@ -98,7 +108,7 @@ struct cc_ctx {
     std::vector<std::unique_ptr<cc::Region>> regions;
     cc::DevMem status;  // int device status word
     // scratch
-    cc::DevMem pair_a, pair_b, vals_out, partials, rp_out, ksg_nx, ksg_ny, ksg_eps;
+    cc::DevMem pair_a, pair_b, vals_out, partials, rp_out, ksg_nx, ksg_ny, ksg_eps, mixed;
     std::map<int, std::unique_ptr<cc::DevMem>> psi_fix;   // n -> int64 [n+1]
     std::map<int, std::unique_ptr<cc::DevMem>> clogc_fix; // n -> int64 [n+1]
 };
@@ -139,5 +149,43 @@ cudaError_t launch_allpairs_f32(const float* A, int64_t lda, const float* B, int
                                 int64_t PA, int64_t PB, int self, float* C, int64_t ldc,
                                 Partial* partials, Partial* result, cudaStream_t st);
 size_t allpairs_partials(int64_t PA, int64_t PB);
+
+// reduced precision (tc_gemm.cu, mixed.cu)
+// State of one histogram selection (keys >= threshold are candidates).
+struct Select {
+    unsigned prefix;     // top-12-bit bin found by the first pass
+    unsigned need;       // keys still needed inside that bin
+    unsigned threshold;  // order-preserving key threshold; 0 = every key
+    unsigned count;      // compacted candidates
+    unsigned overflow;   // candidates beyond capacity
+};
+cudaError_t launch_tc_chunk_extremes(bool fp8, const void* qa, int64_t na, int64_t na_pad,
+                                     const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
+                                     int self, const float* inv_sa, const float* inv_sb,
+                                     float* cmax, float* cmin, int* status, cudaStream_t st);
+cudaError_t launch_quantize(bool fp8, const float* plane, int n_pad, int n, const uint32_t* pts,
+                            int64_t np, int64_t np_pad, int kbytes, void* q, float* inv_scale,
+                            unsigned* emax_bits, cudaStream_t st);
+cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned want,
+                              unsigned* hist, Select* sel, uint32_t* out, unsigned cap,
+                              cudaStream_t st);
+cudaError_t launch_compact_range(const float* v, int64_t N, float sign, const float* lo_val,
+                                 const unsigned* hi_key, uint32_t* out, unsigned cap,
+                                 unsigned* count, unsigned* ovf, cudaStream_t st);
+cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int n_pad, int n,
+                                 const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
+                                 int64_t nb, int self, int64_t na_pad, const uint32_t* ids,
+                                 const unsigned* count, unsigned cap, float sign, float* vals,
+                                 unsigned long long* pair_ids, unsigned long long* best,
+                                 cudaStream_t st);
+cudaError_t launch_second_threshold(const unsigned long long* best, float emax, float acc_rel,
+                                    float* thr, float* bound, cudaStream_t st);
+cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,
+                            const uint32_t* sel_idx, const unsigned* count, unsigned cap,
+                            float sign, int topk, float* out_vals, unsigned long long* out_ids,
+                            cudaStream_t st);
+cudaError_t launch_dot2_pairs(const float* A, int64_t Pa, const float* B, int64_t Pb, int n_pad,
+                              int n, const uint32_t* pa, const uint32_t* pb, int64_t N, float* out,
+                              int* status, cudaStream_t st);
 
 }  // namespace cc

@@ -1,0 +1,436 @@
+// Reduced-precision all-pairs with exact, certified extremes (project
+// addition to the Section 4.2 focus refinement; Section 3: the brick pair's
+// maximum).
+//
+//  1. quantize   each region point's unit-norm standardized vector to BF16, or
+//                to FP8 E4M3 with scale 448 / max|z|; record the point's
+//                quantization error norm e_p = || dequant(q_p) - z_p ||_2.
+//  2. contract   on the tensor cores (tc_gemm.cu) -> per (row, 32-column chunk)
+//                max / min of the approximate values r~.
+//  3. select     the top chunks by chunk max (two 12-bit histogram passes on
+//                order-preserving keys) and re-evaluate every pair in them with
+//                Dot2 (Ogita, Rump, Oishi 2005: TwoProduct by FMA + TwoSum),
+//                an almost exact fp32 dot product of the fp32 planes.
+//  4. certify    |r~ - r| <= B for every pair, with B = 2 e + e^2 +
+//                (1 + e)^2 2^-12 + 2^-20, e = max_p e_p (Cauchy-Schwarz on the
+//                quantization errors plus a conservative accumulation term).
+//                Any pair whose chunk max is below r* - B (r* = best refined
+//                value) cannot beat r*; every chunk at or above it is refined
+//                in a second pass, after which r* is the exact maximum.
+//  5. top-K      of the refined values, sorted descending.
+// The minimum runs the same passes on negated values.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace cc {
+
+__device__ __forceinline__ unsigned okey(float v) {
+    const unsigned b = __float_as_uint(v + 0.0f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float okey_inv(unsigned o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// ---------------------------------------------------------------------------
+// 1. quantization: one warp per region point.
+template <bool FP8>
+__global__ void __launch_bounds__(256)
+    k_quantize(const float* __restrict__ plane, int n_pad, int n, const uint32_t* __restrict__ pts,
+               int64_t np, int64_t np_pad, int kbytes, unsigned char* __restrict__ q,
+               float* __restrict__ inv_scale, unsigned* __restrict__ emax_bits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= np_pad) return;
+    const int kelems = FP8 ? kbytes : kbytes / 2;
+    unsigned char* qrow = q + r * kbytes;
+    if (r >= np) {
+        for (int b = lane * 4; b < kbytes; b += 128) *reinterpret_cast<uint32_t*>(qrow + b) = 0;
+        if (FP8 && lane == 0) inv_scale[r] = 0.f;
+        return;
+    }
+    const float* z = plane + (int64_t)pts[r] * n_pad;
+    float amax = 0.f;
+    if (FP8) {
+        for (int k = lane; k < n; k += 32) amax = fmaxf(amax, fabsf(z[k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    const float s = FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f;
+    float err = 0.f;
+    for (int k = lane * 2; k < kelems; k += 64) {
+        const float z0 = k < n ? z[k] : 0.f, z1 = k + 1 < n ? z[k + 1] : 0.f;
+        float d0, d1;
+        if (FP8) {
+            const __nv_fp8x2_storage_t v =
+                __nv_cvt_float2_to_fp8x2(make_float2(z0 * s, z1 * s), __NV_SATFINITE, __NV_E4M3);
+            *reinterpret_cast<__nv_fp8x2_storage_t*>(qrow + k) = v;
+            const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(v, __NV_E4M3);
+            const float2 back = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+            d0 = back.x / s - z0;
+            d1 = back.y / s - z1;
+        } else {
+            const __nv_bfloat162 v = __floats2bfloat162_rn(z0, z1);
+            *reinterpret_cast<__nv_bfloat162*>(qrow + 2 * k) = v;
+            const float2 back = __bfloat1622float2(v);
+            d0 = back.x - z0;
+            d1 = back.y - z1;
+        }
+        err = fmaf(d0, d0, fmaf(d1, d1, err));
+    }
+    err = warp_sum_f32(err);
+    if (lane == 0) {
+        if (FP8) inv_scale[r] = 1.f / s;
+        // small relative margin for the fp32 accumulation of the error norm
+        atomicMax(emax_bits, __float_as_uint(sqrtf(err) * 1.001f));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3a. two-pass histogram select on order-preserving keys of sign * value.
+// Pass `level` 0 bins the top 12 bits, pass 1 the next 12 among keys whose
+// top 12 bits equal sel->prefix. Values of -inf (empty chunks) are skipped.
+
+__global__ void k_hist12(const float* __restrict__ v, int64_t N, float sign, int level,
+                         const Select* __restrict__ sel, unsigned* __restrict__ hist) {
+    __shared__ unsigned h[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned prefix = level ? sel->prefix : 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = sign * v[i];
+        if (!(x > -CUDART_INF_F)) continue;
+        const unsigned k = okey(x);
+        if (level == 0) atomicAdd(&h[k >> 20], 1u);
+        else if ((k >> 20) == prefix) atomicAdd(&h[(k >> 8) & 0xfffu], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// One block: scan the 4096 bins from the top until `want` keys are covered.
+__global__ void k_pick_bin(unsigned* __restrict__ hist, int level, unsigned want,
+                           Select* __restrict__ sel) {
+    __shared__ unsigned part[1024];
+    // bins are scanned in descending order: thread t owns bins 4095-4t .. 4092-4t
+    const int t = threadIdx.x;
+    unsigned s = 0;
+    for (int j = 0; j < 4; ++j) s += hist[4095 - 4 * t - j];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive prefix sum
+        const unsigned x = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += x;
+        __syncthreads();
+    }
+    const unsigned target = level == 0 ? want : sel->need;
+    const unsigned before = t ? part[t - 1] : 0u;
+    const bool last_group = t == 1023;
+    if ((before < target && part[t] >= target) || (last_group && part[t] < target)) {
+        unsigned acc = before;
+        int bin = 4095 - 4 * t - 3;
+        for (int j = 0; j < 4; ++j) {
+            const int b = 4095 - 4 * t - j;
+            if (acc + hist[b] >= target) {
+                bin = b;
+                break;
+            }
+            acc += hist[b];
+        }
+        if (level == 0) {
+            sel->prefix = (unsigned)bin;
+            sel->need = target - acc;
+        } else {
+            sel->threshold = (sel->prefix << 20) | ((unsigned)bin << 8);
+        }
+        if (part[t] < target) sel->threshold = 0u;  // fewer keys than wanted: take all
+    }
+    __syncthreads();
+    for (int i = t; i < 4096; i += 1024) hist[i] = 0;  // ready for the next pass
+}
+
+// 3b. compact chunk ids whose key lies in [lo_key, hi_key) (hi_key 0 = no cap).
+__global__ void k_compact(const float* __restrict__ v, int64_t N, float sign,
+                          const Select* __restrict__ sel, const float* __restrict__ lo_val,
+                          const unsigned* __restrict__ hi_key_p, uint32_t* __restrict__ out,
+                          unsigned cap, unsigned* __restrict__ count, unsigned* __restrict__ ovf) {
+    const unsigned lo = lo_val ? okey(*lo_val) : sel->threshold;
+    const unsigned hi = hi_key_p ? *hi_key_p : 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = sign * v[i];
+        if (!(x > -CUDART_INF_F)) continue;
+        const unsigned k = okey(x);
+        if (k >= lo && (hi == 0u || k < hi)) {
+            const unsigned slot = atomicAdd(count, 1u);
+            if (slot < cap) out[slot] = (uint32_t)i;
+            else atomicAdd(ovf, 1u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3c. Dot2 re-evaluation of every pair in the candidate chunks. Chunk id i
+// addresses cm[chunk][row] = i, i.e. chunk = i / na_pad, row = i % na_pad.
+// One warp per chunk: the warp holds row a's member vector (n <= 1024) in
+// registers and evaluates its 32 pairs (a, 32 * chunk + j).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float dot2_warp(const float (&x)[32], const float* __restrict__ y,
+                                           int n) {
+    const int lane = threadIdx.x & 31;
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int k = r * 32 + lane;
+        if (k < n) {
+            const float p = __fmul_rn(x[r], y[k]);
+            const float pe = fmaf(x[r], y[k], -p);  // TwoProduct error, exact
+            float t, q;
+            two_sum(s, p, t, q);
+            s = t;
+            c = __fadd_rn(c, __fadd_rn(q, pe));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        float t, q;
+        two_sum(s, s2, t, q);
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, c2), q);
+    }
+    return __fadd_rn(s, c);
+}
+
+__global__ void __launch_bounds__(256)
+    k_refine_chunks(const float* __restrict__ plane_a, const float* __restrict__ plane_b,
+                    int n_pad, int n, const uint32_t* __restrict__ pts_a, int64_t na,
+                    const uint32_t* __restrict__ pts_b, int64_t nb, int self, int64_t na_pad,
+                    const uint32_t* __restrict__ ids, const unsigned* __restrict__ count_p,
+                    unsigned cap, float sign, float* __restrict__ vals,
+                    unsigned long long* __restrict__ pair_ids,
+                    unsigned long long* __restrict__ best) {
+    const int lane = threadIdx.x & 31;
+    const unsigned count = min(*count_p, cap);
+    for (int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); w < count;
+         w += (int64_t)gridDim.x * 8) {
+        const uint32_t id = ids[w];
+        const int64_t chunk = id / na_pad, a = id % na_pad;
+        if (a >= na) continue;
+        float x[32];
+        const float* xa = plane_a + (int64_t)pts_a[a] * n_pad;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const int k = r * 32 + lane;
+            x[r] = k < n ? xa[k] : 0.f;
+        }
+        float mine = -CUDART_INF_F;
+        unsigned long long mine_id = ~0ull;
+        for (int j = 0; j < 32; ++j) {
+            const int64_t b = chunk * 32 + j;
+            const bool ok = b < nb && (!self || b > a);
+            float r = -CUDART_INF_F;
+            if (ok) r = sign * dot2_warp(x, plane_b + (int64_t)pts_b[b] * n_pad, n);
+            if (lane == j) {
+                mine = r;
+                mine_id = ok ? (unsigned long long)(a * nb + b) : ~0ull;
+            }
+        }
+        vals[w * 32 + lane] = mine;
+        pair_ids[w * 32 + lane] = mine_id;
+        if (mine > -CUDART_INF_F) {  // best (signed) value, smallest pair index on ties
+            const unsigned long long key =
+                ((unsigned long long)okey(mine) << 32) | (0xffffffffull - (mine_id & 0xffffffffull));
+            atomicMax(best, key);
+        }
+    }
+}
+
+// r* - B as a value threshold for the second pass (sign-adjusted domain).
+__global__ void k_second_threshold(const unsigned long long* best, float e, float acc_rel,
+                                   float* out_thr, float* out_bound) {
+    const float B = 2.f * e + e * e + (1.f + e) * (1.f + e) * acc_rel + 1e-6f;
+    const float rstar = okey_inv((unsigned)(*best >> 32));
+    *out_thr = rstar - B;
+    *out_bound = B;
+}
+
+// 5. top-K: bitonic sort (descending) of up to 8192 (value, pair) entries in
+// one CTA, taken from the compacted refined values.
+__global__ void __launch_bounds__(1024)
+    k_sort_top(const float* __restrict__ vals, const unsigned long long* __restrict__ pids,
+               const uint32_t* __restrict__ sel_idx, const unsigned* __restrict__ count_p,
+               unsigned cap, float sign, int topk, float* __restrict__ out_vals,
+               unsigned long long* __restrict__ out_ids) {
+    extern __shared__ unsigned long long sort_smem[];
+    unsigned long long* key = sort_smem;
+    unsigned long long* pid = sort_smem + 8192;
+    const unsigned count = min(*count_p, cap);
+    for (int i = threadIdx.x; i < 8192; i += 1024) {
+        if ((unsigned)i < count) {
+            const uint32_t j = sel_idx[i];
+            key[i] = ((unsigned long long)okey(vals[j]) << 32) |
+                     (0xffffffffull - (pids[j] & 0xffffffffull));
+            pid[i] = pids[j];
+        } else {
+            key[i] = 0;
+            pid[i] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int size = 2; size <= 8192; size <<= 1) {
+        for (int d = size >> 1; d > 0; d >>= 1) {
+            for (int i = threadIdx.x; i < 8192; i += 1024) {
+                const int p = i ^ d;
+                if (p > i) {
+                    const bool desc = (i & size) == 0;
+                    if ((key[i] < key[p]) == desc) {
+                        const unsigned long long tk = key[i];
+                        key[i] = key[p];
+                        key[p] = tk;
+                        const unsigned long long tp = pid[i];
+                        pid[i] = pid[p];
+                        pid[p] = tp;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < topk; i += 1024) {
+        const bool ok = (unsigned)i < count;
+        out_vals[i] = ok ? sign * okey_inv((unsigned)(key[i] >> 32)) : -sign * CUDART_INF_F;
+        out_ids[i] = ok ? pid[i] : ~0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_quantize(bool fp8, const float* plane, int n_pad, int n, const uint32_t* pts,
+                            int64_t np, int64_t np_pad, int kbytes, void* q, float* inv_scale,
+                            unsigned* emax_bits, cudaStream_t st) {
+    note_launch();
+    const unsigned blocks = (unsigned)((np_pad + 7) / 8);
+    if (fp8)
+        k_quantize<true><<<blocks, 256, 0, st>>>(plane, n_pad, n, pts, np, np_pad, kbytes,
+                                                 (unsigned char*)q, inv_scale, emax_bits);
+    else
+        k_quantize<false><<<blocks, 256, 0, st>>>(plane, n_pad, n, pts, np, np_pad, kbytes,
+                                                  (unsigned char*)q, inv_scale, emax_bits);
+    return cudaGetLastError();
+}
+
+static unsigned grid_for(int64_t N, int per_block) {
+    int64_t b = (N + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 152 * 8) b = 152 * 8;
+    return (unsigned)b;
+}
+
+// Select keys of sign*v into the top `want` (>= want when ties/bins), compact
+// their indices into out (capacity cap). scratch: hist[4096] zeroed, sel.
+cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned want,
+                              unsigned* hist, Select* sel, uint32_t* out, unsigned cap,
+                              cudaStream_t st) {
+    note_launch(5);
+    k_hist12<<<grid_for(N, 256 * 16), 256, 0, st>>>(v, N, sign, 0, sel, hist);
+    k_pick_bin<<<1, 1024, 0, st>>>(hist, 0, want, sel);
+    k_hist12<<<grid_for(N, 256 * 16), 256, 0, st>>>(v, N, sign, 1, sel, hist);
+    k_pick_bin<<<1, 1024, 0, st>>>(hist, 1, want, sel);
+    k_compact<<<grid_for(N, 256 * 8), 256, 0, st>>>(v, N, sign, sel, nullptr, nullptr, out, cap,
+                                                    &sel->count, &sel->overflow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_range(const float* v, int64_t N, float sign, const float* lo_val,
+                                 const unsigned* hi_key, uint32_t* out, unsigned cap,
+                                 unsigned* count, unsigned* ovf, cudaStream_t st) {
+    note_launch();
+    k_compact<<<grid_for(N, 256 * 8), 256, 0, st>>>(v, N, sign, nullptr, lo_val, hi_key, out, cap,
+                                                    count, ovf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int n_pad, int n,
+                                 const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
+                                 int64_t nb, int self, int64_t na_pad, const uint32_t* ids,
+                                 const unsigned* count, unsigned cap, float sign, float* vals,
+                                 unsigned long long* pair_ids, unsigned long long* best,
+                                 cudaStream_t st) {
+    note_launch();
+    k_refine_chunks<<<152 * 8, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, nb,
+                                             self, na_pad, ids, count, cap, sign, vals, pair_ids,
+                                             best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_second_threshold(const unsigned long long* best, float emax, float acc_rel,
+                                    float* thr, float* bound, cudaStream_t st) {
+    note_launch();
+    k_second_threshold<<<1, 1, 0, st>>>(best, emax, acc_rel, thr, bound);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,
+                            const uint32_t* sel_idx, const unsigned* count, unsigned cap,
+                            float sign, int topk, float* out_vals, unsigned long long* out_ids,
+                            cudaStream_t st) {
+    const int smem = 2 * 8192 * (int)sizeof(unsigned long long);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_sort_top, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_sort_top<<<1, 1024, smem, st>>>(vals, pids, sel_idx, count, cap, sign, topk, out_vals,
+                                      out_ids);
+    return cudaGetLastError();
+}
+
+// 3c for a plain pair batch: Dot2 Pearson/Spearman (precision CC_FP32_DOT2).
+__global__ void __launch_bounds__(256)
+    k_dot2_pairs(const float* __restrict__ A, int64_t Pa, const float* __restrict__ B, int64_t Pb,
+                 int n_pad, int n, const uint32_t* __restrict__ pa, const uint32_t* __restrict__ pb,
+                 int64_t N, float* __restrict__ out, int* status) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); t < N;
+         t += (int64_t)gridDim.x * 8) {
+        const uint32_t p = pa[t], q = pb[t];
+        if (p >= Pa || q >= Pb) {
+            if (lane == 0) {
+                out[t] = CUDART_NAN_F;
+                set_status(status, DEV_BAD_INDEX);
+            }
+            continue;
+        }
+        float x[32];
+        const float* xa = A + (int64_t)p * n_pad;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const int k = r * 32 + lane;
+            x[r] = k < n ? xa[k] : 0.f;
+        }
+        const float r = dot2_warp(x, B + (int64_t)q * n_pad, n);
+        if (lane == 0) out[t] = r;
+    }
+}
+
+cudaError_t launch_dot2_pairs(const float* A, int64_t Pa, const float* B, int64_t Pb, int n_pad,
+                              int n, const uint32_t* pa, const uint32_t* pb, int64_t N, float* out,
+                              int* status, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    note_launch();
+    k_dot2_pairs<<<grid_for(N, 8), 256, 0, st>>>(A, Pa, B, Pb, n_pad, n, pa, pb, N, out, status);
+    return cudaGetLastError();
+}
+
+}  // namespace cc

@@ -1,0 +1,374 @@
+// Reduced-precision all-pairs correlation on the 5th-generation tensor cores
+// (project addition to the paper's Section 4.2 focus refinement: the brick
+// pair's Pearson / Spearman values as one contraction Z_A Z_B^T of unit-norm
+// standardized member vectors).
+//
+// Operands are K-major planes [rows][K] of BF16, or FP8 E4M3 scaled per point
+// (value * 448 / max|value|), loaded by TMA with 128-byte swizzle into a
+// 4-stage shared-memory ring. One elected thread issues tcgen05.mma
+// (M = 128, N = 256, FP32 accumulation in TMEM, two accumulator buffers so the
+// epilogue of one tile overlaps the MMAs of the next). Four epilogue warps
+// read TMEM with tcgen05.ld and emit, per output row and 32-column chunk, the
+// max and min of the approximate correlations (FP8: rescaled by the two
+// per-point inverse scales). No per-pair value is stored: the chunk extremes
+// select the candidates that are re-evaluated exactly afterwards.
+//
+// Warp roles (192 threads, one CTA per SM, persistent over tiles):
+//   warp 0  TMA producer        warp 1  TMEM allocation + MMA issuer
+//   warps 2-5  epilogue (warp w reads TMEM lanes 32*(w%4) .. +31)
+// Every mbarrier wait is bounded (wall clock); on timeout the CTA records
+// DEV_TIMEOUT, the other roles leave their loops, in-flight copies and MMAs
+// are drained with bounded waits, and TMEM is freed before returning.
+#include <cuda.h>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace cc {
+namespace tc {
+
+constexpr int TM = 128, TN = 256, STAGES = 4;
+constexpr int A_BYTES = TM * 128, B_BYTES = TN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 512;  // two 256-column fp32 accumulators
+constexpr uint64_t kTimeoutNs = 4000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity `parity` to complete. Gives up on the
+// wall-clock limit or when another role has set the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_test(b, parity)) return true;
+    const uint64_t t0 = now_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_test(b, parity)) return true;
+        if ((i & 255) == 0) {
+            if (abort_flag && *abort_flag) return false;
+            if (now_ns() - t0 > kTimeoutNs) return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor: FP32 accumulator, A/B BF16 (kind::f16) or E4M3
+// (kind::f8f6f4), both K-major, N = 256, M = 128.
+template <bool FP8>
+__host__ __device__ constexpr uint32_t idesc() {
+    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((uint32_t)(TN >> 3) << 17) |
+           ((uint32_t)(TM >> 4) << 24);
+}
+template <bool FP8>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accum) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc<FP8>()), "r"(accum));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc<FP8>()), "r"(accum));
+    }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+// 32 consecutive fp32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool FP8>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_chunk_extremes(const __grid_constant__ CUtensorMap tma,
+                        const __grid_constant__ CUtensorMap tmb, int num_kb, int64_t na,
+                        int64_t nb, int tiles_m, int tiles_n, int self,
+                        const float* __restrict__ inv_sa, const float* __restrict__ inv_sb,
+                        float* __restrict__ cmax, float* __restrict__ cmin, int64_t na_pad,
+                        int* status) {
+    extern __shared__ unsigned char tc_smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* colscale = reinterpret_cast<float*>(tmem_slot + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int tiles = tiles_m * tiles_n;
+    auto fail = [&]() {
+        *abort_flag = 1;
+        set_status(status, DEV_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
+                const int m0 = (t / tiles_n) * TM, n0 = (t % tiles_n) * TN;
+                for (int kb = 0; kb < num_kb; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(st, &tma, &full[s], kb * 128 / (FP8 ? 1 : 2), m0);
+                    tma_load_2d(st + A_BYTES, &tmb, &full[s], kb * 128 / (FP8 ? 1 : 2), n0);
+                }
+            }
+            // drain: every issued copy has landed before the CTA may exit
+            for (int i = it > STAGES ? it - STAGES : 0; i < it; ++i)
+                mbar_wait(&full[i % STAGES], (i / STAGES) & 1, nullptr);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, tc = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++tc) {
+                const int acc = tc & 1;
+                if (!mbar_wait(&tempty[acc], ((tc >> 1) & 1) ^ 1, abort_flag)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + acc * TN;
+                for (int kb = 0; kb < num_kb; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        mma<FP8>(d, sdesc(a + k * 32), sdesc(a + A_BYTES + k * 32),
+                                 (kb | k) != 0);
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&tfull[acc]);
+            }
+            // drain: all issued MMAs complete before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0, nullptr);
+        }
+    } else {
+        const int q = warp & 3;  // TMEM lane quadrant this warp may access
+        const int et = (warp - 2) * 32 + lane;
+        int tc = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
+            const int acc = tc & 1;
+            const int m0 = (t / tiles_n) * TM, n0 = (t % tiles_n) * TN;
+            if (FP8) {
+                for (int c = et; c < TN; c += 128)
+                    colscale[c] = n0 + c < nb ? inv_sb[n0 + c] : 0.f;
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
+            if (!mbar_wait(&tfull[acc], (tc >> 1) & 1, abort_flag)) {
+                fail();
+                break;
+            }
+            tc_fence_after();
+            const int64_t row = m0 + 32 * q + lane;
+            const bool row_ok = row < na;
+            const float rs = FP8 ? (row_ok ? inv_sa[row] : 0.f) : 1.f;
+#pragma unroll 1
+            for (int c = 0; c < TN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + (uint32_t)(acc * TN + c * 32) + ((uint32_t)(32 * q) << 16), v);
+                const int64_t col0 = n0 + c * 32;
+                float mx = -CUDART_INF_F, mn = CUDART_INF_F;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t col = col0 + j;
+                    const float val = FP8 ? v[j] * rs * colscale[c * 32 + j] : v[j];
+                    const bool ok = row_ok && col < nb && (!self || col > row);
+                    mx = ok ? fmaxf(mx, val) : mx;
+                    mn = ok ? fminf(mn, val) : mn;
+                }
+                const int64_t chunk = (n0 >> 5) + c;
+                if (row < na_pad) {
+                    cmax[chunk * na_pad + row] = mx;
+                    cmin[chunk * na_pad + row] = mn;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+            if (FP8) asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+    }
+}
+
+constexpr size_t smem_bytes() { return 1024 + STAGES * STAGE_BYTES + 256 + 16 + TN * 4; }
+
+}  // namespace tc
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static cudaError_t make_map(CUtensorMap* m, const void* base, bool fp8, int64_t rows,
+                            int64_t kbytes, int box_rows) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+            return e != cudaSuccess ? e : cudaErrorNotSupported;
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    const int esz = fp8 ? 1 : 2;
+    cuuint64_t gdim[2] = {(cuuint64_t)(kbytes / esz), (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)kbytes};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult r = fn(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void*>(base), gdim, gstride, box, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// qa: [na_pad][kbytes] operand A (rows padded to 256), qb likewise; kbytes a
+// multiple of 128. Writes cmax/cmin [nb_pad/32][na_pad].
+cudaError_t launch_tc_chunk_extremes(bool fp8, const void* qa, int64_t na, int64_t na_pad,
+                                     const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
+                                     int self, const float* inv_sa, const float* inv_sb,
+                                     float* cmax, float* cmin, int* status, cudaStream_t st) {
+    if (kbytes % 128 || na_pad % 256 || nb_pad % 256) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    cudaError_t e = make_map(&ma, qa, fp8, na_pad, kbytes, tc::TM);
+    if (e == cudaSuccess) e = make_map(&mb, qb, fp8, nb_pad, kbytes, tc::TN);
+    if (e != cudaSuccess) return e;
+    const int tiles_m = (int)((na + tc::TM - 1) / tc::TM);
+    const int tiles_n = (int)((nb + tc::TN - 1) / tc::TN);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = tiles_m * tiles_n;
+    const int grid = tiles < sms ? tiles : sms;
+    const size_t smem = tc::smem_bytes();
+    auto kern = fp8 ? tc::k_tc_chunk_extremes<true> : tc::k_tc_chunk_extremes<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    kern<<<grid, tc::THREADS, smem, st>>>(ma, mb, (int)(kbytes / 128), na, nb, tiles_m, tiles_n,
+                                          self, inv_sa, inv_sb, cmax, cmin, na_pad, status);
+    return cudaGetLastError();
+}
+
+}  // namespace cc

@@ -1,0 +1,128 @@
+"""Reduced-precision all-pairs (BF16 / FP8 E4M3 tensor-core contraction) with
+Dot2 re-evaluation and certified extremes, against the FP64 oracle on every
+pair. Refined values are compensated fp32 products of the fp32 planes, so they
+are held to 1e-6 of the exact correlation."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+TOL_REFINED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def cc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_03308_gb300 import Context, build
+    build.build()
+    ctx = Context(0)
+    yield ctx
+    ctx.close()
+
+
+def two_fields(n, box_a, box_b, seed=2):
+    Fa = gen.field(seed, 352, 256, 20, n, box=box_a)
+    Fb = gen.field(seed, 352, 256, 20, n, box=box_b)
+    return Fa, Fb
+
+
+def all_values(orc, kind, Fa, Fb):
+    na, nb = Fa[0].size, Fb[0].size
+    A = np.arange(na, dtype=np.uint32)
+    B = np.arange(nb, dtype=np.uint32)
+    return orc.eval_pairs(Fa, kind, np.repeat(A, nb), np.tile(B, na), Fb=Fb)
+
+
+def check(res, ids, vals, cert, full, count, topk):
+    assert res["count"] == count
+    assert cert["certified_max"] == 1 and cert["certified_min"] == 1, cert
+    assert abs(res["max"] - full.max()) < TOL_REFINED, (res["max"], full.max())
+    assert abs(res["min"] - full.min()) < TOL_REFINED, (res["min"], full.min())
+    assert abs(full[res["argmax"]] - full.max()) < TOL_REFINED
+    assert abs(full[res["argmin"]] - full.min()) < TOL_REFINED
+    if topk:
+        assert np.all(np.diff(vals) <= 0) and vals[0] == res["max"]
+        assert np.all(ids < full.size)
+        assert np.abs(full[ids.astype(np.int64)] - vals).max() < TOL_REFINED
+        kth = np.sort(full)[::-1][topk - 1]
+        assert vals[-1] >= kth - 2 * cert["bound"]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_pearson_n1000_cross_ragged(cc, orc, prec):
+    from paper_2309_03308_gb300 import CC_BF16, CC_FP8_E4M3, CC_PEARSON, Params
+    p = {"bf16": CC_BF16, "fp8": CC_FP8_E4M3}[prec]
+    Fa, Fb = two_fields(1000, (64, 64, 0, 89, 74, 4), (256, 160, 0, 291, 180, 1))  # 1000 x 700
+    fa, fb = cc.load_field(Fa), cc.load_field(Fb)
+    (ra,) = cc.define_regions(fa, [(0, 0, 0, 25, 10, 4)])
+    (rb,) = cc.define_regions(fb, [(0, 0, 0, 35, 20, 1)])
+    full = all_values(orc, oracle.PEARSON, Fa, Fb)
+    res, ids, vals, cert = cc.all_pairs_topk(ra, rb, Params(CC_PEARSON, precision=p), topk=64)
+    check(res, ids, vals, cert, full, 1000 * 700, 64)
+    assert cert["bound"] < (0.02 if prec == "bf16" else 0.2)
+
+
+def test_self_pair_bf16(cc, orc):
+    from paper_2309_03308_gb300 import CC_BF16, CC_PEARSON, Params
+    Fa = gen.field(2, 352, 256, 20, 1000, box=(100, 100, 0, 132, 116, 2))  # 1024 points
+    fa = cc.load_field(Fa)
+    (ra,) = cc.define_regions(fa, [(0, 0, 0, 32, 16, 2)])
+    res, ids, vals, cert = cc.all_pairs_topk(ra, ra, Params(CC_PEARSON, precision=CC_BF16),
+                                             topk=100)
+    full = all_values(orc, oracle.PEARSON, Fa, Fa).reshape(1024, 1024)
+    mask = np.triu(np.ones((1024, 1024), bool), 1)
+    full = np.where(mask, full, np.nan).ravel()
+    valid = full[~np.isnan(full)]
+    assert res["count"] == 1024 * 1023 // 2
+    assert cert["certified_max"] == 1 and cert["certified_min"] == 1
+    assert abs(res["max"] - valid.max()) < TOL_REFINED
+    assert abs(res["min"] - valid.min()) < TOL_REFINED
+    a, b = divmod(res["argmax"], 1024)
+    assert a < b
+    assert np.abs(full[ids.astype(np.int64)] - vals).max() < TOL_REFINED
+
+
+def test_spearman_n100_and_cc_all_pairs_route(cc, orc):
+    from paper_2309_03308_gb300 import CC_BF16, CC_FP8_E4M3, CC_SPEARMAN, Params
+    Fa, Fb = two_fields(100, (64, 64, 0, 96, 96, 2), (256, 160, 0, 288, 176, 1))  # 2048 x 512
+    fa, fb = cc.load_field(Fa), cc.load_field(Fb)
+    (ra,) = cc.define_regions(fa, [(0, 0, 0, 32, 32, 2)])
+    (rb,) = cc.define_regions(fb, [(0, 0, 0, 32, 16, 1)])
+    full = all_values(orc, oracle.SPEARMAN, Fa, Fb)
+    for p in (CC_BF16, CC_FP8_E4M3):
+        res = cc.all_pairs(ra, rb, Params(CC_SPEARMAN, precision=p))
+        assert abs(res["max"] - full.max()) < TOL_REFINED
+        assert abs(res["min"] - full.min()) < TOL_REFINED
+        assert abs(full[res["argmax"]] - full.max()) < TOL_REFINED
+
+
+def test_dot2_pairs_n1000(cc, orc):
+    from paper_2309_03308_gb300 import CC_FP32, CC_FP32_DOT2, CC_PEARSON, CC_SPEARMAN, Params
+    F = gen.field(2, 352, 256, 20, 1000, box=(10, 10, 0, 42, 42, 1))
+    fid = cc.load_field(F)
+    rng = np.random.default_rng(3)
+    pa = rng.integers(0, 1024, 3000).astype(np.uint32)
+    pb = rng.integers(0, 1024, 3000).astype(np.uint32)
+    for kind in (CC_PEARSON, CC_SPEARMAN):
+        ref = orc.eval_pairs(F, kind, pa, pb)
+        d2 = cc.eval_pairs(fid, fid, Params(kind, precision=CC_FP32_DOT2), pa, pb)
+        f32 = cc.eval_pairs(fid, fid, Params(kind, precision=CC_FP32), pa, pb)
+        assert np.abs(d2 - ref).max() < TOL_REFINED
+        assert np.abs(d2 - ref).max() <= np.abs(f32 - ref).max() + 1e-7
+
+
+def test_mixed_argument_errors(cc):
+    from paper_2309_03308_gb300 import CC_BF16, CC_MI_KSG, CC_PEARSON, CCError, Params
+    F = gen.field(3, 8, 8, 2, 40)
+    fid = cc.load_field(F)
+    (r,) = cc.define_regions(fid, [(0, 0, 0, 8, 8, 2)])
+    with pytest.raises(CCError):
+        cc.all_pairs_topk(r, r, Params(CC_PEARSON, precision=CC_BF16), topk=5000)
+    with pytest.raises(CCError):
+        cc.all_pairs_topk(r, r, Params(CC_MI_KSG, precision=CC_BF16))
+    with pytest.raises(CCError):
+        cc.all_pairs_topk(r, r, Params(CC_PEARSON))  # FP32 is not a reduced precision
