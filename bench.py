@@ -1,23 +1,27 @@
 """Throughput of the correlation hot path on one GB300 (or N independent ranks).
 
-Workload (focus refinement at paper scale): a 352x256x20 ensemble field with
-n = 100 members (seeded synthetic stand-in for the paper's weather ensemble)
-and two 32x32x20 regions (20,480 points each). One step runs the whole path
-on the resident field:
-  a1  ingest: per-point planes (FP64 stats, z-scores, ranks, sorted values)
-  a3  all 419,430,400 cross pairs, Pearson, FP32, every value stored + extremes
-  a4  the same for Spearman
-  a12 2,000,000 seeded uniform cross pairs
-  a6  KSG MI (k = 10) on them + extremes
-  a5  16x16-bin histogram MI on them + extremes
-The metric counts point-pair measure evaluations per second over the step
-(2 x 419,430,400 + 2 x 2,000,000 per step); per-measure rates are reported
-beside it. Multi-GPU (torchrun): every rank runs its own replica with its own
-sampler stream (weak scaling); the only collective is the timing barrier and
-max.
+Headline workload (focus refinement at paper scale): a 352x256x20 ensemble
+with n = 100 members (seeded synthetic stand-in for the paper's weather
+ensemble) and two 32x32x20 regions (20,480 points each). One step runs every
+built stage of the path on the resident field:
+  ingest      per-point planes (FP64 stats, z-scores, ranks, sorted values)
+  fp32 x2     all 419,430,400 cross pairs, Pearson and Spearman, FP32 SIMT,
+              every value stored, extremes fused
+  bf16, fp8   the same Pearson pairs on the tensor cores, certified exact
+              extremes (Dot2 re-evaluation) and the top-4096 list
+  sample      2,000,000 seeded uniform cross pairs
+  ksg, hist   KSG MI (k = 10) and 16x16-bin MI on them, with extremes
+`value` counts point-pair measure evaluations per second over the step.
+
+A second workload with n = 1000 (the same two regions, only those boxes
+generated) is timed in the same run and reported under "m1000": FP32 SIMT vs
+BF16 vs FP8 all-pairs extremes and KSG on 1,000,000 sampled pairs.
+
+Multi-GPU (torchrun): every rank runs its own replica with its own sampler
+stream (weak scaling); the only collectives are the timing barrier and max.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same step and scales it to the step.
+sample of each stage and scales it to the step.
 """
 from __future__ import annotations
 
@@ -38,23 +42,11 @@ import gen  # noqa: E402
 from gen import configs  # noqa: E402
 
 METRIC = "KSG-MI & Pearson point-pairs/s at M=100/1000 vs plain FP32 GPU, roofline %"
-CFG = configs.FOCUS
+FOC = configs.FOCUS
+PRE = configs.PRECISION
 N_ALL = 20480 * 20480
-N_SAMPLED = CFG["sampled_pairs"]
-PAIRS_PER_STEP = 2 * N_ALL + 2 * N_SAMPLED
 N_SMS = 152
 FP32_LANES = 128
-
-# Algorithmic work per unit (stated in the design doc):
-#   Pearson/Spearman all-pairs: 2n flops per pair (n multiply-adds).
-#   KSG: n(n-1) Chebyshev distance evaluations + 2n(n-1) marginal comparisons
-#        per pair (definition count), i.e. 3n(n-1) ALU operations.
-#   ingest: read n*P*4 bytes, write planes 22 bytes per point-member + 16 per point.
-ALG = {
-    "allpairs_pearson": ("alu_flop", lambda n: 2.0 * n * N_ALL),
-    "allpairs_spearman": ("alu_flop", lambda n: 2.0 * n * N_ALL),
-    "ksg": ("alu_op", lambda n: 3.0 * n * (n - 1) * N_SAMPLED),
-}
 
 
 def peaks():
@@ -62,8 +54,28 @@ def peaks():
     if os.path.exists(path):
         d = json.load(open(path))
         return dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2070.0),
+                    bf16_tflops=d.get("bf16_tflops_sustained", d["bf16_tflops"]),
                     source="measured")
-    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, bf16_tflops=1700.0, source="fallback")
+
+
+def peak_of(kind, pk):
+    """(peak, unit, source note) of a roofline kind."""
+    alu = N_SMS * FP32_LANES * pk["sm_max_mhz"] * 1e6 / 1e12
+    if kind == "fp32_flop":
+        return 2 * alu, "TFLOP/s", f"derived: {N_SMS} SMs x {FP32_LANES} lanes x 2 flop x " \
+                                   f"{pk['sm_max_mhz']:.0f} MHz"
+    if kind == "alu_op":
+        return alu, "Tops/s", f"derived: {N_SMS} SMs x {FP32_LANES} lanes x " \
+                              f"{pk['sm_max_mhz']:.0f} MHz"
+    if kind == "bf16":
+        return pk["bf16_tflops"], "TFLOP/s", f"{pk['source']} sustained bf16"
+    if kind == "fp8":
+        return 2 * pk["bf16_tflops"], "TFLOP/s", f"{pk['source']} sustained bf16 x 2 (nominal " \
+                                                 "fp8/bf16 ratio)"
+    if kind == "hbm":
+        return pk["hbm_gbs"], "GB/s", f"{pk['source']} copy bandwidth"
+    raise ValueError(kind)
 
 
 class Clocks:
@@ -122,76 +134,114 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-# ----------------------------------------------------------------------------- GPU arm
-def run_ours(args, rank, world, local_rank):
-    import torch
-    import paper_2309_03308_gb300 as pg
-    from paper_2309_03308_gb300 import Params, build
+# ----------------------------------------------------------------------------- workloads
+class Workload:
+    """Fields, regions, buffers and the ordered stage list of one step."""
 
-    build.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
-    torch.cuda.set_stream(stream)
-    n = CFG["n"]
-    if args.workload == "focus":
-        F_host = gen.field(CFG["seed"], CFG["X"], CFG["Y"], CFG["Z"], CFG["n"])
-    else:  # focus-regions: only the two boxes, as two fields (profiling case, ~0.2 GB)
-        F_host = np.stack([gen.field(CFG["seed"], CFG["X"], CFG["Y"], CFG["Z"], n, box=b)
-                           for b in (CFG["box_a"], CFG["box_b"])])
-    F_dev = torch.from_numpy(F_host).to(dev)
-    F_pin = torch.from_numpy(F_host).pin_memory()
-    cc = pg.Context(local_rank, stream=stream.cuda_stream)
-    if args.workload == "focus":
-        fid = fid_b = cc.load_field(F_dev)
-        ra, rb = cc.define_regions(fid, [CFG["box_a"], CFG["box_b"]])
-    else:
-        fid, fid_b = cc.load_field(F_dev[0]), cc.load_field(F_dev[1])
-        (ra,) = cc.define_regions(fid, [(0, 0, 0, 32, 32, 20)])
-        (rb,) = cc.define_regions(fid_b, [(0, 0, 0, 32, 32, 20)])
-    vals_p = torch.empty((20480, 20480), device=dev)
-    vals_s = torch.empty((20480, 20480), device=dev)
-    pa = torch.empty(N_SAMPLED, dtype=torch.int32, device=dev)
-    pb = torch.empty(N_SAMPLED, dtype=torch.int32, device=dev)
-    ksg = torch.empty(N_SAMPLED, device=dev)
-    hist = torch.empty(N_SAMPLED, device=dev)
-    offs = np.array([0, N_SAMPLED], np.int64)
-    p_pear, p_spear = Params(pg.CC_PEARSON), Params(pg.CC_SPEARMAN)
-    p_ksg, p_hist = Params(pg.CC_MI_KSG, k=CFG["k"]), Params(pg.CC_MI_BINNED, bins=CFG["bins"])
-    names = ["ingest", "allpairs_pearson", "allpairs_spearman", "sample", "ksg", "hist"]
+    def __init__(self, name, cc, dev, rank, n, boxes_only, sampled, k, with_store, topk):
+        import torch
+        import paper_2309_03308_gb300 as pg
+        from paper_2309_03308_gb300 import Params
+        cfg = FOC if n == 100 else PRE
+        self.name, self.n, self.cc, self.rank = name, n, cc, rank
+        if boxes_only:
+            self.F_host = np.stack([gen.field(cfg["seed"], cfg["X"], cfg["Y"], cfg["Z"], n, box=b)
+                                    for b in (cfg["box_a"], cfg["box_b"])])
+        else:
+            self.F_host = gen.field(cfg["seed"], cfg["X"], cfg["Y"], cfg["Z"], n)
+        self.boxes_only = boxes_only
+        self.F_dev = torch.from_numpy(self.F_host).to(dev)
+        self.F_pin = torch.from_numpy(self.F_host).pin_memory()
+        if boxes_only:
+            self.fa, self.fb = cc.load_field(self.F_dev[0]), cc.load_field(self.F_dev[1])
+            (self.ra,) = cc.define_regions(self.fa, [(0, 0, 0, 32, 32, 20)])
+            (self.rb,) = cc.define_regions(self.fb, [(0, 0, 0, 32, 32, 20)])
+        else:
+            self.fa = self.fb = cc.load_field(self.F_dev)
+            self.ra, self.rb = cc.define_regions(self.fa, [cfg["box_a"], cfg["box_b"]])
+        self.sampled = sampled
+        self.pa = torch.empty(sampled, dtype=torch.int32, device=dev)
+        self.pb = torch.empty(sampled, dtype=torch.int32, device=dev)
+        self.ksg = torch.empty(sampled, device=dev)
+        self.hist = torch.empty(sampled, device=dev)
+        self.vals = [torch.empty((20480, 20480), device=dev) for _ in range(2)] if with_store \
+            else [None, None]
+        self.offs = np.array([0, sampled], np.int64)
+        self.results = {}
+        P = pg
+        self.stages = []  # (name, fn(i, host), pairs, roofline kind, algorithmic work)
+        self.stages.append(("ingest", self._ingest, 0, "hbm",
+                            self.F_host.nbytes + self.F_host.nbytes * 20 // 4))
+        self.stages.append(("allpairs_pearson_fp32",
+                            lambda i, h: self._allpairs("pearson_fp32", Params(P.CC_PEARSON),
+                                                        self.vals[0]),
+                            N_ALL, "fp32_flop", 2.0 * n * N_ALL))
+        if with_store:
+            self.stages.append(("allpairs_spearman_fp32",
+                                lambda i, h: self._allpairs("spearman_fp32",
+                                                            Params(P.CC_SPEARMAN), self.vals[1]),
+                                N_ALL, "fp32_flop", 2.0 * n * N_ALL))
+        for tag, prec, kind in (("bf16", P.CC_BF16, "bf16"), ("fp8", P.CC_FP8_E4M3, "fp8")):
+            self.stages.append((f"allpairs_pearson_{tag}",
+                                (lambda prec, tag: lambda i, h: self._topk(
+                                    f"pearson_{tag}", Params(P.CC_PEARSON, precision=prec),
+                                    topk))(prec, tag),
+                                N_ALL, kind, 2.0 * n * N_ALL))
+        self.stages.append(("sample", self._sample, 0, None, 0))
+        self.stages.append(("ksg", lambda i, h: self._eval("ksg", Params(P.CC_MI_KSG, k=k),
+                                                           self.ksg),
+                            sampled, "alu_op", 3.0 * n * (n - 1) * sampled))
+        if n == 100:
+            self.stages.append(("hist", lambda i, h: self._eval(
+                "hist", Params(P.CC_MI_BINNED, bins=FOC["bins"]), self.hist),
+                                sampled, None, 0))
+        self.pairs_per_step = sum(s[2] for s in self.stages)
+        self.step_i = 0
 
-    def step(i, ev=None, host=False):
-        def mark(j):
+    def _ingest(self, i, host):
+        cc = self.cc
+        if self.boxes_only:
+            for j, fid in enumerate((self.fa, self.fb)):
+                cc.update_field(fid, self.F_pin[j].numpy() if host else self.F_dev[j])
+        else:
+            cc.update_field(self.fa, self.F_pin.numpy() if host else self.F_dev)
+
+    def _allpairs(self, tag, prm, values):
+        self.results[tag] = self.cc.all_pairs(self.ra, self.rb, prm, values=values)
+
+    def _topk(self, tag, prm, topk):
+        res, ids, vals, cert = self.cc.all_pairs_topk(self.ra, self.rb, prm, topk=topk)
+        self.results[tag] = dict(res, certified=bool(cert["certified_max"] and
+                                                     cert["certified_min"]),
+                                 bound=cert["bound"], refined_pairs=cert["refined_pairs"])
+
+    def _sample(self, i, host):
+        self.cc.sample_pairs(self.ra, self.rb, 7, self.sampled, stream=self.rank * 1000003 + i,
+                             pa=self.pa, pb=self.pb)
+
+    def _eval(self, tag, prm, out):
+        if self.boxes_only:
+            self.cc.eval_pairs(self.fa, self.fb, prm, self.pa, self.pb, out=out)
+            self.results[tag] = None
+        else:
+            self.results[tag] = self.cc.segment_extremes(self.fa, prm, self.pa, self.pb,
+                                                         self.offs, values=out)[0]
+
+    def step(self, i, stream, ev=None, host=False):
+        for j, (name, fn, *_rest) in enumerate(self.stages):
             if ev is not None:
                 ev[j].record(stream)
-        mark(0)
-        if args.workload == "focus":
-            cc.update_field(fid, F_pin.numpy() if host else F_dev)  # host: H2D inside the call
-        else:
-            cc.update_field(fid, F_pin[0].numpy() if host else F_dev[0])
-            cc.update_field(fid_b, F_pin[1].numpy() if host else F_dev[1])
-        mark(1)
-        rp = cc.all_pairs(ra, rb, p_pear, values=vals_p)
-        mark(2)
-        rs = cc.all_pairs(ra, rb, p_spear, values=vals_s)
-        mark(3)
-        cc.sample_pairs(ra, rb, CFG["sampler_seed"], N_SAMPLED, stream=rank * 1000003 + i,
-                        pa=pa, pb=pb)
-        mark(4)
-        if args.workload == "focus":
-            rk = cc.segment_extremes(fid, p_ksg, pa, pb, offs, values=ksg)
-            mark(5)
-            rh = cc.segment_extremes(fid, p_hist, pa, pb, offs, values=hist)
-        else:
-            rk = [cc.eval_pairs(fid, fid_b, p_ksg, pa, pb, out=ksg)]
-            mark(5)
-            rh = [cc.eval_pairs(fid, fid_b, p_hist, pa, pb, out=hist)]
-        mark(6)
-        if host:  # device -> host read of the step's results
-            ksg_h = ksg.cpu()
-            hist_h = hist.cpu()
-            return rp, rs, rk, rh, ksg_h, hist_h
-        return rp, rs, rk, rh
+            fn(i, host)
+        if ev is not None:
+            ev[len(self.stages)].record(stream)
+        if host:  # device -> host read of the step's sampled results
+            return self.ksg.cpu(), self.hist.cpu()
+        return None
+
+
+def time_workload(wl, args, stream, world, dev, clocks=None):
+    import torch
+    import paper_2309_03308_gb300 as pg
 
     def barrier():
         if world > 1:
@@ -205,125 +255,167 @@ def run_ours(args, rank, world, local_rank):
         return t.item()
 
     for i in range(args.warmup):
-        step(i)
+        wl.step(i, stream)
     torch.cuda.synchronize()
     barrier()
-
-    # device-resident timed region
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
-    launches0 = pg.launch_count()
-    with Clocks(local_rank) as clk:
+    ns = len(wl.stages)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(ns + 1)]
+           for _ in range(args.steps)]
+    l0 = pg.launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    ctxm = clocks if clocks is not None else _Null()
+    with ctxm:
         torch.cuda.synchronize()
         barrier()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for i in range(args.steps):
-            res = step(args.warmup + i, evs[i])
+            wl.step(args.warmup + i, stream, evs[i])
         t1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    launches = pg.launch_count() - launches0
-    ms = t0.elapsed_time(t1)
-    ms = max_over_ranks(ms)
-    stage_ms = {nm: statistics.median([evs[i][j].elapsed_time(evs[i][j + 1])
-                                       for i in range(args.steps)])
-                for j, nm in enumerate(names)}
-
-    # end-to-end through the public API with host buffers
+    launches = pg.launch_count() - l0
+    ms = max_over_ranks(t0.elapsed_time(t1)) / args.steps
+    stage_ms = {name: statistics.median([evs[i][j].elapsed_time(evs[i][j + 1])
+                                         for i in range(args.steps)])
+                for j, (name, *_r) in enumerate(wl.stages)}
+    # end to end through the public API with host buffers
     torch.cuda.synchronize()
     barrier()
     e0 = time.perf_counter()
     for i in range(args.steps):
-        step(args.warmup + args.steps + i, host=True)
+        wl.step(args.warmup + args.steps + i, stream, host=True)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3)
+    e2e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3) / args.steps
+    return ms, stage_ms, e2e_ms, launches // args.steps * args.steps
 
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def stage_rooflines(wl, stage_ms, pk):
+    out = {}
+    for name, _fn, pairs, kind, work in wl.stages:
+        if not kind or stage_ms[name] <= 0:
+            continue
+        peak, unit, src = peak_of(kind, pk)
+        scale = 1e9 if kind == "hbm" else 1e12
+        achieved = work / (stage_ms[name] * 1e-3) / scale
+        out[name] = {"bound": {"fp32_flop": "alu", "alu_op": "alu", "bf16": "tensor",
+                               "fp8": "tensor", "hbm": "hbm"}[kind],
+                     "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                     "peak_source": src}
+    return out
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2309_03308_gb300 as pg
+    from paper_2309_03308_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
+    torch.cuda.set_stream(stream)
+    cc = pg.Context(local_rank, stream=stream.cuda_stream)
     pk = peaks()
-    ms_step = ms / args.steps
-    value = PAIRS_PER_STEP * world / (ms_step * 1e-3)
-    # dominant kernel by time share among the algorithmic stages
-    dom = max(ALG, key=lambda k: stage_ms[k])
-    kind, work = ALG[dom]
-    alu_ops = N_SMS * FP32_LANES * pk["sm_max_mhz"] * 1e6
-    if kind == "alu_flop":
-        peak, unit, achieved = 2 * alu_ops / 1e12, "TFLOP/s", work(n) / (stage_ms[dom] * 1e-3) / 1e12
-    else:
-        peak, unit, achieved = alu_ops / 1e12, "Tops/s", work(n) / (stage_ms[dom] * 1e-3) / 1e12
+    boxes_only = args.workload == "focus-regions"
+    wl = Workload("focus", cc, dev, rank, 100, boxes_only, FOC["sampled_pairs"], FOC["k"],
+                  with_store=True, topk=PRE["topk"])
+    with Clocks(local_rank) as clk:
+        ms, stage_ms, e2e_ms, launches = time_workload(wl, args, stream, world, dev)
+    roof = stage_rooflines(wl, stage_ms, pk)
+    dom = max(roof, key=lambda k: stage_ms[k])
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if os.path.exists(tpath):
-        traffic = json.load(open(tpath)).get(CFG["name"], {}).get(dom)
-    rp, rs, rk, rh = res
-    if args.workload != "focus":
-        rk = rh = [{"max": None}]
+        traffic = json.load(open(tpath)).get(FOC["name"], {}).get(dom)
+    dominant = dict(roof[dom], kernel=dom, traffic=traffic)
+    r = wl.results
     line = {
         "metric": METRIC,
-        "value": value,
+        "value": wl.pairs_per_step * world / (ms * 1e-3),
         "unit": "point-pairs/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_step,
+        "ms_per_step": ms,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded Gaussian random field + latent signal; stand-in for the "
                 "paper's ensembles)",
-        "config": {"workload": CFG["name"] if args.workload == "focus" else
-                   CFG["name"] + "-regions-only",
-                   "field": "352x256x20" if args.workload == "focus" else "two 32x32x20 boxes",
-                   "members": n,
-                   "regions": "2 x 32x32x20 (20480 points each)",
-                   "allpairs_per_measure": N_ALL, "sampled_pairs": N_SAMPLED,
-                   "ksg_k": CFG["k"], "hist_bins": CFG["bins"],
+        "config": {"workload": FOC["name"] + ("-regions-only" if boxes_only else ""),
+                   "field": "two 32x32x20 boxes" if boxes_only else "352x256x20",
+                   "members": 100, "regions": "2 x 32x32x20 (20480 points each)",
+                   "pairs_per_step": {s[0]: s[2] for s in wl.stages if s[2]},
+                   "ksg_k": FOC["k"], "hist_bins": FOC["bins"], "topk": PRE["topk"],
                    "l2": "inputs larger than L2 (field 721 MB rewritten as 4.6 GB of planes "
-                         "every step)",
+                         "every step; stored value matrices 3.4 GB)",
                    "parallelism": f"replicas x{world}"},
+        "stage_ms": stage_ms,
         "measures": {
-            "pearson_allpairs_pairs_per_s": N_ALL / (stage_ms["allpairs_pearson"] * 1e-3),
-            "spearman_allpairs_pairs_per_s": N_ALL / (stage_ms["allpairs_spearman"] * 1e-3),
-            "ksg_pairs_per_s": N_SAMPLED / (stage_ms["ksg"] * 1e-3),
-            "hist_pairs_per_s": N_SAMPLED / (stage_ms["hist"] * 1e-3),
-            "stage_ms": stage_ms,
-        },
-        "results": {"pearson_max": rp["max"], "spearman_max": rs["max"], "ksg_max": rk[0]["max"],
-                    "hist_max": rh[0]["max"]},
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": f"derived: {N_SMS} SMs x {FP32_LANES} FP32 lanes x "
-                                    f"{pk['sm_max_mhz']:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"},
-        "e2e": {"value": PAIRS_PER_STEP * world / (e2e_ms / args.steps * 1e-3),
-                "unit": "point-pairs/s",
-                "h2d_bytes_per_step": int(F_host.nbytes),
-                "d2h_bytes_per_step": int(2 * 4 * N_SAMPLED + 4 * 40)},
+            "pearson_fp32_pairs_per_s": N_ALL / (stage_ms["allpairs_pearson_fp32"] * 1e-3),
+            "pearson_bf16_pairs_per_s": N_ALL / (stage_ms["allpairs_pearson_bf16"] * 1e-3),
+            "pearson_fp8_pairs_per_s": N_ALL / (stage_ms["allpairs_pearson_fp8"] * 1e-3),
+            "ksg_pairs_per_s": FOC["sampled_pairs"] / (stage_ms["ksg"] * 1e-3),
+            "hist_pairs_per_s": FOC["sampled_pairs"] / (stage_ms["hist"] * 1e-3)},
+        "results": {k: (v if v is None else {kk: vv for kk, vv in v.items()})
+                    for k, v in r.items()},
+        "roofline": dominant,
+        "stage_roofline": roof,
+        "e2e": {"value": wl.pairs_per_step * world / (e2e_ms * 1e-3), "unit": "point-pairs/s",
+                "h2d_bytes_per_step": int(wl.F_host.nbytes),
+                "d2h_bytes_per_step": int(2 * 4 * FOC["sampled_pairs"] + 8 * 40)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if not args.skip_m1000:
+        wl2 = Workload("m1000", cc, dev, rank, 1000, True, PRE["sampled_pairs"], PRE["k"],
+                       with_store=False, topk=PRE["topk"])
+        ms2, st2, e2e2, l2 = time_workload(wl2, args, stream, world, dev)
+        roof2 = stage_rooflines(wl2, st2, pk)
+        fp32 = st2["allpairs_pearson_fp32"]
+        line["m1000"] = {
+            "workload": PRE["name"], "ms_per_step": ms2, "stage_ms": st2,
+            "value": wl2.pairs_per_step * world / (ms2 * 1e-3),
+            "pearson_fp32_pairs_per_s": N_ALL / (fp32 * 1e-3),
+            "pearson_bf16_pairs_per_s": N_ALL / (st2["allpairs_pearson_bf16"] * 1e-3),
+            "pearson_fp8_pairs_per_s": N_ALL / (st2["allpairs_pearson_fp8"] * 1e-3),
+            "speedup_bf16_vs_fp32": fp32 / st2["allpairs_pearson_bf16"],
+            "speedup_fp8_vs_fp32": fp32 / st2["allpairs_pearson_fp8"],
+            "ksg_pairs_per_s": PRE["sampled_pairs"] / (st2["ksg"] * 1e-3),
+            "results": wl2.results, "stage_roofline": roof2, "gpu_launches": int(l2),
+            "e2e_ms_per_step": e2e2}
     cc.close()
     return line
 
 
 # ----------------------------------------------------------------------------- oracle
-def oracle_sample_rates(F, threads=None, budget_s=12.0):
-    """Time the FP64 oracle on bounded samples of each stage; seconds per pair."""
+STAGE_MEASURE = {"allpairs_pearson_fp32": 0, "allpairs_spearman_fp32": 1,
+                 "allpairs_pearson_bf16": 0, "allpairs_pearson_fp8": 0, "ksg": 3, "hist": 2}
+
+
+def oracle_sample_rates(F, budget_s=12.0):
+    """Seconds per pair of the FP64 oracle for each measure, on bounded samples."""
     import oracle
     o = oracle.get()
-    if threads:
-        o.set_threads(threads)
-    A = oracle.box_points(CFG["X"], CFG["Y"], CFG["Z"], CFG["box_a"])
-    B = oracle.box_points(CFG["X"], CFG["Y"], CFG["Z"], CFG["box_b"])
+    A = oracle.box_points(FOC["X"], FOC["Y"], FOC["Z"], FOC["box_a"])
+    B = oracle.box_points(FOC["X"], FOC["Y"], FOC["Z"], FOC["box_b"])
     rng = np.random.default_rng(99)
-    rates = {}
-    plan = [("allpairs_pearson", oracle.PEARSON, {}, 40000),
-            ("allpairs_spearman", oracle.SPEARMAN, {}, 20000),
-            ("ksg", oracle.MI_KSG, {"k": CFG["k"]}, 4000),
-            ("hist", oracle.MI_BINNED, {"bins": CFG["bins"]}, 40000)]
+    plan = [(0, {}, 40000), (1, {}, 20000), (3, {"k": FOC["k"]}, 4000),
+            (2, {"bins": FOC["bins"]}, 40000)]
     per = budget_s / len(plan)
-    samples = {}
-    for name, kind, kw, m in plan:
+    rates, samples = {}, {}
+    for kind, kw, m in plan:
         ia = A[rng.integers(0, len(A), m)]
         ib = B[rng.integers(0, len(B), m)]
         t = time.perf_counter()
@@ -332,44 +424,47 @@ def oracle_sample_rates(F, threads=None, budget_s=12.0):
         m = int(max(64, min(m, per / max(t64, 1e-9))))
         t = time.perf_counter()
         o.eval_pairs(F, kind, ia[:m], ib[:m], **kw)
-        rates[name] = (time.perf_counter() - t) / m
-        samples[name] = m
+        rates[kind] = (time.perf_counter() - t) / m
+        samples[["pearson", "spearman", "hist", "ksg"][kind]] = m
     return rates, samples, o.threads()
 
 
 def oracle_step_seconds(rates):
-    return (rates["allpairs_pearson"] * N_ALL + rates["allpairs_spearman"] * N_ALL +
-            (rates["ksg"] + rates["hist"]) * N_SAMPLED)
+    pairs = {"allpairs_pearson_fp32": N_ALL, "allpairs_spearman_fp32": N_ALL,
+             "allpairs_pearson_bf16": N_ALL, "allpairs_pearson_fp8": N_ALL,
+             "ksg": FOC["sampled_pairs"], "hist": FOC["sampled_pairs"]}
+    return sum(rates[STAGE_MEASURE[s]] * p for s, p in pairs.items()), sum(pairs.values())
 
 
 def cpu_baseline_line(F):
     rates, samples, cores = oracle_sample_rates(F)
-    t = oracle_step_seconds(rates)
-    return {"value": PAIRS_PER_STEP / t, "unit": "point-pairs/s", "cores": cores, "kind": "oracle",
+    t, pairs = oracle_step_seconds(rates)
+    return {"value": pairs / t, "unit": "point-pairs/s", "cores": cores, "kind": "oracle",
             "sample": "FP64 oracle timed on " + ", ".join(f"{v} {k} pairs" for k, v in
                                                          samples.items()) +
-                      " drawn from the step's region pair; per-pair time scaled to the step"}
+                      " drawn from the step's region pair; per-pair times scaled to the "
+                      "step's pair counts"}
 
 
 def run_reference(args):
-    F = gen.field(CFG["seed"], CFG["X"], CFG["Y"], CFG["Z"], CFG["n"])
-    import oracle
+    F = gen.field(FOC["seed"], FOC["X"], FOC["Y"], FOC["Z"], FOC["n"])
     budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_sample_rates(F, budget_s=budget)
-    times, samples, cores = [], None, None
+    times, samples, cores, pairs = [], None, None, 0
     for _ in range(args.steps):
         rates, samples, cores = oracle_sample_rates(F, budget_s=budget)
-        times.append(oracle_step_seconds(rates))
+        t, pairs = oracle_step_seconds(rates)
+        times.append(t)
     t = statistics.median(times)
-    value = PAIRS_PER_STEP / t
+    value = pairs / t
     desc = ("FP64 oracle on " + ", ".join(f"{v} {k} pairs" for k, v in samples.items()) +
             " per step, scaled to the full step")
     return {"metric": METRIC, "value": value, "unit": "point-pairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": CFG["name"], "members": CFG["n"]},
+            "config": {"workload": FOC["name"], "members": FOC["n"]},
             "cpu_baseline": {"value": value, "unit": "point-pairs/s", "cores": cores,
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "point-pairs/s", "h2d_bytes_per_step": 0,
@@ -383,6 +478,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-m1000", action="store_true",
+                    help="do not time the n = 1000 workload")
     ap.add_argument("--workload", default="focus", choices=["focus", "focus-regions"],
                     help="focus-regions generates only the two boxes (small case for ncu)")
     args = ap.parse_args()
@@ -402,9 +499,9 @@ def main():
     line = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu_baseline:
-            F = gen.field(CFG["seed"], CFG["X"], CFG["Y"], CFG["Z"], CFG["n"])
+            F = gen.field(FOC["seed"], FOC["X"], FOC["Y"], FOC["Z"], FOC["n"])
             line["cpu_baseline"] = cpu_baseline_line(F)
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=float), flush=True)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
