@@ -299,6 +299,86 @@ cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t region_b,
                             const cc_params* params, int topk, uint64_t* ids, float* vals,
                             cc_rp_result* out, cc_mixed_info* info);
 
+/* ------------------------------------------------- Bayesian optimal sampling (BOS) */
+
+/*
+ * Batched Bayesian optimal sampling of the brick-pair maxima (Section 3.1;
+ * UCB kappa from Section 6). For every region pair a Gaussian process with
+ * Matern nu = 5/2 covariance (ARD length scales 0.25 x the regions' extents
+ * in voxels) models the objective measure over the 6D position space; each
+ * round proposes `per_round` samples by UCB with kriging-believer batch
+ * selection from the top `shortlist` entries of a fixed seeded pool of
+ * `pool` continuous positions, maps them to voxels by probabilistic
+ * reparameterization (floor + Bernoulli(fraction)), evaluates Pearson,
+ * Spearman, binned MI and KSG at every sample in one persistent launch, and
+ * conditions each GP on its new values. Signal variance, noise (1e-4 of it)
+ * and the constant prior mean come from the first round's values unless a
+ * prior mean per pool entry is set. The first `per_round` pool entries are
+ * the initial random samples. Random numbers: Philox4x64-10 with key
+ * {seed, 0xB05B05} for pool entry c of pair r at counters {c, r, 0, 0} and
+ * {c, r, 1, 0} (position_d = u24(word_d) * (extent_d - 1), u24 = top 24 bits
+ * / 2^24, fp32), and key {seed, 0xB0517D} for proposal j of round t at
+ * {j, r, 2 + t, 0} and {j, r, 2 + t, 1}. In a self pair whose two voxels
+ * coincide, the second moves to the next point of the region in enumeration
+ * order (wrapping).
+ */
+typedef struct cc_bos cc_bos;
+
+typedef struct {
+    int32_t pool;       /* pool entries per region pair: power of two in [256, 8192] */
+    int32_t per_round;  /* proposals per round and region pair, 1..32 */
+    int32_t rounds;     /* rounds provisioned; per_round * rounds + shortlist <= pool */
+    int32_t shortlist;  /* UCB shortlist for the batch selection, multiple of 16 in [16, 128] */
+    float kappa;        /* UCB weight: mu + kappa * sigma */
+    int32_t objective;  /* measure the GP models: CC_PEARSON .. CC_MI_KSG */
+    int32_t k;          /* KSG neighbours (-1: ceil(3n/100)) */
+    int32_t bins;       /* histogram bins, 2..16 */
+    uint64_t seed;
+} cc_bos_params;
+
+/*
+ * Create the sampling state for n_rp region pairs (rp_a[i], rp_b[i]) of one
+ * field (host arrays). Device memory: pool * (6 + 2 + per_round * rounds) * 4
+ * bytes per region pair, plus small arrays.
+ */
+cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, const int32_t* rp_b,
+                        int n_rp, const cc_bos_params* params, cc_bos** out);
+
+/*
+ * Prior mean per pool entry, float [n_rp][pool] (e.g. a surrogate's
+ * prediction); before the first round only. NULL restores the constant mean.
+ */
+cc_status cc_bos_set_prior(cc_ctx* ctx, cc_bos* bos, const float* prior, int prior_is_device);
+
+/*
+ * Run `rounds` rounds. use_graph != 0 captures one round into a CUDA graph on
+ * first use and replays it. The evaluation kernel's launch shape is chosen by
+ * timing a few shapes on the first call (cached per device and problem shape;
+ * also in the file named by the environment variable CCORR_AUTOTUNE_CACHE).
+ * Asynchronous.
+ */
+cc_status cc_bos_run(cc_ctx* ctx, cc_bos* bos, int rounds, int use_graph);
+
+/*
+ * Running extremes of the evaluated samples, host cc_rp_result [4][n_rp]
+ * (measure-major: Pearson, Spearman, binned MI, KSG); argmax / argmin hold
+ * (point_a << 32) | point_b, count the samples evaluated.
+ */
+cc_status cc_bos_results(cc_ctx* ctx, cc_bos* bos, cc_rp_result* out);
+
+/*
+ * Inspect region pair rp (host outputs, each may be NULL): pool [pool][6],
+ * posterior mean and variance [pool], observed pool entries and objective
+ * values [n_obs], the last round's point pairs [per_round] and measure values
+ * [4][per_round]; *n_obs = observations so far.
+ */
+cc_status cc_bos_inspect(cc_ctx* ctx, cc_bos* bos, int rp, float* pool, float* mu, float* var,
+                         int32_t* obs, float* y, uint32_t* pa, uint32_t* pb, float* vals,
+                         int32_t* n_obs);
+
+/* Release the sampling state. */
+cc_status cc_bos_destroy(cc_ctx* ctx, cc_bos* bos);
+
 /* ------------------------------------------------------------ allocation-free form */
 
 /*

@@ -73,6 +73,18 @@ def bernoulli_voxels(orc, seed: int, rp: int, rnd: int, j: int, theta: np.ndarra
     return (f.astype(np.int64) + (u < frac)).astype(np.int64)
 
 
+def self_pair_fix(v, ext):
+    """READING: in a self brick pair a sample never pairs a point with itself;
+    when both voxels coincide, the second moves to the next point of the brick
+    in enumeration order (x fastest), wrapping around."""
+    v = np.array(v, np.int64)
+    if tuple(v[:3]) == tuple(v[3:]):
+        ex, ey, ez = ext
+        l = (v[3] + ex * (v[4] + ey * v[5]) + 1) % (ex * ey * ez)
+        v[3], v[4], v[5] = l % ex, (l // ex) % ey, l // (ex * ey)
+    return v
+
+
 def matern52(X1, X2, ell, sf2):
     """Matern nu = 5/2 covariance with ARD length scales (FP64)."""
     X1 = np.asarray(X1, np.float64) / ell

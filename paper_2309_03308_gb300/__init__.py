@@ -207,8 +207,69 @@ class Context:
         cert = {f: getattr(info, f) for f, _ in _lib.cc_mixed_info._fields_}
         return _res(res), ids[:topk], vals[:topk], cert
 
+    def bos_create(self, fid: int, rp_a, rp_b, pool=2048, per_round=32, rounds=30,
+                   shortlist=128, kappa=0.5, objective=CC_MI_KSG, k=10, bins=16, seed=3):
+        """Batched BOS state over region pairs (rp_a[i], rp_b[i]) of field fid."""
+        a = np.ascontiguousarray(rp_a, np.int32)
+        b = np.ascontiguousarray(rp_b, np.int32)
+        prm = _lib.cc_bos_params(pool, per_round, rounds, shortlist, kappa, objective, k, bins,
+                                 seed)
+        h = ctypes.c_void_p()
+        self._check(self.lib.cc_bos_create(self.h, fid, a.ctypes.data, b.ctypes.data, len(a),
+                                           ctypes.byref(prm), ctypes.byref(h)))
+        return Bos(self, h, len(a), prm)
+
     def sync(self):
         self._check(self.lib.cc_sync(self.h))
+
+
+class Bos:
+    """cc_bos handle: batched Bayesian optimal sampling over region pairs."""
+
+    def __init__(self, ctx: Context, h, n_rp: int, prm):
+        self.ctx, self.h, self.n_rp, self.prm = ctx, h, n_rp, prm
+
+    def set_prior(self, prior):
+        p, dev = _ptr(prior) if prior is not None else (None, 0)
+        self.ctx._check(self.ctx.lib.cc_bos_set_prior(self.ctx.h, self.h, p, dev))
+
+    def run(self, rounds: int, use_graph: bool = True):
+        self.ctx._check(self.ctx.lib.cc_bos_run(self.ctx.h, self.h, rounds, int(use_graph)))
+
+    def results(self):
+        """[4][n_rp] dicts (Pearson, Spearman, binned MI, KSG); argmax = (a << 32) | b."""
+        res = (_lib.cc_rp_result * (4 * self.n_rp))()
+        self.ctx._check(self.ctx.lib.cc_bos_results(self.ctx.h, self.h, res))
+        return [[_res(res[m * self.n_rp + i]) for i in range(self.n_rp)] for m in range(4)]
+
+    def inspect(self, rp: int):
+        Q, R, T = self.prm.pool, self.prm.per_round, self.prm.rounds
+        pool = np.empty((Q, 6), np.float32)
+        mu = np.empty(Q, np.float32)
+        var = np.empty(Q, np.float32)
+        obs = np.empty(R * T, np.int32)
+        y = np.empty(R * T, np.float32)
+        pa = np.empty(R, np.uint32)
+        pb = np.empty(R, np.uint32)
+        vals = np.empty((4, R), np.float32)
+        n = ctypes.c_int32()
+        self.ctx._check(self.ctx.lib.cc_bos_inspect(
+            self.ctx.h, self.h, rp, pool.ctypes.data, mu.ctypes.data, var.ctypes.data,
+            obs.ctypes.data, y.ctypes.data, pa.ctypes.data, pb.ctypes.data, vals.ctypes.data,
+            ctypes.byref(n)))
+        s = n.value
+        return dict(pool=pool, mu=mu, var=var, obs=obs[:s], y=y[:s], pa=pa, pb=pb, vals=vals)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.cc_bos_destroy(self.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:

@@ -46,6 +46,13 @@ class cc_mixed_info(ctypes.Structure):
                 ("certified_min", ctypes.c_int32), ("refined_pairs", ctypes.c_int64)]
 
 
+class cc_bos_params(ctypes.Structure):
+    _fields_ = [("pool", ctypes.c_int32), ("per_round", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("shortlist", ctypes.c_int32),
+                ("kappa", ctypes.c_float), ("objective", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("bins", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I32 = ctypes.c_int32
@@ -73,6 +80,13 @@ SIGNATURES = {
                                  _P]),
     "cc_all_pairs": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _P, _I64, _P]),
     "cc_all_pairs_topk": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _I, _P, _P, _P, _P]),
+    "cc_bos_create": (_S, [_P, _I32, _P, _P, _I, ctypes.POINTER(cc_bos_params),
+                           ctypes.POINTER(_P)]),
+    "cc_bos_set_prior": (_S, [_P, _P, _P, _I]),
+    "cc_bos_run": (_S, [_P, _P, _I, _I]),
+    "cc_bos_results": (_S, [_P, _P, _P]),
+    "cc_bos_inspect": (_S, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I32)]),
+    "cc_bos_destroy": (_S, [_P, _P]),
     "cc_all_pairs_static": (_S, [_P, _I64, _P, _I64, _I, _I64, _I64, _I, _P, _I64, _P, _P]),
     "cc_launch_count": (_S, [ctypes.POINTER(_U64)]),
 }

@@ -1,0 +1,1041 @@
+// Bayesian optimal sampling of brick-pair maxima, batched over all region
+// pairs (Section 3.1; Section 6: UCB with kappa = 0.5). One round:
+//
+//   propose    per region pair, UCB mu + kappa * sigma over a fixed seeded pool
+//              of Q continuous 6D positions; the top-M form a shortlist whose
+//              posterior covariance is built, and R proposals are picked
+//              greedily with the kriging-believer update
+//              (cov -= cov[:, c] cov[c, :] / (cov[c, c] + noise)).
+//   round      probabilistic reparameterization: voxel = floor(theta) +
+//              Bernoulli(theta - floor(theta)) (Philox4x64-10).
+//   evaluate   Pearson, Spearman, binned MI and KSG for every (pair, proposal)
+//              in ONE persistent launch: warps pull (measure, pair) items from a
+//              work queue, longest measure (KSG) first.
+//   extremes   running max / min per region pair and measure.
+//   condition  the GP of each region pair absorbs the R new observations of the
+//              objective measure. The state keeps V = L^-1 K(X, pool) (L the
+//              Cholesky factor over the observations X), so conditioning needs
+//              only the new rows V2 = L22^-1 (K(P, pool) - V[:, P]^T V) with
+//              L22 = chol(posterior cov(P, P) + noise): mean and variance of all
+//              pool entries then update as mu += V2^T beta2, var -= colsum(V2^2).
+//
+// Matern nu = 5/2 kernel with ARD length scales 0.25 x extent (voxels); the
+// signal variance is the variance of the first round's objective values, the
+// noise variance 1e-4 of it, the prior mean their mean (or a supplied value
+// per pool entry, e.g. a learned surrogate's prediction). The whole round is
+// captured once into a CUDA graph and replayed; kernels read the round number
+// from device memory. The evaluation kernel's launch shape is autotuned.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "ksg_dev.cuh"
+
+namespace cc {
+
+double digamma_int_host(int m);
+
+constexpr uint64_t kPoolKey = 0xB05B05ull, kRoundKey = 0xB0517Dull;
+constexpr int kBosThreads = 256;
+
+struct BosDev {
+    int n_rp, Q, R, T, M;
+    float kappa;
+    uint64_t seed;
+    int objective, k, bins;
+    int n, n_pad, X, Y;
+    const int* box;      // [n_rp][12]: a.x0 y0 z0 ext_x ext_y ext_z, b likewise
+    const int* self;     // [n_rp]
+    float* pool;         // [n_rp][Q][6]
+    float* V;            // [n_rp][R*T][Q]
+    float* mu;           // [n_rp][Q]
+    float* var;          // [n_rp][Q]
+    unsigned* sel;       // [n_rp][Q/32]
+    int* obs;            // [n_rp][R*T]
+    float* y;            // [n_rp][R*T]
+    float* beta;         // [n_rp][R*T]
+    float* hyp;          // [n_rp][4]: prior mean, signal var, noise var
+    const float* prior;  // [n_rp][Q] or null
+    int* picks;          // [n_rp][R]
+    uint32_t* pa;        // [n_rp*R]
+    uint32_t* pb;
+    float* vals;         // [4][n_rp*R]
+    Partial* best;       // [4][n_rp], argmax/argmin = (pa << 32) | pb
+    int* round;
+    int* queue;
+    int* status;
+    // field planes
+    const float* zhat;
+    const float* rhat;
+    const float* fvals;
+    const float* sorted;
+    const uint16_t* perm;
+    const uint8_t* bins_p;
+    const long long* hmarg;
+    const long long* psi_fix;
+    const long long* clogc_fix;
+    double psi_nk;
+};
+
+__device__ __forceinline__ unsigned okey32(float v) {
+    const unsigned b = __float_as_uint(v + 0.0f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float matern52(const float* a, const float* b, const float* inv_ell,
+                                          float sf2) {
+    float r2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const float t = (a[d] - b[d]) * inv_ell[d];
+        r2 = fmaf(t, t, r2);
+    }
+    const float r = sqrtf(r2) * 2.2360679774997896f;  // sqrt(5) r
+    return sf2 * (1.f + r + r * r * (1.f / 3.f)) * expf(-r);
+}
+
+__device__ __forceinline__ void inv_ell_of(const BosDev& d, int rp, float* inv_ell) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) inv_ell[3 * a + j] = 1.f / (0.25f * (float)d.box[rp * 12 + 6 * a + 3 + j]);
+}
+
+// ---------------------------------------------------------------------------
+// pool: candidate c of pair rp from Philox blocks {c, rp, 0, 0} and {c, rp, 1, 0}
+__global__ void k_bos_pool(BosDev d) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)d.n_rp * d.Q) return;
+    const int rp = (int)(i / d.Q), c = (int)(i % d.Q);
+    uint64_t w0[4] = {(uint64_t)c, (uint64_t)rp, 0, 0}, w1[4] = {(uint64_t)c, (uint64_t)rp, 1, 0};
+    philox4x64_10(w0, d.seed, kPoolKey);
+    philox4x64_10(w1, d.seed, kPoolKey);
+    const uint64_t w[6] = {w0[0], w0[1], w0[2], w0[3], w1[0], w1[1]};
+    float* out = d.pool + i * 6;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        const int ext = d.box[rp * 12 + (a < 3 ? 3 + a : 6 + 3 + (a - 3))];
+        out[a] = __fmul_rn(u24(w[a]), (float)(ext - 1));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// propose: one CTA per region pair. Dynamic smem: Q keys (8 B), M shortlist
+// ids, M x M covariance, M x 6 positions, M means, a row buffer.
+__global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
+    extern __shared__ __align__(16) unsigned char bs[];
+    const int rp = blockIdx.x, tid = threadIdx.x;
+    const int r = *d.round, R = d.R, Q = d.Q, M = d.M;
+    unsigned* sel = d.sel + (int64_t)rp * (Q / 32);
+    int* picks = d.picks + rp * R;
+    if (r == 0) {
+        if (tid < R) {
+            picks[tid] = tid;
+            atomicOr(&sel[tid >> 5], 1u << (tid & 31));
+        }
+        return;
+    }
+    const int s = r * R;
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(bs);
+    int* SL = reinterpret_cast<int*>(key + Q);
+    float* cov = reinterpret_cast<float*>(SL + M);
+    float* pos = cov + M * M;
+    float* msl = pos + M * 6;
+    float* rowbuf = msl + M;        // 8 rows x M
+    float* red_v = rowbuf + 8 * M;  // per-warp argmax
+    int* red_i = reinterpret_cast<int*>(red_v + 32);
+    const float* mu = d.mu + (int64_t)rp * Q;
+    const float* var = d.var + (int64_t)rp * Q;
+    const float kappa = d.kappa, sf2 = d.hyp[rp * 4 + 1], sn2 = d.hyp[rp * 4 + 2];
+    for (int c = tid; c < Q; c += blockDim.x) {
+        const bool taken = (sel[c >> 5] >> (c & 31)) & 1u;
+        const float u = mu[c] + kappa * sqrtf(fmaxf(var[c], 0.f));
+        key[c] = taken ? 0ull
+                       : ((unsigned long long)okey32(u) << 32) | (0xffffffffull - (unsigned)c);
+    }
+    __syncthreads();
+    for (int size = 2; size <= Q; size <<= 1) {  // bitonic sort, descending
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < Q; i += blockDim.x) {
+                const int p = i ^ stride;
+                if (p > i) {
+                    const bool desc = (i & size) == 0;
+                    const unsigned long long a = key[i], b = key[p];
+                    if ((a < b) == desc) {
+                        key[i] = b;
+                        key[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    float inv_ell[6];
+    inv_ell_of(d, rp, inv_ell);
+    for (int i = tid; i < M; i += blockDim.x) {
+        const int c = (int)(0xffffffffull - (key[i] & 0xffffffffull));
+        SL[i] = c;
+        msl[i] = mu[c];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) pos[i * 6 + a] = d.pool[((int64_t)rp * Q + c) * 6 + a];
+    }
+    __syncthreads();
+    // posterior covariance among the shortlist: K(SL, SL) - V[:, SL]^T V[:, SL]
+    const int ti = tid >> 4, tj = tid & 15;  // 16 x 16 threads, (M/16)^2 entries each
+    const int per = M / 16;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    const float* Vr = d.V + (int64_t)rp * (R * d.T) * Q;
+    for (int t0 = 0; t0 < s; t0 += 8) {
+        for (int e = tid; e < 8 * M; e += blockDim.x) {
+            const int t = t0 + e / M, i = e % M;
+            rowbuf[e] = t < s ? Vr[(int64_t)t * Q + SL[i]] : 0.f;
+        }
+        __syncthreads();
+        for (int t = 0; t < 8; ++t) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i >= per) break;
+                const float a = rowbuf[t * M + ti * per + i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j >= per) break;
+                    acc[i][j] = fmaf(a, rowbuf[t * M + tj * per + j], acc[i][j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i >= per) break;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j >= per) break;
+            const int a = ti * per + i, b = tj * per + j;
+            cov[a * M + b] = matern52(pos + a * 6, pos + b * 6, inv_ell, sf2) - acc[i][j];
+        }
+    }
+    __syncthreads();
+    // greedy picks with the kriging-believer update
+    float* col = rowbuf;
+    for (int j = 0; j < R; ++j) {
+        float bv = -CUDART_INF_F;
+        int bi = 0x7fffffff;
+        for (int i = tid; i < M; i += blockDim.x) {
+            if (SL[i] < 0) continue;  // taken this round
+            const float u = msl[i] + kappa * sqrtf(fmaxf(cov[i * M + i], 0.f));
+            if (u > bv || (u == bv && i < bi)) {
+                bv = u;
+                bi = i;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if ((tid & 31) == 0) {
+            red_v[tid >> 5] = bv;
+            red_i[tid >> 5] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                if (red_v[w] > red_v[0] || (red_v[w] == red_v[0] && red_i[w] < red_i[0])) {
+                    red_v[0] = red_v[w];
+                    red_i[0] = red_i[w];
+                }
+            const int c = red_i[0];
+            picks[j] = SL[c];
+            atomicOr(&sel[SL[c] >> 5], 1u << (SL[c] & 31));
+        }
+        __syncthreads();
+        const int c = red_i[0];
+        for (int i = tid; i < M; i += blockDim.x) col[i] = cov[i * M + c];
+        __syncthreads();
+        const float inv = 1.f / (col[c] + sn2);
+        for (int e = tid; e < M * M; e += blockDim.x) cov[e] -= col[e / M] * col[e % M] * inv;
+        if (tid == 0) SL[c] = -1 - SL[c];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// probabilistic reparameterization of proposal j: blocks {j, rp, 2 + r, 0/1}
+__global__ void k_bos_round_pairs(BosDev d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n_rp * d.R) return;
+    const int rp = i / d.R, j = i % d.R, r = *d.round;
+    const int c = d.picks[rp * d.R + j];
+    const float* th = d.pool + ((int64_t)rp * d.Q + c) * 6;
+    uint64_t w0[4] = {(uint64_t)j, (uint64_t)rp, (uint64_t)(2 + r), 0};
+    uint64_t w1[4] = {(uint64_t)j, (uint64_t)rp, (uint64_t)(2 + r), 1};
+    philox4x64_10(w0, d.seed, kRoundKey);
+    philox4x64_10(w1, d.seed, kRoundKey);
+    const uint64_t w[6] = {w0[0], w0[1], w0[2], w0[3], w1[0], w1[1]};
+    int v[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        const float f = floorf(th[a]);
+        v[a] = (int)f + (u24(w[a]) < __fsub_rn(th[a], f) ? 1 : 0);
+    }
+    const int* bx = d.box + rp * 12;
+    if (d.self[rp]) {  // a self pair never pairs a point with itself
+        if (v[0] == v[3] && v[1] == v[4] && v[2] == v[5]) {
+            const int np = bx[3] * bx[4] * bx[5];
+            int l = v[3] + bx[3] * (v[4] + bx[4] * v[5]);
+            l = (l + 1) % np;
+            v[3] = l % bx[3];
+            v[4] = (l / bx[3]) % bx[4];
+            v[5] = l / (bx[3] * bx[4]);
+        }
+    }
+    d.pa[i] = (uint32_t)((bx[0] + v[0]) + d.X * ((bx[1] + v[1]) + d.Y * (bx[2] + v[2])));
+    d.pb[i] = (uint32_t)((bx[6] + v[3]) + d.X * ((bx[7] + v[4]) + d.Y * (bx[8] + v[5])));
+}
+
+// ---------------------------------------------------------------------------
+// evaluate: persistent work queue over (measure, pair) items, KSG first.
+template <int KMAX>
+__global__ void k_bos_eval(BosDev d, int warps_per_block) {
+    extern __shared__ __align__(16) unsigned char es[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = d.n, n_pad = d.n_pad, B = d.bins;
+    long long* psi = reinterpret_cast<long long*>(es);
+    long long* clogc = psi + ((n + 2) & ~1);
+    const size_t slot = ksg_slot_bytes(n_pad);
+    unsigned char* wbase = reinterpret_cast<unsigned char*>(clogc + ((n + 2) & ~1)) +
+                           (size_t)warp * (slot + 256 * sizeof(int));
+    int* hist = reinterpret_cast<int*>(wbase + slot);
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+        psi[i] = d.psi_fix[i];
+        clogc[i] = d.clogc_fix[i];
+    }
+    for (int c = lane; c < B * B; c += 32) hist[c] = 0;
+    __syncthreads();
+    const int per = d.n_rp * d.R, total = 4 * per;
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(d.queue, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        const int measure = 3 - item / per, t = item % per;
+        const uint32_t p = d.pa[t], q = d.pb[t];
+        const int64_t ra = (int64_t)p * n_pad, rb = (int64_t)q * n_pad;
+        float value = 0.f;
+        if (measure == CC_MI_KSG) {
+            ksg_stage(wbase, n, n_pad, d.sorted + ra, d.perm + ra, d.fvals + ra, d.sorted + rb,
+                      d.perm + rb, d.fvals + rb);
+            long long acc = 0;
+            for (int ti = lane; ti < n; ti += 32)
+                acc += ksg_sample<KMAX>(wbase, n, n_pad, d.k, ti, psi, nullptr, nullptr, nullptr);
+            acc = warp_sum_i64(acc);
+            value = (float)(d.psi_nk - ((double)acc / kFixScale) / (double)n);
+        } else if (measure == CC_MI_BINNED) {
+            const uint8_t* ba = d.bins_p + ra;
+            const uint8_t* bb = d.bins_p + rb;
+            for (int m = lane; m < n; m += 32) atomicAdd(&hist[ba[m] * B + bb[m]], 1);
+            __syncwarp();
+            long long s = 0;
+            for (int c = lane; c < B * B; c += 32) {
+                s += clogc[hist[c]];
+                hist[c] = 0;
+            }
+            s = warp_sum_i64(s);
+            value = (float)(log((double)n) + ((double)(s - d.hmarg[p] - d.hmarg[q]) / kFixScale) / n);
+        } else {
+            const float* A = (measure == CC_SPEARMAN ? d.rhat : d.zhat) + ra;
+            const float* Bp = (measure == CC_SPEARMAN ? d.rhat : d.zhat) + rb;
+            float acc = 0.f;
+            for (int m = lane; m < n_pad; m += 32) acc = fmaf(A[m], Bp[m], acc);
+            value = warp_sum_f32(acc);
+        }
+        if (lane == 0) d.vals[(int64_t)measure * per + t] = value;
+        __syncwarp();
+    }
+}
+
+// running extremes per (measure, region pair); index = (pa << 32) | pb
+__global__ void k_bos_extremes(BosDev d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * d.n_rp) return;
+    const int m = i / d.n_rp, rp = i % d.n_rp, per = d.n_rp * d.R;
+    Partial b = d.best[i];
+    if (*d.round == 0) {
+        b.max = -CUDART_INF_F;
+        b.min = CUDART_INF_F;
+        b.argmax = b.argmin = ~0ull;
+        b.count = 0;
+    }
+    for (int j = 0; j < d.R; ++j) {
+        const int t = rp * d.R + j;
+        const float v = d.vals[(int64_t)m * per + t];
+        const unsigned long long id = ((unsigned long long)d.pa[t] << 32) | d.pb[t];
+        if (v > b.max || (v == b.max && id < b.argmax)) {
+            b.max = v;
+            b.argmax = id;
+        }
+        if (v < b.min || (v == b.min && id < b.argmin)) {
+            b.min = v;
+            b.argmin = id;
+        }
+        b.count++;
+    }
+    d.best[i] = b;
+}
+
+// ---------------------------------------------------------------------------
+// condition: one CTA per region pair absorbs the round's R observations.
+__global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
+    extern __shared__ __align__(16) unsigned char cs[];
+    const int rp = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int r = *d.round, R = d.R, Q = d.Q, S = R * d.T;
+    const int s = r * R;
+    double* Lf = reinterpret_cast<double*>(cs);            // R x R (fp64 Cholesky)
+    float* G = reinterpret_cast<float*>(Lf + R * R);       // 32 rows x R of V[:, P]
+    float* covP = G + 32 * R;                              // R x R
+    float* L = covP + R * R;                               // R x R fp32 copy
+    float* gb = L + R * R;                        // R: V[:, P]^T beta
+    float* b2 = gb + R;                           // R: new beta
+    float* pp = b2 + R;                           // R x 6 pick positions
+    float* yv = pp + R * 6;                       // R
+    float* mP = yv + R;                           // R prior at picks
+    float* hyp = mP + R;                          // 4
+    const int* P = d.picks + rp * R;
+    const int per = d.n_rp * R;
+    float* Vr = d.V + (int64_t)rp * S * Q;
+    float* mu = d.mu + (int64_t)rp * Q;
+    float* var = d.var + (int64_t)rp * Q;
+    if (tid < R) {
+        yv[tid] = d.vals[(int64_t)d.objective * per + rp * R + tid];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) pp[tid * 6 + a] = d.pool[((int64_t)rp * Q + P[tid]) * 6 + a];
+    }
+    __syncthreads();
+    if (r == 0 && tid == 0) {
+        float m = 0.f, v = 0.f;
+        for (int j = 0; j < R; ++j) m += yv[j];
+        m /= R;
+        for (int j = 0; j < R; ++j) v += (yv[j] - m) * (yv[j] - m);
+        v = fmaxf(v / R, 1e-12f);
+        d.hyp[rp * 4 + 0] = m;
+        d.hyp[rp * 4 + 1] = v;
+        d.hyp[rp * 4 + 2] = 1e-4f * v;
+    }
+    __syncthreads();
+    if (tid < 4) hyp[tid] = d.hyp[rp * 4 + tid];
+    __syncthreads();
+    const float m0 = hyp[0], sf2 = hyp[1], sn2 = hyp[2];
+    if (r == 0) {
+        for (int c = tid; c < Q; c += blockDim.x) {
+            mu[c] = d.prior ? d.prior[(int64_t)rp * Q + c] : m0;
+            var[c] = sf2;
+        }
+    }
+    if (tid < R) mP[tid] = d.prior ? d.prior[(int64_t)rp * Q + P[tid]] : m0;
+    float inv_ell[6];
+    inv_ell_of(d, rp, inv_ell);
+    // covP = V[:, P]^T V[:, P] and gb = V[:, P]^T beta over the s old rows
+    float cacc[4] = {0.f, 0.f, 0.f, 0.f};  // entries tid, tid+256, ... of R x R
+    float gacc = 0.f;
+    for (int t0 = 0; t0 < s; t0 += 32) {
+        for (int e = tid; e < 32 * R; e += blockDim.x) {
+            const int t = t0 + e / R, j = e % R;
+            G[e] = t < s ? Vr[(int64_t)t * Q + P[j]] : 0.f;
+        }
+        __syncthreads();
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * blockDim.x;
+            if (e < R * R) {
+                const int i = e / R, j = e % R;
+                float a = cacc[q];
+                for (int t = 0; t < 32; ++t) a = fmaf(G[t * R + i], G[t * R + j], a);
+                cacc[q] = a;
+            }
+        }
+        if (tid < R)
+            for (int t = 0; t < 32 && t0 + t < s; ++t)
+                gacc = fmaf(G[t * R + tid], d.beta[(int64_t)rp * S + t0 + t], gacc);
+        __syncthreads();
+    }
+    for (int q = 0; q < 4; ++q) {
+        const int e = tid + q * blockDim.x;
+        if (e < R * R) {
+            const int i = e / R, j = e % R;
+            covP[e] = matern52(pp + i * 6, pp + j * 6, inv_ell, sf2) - cacc[q] + (i == j ? sn2 : 0.f);
+        }
+    }
+    if (tid < R) gb[tid] = gacc;
+    __syncthreads();
+    // Cholesky of covP (fp64, warp 0: lane = row)
+    if (tid < 32) {
+        for (int j = 0; j < R; ++j) {
+            if (lane == j) {
+                double sum = covP[j * R + j];
+                for (int q = 0; q < j; ++q) sum -= Lf[j * R + q] * Lf[j * R + q];
+                Lf[j * R + j] = sqrt(fmax(sum, 1e-12 * (double)sf2));
+            }
+            __syncwarp();
+            if (lane > j && lane < R) {
+                double sum = covP[lane * R + j];
+                for (int q = 0; q < j; ++q) sum -= Lf[lane * R + q] * Lf[j * R + q];
+                Lf[lane * R + j] = sum / Lf[j * R + j];
+            }
+            __syncwarp();
+        }
+        for (int e = lane; e < R * R; e += 32) {
+            const int i = e / R, j = e % R;
+            L[e] = j <= i ? (float)Lf[e] : 0.f;
+        }
+        __syncwarp();
+        if (lane == 0) {  // beta2 = L22^-1 (y - m_P - V[:, P]^T beta1)
+            for (int i = 0; i < R; ++i) {
+                double v = (double)yv[i] - mP[i] - gb[i];
+                for (int q = 0; q < i; ++q) v -= Lf[i * R + q] * (double)b2[q];
+                b2[i] = (float)(v / Lf[i * R + i]);
+            }
+        }
+    }
+    __syncthreads();
+    // new rows: V2 = L22^-1 (K(P, pool) - V[:, P]^T V), then mu, var updates
+    for (int c0 = 0; c0 < Q; c0 += blockDim.x) {
+        const int c = c0 + tid;
+        float w[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) w[i] = 0.f;
+        for (int t0 = 0; t0 < s; t0 += 32) {
+            __syncthreads();
+            for (int e = tid; e < 32 * R; e += blockDim.x) {
+                const int t = t0 + e / R, j = e % R;
+                G[e] = t < s ? Vr[(int64_t)t * Q + P[j]] : 0.f;
+            }
+            __syncthreads();
+            if (c < Q) {
+                for (int t = 0; t < 32 && t0 + t < s; ++t) {
+                    const float v = Vr[(int64_t)(t0 + t) * Q + c];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i < R) w[i] = fmaf(G[t * R + i], v, w[i]);
+                }
+            }
+        }
+        if (c < Q) {
+            const float* pc = d.pool + ((int64_t)rp * Q + c) * 6;
+            float pcl[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) pcl[a] = pc[a];
+            float dv = 0.f, dm = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (i < R) {
+                    float x = matern52(pp + i * 6, pcl, inv_ell, sf2) - w[i];
+                    for (int q = 0; q < i; ++q) x = fmaf(-L[i * R + q], w[q], x);
+                    x /= L[i * R + i];
+                    w[i] = x;
+                    Vr[(int64_t)(s + i) * Q + c] = x;
+                    dv = fmaf(x, x, dv);
+                    dm = fmaf(x, b2[i], dm);
+                }
+            }
+            var[c] -= dv;
+            mu[c] += dm;
+        }
+    }
+    if (tid < R) {
+        d.obs[(int64_t)rp * S + s + tid] = P[tid];
+        d.y[(int64_t)rp * S + s + tid] = yv[tid];
+        d.beta[(int64_t)rp * S + s + tid] = b2[tid];
+    }
+}
+
+__global__ void k_bos_advance(BosDev d) {
+    *d.round += 1;
+    *d.queue = 0;
+}
+
+}  // namespace cc
+
+// ============================================================================
+// host side
+using namespace cc;
+
+struct cc_bos {
+    BosDev d{};
+    int field = -1;
+    uint64_t field_version = ~0ull;
+    DevMem box, self, pool, V, mu, var, sel, obs, y, beta, hyp, prior, picks, pa, pb, vals, best,
+        counters;
+    int eval_warps = 8, eval_blocks_per_sm = 4;
+    bool tuned = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rounds_done = 0;
+    std::vector<int32_t> rp_a, rp_b;
+};
+
+namespace {
+
+cc_status bfail(cc_ctx* c, cc_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define BK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t _e = (call);                                                             \
+        if (_e != cudaSuccess) {                                                             \
+            cudaGetLastError();                                                              \
+            return bfail(ctx, _e == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA,    \
+                         "%s: %s", #call, cudaGetErrorString(_e));                           \
+        }                                                                                    \
+    } while (0)
+
+size_t propose_smem(const BosDev& d) {
+    const int M = d.M;
+    return (size_t)d.Q * 8 + M * 4 + (size_t)M * M * 4 + M * 6 * 4 + M * 4 + 8 * M * 4 + 32 * 8;
+}
+size_t condition_smem(const BosDev& d) {
+    const int R = d.R;
+    return 32 * R * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 + R * 6 * 4 + 2 * R * 4 + 16;
+}
+size_t eval_smem(const BosDev& d, int warps) {
+    const int pl = (d.n + 2) & ~1;
+    return 2 * pl * 8 + (size_t)warps * (ksg_slot_bytes(d.n_pad) + 256 * 4);
+}
+
+// set_attr: raise the kernel's dynamic shared-memory limit first (not while
+// a stream is being captured; the autotuner sets it for the largest shape).
+template <int KMAX>
+cudaError_t eval_launch(const BosDev& d, int warps, int blocks, bool set_attr, cudaStream_t st) {
+    const size_t smem = eval_smem(d, warps);
+    if (set_attr) {
+        cudaError_t e = cudaFuncSetAttribute(
+            k_bos_eval<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    note_launch();
+    k_bos_eval<KMAX><<<blocks, warps * 32, smem, st>>>(d, warps);
+    return cudaGetLastError();
+}
+
+template <int KMAX>
+cudaError_t eval_attr(const BosDev& d, int warps) {
+    return cudaFuncSetAttribute(k_bos_eval<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)eval_smem(d, warps));
+}
+
+cudaError_t set_eval_attr(const BosDev& d, int warps) {
+    const int k = d.k;
+    if (k <= 1) return eval_attr<1>(d, warps);
+    if (k == 2) return eval_attr<2>(d, warps);
+    if (k == 3) return eval_attr<3>(d, warps);
+    if (k <= 4) return eval_attr<4>(d, warps);
+    if (k <= 8) return eval_attr<8>(d, warps);
+    if (k <= 10) return eval_attr<10>(d, warps);
+    if (k <= 16) return eval_attr<16>(d, warps);
+    return eval_attr<32>(d, warps);
+}
+
+cudaError_t launch_eval(const BosDev& d, int warps, int blocks, bool set_attr, cudaStream_t st) {
+    const int k = d.k;
+    if (k <= 1) return eval_launch<1>(d, warps, blocks, set_attr, st);
+    if (k == 2) return eval_launch<2>(d, warps, blocks, set_attr, st);
+    if (k == 3) return eval_launch<3>(d, warps, blocks, set_attr, st);
+    if (k <= 4) return eval_launch<4>(d, warps, blocks, set_attr, st);
+    if (k <= 8) return eval_launch<8>(d, warps, blocks, set_attr, st);
+    if (k <= 10) return eval_launch<10>(d, warps, blocks, set_attr, st);
+    if (k <= 16) return eval_launch<16>(d, warps, blocks, set_attr, st);
+    return eval_launch<32>(d, warps, blocks, set_attr, st);
+}
+
+int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// One round, queued on st (also the body of the captured graph).
+cudaError_t enqueue_round(cc_bos* b, cudaStream_t st) {
+    const BosDev& d = b->d;
+    cudaError_t e;
+    note_launch();
+    k_bos_propose<<<d.n_rp, kBosThreads, propose_smem(d), st>>>(d);
+    if ((e = cudaGetLastError())) return e;
+    note_launch();
+    k_bos_round_pairs<<<(d.n_rp * d.R + 255) / 256, 256, 0, st>>>(d);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_eval(d, b->eval_warps, sm_count() * b->eval_blocks_per_sm, false, st)))
+        return e;
+    note_launch();
+    k_bos_extremes<<<(4 * d.n_rp + 255) / 256, 256, 0, st>>>(d);
+    if ((e = cudaGetLastError())) return e;
+    note_launch();
+    k_bos_condition<<<d.n_rp, kBosThreads, condition_smem(d), st>>>(d);
+    if ((e = cudaGetLastError())) return e;
+    note_launch();
+    k_bos_advance<<<1, 1, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+// Autotuner cache: "device|n|n_rp|R|k -> warps blocks_per_sm", in memory and,
+// when CCORR_AUTOTUNE_CACHE names a file, as JSON lines there.
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, std::pair<int, int>>> g_tune;
+
+std::string tune_key(const BosDev& d) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    std::ostringstream os;
+    os << prop.name << "|n=" << d.n << "|rp=" << d.n_rp << "|R=" << d.R << "|k=" << d.k;
+    return os.str();
+}
+
+bool tune_lookup(const std::string& key, int* w, int* b) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto& kv : g_tune)
+        if (kv.first == key) {
+            *w = kv.second.first;
+            *b = kv.second.second;
+            return true;
+        }
+    const char* path = getenv("CCORR_AUTOTUNE_CACHE");
+    if (!path) return false;
+    std::ifstream in(path);
+    std::string line;
+    while (std::getline(in, line)) {
+        const std::string tag = "{\"key\": \"" + key + "\", ";
+        if (line.rfind(tag, 0) == 0) {
+            int ww = 0, bb = 0;
+            if (sscanf(line.c_str() + tag.size(), "\"warps\": %d, \"blocks_per_sm\": %d", &ww,
+                       &bb) == 2) {
+                g_tune.push_back({key, {ww, bb}});
+                *w = ww;
+                *b = bb;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+void tune_store(const std::string& key, int w, int b) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.push_back({key, {w, b}});
+    const char* path = getenv("CCORR_AUTOTUNE_CACHE");
+    if (!path) return;
+    std::ofstream out(path, std::ios::app);
+    out << "{\"key\": \"" << key << "\", \"warps\": " << w << ", \"blocks_per_sm\": " << b
+        << "}\n";
+}
+
+}  // namespace
+
+extern "C" {
+
+cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, const int32_t* rp_b,
+                        int n_rp, const cc_bos_params* prm, cc_bos** out) {
+    if (!ctx) return CC_ERR_INVALID_ARG;
+    if (!rp_a || !rp_b || !prm || !out || n_rp < 1)
+        return bfail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    if (field_id < 0 || field_id >= (int)ctx->fields.size() || !ctx->fields[field_id])
+        return bfail(ctx, CC_ERR_INVALID_ARG, "unknown field");
+    Field& f = *ctx->fields[field_id];
+    const int Q = prm->pool, R = prm->per_round, T = prm->rounds, M = prm->shortlist;
+    if (Q < 256 || Q > 8192 || (Q & (Q - 1)) || R < 1 || R > 32 || T < 1 ||
+        M < 16 || M > 128 || M % 16 || (int64_t)R * T + M > Q)
+        return bfail(ctx, CC_ERR_INVALID_ARG,
+                     "need pool a power of two in [256, 8192], 1 <= per_round <= 32, shortlist "
+                     "a multiple of 16 in [16, 128], per_round * rounds + shortlist <= pool");
+    if (prm->objective < CC_PEARSON || prm->objective > CC_MI_KSG)
+        return bfail(ctx, CC_ERR_INVALID_ARG, "unknown objective measure");
+    const int k = prm->k == -1 ? (3 * f.n + 99) / 100 : prm->k;
+    if (k < 1 || k > f.n - 1 || k > 32 || prm->bins < 2 || prm->bins > 16)
+        return bfail(ctx, CC_ERR_INVALID_ARG, "k in [1, min(n-1, 32)], bins in [2, 16]");
+    std::vector<int> box(12 * n_rp), self(n_rp);
+    for (int i = 0; i < n_rp; ++i) {
+        const int ids[2] = {rp_a[i], rp_b[i]};
+        for (int s = 0; s < 2; ++s) {
+            if (ids[s] < 0 || ids[s] >= (int)ctx->regions.size() || !ctx->regions[ids[s]] ||
+                ctx->regions[ids[s]]->field != field_id)
+                return bfail(ctx, CC_ERR_INVALID_ARG, "region pair %d: bad region", i);
+            const cc_box& bx = ctx->regions[ids[s]]->box;
+            int* o = &box[12 * i + 6 * s];
+            o[0] = bx.x0;
+            o[1] = bx.y0;
+            o[2] = bx.z0;
+            o[3] = bx.x1 - bx.x0;
+            o[4] = bx.y1 - bx.y0;
+            o[5] = bx.z1 - bx.z0;
+        }
+        self[i] = rp_a[i] == rp_b[i];
+        if (self[i] && box[12 * i + 3] * box[12 * i + 4] * box[12 * i + 5] < 2)
+            return bfail(ctx, CC_ERR_INVALID_ARG, "self pair needs two points");
+    }
+    cc_bos* b = new (std::nothrow) cc_bos();
+    if (!b) return CC_ERR_OOM;
+    std::unique_ptr<cc_bos> guard(b);
+    b->field = field_id;
+    b->rp_a.assign(rp_a, rp_a + n_rp);
+    b->rp_b.assign(rp_b, rp_b + n_rp);
+    BosDev& d = b->d;
+    d.n_rp = n_rp;
+    d.Q = Q;
+    d.R = R;
+    d.T = T;
+    d.M = M;
+    d.kappa = prm->kappa;
+    d.seed = prm->seed;
+    d.objective = prm->objective;
+    d.k = k;
+    d.bins = prm->bins;
+    d.n = f.n;
+    d.n_pad = f.n_pad;
+    d.X = f.X;
+    d.Y = f.Y;
+    const int64_t S = (int64_t)R * T;
+    BK(b->box.alloc(box.size() * 4));
+    BK(b->self.alloc(self.size() * 4));
+    BK(b->pool.alloc((size_t)n_rp * Q * 6 * 4));
+    BK(b->V.alloc((size_t)n_rp * S * Q * 4));
+    BK(b->mu.alloc((size_t)n_rp * Q * 4));
+    BK(b->var.alloc((size_t)n_rp * Q * 4));
+    BK(b->sel.alloc((size_t)n_rp * (Q / 32) * 4));
+    BK(b->obs.alloc((size_t)n_rp * S * 4));
+    BK(b->y.alloc((size_t)n_rp * S * 4));
+    BK(b->beta.alloc((size_t)n_rp * S * 4));
+    BK(b->hyp.alloc((size_t)n_rp * 4 * 4));
+    BK(b->picks.alloc((size_t)n_rp * R * 4));
+    BK(b->pa.alloc((size_t)n_rp * R * 4));
+    BK(b->pb.alloc((size_t)n_rp * R * 4));
+    BK(b->vals.alloc((size_t)4 * n_rp * R * 4));
+    BK(b->best.alloc((size_t)4 * n_rp * sizeof(Partial)));
+    BK(b->counters.alloc(16));
+    cudaStream_t st = ctx->stream;
+    BK(cudaMemcpyAsync(b->box.p, box.data(), box.size() * 4, cudaMemcpyHostToDevice, st));
+    BK(cudaMemcpyAsync(b->self.p, self.data(), self.size() * 4, cudaMemcpyHostToDevice, st));
+    BK(cudaMemsetAsync(b->sel.p, 0, b->sel.bytes, st));
+    BK(cudaMemsetAsync(b->counters.p, 0, 16, st));
+    BK(cudaMemsetAsync(b->beta.p, 0, b->beta.bytes, st));
+    d.box = b->box.as<int>();
+    d.self = b->self.as<int>();
+    d.pool = b->pool.as<float>();
+    d.V = b->V.as<float>();
+    d.mu = b->mu.as<float>();
+    d.var = b->var.as<float>();
+    d.sel = b->sel.as<unsigned>();
+    d.obs = b->obs.as<int>();
+    d.y = b->y.as<float>();
+    d.beta = b->beta.as<float>();
+    d.hyp = b->hyp.as<float>();
+    d.prior = nullptr;
+    d.picks = b->picks.as<int>();
+    d.pa = b->pa.as<uint32_t>();
+    d.pb = b->pb.as<uint32_t>();
+    d.vals = b->vals.as<float>();
+    d.best = b->best.as<Partial>();
+    d.round = b->counters.as<int>();
+    d.queue = b->counters.as<int>() + 1;
+    d.status = ctx->status.as<int>();
+    note_launch();
+    k_bos_pool<<<(unsigned)(((int64_t)n_rp * Q + 255) / 256), 256, 0, st>>>(d);
+    BK(cudaGetLastError());
+    BK(cudaFuncSetAttribute(k_bos_propose, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)propose_smem(d)));
+    BK(cudaFuncSetAttribute(k_bos_condition, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)condition_smem(d)));
+    BK(cudaStreamSynchronize(st));
+    *out = guard.release();
+    return CC_OK;
+}
+
+cc_status cc_bos_set_prior(cc_ctx* ctx, cc_bos* b, const float* prior, int prior_is_device) {
+    if (!ctx || !b) return CC_ERR_INVALID_ARG;
+    if (b->rounds_done > 0)
+        return bfail(ctx, CC_ERR_INVALID_ARG, "the prior must be set before the first round");
+    if (!prior) {
+        b->d.prior = nullptr;
+        return CC_OK;
+    }
+    const size_t bytes = (size_t)b->d.n_rp * b->d.Q * 4;
+    BK(b->prior.alloc(bytes));
+    BK(cudaMemcpyAsync(b->prior.p, prior, bytes,
+                       prior_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->stream));
+    b->d.prior = b->prior.as<float>();
+    if (b->exec) {  // the captured graph holds the old parameters
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
+    return CC_OK;
+}
+
+cc_status cc_bos_run(cc_ctx* ctx, cc_bos* b, int rounds, int use_graph) {
+    if (!ctx || !b || rounds < 0) return CC_ERR_INVALID_ARG;
+    if (b->rounds_done + rounds > b->d.T)
+        return bfail(ctx, CC_ERR_INVALID_ARG, "only %d rounds were provisioned", b->d.T);
+    Field& f = *ctx->fields[b->field];
+    // field planes (bins for the binned measure, tables) are bound at the first round
+    if (b->field_version != f.version) {
+        if (b->rounds_done > 0)
+            return bfail(ctx, CC_ERR_INVALID_ARG, "the field changed during sampling");
+        cc_params p{CC_MI_BINNED, b->d.k, b->d.bins, 0, 0};
+        // evaluate one in-range pair so the bins and tables of the field exist
+        uint32_t one = 0;
+        float tmp = 0.f;
+        cc_status s = cc_eval_pairs(ctx, b->field, b->field, &p, &one, &one, 1, 0, &tmp, 0);
+        if (s) return s;
+        p.measure = CC_MI_KSG;
+        if ((s = cc_eval_pairs(ctx, b->field, b->field, &p, &one, &one, 1, 0, &tmp, 0))) return s;
+        b->d.zhat = f.zhat.as<float>();
+        b->d.rhat = f.rhat.as<float>();
+        b->d.fvals = f.vals.as<float>();
+        b->d.sorted = f.sorted.as<float>();
+        b->d.perm = f.perm.as<uint16_t>();
+        b->d.bins_p = f.bins[b->d.bins]->as<uint8_t>();
+        b->d.hmarg = (const long long*)f.hmarg[b->d.bins]->as<int64_t>();
+        b->d.psi_fix = (const long long*)ctx->psi_fix[f.n]->as<int64_t>();
+        b->d.clogc_fix = (const long long*)ctx->clogc_fix[f.n]->as<int64_t>();
+        b->d.psi_nk = digamma_int_host(f.n) + digamma_int_host(b->d.k);
+        b->field_version = f.version;
+    }
+    cudaStream_t st = ctx->stream;
+    if (!b->tuned) {
+        const std::string key = tune_key(b->d);
+        int w = 8, bps = 4;
+        if (!tune_lookup(key, &w, &bps)) {
+            // time the evaluation on the first round's proposals for each shape
+            note_launch(2);
+            k_bos_propose<<<b->d.n_rp, kBosThreads, propose_smem(b->d), st>>>(b->d);
+            k_bos_round_pairs<<<(b->d.n_rp * b->d.R + 255) / 256, 256, 0, st>>>(b->d);
+            BK(cudaGetLastError());
+            float best_ms = 1e30f;
+            cudaEvent_t e0, e1;
+            BK(cudaEventCreate(&e0));
+            BK(cudaEventCreate(&e1));
+            const int shapes[6][2] = {{4, 4}, {4, 8}, {8, 2}, {8, 4}, {16, 1}, {16, 2}};
+            for (auto& sh : shapes) {
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    BK(cudaMemsetAsync(b->d.queue, 0, 4, st));
+                    BK(cudaEventRecord(e0, st));
+                    BK(launch_eval(b->d, sh[0], sm_count() * sh[1], true, st));
+                    BK(cudaEventRecord(e1, st));
+                    BK(cudaEventSynchronize(e1));
+                    BK(cudaEventElapsedTime(&ms, e0, e1));
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    w = sh[0];
+                    bps = sh[1];
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            BK(cudaMemsetAsync(b->d.queue, 0, 4, st));
+            tune_store(key, w, bps);
+        }
+        b->eval_warps = w;
+        b->eval_blocks_per_sm = bps;
+        BK(set_eval_attr(b->d, w));
+        b->tuned = true;
+    }
+    for (int r = 0; r < rounds; ++r) {
+        if (use_graph) {
+            if (!b->exec) {
+                BK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = enqueue_round(b, st);
+                cudaGraph_t g = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(st, &g);
+                if (e != cudaSuccess || e2 != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    cudaGetLastError();
+                    return bfail(ctx, CC_ERR_CUDA, "graph capture failed: %s",
+                                 cudaGetErrorString(e ? e : e2));
+                }
+                b->graph = g;
+                BK(cudaGraphInstantiate(&b->exec, g, 0));
+            }
+            note_launch(6);
+            BK(cudaGraphLaunch(b->exec, st));
+        } else {
+            BK(enqueue_round(b, st));
+        }
+        b->rounds_done++;
+    }
+    return CC_OK;
+}
+
+cc_status cc_bos_results(cc_ctx* ctx, cc_bos* b, cc_rp_result* out) {
+    if (!ctx || !b || !out) return CC_ERR_INVALID_ARG;
+    std::vector<Partial> h(4 * (size_t)b->d.n_rp);
+    BK(cudaMemcpyAsync(h.data(), b->best.p, h.size() * sizeof(Partial), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    BK(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < h.size(); ++i)
+        out[i] = cc_rp_result{h[i].max, h[i].min, h[i].argmax, h[i].argmin, h[i].count};
+    return CC_OK;
+}
+
+cc_status cc_bos_inspect(cc_ctx* ctx, cc_bos* b, int rp, float* pool, float* mu, float* var,
+                         int32_t* obs, float* y, uint32_t* pa, uint32_t* pb, float* vals,
+                         int32_t* n_obs) {
+    if (!ctx || !b || rp < 0 || rp >= b->d.n_rp) return CC_ERR_INVALID_ARG;
+    const BosDev& d = b->d;
+    const int64_t S = (int64_t)d.R * d.T, s = (int64_t)b->rounds_done * d.R;
+    cudaStream_t st = ctx->stream;
+    if (pool) BK(cudaMemcpyAsync(pool, d.pool + (int64_t)rp * d.Q * 6, d.Q * 24, cudaMemcpyDeviceToHost, st));
+    if (mu) BK(cudaMemcpyAsync(mu, d.mu + (int64_t)rp * d.Q, d.Q * 4, cudaMemcpyDeviceToHost, st));
+    if (var) BK(cudaMemcpyAsync(var, d.var + (int64_t)rp * d.Q, d.Q * 4, cudaMemcpyDeviceToHost, st));
+    if (obs && s) BK(cudaMemcpyAsync(obs, d.obs + rp * S, s * 4, cudaMemcpyDeviceToHost, st));
+    if (y && s) BK(cudaMemcpyAsync(y, d.y + rp * S, s * 4, cudaMemcpyDeviceToHost, st));
+    if (pa) BK(cudaMemcpyAsync(pa, d.pa + rp * d.R, d.R * 4, cudaMemcpyDeviceToHost, st));
+    if (pb) BK(cudaMemcpyAsync(pb, d.pb + rp * d.R, d.R * 4, cudaMemcpyDeviceToHost, st));
+    if (vals)
+        for (int m = 0; m < 4; ++m)
+            BK(cudaMemcpyAsync(vals + m * d.R, d.vals + (int64_t)m * d.n_rp * d.R + rp * d.R,
+                               d.R * 4, cudaMemcpyDeviceToHost, st));
+    if (n_obs) *n_obs = (int32_t)s;
+    BK(cudaStreamSynchronize(st));
+    return CC_OK;
+}
+
+cc_status cc_bos_destroy(cc_ctx* ctx, cc_bos* b) {
+    if (!b) return CC_ERR_INVALID_ARG;
+    if (ctx) cudaStreamSynchronize(ctx->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+    return CC_OK;
+}
+
+}  // extern "C"

@@ -29,6 +29,31 @@ __device__ __forceinline__ float warp_sum_f32(float v) {
     return v;
 }
 
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC 2011) from its published
+// definition: 10 rounds of two 64x64->128 multiplies with the Weyl key
+// schedule. c: counter in, output block out.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t lo0 = 0xD2E7470EE14C6C93ull * c[0];
+        const uint64_t hi0 = __umul64hi(0xD2E7470EE14C6C93ull, c[0]);
+        const uint64_t lo1 = 0xCA5A826395121157ull * c[2];
+        const uint64_t hi1 = __umul64hi(0xCA5A826395121157ull, c[2]);
+        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B97F4A7C15ull;
+        k1 += 0xBB67AE8584CAA73Bull;
+    }
+}
+
+// Uniform [0, 1) with 24 random bits (exact in fp32): top 24 bits of a word.
+__device__ __forceinline__ float u24(uint64_t w) {
+    return (float)(unsigned)(w >> 40) * 5.9604644775390625e-8f;
+}
+
 // (value, index) extremes with the smallest index winning ties.
 struct Ext {
     float vmax, vmin;

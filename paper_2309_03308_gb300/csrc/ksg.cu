@@ -7,12 +7,13 @@
 //   n_x,i = 1 + #{j != i : |x_i - x_j| < eps_i}, n_y,i likewise
 //   MI    = psi(n) + psi(k) - (1/n) sum_i [psi(n_x,i) + psi(n_y,i)]
 //
-// Design (one warp per group of up to 4 pairs, one lane per sample i):
+// Design (one warp per group of pairs, one lane per sample i; the device
+// steps are in ksg_dev.cuh):
 //   For each pair the warp stages (x, y) in x-sorted order, (y, x) in
 //   y-sorted order and each sample's y-sorted position in shared memory; the
 //   per-point sorted values and argsorts come from ingest, so staging is
 //   gathers only. The samples of the group's pairs form one stream that the
-//   lanes take 32 at a time, so no lane idles at the end of a pair.
+//   lanes take 32 at a time, so fewer lanes idle at the end of a pair.
 //
 //   eps_i: walk outward from i along ONE axis in non-decreasing axis distance
 //   (two pointers over that axis's sorted order); every visited j offers d_ij.
@@ -33,97 +34,15 @@
 //
 //   The digamma sum uses a fixed-point table (2^-40), exact and order
 //   independent; psi(n) + psi(k) and the final scaling are FP64.
-#include "device.cuh"
 #include "internal.cuh"
+#include "ksg_dev.cuh"
 
 namespace cc {
 
 double digamma_int_host(int m);
 
-// KMAX >= k: the list holds KMAX - k copies of -inf below the k real entries,
-// so its last entry is always the k-th smallest seen.
-template <int KMAX>
-__device__ __forceinline__ void topk_insert(float (&top)[KMAX], float d) {
-#pragma unroll
-    for (int m = KMAX - 1; m > 0; --m) top[m] = fminf(top[m], fmaxf(top[m - 1], d));
-    top[0] = fminf(top[0], d);
-}
-
-// ascending odd-even transposition sort of a register array
-template <int KMAX>
-__device__ __forceinline__ void sort_net(float (&t)[KMAX]) {
-#pragma unroll
-    for (int r = 0; r < KMAX; ++r) {
-#pragma unroll
-        for (int i = r & 1; i + 1 < KMAX; i += 2) {
-            const float a = t[i], b = t[i + 1];
-            t[i] = fminf(a, b);
-            t[i + 1] = fmaxf(a, b);
-        }
-    }
-}
-
-// first index j in [lo, hi) with pred(j) true (pred monotone false -> true)
-template <class Pred>
-__device__ __forceinline__ int lower_search(int lo, int hi, Pred pred) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (pred(mid)) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
-}
-
 constexpr int kKsgWarps = 4;
 constexpr int kMaxGroup = 4;
-
-__host__ __device__ constexpr size_t ksg_slot_bytes(int n_pad) {
-    return (size_t)n_pad * (2 * sizeof(float2) + 2 * sizeof(uint16_t));
-}
-
-// One walk along sorted pairs W (walk value, other value) from position s.
-// State: L / R = next unvisited positions on each side, dL / dR their axis
-// distances (inf when exhausted), cL / cR their entries.
-struct Walk {
-    const float2* W;
-    int n, L, R;
-    float pv, ov, dL, dR;
-    float2 cL, cR;
-    __device__ __forceinline__ void init(const float2* w, int n_, int s, float p, float o) {
-        W = w;
-        n = n_;
-        pv = p;
-        ov = o;
-        L = s - 1;
-        R = s + 1;
-        cL = W[L >= 0 ? L : s];
-        cR = W[R < n ? R : s];
-        dL = L >= 0 ? __fsub_rn(pv, cL.x) : CUDART_INF_F;
-        dR = R < n ? __fsub_rn(cR.x, pv) : CUDART_INF_F;
-    }
-    __device__ __forceinline__ float next_axis() const { return fminf(dL, dR); }
-    // visit the nearer side's candidate; returns its Chebyshev distance
-    __device__ __forceinline__ float step() {
-        const bool right = dR < dL;
-        const float da = right ? dR : dL;
-        const float oj = right ? cR.y : cL.y;
-        const float d = fmaxf(da, fabsf(__fsub_rn(ov, oj)));
-        const int np = right ? R + 1 : L - 1;
-        const bool inb = right ? np < n : np >= 0;
-        const float2 c = W[inb ? np : (right ? R : L)];
-        const float nd = !inb ? CUDART_INF_F : (right ? __fsub_rn(c.x, pv) : __fsub_rn(pv, c.x));
-        if (right) {
-            R = np;
-            dR = nd;
-            cR = c;
-        } else {
-            L = np;
-            dL = nd;
-            cL = c;
-        }
-        return d;
-    }
-};
 
 template <int KMAX>
 __global__ void __launch_bounds__(kKsgWarps * 32)
@@ -159,25 +78,10 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
                 continue;
             }
             valid |= 1u << sl;
-            unsigned char* b = wbase + sl * slot_bytes;
-            float2* XO = reinterpret_cast<float2*>(b);
-            float2* YO = XO + n_pad;
-            uint16_t* upos = reinterpret_cast<uint16_t*>(YO + n_pad);
-            uint16_t* invq = upos + n_pad;
             const int64_t ra = (int64_t)p * n_pad, rb = (int64_t)q * n_pad;
-            for (int m = lane; m < n; m += 32) {
-                const int mq = perm_b[rb + m];
-                invq[mq] = (uint16_t)m;
-                YO[m] = make_float2(sorted_b[rb + m], vals_a[ra + mq]);
-            }
-            __syncwarp();
-            for (int m = lane; m < n; m += 32) {
-                const int mp = perm_a[ra + m];
-                XO[m] = make_float2(sorted_a[ra + m], vals_b[rb + mp]);
-                upos[m] = invq[mp];
-            }
+            ksg_stage(wbase + sl * slot_bytes, n, n_pad, sorted_a + ra, perm_a + ra, vals_a + ra,
+                      sorted_b + rb, perm_b + rb, vals_b + rb);
         }
-        __syncwarp();
 
         long long acc[kMaxGroup];
 #pragma unroll
@@ -186,47 +90,10 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
         for (int it = lane; it < items; it += 32) {
             const int sl = it / n, ti = it - sl * n;
             if (!((valid >> sl) & 1u)) continue;
-            unsigned char* b = wbase + sl * slot_bytes;
-            const float2* XO = reinterpret_cast<const float2*>(b);
-            const float2* YO = XO + n_pad;
-            const uint16_t* upos = reinterpret_cast<const uint16_t*>(YO + n_pad);
-            const float2 zi = XO[ti];
-            const int ui = upos[ti];
-            // walk along the axis with the wider local spacing
-            const int h = 4;
-            const float span_x = __fsub_rn(XO[min(ti + h, n - 1)].x, XO[max(ti - h, 0)].x);
-            const float span_y = __fsub_rn(YO[min(ui + h, n - 1)].x, YO[max(ui - h, 0)].x);
-            const bool on_y = span_y > span_x;
-            const float2* O = on_y ? XO : YO;  // other axis order (sorted in .x)
-            const int s = on_y ? ui : ti;
-            Walk w;
-            w.init(on_y ? YO : XO, n, s, on_y ? zi.y : zi.x, on_y ? zi.x : zi.y);
-
-            float top[KMAX];
-#pragma unroll
-            for (int m = 0; m < KMAX; ++m)
-                top[m] = m >= KMAX - k ? w.step() : -CUDART_INF_F;  // the k axis-nearest
-            sort_net<KMAX>(top);
-            while (w.next_axis() < top[KMAX - 1]) {
-                const float d = w.step();
-                if (d < top[KMAX - 1]) topk_insert<KMAX>(top, d);
-            }
-            const float eps = top[KMAX - 1];
-            const float pv = w.pv, ov = w.ov;
-            int L = w.L, R = w.R;
-            // walk axis: trim the visited window (L, R) to axis distance < eps
-            while (L + 1 < s && !(__fsub_rn(pv, w.W[L + 1].x) < eps)) ++L;
-            while (R - 1 > s && !(__fsub_rn(w.W[R - 1].x, pv) < eps)) --R;
-            const int c_walk = eps > 0.f ? R - L - 1 : 1;
-            // other axis: [a, b) with a = first j with fl(ov - O[j].x) < eps,
-            // b = first j with fl(O[j].x - ov) >= eps
-            const int a = lower_search(0, n, [&](int j) { return __fsub_rn(ov, O[j].x) < eps; });
-            const int bb =
-                lower_search(0, n, [&](int j) { return !(__fsub_rn(O[j].x, ov) < eps); });
-            const int c_oth = max(bb - a, 1);
-            const int cx = on_y ? c_oth : c_walk;
-            const int cy = on_y ? c_walk : c_oth;
-            const long long v = psi[cx] + psi[cy];
+            int cx, cy;
+            float eps;
+            const long long v = ksg_sample<KMAX>(wbase + sl * slot_bytes, n, n_pad, k, ti, psi,
+                                                 nx_out ? &cx : nullptr, &cy, &eps);
 #pragma unroll
             for (int u = 0; u < kMaxGroup; ++u)
                 if (u == sl) acc[u] += v;
@@ -290,7 +157,7 @@ cudaError_t launch_ksg_pairs(const Field& fa, const Field& fb, int k, const int6
     if (k <= 1) CC_KSG(1);
     if (k == 2) CC_KSG(2);
     if (k == 3) CC_KSG(3);
-    if (k == 4) CC_KSG(4);
+    if (k <= 4) CC_KSG(4);
     if (k <= 8) CC_KSG(8);
     if (k <= 10) CC_KSG(10);
     if (k <= 16) CC_KSG(16);

@@ -138,26 +138,7 @@ cudaError_t launch_hist_pairs(const uint8_t* bins_a, const int64_t* hm_a, int64_
 }
 
 // ----------------------------------------------------------------------------
-// Uniform pair sampler (Section 3.1). Philox4x64-10 (Salmon, Moraes, Dror,
-// Shaw, SC 2011) from its published definition: 10 rounds of two 64x64->128
-// multiplies with the Weyl key schedule.
-__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t lo0 = 0xD2E7470EE14C6C93ull * c[0];
-        const uint64_t hi0 = __umul64hi(0xD2E7470EE14C6C93ull, c[0]);
-        const uint64_t lo1 = 0xCA5A826395121157ull * c[2];
-        const uint64_t hi1 = __umul64hi(0xCA5A826395121157ull, c[2]);
-        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0;
-        c[1] = lo1;
-        c[2] = n2;
-        c[3] = lo0;
-        k0 += 0x9E3779B97F4A7C15ull;
-        k1 += 0xBB67AE8584CAA73Bull;
-    }
-}
-
+// Uniform pair sampler (Section 3.1) on Philox4x64-10 (device.cuh).
 __global__ void k_sample_pairs(const uint32_t* __restrict__ pts_a, int64_t na,
                                const uint32_t* __restrict__ pts_b, int64_t nb, int self,
                                uint64_t seed, uint64_t sstream, uint64_t first, int64_t N,
