@@ -379,6 +379,77 @@ cc_status cc_bos_inspect(cc_ctx* ctx, cc_bos* bos, int rp, float* pool, float* m
 /* Release the sampling state. */
 cc_status cc_bos_destroy(cc_ctx* ctx, cc_bos* bos);
 
+/* ------------------------------------------------------------- learned surrogate */
+
+/*
+ * A small pairwise network that predicts a measure (e.g. KSG MI) from two
+ * points' member vectors, the network the paper's Section 7 proposes as
+ * future work. Used as the BOS prior mean (cc_bos_set_prior) and to screen all
+ * pairs of a region pair; exact evaluation stays the judge of every maximum.
+ *   encoder  z (n) -> h1 = GELU(W1 z + b1) (128) -> e = W2 h1 + b2 (64)
+ *   head     x = [e_i, e_j, |e_i - e_j|, off] (195) -> h3 = GELU(W3 x + b3)
+ *            (128) -> y = w4 . h3 + b4, prediction = y * sd + mean
+ * z = (v - mean) / sample std of the point's members; off = (position_j -
+ * position_i) / (X, Y, Z); GELU = 0.5 x (1 + erf(x / sqrt 2)). Parameters are
+ * one flat fp32 vector: W1 (128 x n, row-major), b1, W2 (64 x 128), b2,
+ * W3 (128 x 195), b3, w4 (128), b4 -- 46,401 values for n = 100. Training:
+ * MSE on targets standardized by their mean and sd, Adam (beta 0.9 / 0.999,
+ * eps 1e-8) on fp32 master weights, BF16 weights and activations in every
+ * contraction with fp32 accumulation, each pair's order swapped with
+ * probability 1/2.
+ */
+typedef struct cc_sur cc_sur;
+
+/* New surrogate for n-member fields with seeded N(0, 1/fan_in) weights. */
+cc_status cc_sur_create(cc_ctx* ctx, int n_members, uint64_t seed, cc_sur** out);
+
+/* Replace the parameters (host, flat layout above); resets the Adam state. */
+cc_status cc_sur_set_params(cc_ctx* ctx, cc_sur* sur, const float* params);
+
+/* Copy the parameters out (params may be NULL) and report count and target scale. */
+cc_status cc_sur_get_params(cc_ctx* ctx, cc_sur* sur, float* params, int64_t* n_params,
+                            float* target_mean, float* target_sd);
+
+/* Set the target standardization (mean, sd > 0) used by the loss and predictions. */
+cc_status cc_sur_set_target_scale(cc_ctx* ctx, cc_sur* sur, float mean, float sd);
+
+/*
+ * Loss (mean squared error on standardized targets) and its gradient (host,
+ * flat layout) for one batch of pairs of field_id, without swapping or
+ * updating. pa, pb, target, grad are host arrays.
+ */
+cc_status cc_sur_loss_grad(cc_ctx* ctx, cc_sur* sur, int32_t field_id, const uint32_t* pa,
+                           const uint32_t* pb, const float* target, int64_t n_pairs, float* loss,
+                           float* grad);
+
+/*
+ * Train for `epochs` epochs on pairs (pa[t], pb[t]) of field_id with target
+ * values target[t] (host or device, on_device); the target mean and sd of
+ * this set become the standardization. Mini-batches of `batch` pairs in a
+ * seeded random order per epoch, learning rate lr. epoch_loss (host, epochs
+ * entries, may be NULL) receives the mean standardized training loss.
+ */
+cc_status cc_sur_train(cc_ctx* ctx, cc_sur* sur, int32_t field_id, const uint32_t* pa,
+                       const uint32_t* pb, const float* target, int64_t n_pairs, int on_device,
+                       int epochs, int batch, float lr, uint64_t seed, float* epoch_loss);
+
+/* Predictions for a batch of point pairs of field_id (host or device arrays). */
+cc_status cc_sur_predict(cc_ctx* ctx, cc_sur* sur, int32_t field_id, const uint32_t* pa,
+                         const uint32_t* pb, int64_t n_pairs, int pairs_on_device, float* out,
+                         int out_on_device);
+
+/*
+ * Screen all pairs of two regions of one field: the topk (1..8192) largest
+ * predictions in descending order, with linear pair indices a * |B| + b (host
+ * arrays). Self region pairs consider a < b only. The head's first layer is
+ * split so each point's projections are computed once.
+ */
+cc_status cc_sur_screen(cc_ctx* ctx, cc_sur* sur, int32_t region_a, int32_t region_b, int topk,
+                        uint64_t* ids, float* preds);
+
+/* Release the surrogate. */
+cc_status cc_sur_destroy(cc_ctx* ctx, cc_sur* sur);
+
 /* ------------------------------------------------------------ allocation-free form */
 
 /*

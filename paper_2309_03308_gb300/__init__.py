@@ -272,6 +272,82 @@ class Bos:
             pass
 
 
+class Surrogate:
+    """cc_sur handle: the learned pairwise predictor (BF16 training/inference)."""
+
+    def __init__(self, ctx: Context, n_members: int, seed: int = 0):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._check(ctx.lib.cc_sur_create(ctx.h, n_members, seed, ctypes.byref(h)))
+        self.h = h
+
+    def params(self):
+        n = ctypes.c_int64()
+        m, s = ctypes.c_float(), ctypes.c_float()
+        self.ctx._check(self.ctx.lib.cc_sur_get_params(self.ctx.h, self.h, None, ctypes.byref(n),
+                                                       ctypes.byref(m), ctypes.byref(s)))
+        out = np.empty(n.value, np.float32)
+        self.ctx._check(self.ctx.lib.cc_sur_get_params(self.ctx.h, self.h, out.ctypes.data, None,
+                                                       None, None))
+        return out, m.value, s.value
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        self.ctx._check(self.ctx.lib.cc_sur_set_params(self.ctx.h, self.h, flat.ctypes.data))
+
+    def set_target_scale(self, mean: float, sd: float):
+        self.ctx._check(self.ctx.lib.cc_sur_set_target_scale(self.ctx.h, self.h, mean, sd))
+
+    def loss_grad(self, fid: int, pa, pb, target):
+        pa = np.ascontiguousarray(pa, np.uint32)
+        pb = np.ascontiguousarray(pb, np.uint32)
+        t = np.ascontiguousarray(target, np.float32)
+        grad = np.empty(self.params()[0].shape[0], np.float32)
+        loss = ctypes.c_float()
+        self.ctx._check(self.ctx.lib.cc_sur_loss_grad(self.ctx.h, self.h, fid, pa.ctypes.data,
+                                                      pb.ctypes.data, t.ctypes.data, len(pa),
+                                                      ctypes.byref(loss), grad.ctypes.data))
+        return loss.value, grad
+
+    def train(self, fid: int, pa, pb, target, epochs=1, batch=4096, lr=1e-3, seed=0):
+        a, dev = _ptr(pa)
+        b, _ = _ptr(pb)
+        t, _ = _ptr(target)
+        losses = np.empty(max(epochs, 1), np.float32)
+        self.ctx._check(self.ctx.lib.cc_sur_train(self.ctx.h, self.h, fid, a, b, t,
+                                                  int(pa.shape[0]), dev, epochs, batch, lr, seed,
+                                                  losses.ctypes.data))
+        return losses[:epochs]
+
+    def predict(self, fid: int, pa, pb, out=None):
+        a, pdev = _ptr(pa)
+        b, _ = _ptr(pb)
+        if out is None:
+            out = np.empty(int(pa.shape[0]), np.float32)
+        o, odev = _ptr(out)
+        self.ctx._check(self.ctx.lib.cc_sur_predict(self.ctx.h, self.h, fid, a, b,
+                                                    int(pa.shape[0]), pdev, o, odev))
+        return out
+
+    def screen(self, ra: int, rb: int, topk: int):
+        ids = np.empty(topk, np.uint64)
+        preds = np.empty(topk, np.float32)
+        self.ctx._check(self.ctx.lib.cc_sur_screen(self.ctx.h, self.h, ra, rb, topk,
+                                                   ids.ctypes.data, preds.ctypes.data))
+        return ids, preds
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.cc_sur_destroy(self.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def launch_count() -> int:
     """Kernels launched by libccorr.so in this process so far."""
     c = ctypes.c_uint64()

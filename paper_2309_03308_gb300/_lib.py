@@ -87,6 +87,17 @@ SIGNATURES = {
     "cc_bos_results": (_S, [_P, _P, _P]),
     "cc_bos_inspect": (_S, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I32)]),
     "cc_bos_destroy": (_S, [_P, _P]),
+    "cc_sur_create": (_S, [_P, _I, _U64, ctypes.POINTER(_P)]),
+    "cc_sur_set_params": (_S, [_P, _P, _P]),
+    "cc_sur_get_params": (_S, [_P, _P, _P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(ctypes.c_float)]),
+    "cc_sur_set_target_scale": (_S, [_P, _P, ctypes.c_float, ctypes.c_float]),
+    "cc_sur_loss_grad": (_S, [_P, _P, _I32, _P, _P, _P, _I64, ctypes.POINTER(ctypes.c_float),
+                              _P]),
+    "cc_sur_train": (_S, [_P, _P, _I32, _P, _P, _P, _I64, _I, _I, _I, ctypes.c_float, _U64, _P]),
+    "cc_sur_predict": (_S, [_P, _P, _I32, _P, _P, _I64, _I, _P, _I]),
+    "cc_sur_screen": (_S, [_P, _P, _I32, _I32, _I, _P, _P]),
+    "cc_sur_destroy": (_S, [_P, _P]),
     "cc_all_pairs_static": (_S, [_P, _I64, _P, _I64, _I, _I64, _I64, _I, _P, _I64, _P, _P]),
     "cc_launch_count": (_S, [ctypes.POINTER(_U64)]),
 }

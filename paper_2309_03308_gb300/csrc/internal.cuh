@@ -184,6 +184,9 @@ cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,
                             const uint32_t* sel_idx, const unsigned* count, unsigned cap,
                             float sign, int topk, float* out_vals, unsigned long long* out_ids,
                             cudaStream_t st);
+cudaError_t launch_sort_top_ids(const float* vals, const uint32_t* sel_idx, const unsigned* count,
+                                unsigned cap, int topk, float* out_vals,
+                                unsigned long long* out_ids, cudaStream_t st);
 cudaError_t launch_dot2_pairs(const float* A, int64_t Pa, const float* B, int64_t Pb, int n_pad,
                               int n, const uint32_t* pa, const uint32_t* pb, int64_t N, float* out,
                               int* status, cudaStream_t st);

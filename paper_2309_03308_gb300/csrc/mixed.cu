@@ -281,9 +281,9 @@ __global__ void __launch_bounds__(1024)
     for (int i = threadIdx.x; i < 8192; i += 1024) {
         if ((unsigned)i < count) {
             const uint32_t j = sel_idx[i];
-            key[i] = ((unsigned long long)okey(vals[j]) << 32) |
-                     (0xffffffffull - (pids[j] & 0xffffffffull));
-            pid[i] = pids[j];
+            const unsigned long long id = pids ? pids[j] : (unsigned long long)j;
+            key[i] = ((unsigned long long)okey(vals[j]) << 32) | (0xffffffffull - (id & 0xffffffffull));
+            pid[i] = id;
         } else {
             key[i] = 0;
             pid[i] = ~0ull;
@@ -394,6 +394,13 @@ cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,
     k_sort_top<<<1, 1024, smem, st>>>(vals, pids, sel_idx, count, cap, sign, topk, out_vals,
                                       out_ids);
     return cudaGetLastError();
+}
+
+// top-k of vals[sel_idx[i]] where the selected index is itself the id
+cudaError_t launch_sort_top_ids(const float* vals, const uint32_t* sel_idx, const unsigned* count,
+                                unsigned cap, int topk, float* out_vals,
+                                unsigned long long* out_ids, cudaStream_t st) {
+    return launch_sort_top(vals, nullptr, sel_idx, count, cap, 1.f, topk, out_vals, out_ids, st);
 }
 
 // 3c for a plain pair batch: Dot2 Pearson/Spearman (precision CC_FP32_DOT2).

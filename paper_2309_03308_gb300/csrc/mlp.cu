@@ -1,0 +1,854 @@
+// Learned pairwise surrogate (project addition; the paper's Section 7 names
+// a network predicting MI as future work): BF16 training and inference.
+//
+//   encoder  z (n) -> h1 = GELU(W1 z + b1) (128) -> e = W2 h1 + b2 (64)
+//   head     x = [e_i, e_j, |e_i - e_j|, off] (195) -> h3 = GELU(W3 x + b3)
+//            (128) -> y = w4 . h3 + b4
+// z = zhat * sqrt(n - 1) (the member vector's z-score), off = position
+// difference / field size, GELU in the erf form. MSE on standardized targets,
+// Adam (beta 0.9 / 0.999, eps 1e-8) on fp32 master weights; GEMM inputs are
+// BF16 (weights and activations) or fp32 (back-propagated gradients), all
+// accumulation fp32. Parameters are one flat fp32 vector: W1 (128 x n), b1,
+// W2 (64 x 128), b2, W3 (128 x 195), b3, w4 (128), b4.
+//
+// The all-pairs screen splits the head's first layer: W3 x = Wa e_i + Wb e_j
+// + Wc |e_i - e_j| + Wd off, with Wa e_i and Wb e_j computed once per point,
+// so a pair costs the 128 x 64 contraction of |e_i - e_j| plus 128 GELUs.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace cc {
+
+constexpr int kH1 = 128, kE = 64, kH3 = 128, kHeadIn = 3 * kE + 3;
+
+struct SurOff {
+    int64_t W1, b1, W2, b2, W3, b3, w4, b4, total;
+    explicit SurOff(int n) {
+        W1 = 0;
+        b1 = W1 + (int64_t)kH1 * n;
+        W2 = b1 + kH1;
+        b2 = W2 + (int64_t)kE * kH1;
+        W3 = b2 + kE;
+        b3 = W3 + (int64_t)kH3 * kHeadIn;
+        w4 = b3 + kH3;
+        b4 = w4 + kH3;
+        total = b4 + 1;
+    }
+};
+
+__device__ __forceinline__ float ld(const float* p) { return *p; }
+__device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ float gelu(float x) {
+    return 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) +
+           x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// ---------------------------------------------------------------------------
+// C[m][n] (+)= sum_k A(m, k) B(k, n); A(m, k) = A[m * sam + k * sak],
+// B(k, n) = B[k * sbk + n * sbn]; C row stride ldc. 64 x 64 tiles, 256
+// threads with 4 x 4 outputs, K staged 16 at a time through shared memory.
+template <class TA, class TB>
+__global__ void __launch_bounds__(256)
+    k_mm(const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
+         int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc, int M, int N, int K,
+         int accumulate) {
+    __shared__ float As[16][64 + 1];
+    __shared__ float Bs[16][64 + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int kk = e / 64, mm = e % 64;
+            const int m = m0 + mm, k = k0 + kk;
+            As[kk][mm] = (m < M && k < K) ? ld(A + m * sam + k * sak) : 0.f;
+            const int n = n0 + mm;
+            Bs[kk][mm] = (n < N && k < K) ? ld(B + k * sbk + n * sbn) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n >= N) continue;
+            float* c = C + (int64_t)m * ldc + n;
+            *c = accumulate ? *c + acc[i][j] : acc[i][j];
+        }
+    }
+}
+
+template <class TA, class TB>
+static cudaError_t mm(const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk, int64_t sbn,
+                      float* C, int64_t ldc, int M, int N, int K, int acc, cudaStream_t st) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    note_launch();
+    k_mm<TA, TB><<<grid, 256, 0, st>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, acc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// encoder inputs: row r of X0 = z-scores of point pts[r] (bf16)
+__global__ void k_sur_gather_z(const float* __restrict__ zhat, int n, int n_pad, float scale,
+                               const uint32_t* __restrict__ pts, int64_t rows,
+                               __nv_bfloat16* __restrict__ X0) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / n;
+        const int k = (int)(e % n);
+        X0[e] = __float2bfloat16_rn(zhat[(int64_t)pts[r] * n_pad + k] * scale);
+    }
+}
+
+// act = GELU(pre + bias) (bf16), pre keeps the pre-activation (fp32)
+__global__ void k_sur_bias_gelu(float* __restrict__ pre, const float* __restrict__ bias, int64_t rows,
+                                int cols, __nv_bfloat16* __restrict__ act) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float a = pre[e] + bias[e % cols];
+        pre[e] = a;
+        act[e] = __float2bfloat16_rn(gelu(a));
+    }
+}
+
+// head input x = [e_i, e_j, |e_i - e_j|, off]; encoder rows 0..B-1 hold i,
+// rows B..2B-1 hold j
+__global__ void k_sur_head_input(const float* __restrict__ Ef, const float* __restrict__ b2,
+                                 const uint32_t* __restrict__ pi, const uint32_t* __restrict__ pj,
+                                 int X, int Y, int Z, int64_t B, __nv_bfloat16* __restrict__ X3,
+                                 float* __restrict__ Eout) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < B * kHeadIn;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / kHeadIn;
+        const int c = (int)(e % kHeadIn);
+        float v;
+        if (c < 3 * kE) {
+            const int q = c % kE;
+            const float ei = Ef[b * kE + q] + b2[q];
+            const float ej = Ef[(B + b) * kE + q] + b2[q];
+            if (c < kE) {
+                v = ei;
+                Eout[b * kE + q] = ei;
+                Eout[(B + b) * kE + q] = ej;
+            } else {
+                v = c < 2 * kE ? ej : fabsf(ei - ej);
+            }
+        } else {
+            const int a = c - 3 * kE;
+            const int64_t p = pi[b], q = pj[b];
+            const int64_t dp = a == 0 ? (q % X) - (p % X)
+                               : a == 1 ? ((q / X) % Y) - ((p / X) % Y)
+                                        : (q / ((int64_t)X * Y)) - (p / ((int64_t)X * Y));
+            v = (float)dp / (float)(a == 0 ? X : a == 1 ? Y : Z);
+        }
+        X3[e] = __float2bfloat16_rn(v);
+    }
+}
+
+// y = w4 . h3 + b4; loss terms and dy = 2 (y - t) / B (one warp per row)
+__global__ void k_sur_out(const __nv_bfloat16* __restrict__ H3, const float* __restrict__ w4,
+                          const float* __restrict__ b4, const float* __restrict__ t, int64_t B,
+                          float tmean, float tinv, float* __restrict__ y, float* __restrict__ dy,
+                          double* __restrict__ loss) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B;
+         b += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        float s = 0.f;
+        for (int h = lane; h < kH3; h += 32) s = fmaf(__bfloat162float(H3[b * kH3 + h]), w4[h], s);
+        s = warp_sum_f32(s) + b4[0];
+        if (lane == 0) {
+            y[b] = s;
+            if (t) {
+                const float r = s - (t[b] - tmean) * tinv;
+                dy[b] = 2.f * r / (float)B;
+                atomicAdd(loss, (double)r * r);
+            }
+        }
+    }
+}
+
+// dA = (dy outer w4) * gelu'(pre)   (head) or dA = dH * gelu'(pre) (encoder)
+__global__ void k_sur_gelu_bwd(const float* __restrict__ pre, const float* __restrict__ dy,
+                               const float* __restrict__ w4, const float* __restrict__ dH,
+                               int64_t rows, int cols, float* __restrict__ dA) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float g = dH ? dH[e] : dy[e / cols] * w4[e % cols];
+        dA[e] = g * gelu_grad(pre[e]);
+    }
+}
+
+// column sums of a [rows][cols] fp32 matrix into out (one block per column)
+__global__ void k_sur_colsum(const float* __restrict__ A, int64_t rows, int cols,
+                             float* __restrict__ out) {
+    __shared__ float red[256];
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += A[r * cols + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+
+// dE rows from dX3: de_i = dx[:, 0:64] + dx[:, 128:192] sign(e_i - e_j),
+//                   de_j = dx[:, 64:128] - dx[:, 128:192] sign(e_i - e_j)
+__global__ void k_sur_split(const float* __restrict__ dX3, const float* __restrict__ E, int64_t B,
+                            float* __restrict__ dE) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < B * kE;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / kE;
+        const int q = (int)(e % kE);
+        const float d = E[b * kE + q] - E[(B + b) * kE + q];
+        const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+        const float dd = dX3[b * kHeadIn + 2 * kE + q] * sg;
+        dE[b * kE + q] = dX3[b * kHeadIn + q] + dd;
+        dE[(B + b) * kE + q] = dX3[b * kHeadIn + kE + q] - dd;
+    }
+}
+
+__global__ void k_sur_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                           float* __restrict__ v, int64_t P, float lr, float c1, float c2,
+                           __nv_bfloat16* __restrict__ wb) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+        w[i] = wi;
+        wb[i] = __float2bfloat16_rn(wi);
+    }
+}
+
+// o = o * a + b
+__global__ void k_sur_affine(float* __restrict__ o, int64_t n, float a, float b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = fmaf(o[i], a, b);
+}
+
+// rows of a [rows][cols] matrix += bias
+__global__ void k_sur_add_bias(float* __restrict__ A, const float* __restrict__ bias, int64_t rows,
+                               int cols) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols;
+         e += (int64_t)gridDim.x * blockDim.x)
+        A[e] += bias[e % cols];
+}
+
+__global__ void k_sur_cast(const float* __restrict__ w, int64_t P, __nv_bfloat16* __restrict__ wb) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+         i += (int64_t)gridDim.x * blockDim.x)
+        wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+// training batch: rows 0..B-1 = first points, B..2B-1 = second points; each
+// pair is swapped with probability 1/2 (Philox block {step, b, 7, 0})
+__global__ void k_sur_batch(const uint32_t* __restrict__ pa, const uint32_t* __restrict__ pb,
+                            const float* __restrict__ tgt, const int64_t* __restrict__ order,
+                            int64_t start, int64_t B, uint64_t seed, uint64_t step, int swap,
+                            uint32_t* __restrict__ pts, float* __restrict__ tb) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = order ? order[start + b] : start + b;
+        uint32_t x = pa[s], y = pb[s];
+        if (swap) {
+            uint64_t c[4] = {step, (uint64_t)b, 7, 0};
+            philox4x64_10(c, seed, 0x5ee9ull);
+            if (c[0] & 1) {
+                const uint32_t tmp = x;
+                x = y;
+                y = tmp;
+            }
+        }
+        pts[b] = x;
+        pts[B + b] = y;
+        tb[b] = tgt ? tgt[s] : 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// All-pairs screen: pred[a][b] = head(e_a, e_b) with U = Wa e + b3 and
+// Vb = Wb e precomputed per point (fp32). One CTA per 16 rows x 64 columns.
+constexpr int kScrI = 16, kScrJ = 64;
+
+__global__ void __launch_bounds__(256)
+    k_sur_screen(const float* __restrict__ Ea, const float* __restrict__ Ua,
+                 const float* __restrict__ Eb, const float* __restrict__ Vb,
+                 const float* __restrict__ w, int64_t oW3, int64_t ow4, int64_t ob4,
+                 const uint32_t* __restrict__ pts_a, const uint32_t* __restrict__ pts_b,
+                 int64_t na, int64_t nb, int self, int X, int Y, int Z, float tmean, float tsd,
+                 float* __restrict__ pred) {
+    extern __shared__ float sm[];
+    float* Wc = sm;                          // [128][64]
+    float* Wd = Wc + kH3 * kE;               // [128][3]
+    float* w4 = Wd + kH3 * 3;                // [128]
+    float* ea = w4 + kH3;                    // [16][64]
+    float* eb = ea + kScrI * kE;             // [64][64]
+    float* ua = eb + kScrJ * kE;             // [16][128]
+    float* vb = ua + kScrI * kH3;            // [64][128]
+    const int tid = threadIdx.x;
+    const int64_t a0 = (int64_t)blockIdx.y * kScrI, b0 = (int64_t)blockIdx.x * kScrJ;
+    for (int e = tid; e < kH3 * kE; e += 256) {
+        const int h = e / kE, q = e % kE;
+        Wc[e] = w[oW3 + (int64_t)h * kHeadIn + 2 * kE + q];
+    }
+    for (int e = tid; e < kH3 * 3; e += 256)
+        Wd[e] = w[oW3 + (int64_t)(e / 3) * kHeadIn + 3 * kE + e % 3];
+    for (int e = tid; e < kH3; e += 256) w4[e] = w[ow4 + e];
+    for (int e = tid; e < kScrI * kE; e += 256) {
+        const int64_t a = a0 + e / kE;
+        ea[e] = a < na ? Ea[a * kE + e % kE] : 0.f;
+    }
+    for (int e = tid; e < kScrJ * kE; e += 256) {
+        const int64_t b = b0 + e / kE;
+        eb[e] = b < nb ? Eb[b * kE + e % kE] : 0.f;
+    }
+    for (int e = tid; e < kScrI * kH3; e += 256) {
+        const int64_t a = a0 + e / kH3;
+        ua[e] = a < na ? Ua[a * kH3 + e % kH3] : 0.f;
+    }
+    for (int e = tid; e < kScrJ * kH3; e += 256) {
+        const int64_t b = b0 + e / kH3;
+        vb[e] = b < nb ? Vb[b * kH3 + e % kH3] : 0.f;
+    }
+    __syncthreads();
+    const float b4 = w[ob4];
+    // 1024 pairs per CTA, 4 per thread
+    for (int pidx = tid; pidx < kScrI * kScrJ; pidx += 256) {
+        const int li = pidx / kScrJ, lj = pidx % kScrJ;
+        const int64_t a = a0 + li, b = b0 + lj;
+        if (a >= na || b >= nb) continue;
+        float d[kE];
+#pragma unroll
+        for (int q = 0; q < kE; ++q) d[q] = fabsf(ea[li * kE + q] - eb[lj * kE + q]);
+        const int64_t p = pts_a[a], qq = pts_b[b];
+        const float o0 = (float)((qq % X) - (p % X)) / (float)X;
+        const float o1 = (float)(((qq / X) % Y) - ((p / X) % Y)) / (float)Y;
+        const float o2 = (float)((qq / ((int64_t)X * Y)) - (p / ((int64_t)X * Y))) / (float)Z;
+        float y = b4;
+        for (int h = 0; h < kH3; ++h) {
+            float s = ua[li * kH3 + h] + vb[lj * kH3 + h];
+            s = fmaf(Wd[h * 3 + 0], o0, s);
+            s = fmaf(Wd[h * 3 + 1], o1, s);
+            s = fmaf(Wd[h * 3 + 2], o2, s);
+            const float* wr = Wc + h * kE;
+#pragma unroll
+            for (int q = 0; q < kE; ++q) s = fmaf(wr[q], d[q], s);
+            y = fmaf(w4[h], gelu(s), y);
+        }
+        float v = y * tsd + tmean;
+        if (self && b <= a) v = -CUDART_INF_F;  // each unordered pair once
+        pred[a * nb + b] = v;
+    }
+}
+
+}  // namespace cc
+
+// ============================================================================
+using namespace cc;
+
+struct cc_sur {
+    int n = 0;
+    SurOff off{1};
+    DevMem w, wb, g, m, v;
+    int64_t step = 0;
+    float tmean = 0.f, tsd = 1.f;
+    // batch scratch
+    int64_t cap = 0;
+    DevMem pts, tb, X0, A1, H1, Ef, E, X3, A3, H3, y, dy, dA3, dX3, dE, dH1, dA1, loss;
+    DevMem order;
+};
+
+namespace {
+
+cc_status sfail(cc_ctx* c, cc_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define SK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t _e = (call);                                                             \
+        if (_e != cudaSuccess) {                                                             \
+            cudaGetLastError();                                                              \
+            return sfail(ctx, _e == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA,    \
+                         "%s: %s", #call, cudaGetErrorString(_e));                           \
+        }                                                                                    \
+    } while (0)
+
+unsigned grid1(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+cc_status ensure_batch(cc_ctx* ctx, cc_sur* s, int64_t B) {
+    if (B <= s->cap) return CC_OK;
+    const int n = s->n;
+    SK(s->pts.alloc(8 * B));
+    SK(s->tb.alloc(4 * B));
+    SK(s->X0.alloc(2 * 2 * B * n));
+    SK(s->A1.alloc(4 * 2 * B * kH1));
+    SK(s->H1.alloc(2 * 2 * B * kH1));
+    SK(s->Ef.alloc(4 * 2 * B * kE));
+    SK(s->E.alloc(4 * 2 * B * kE));
+    SK(s->X3.alloc(2 * B * kHeadIn));
+    SK(s->A3.alloc(4 * B * kH3));
+    SK(s->H3.alloc(2 * B * kH3));
+    SK(s->y.alloc(4 * B));
+    SK(s->dy.alloc(4 * B));
+    SK(s->dA3.alloc(4 * B * kH3));
+    SK(s->dX3.alloc(4 * B * kHeadIn));
+    SK(s->dE.alloc(4 * 2 * B * kE));
+    SK(s->dH1.alloc(4 * 2 * B * kH1));
+    SK(s->dA1.alloc(4 * 2 * B * kH1));
+    SK(s->loss.alloc(8));
+    s->cap = B;
+    return CC_OK;
+}
+
+typedef __nv_bfloat16 bf16;
+
+// forward over a batch whose point list (2B entries) is in s->pts; with t,
+// also the loss (sum of squares into s->loss) and dy
+cc_status forward(cc_ctx* ctx, cc_sur* s, const Field& f, int64_t B, const float* t) {
+    cudaStream_t st = ctx->stream;
+    const int n = s->n;
+    const SurOff& o = s->off;
+    const bf16* wb = s->wb.as<bf16>();
+    const float* w = s->w.as<float>();
+    note_launch(5);
+    k_sur_gather_z<<<grid1(2 * B * n), 256, 0, st>>>(f.zhat.as<float>(), n, f.n_pad,
+                                                     sqrtf((float)(n - 1)), s->pts.as<uint32_t>(),
+                                                     2 * B, s->X0.as<bf16>());
+    SK(mm(s->X0.as<bf16>(), n, 1, wb + o.W1, 1, n, s->A1.as<float>(), kH1, (int)(2 * B), kH1, n,
+          0, st));
+    k_sur_bias_gelu<<<grid1(2 * B * kH1), 256, 0, st>>>(s->A1.as<float>(), w + o.b1, 2 * B, kH1,
+                                                        s->H1.as<bf16>());
+    SK(mm(s->H1.as<bf16>(), kH1, 1, wb + o.W2, 1, kH1, s->Ef.as<float>(), kE, (int)(2 * B), kE,
+          kH1, 0, st));
+    const uint32_t* pts = s->pts.as<uint32_t>();
+    k_sur_head_input<<<grid1(B * kHeadIn), 256, 0, st>>>(s->Ef.as<float>(), w + o.b2, pts,
+                                                         pts + B, f.X, f.Y, f.Z, B,
+                                                         s->X3.as<bf16>(), s->E.as<float>());
+    SK(mm(s->X3.as<bf16>(), kHeadIn, 1, wb + o.W3, 1, kHeadIn, s->A3.as<float>(), kH3, (int)B, kH3,
+          kHeadIn, 0, st));
+    k_sur_bias_gelu<<<grid1(B * kH3), 256, 0, st>>>(s->A3.as<float>(), w + o.b3, B, kH3,
+                                                    s->H3.as<bf16>());
+    if (t) SK(cudaMemsetAsync(s->loss.p, 0, 8, st));
+    k_sur_out<<<grid1(B * 32), 256, 0, st>>>(s->H3.as<bf16>(), w + o.w4, w + o.b4, t, B, s->tmean,
+                                             1.f / s->tsd, s->y.as<float>(), s->dy.as<float>(),
+                                             s->loss.as<double>());
+    SK(cudaGetLastError());
+    return CC_OK;
+}
+
+// gradients of the batch loss into s->g (overwritten)
+cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
+    cudaStream_t st = ctx->stream;
+    const int n = s->n;
+    const SurOff& o = s->off;
+    const bf16* wb = s->wb.as<bf16>();
+    float* g = s->g.as<float>();
+    // head output layer
+    SK(mm(s->H3.as<bf16>(), 1, kH3, s->dy.as<float>(), 1, 0, g + o.w4, 1, kH3, 1, (int)B, 0, st));
+    note_launch(5);
+    k_sur_colsum<<<1, 256, 0, st>>>(s->dy.as<float>(), B, 1, g + o.b4);
+    k_sur_gelu_bwd<<<grid1(B * kH3), 256, 0, st>>>(s->A3.as<float>(), s->dy.as<float>(),
+                                                   s->w.as<float>() + o.w4, nullptr, B, kH3,
+                                                   s->dA3.as<float>());
+    SK(mm(s->dA3.as<float>(), 1, kH3, s->X3.as<bf16>(), kHeadIn, 1, g + o.W3, kHeadIn, kH3, kHeadIn,
+          (int)B, 0, st));
+    k_sur_colsum<<<kH3, 256, 0, st>>>(s->dA3.as<float>(), B, kH3, g + o.b3);
+    SK(mm(s->dA3.as<float>(), kH3, 1, wb + o.W3, kHeadIn, 1, s->dX3.as<float>(), kHeadIn, (int)B,
+          kHeadIn, kH3, 0, st));
+    k_sur_split<<<grid1(B * kE), 256, 0, st>>>(s->dX3.as<float>(), s->E.as<float>(), B,
+                                               s->dE.as<float>());
+    // encoder
+    SK(mm(s->dE.as<float>(), 1, kE, s->H1.as<bf16>(), kH1, 1, g + o.W2, kH1, kE, kH1, (int)(2 * B),
+          0, st));
+    note_launch(3);
+    k_sur_colsum<<<kE, 256, 0, st>>>(s->dE.as<float>(), 2 * B, kE, g + o.b2);
+    SK(mm(s->dE.as<float>(), kE, 1, wb + o.W2, kH1, 1, s->dH1.as<float>(), kH1, (int)(2 * B), kH1,
+          kE, 0, st));
+    k_sur_gelu_bwd<<<grid1(2 * B * kH1), 256, 0, st>>>(s->A1.as<float>(), nullptr, nullptr,
+                                                       s->dH1.as<float>(), 2 * B, kH1,
+                                                       s->dA1.as<float>());
+    SK(mm(s->dA1.as<float>(), 1, kH1, s->X0.as<bf16>(), n, 1, g + o.W1, n, kH1, n, (int)(2 * B), 0,
+          st));
+    k_sur_colsum<<<kH1, 256, 0, st>>>(s->dA1.as<float>(), 2 * B, kH1, g + o.b1);
+    SK(cudaGetLastError());
+    return CC_OK;
+}
+
+Field* sfield(cc_ctx* ctx, int32_t id) {
+    if (id < 0 || id >= (int32_t)ctx->fields.size()) return nullptr;
+    return ctx->fields[id].get();
+}
+
+}  // namespace
+
+extern "C" {
+
+cc_status cc_sur_create(cc_ctx* ctx, int n_members, uint64_t seed, cc_sur** out) {
+    if (!ctx || !out || n_members < 2 || n_members > 1024)
+        return sfail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    cc_sur* s = new (std::nothrow) cc_sur();
+    if (!s) return CC_ERR_OOM;
+    std::unique_ptr<cc_sur> guard(s);
+    s->n = n_members;
+    s->off = SurOff(n_members);
+    const int64_t P = s->off.total;
+    SK(s->w.alloc(4 * P));
+    SK(s->wb.alloc(2 * P));
+    SK(s->g.alloc(4 * P));
+    SK(s->m.alloc(4 * P));
+    SK(s->v.alloc(4 * P));
+    // seeded init: weights ~ N(0, 1 / fan_in) from Philox + Box-Muller, biases 0
+    std::vector<float> h(P, 0.f);
+    auto fill = [&](int64_t o, int rows, int cols, uint64_t tag) {
+        for (int64_t i = 0; i < (int64_t)rows * cols; ++i) {
+            uint64_t x = seed * 0x9E3779B97F4A7C15ull + tag * 0xD1B54A32D192ED03ull + (uint64_t)i;
+            x ^= x >> 30;
+            x *= 0xBF58476D1CE4E5B9ull;
+            x ^= x >> 27;
+            x *= 0x94D049BB133111EBull;
+            x ^= x >> 31;
+            const double u1 = ((double)(x >> 11) + 0.5) / 9007199254740992.0;
+            x = x * 0x2545F4914F6CDD1Dull + 1;
+            const double u2 = ((double)(x >> 11) + 0.5) / 9007199254740992.0;
+            h[o + i] = (float)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2) / sqrt((double)cols));
+        }
+    };
+    fill(s->off.W1, kH1, n_members, 1);
+    fill(s->off.W2, kE, kH1, 2);
+    fill(s->off.W3, kH3, kHeadIn, 3);
+    fill(s->off.w4, 1, kH3, 4);
+    cc_status st = cc_sur_set_params(ctx, s, h.data());
+    if (st) return st;
+    *out = guard.release();
+    return CC_OK;
+}
+
+cc_status cc_sur_set_params(cc_ctx* ctx, cc_sur* s, const float* params) {
+    if (!ctx || !s || !params) return CC_ERR_INVALID_ARG;
+    const int64_t P = s->off.total;
+    SK(cudaMemcpyAsync(s->w.p, params, 4 * P, cudaMemcpyHostToDevice, ctx->stream));
+    SK(cudaMemsetAsync(s->m.p, 0, 4 * P, ctx->stream));
+    SK(cudaMemsetAsync(s->v.p, 0, 4 * P, ctx->stream));
+    note_launch();
+    k_sur_cast<<<grid1(P), 256, 0, ctx->stream>>>(s->w.as<float>(), P, s->wb.as<bf16>());
+    SK(cudaGetLastError());
+    SK(cudaStreamSynchronize(ctx->stream));
+    s->step = 0;
+    return CC_OK;
+}
+
+cc_status cc_sur_get_params(cc_ctx* ctx, cc_sur* s, float* params, int64_t* n_params,
+                            float* target_mean, float* target_sd) {
+    if (!ctx || !s) return CC_ERR_INVALID_ARG;
+    if (n_params) *n_params = s->off.total;
+    if (target_mean) *target_mean = s->tmean;
+    if (target_sd) *target_sd = s->tsd;
+    if (params) {
+        SK(cudaMemcpyAsync(params, s->w.p, 4 * s->off.total, cudaMemcpyDeviceToHost, ctx->stream));
+        SK(cudaStreamSynchronize(ctx->stream));
+    }
+    return CC_OK;
+}
+
+cc_status cc_sur_set_target_scale(cc_ctx* ctx, cc_sur* s, float mean, float sd) {
+    if (!ctx || !s || !(sd > 0.f)) return sfail(ctx, CC_ERR_INVALID_ARG, "sd must be > 0");
+    s->tmean = mean;
+    s->tsd = sd;
+    return CC_OK;
+}
+
+cc_status cc_sur_loss_grad(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t* pa,
+                           const uint32_t* pb, const float* target, int64_t n_pairs, float* loss,
+                           float* grad) {
+    if (!ctx || !s || !pa || !pb || !target || n_pairs < 1)
+        return sfail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    Field* f = sfield(ctx, field_id);
+    if (!f || f->n != s->n) return sfail(ctx, CC_ERR_INVALID_ARG, "field does not match");
+    cc_status st = ensure_batch(ctx, s, n_pairs);
+    if (st) return st;
+    std::vector<uint32_t> pts(2 * n_pairs);
+    for (int64_t i = 0; i < n_pairs; ++i) {
+        if (pa[i] >= (uint64_t)f->P || pb[i] >= (uint64_t)f->P)
+            return sfail(ctx, CC_ERR_INVALID_ARG, "point id out of range");
+        pts[i] = pa[i];
+        pts[n_pairs + i] = pb[i];
+    }
+    SK(cudaMemcpyAsync(s->pts.p, pts.data(), 8 * n_pairs, cudaMemcpyHostToDevice, ctx->stream));
+    SK(cudaMemcpyAsync(s->tb.p, target, 4 * n_pairs, cudaMemcpyHostToDevice, ctx->stream));
+    if ((st = forward(ctx, s, *f, n_pairs, s->tb.as<float>()))) return st;
+    if ((st = backward(ctx, s, n_pairs))) return st;
+    double l = 0;
+    SK(cudaMemcpyAsync(&l, s->loss.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (grad)
+        SK(cudaMemcpyAsync(grad, s->g.p, 4 * s->off.total, cudaMemcpyDeviceToHost, ctx->stream));
+    SK(cudaStreamSynchronize(ctx->stream));
+    if (loss) *loss = (float)(l / n_pairs);
+    return CC_OK;
+}
+
+cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t* pa,
+                       const uint32_t* pb, const float* target, int64_t n_pairs, int on_device,
+                       int epochs, int batch, float lr, uint64_t seed, float* epoch_loss) {
+    if (!ctx || !s || !pa || !pb || !target || n_pairs < 1 || epochs < 0 || batch < 1 ||
+        !(lr > 0.f))
+        return sfail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    Field* f = sfield(ctx, field_id);
+    if (!f || f->n != s->n) return sfail(ctx, CC_ERR_INVALID_ARG, "field does not match");
+    cudaStream_t st = ctx->stream;
+    const uint32_t *da = pa, *db = pb;
+    const float* dt = target;
+    DevMem ha, hb, ht;
+    if (!on_device) {
+        SK(ha.alloc(4 * n_pairs));
+        SK(hb.alloc(4 * n_pairs));
+        SK(ht.alloc(4 * n_pairs));
+        SK(cudaMemcpyAsync(ha.p, pa, 4 * n_pairs, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(hb.p, pb, 4 * n_pairs, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(ht.p, target, 4 * n_pairs, cudaMemcpyHostToDevice, st));
+        da = ha.as<uint32_t>();
+        db = hb.as<uint32_t>();
+        dt = ht.as<float>();
+    }
+    // target standardization from the training targets
+    {
+        std::vector<float> h(n_pairs);
+        SK(cudaMemcpyAsync(h.data(), dt, 4 * n_pairs, cudaMemcpyDeviceToHost, st));
+        SK(cudaStreamSynchronize(st));
+        double m = 0, v = 0;
+        for (float x : h) m += x;
+        m /= n_pairs;
+        for (float x : h) v += (x - m) * (x - m);
+        v /= n_pairs;
+        s->tmean = (float)m;
+        s->tsd = (float)std::max(sqrt(v), 1e-6);
+    }
+    const int64_t B = std::min<int64_t>(batch, n_pairs);
+    cc_status r = ensure_batch(ctx, s, B);
+    if (r) return r;
+    const int64_t steps = n_pairs / B;
+    // per-epoch shuffle: a seeded permutation (host Fisher-Yates on SplitMix64)
+    std::vector<int64_t> order(n_pairs);
+    SK(s->order.ensure(8 * n_pairs));
+    uint64_t rs = seed ^ 0xA0761D6478BD642Full;
+    auto next = [&]() {
+        rs += 0x9E3779B97F4A7C15ull;
+        uint64_t z = rs;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int64_t i = 0; i < n_pairs; ++i) order[i] = i;
+        for (int64_t i = n_pairs - 1; i > 0; --i) std::swap(order[i], order[next() % (i + 1)]);
+        SK(cudaMemcpyAsync(s->order.p, order.data(), 8 * n_pairs, cudaMemcpyHostToDevice, st));
+        double sum = 0;
+        for (int64_t k = 0; k < steps; ++k) {
+            note_launch();
+            k_sur_batch<<<grid1(B), 256, 0, st>>>(da, db, dt, s->order.as<int64_t>(), k * B, B,
+                                                  seed, (uint64_t)s->step, 1,
+                                                  s->pts.as<uint32_t>(), s->tb.as<float>());
+            if ((r = forward(ctx, s, *f, B, s->tb.as<float>()))) return r;
+            if ((r = backward(ctx, s, B))) return r;
+            s->step++;
+            const float c1 = 1.f - powf(0.9f, (float)s->step), c2 = 1.f - powf(0.999f, (float)s->step);
+            note_launch();
+            k_sur_adam<<<grid1(s->off.total), 256, 0, st>>>(s->w.as<float>(), s->g.as<float>(),
+                                                            s->m.as<float>(), s->v.as<float>(),
+                                                            s->off.total, lr, c1, c2,
+                                                            s->wb.as<bf16>());
+            SK(cudaGetLastError());
+            if (epoch_loss && (k % 64 == 63 || k == steps - 1)) {
+                double l = 0;
+                SK(cudaMemcpyAsync(&l, s->loss.p, 8, cudaMemcpyDeviceToHost, st));
+                SK(cudaStreamSynchronize(st));
+                sum += l / B;
+            }
+        }
+        if (epoch_loss) epoch_loss[ep] = (float)(sum / ((steps + 63) / 64));
+    }
+    SK(cudaStreamSynchronize(st));
+    return CC_OK;
+}
+
+cc_status cc_sur_predict(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t* pa,
+                         const uint32_t* pb, int64_t n_pairs, int pairs_on_device, float* out,
+                         int out_on_device) {
+    if (!ctx || !s || !pa || !pb || !out || n_pairs < 0)
+        return sfail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    Field* f = sfield(ctx, field_id);
+    if (!f || f->n != s->n) return sfail(ctx, CC_ERR_INVALID_ARG, "field does not match");
+    cudaStream_t st = ctx->stream;
+    const int64_t B = std::min<int64_t>(n_pairs, 1 << 16);
+    cc_status r = ensure_batch(ctx, s, std::max<int64_t>(B, 1));
+    if (r) return r;
+    DevMem hpa, hpb, hout;
+    const uint32_t *da = pa, *db = pb;
+    float* dout = out;
+    if (!pairs_on_device) {
+        SK(hpa.alloc(4 * std::max<int64_t>(n_pairs, 1)));
+        SK(hpb.alloc(4 * std::max<int64_t>(n_pairs, 1)));
+        SK(cudaMemcpyAsync(hpa.p, pa, 4 * n_pairs, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(hpb.p, pb, 4 * n_pairs, cudaMemcpyHostToDevice, st));
+        da = hpa.as<uint32_t>();
+        db = hpb.as<uint32_t>();
+    }
+    if (!out_on_device) {
+        SK(hout.alloc(4 * std::max<int64_t>(n_pairs, 1)));
+        dout = hout.as<float>();
+    }
+    for (int64_t s0 = 0; s0 < n_pairs; s0 += B) {
+        const int64_t b = std::min(B, n_pairs - s0);
+        note_launch();
+        k_sur_batch<<<grid1(b), 256, 0, st>>>(da, db, nullptr, nullptr, s0, b, 0, 0, 0,
+                                              s->pts.as<uint32_t>(), s->tb.as<float>());
+        if ((r = forward(ctx, s, *f, b, nullptr))) return r;
+        // de-standardize y into the output
+        SK(cudaMemcpyAsync(dout + s0, s->y.p, 4 * b, cudaMemcpyDeviceToDevice, st));
+    }
+    // outputs hold standardized predictions: back to the target's units
+    note_launch();
+    k_sur_affine<<<grid1(n_pairs), 256, 0, st>>>(dout, n_pairs, s->tsd, s->tmean);
+    SK(cudaGetLastError());
+    if (!out_on_device) {
+        SK(cudaMemcpyAsync(out, dout, 4 * n_pairs, cudaMemcpyDeviceToHost, st));
+        SK(cudaStreamSynchronize(st));
+    }
+    return CC_OK;
+}
+
+cc_status cc_sur_screen(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t region_b, int topk,
+                        uint64_t* ids, float* preds) {
+    if (!ctx || !s || topk < 1 || topk > 8192 || !ids || !preds)
+        return sfail(ctx, CC_ERR_INVALID_ARG, "bad arguments (1 <= topk <= 8192)");
+    if (region_a < 0 || region_a >= (int)ctx->regions.size() || !ctx->regions[region_a] ||
+        region_b < 0 || region_b >= (int)ctx->regions.size() || !ctx->regions[region_b])
+        return sfail(ctx, CC_ERR_INVALID_ARG, "unknown region");
+    Region& ra = *ctx->regions[region_a];
+    Region& rb = *ctx->regions[region_b];
+    if (ra.field != rb.field) return sfail(ctx, CC_ERR_INVALID_ARG, "regions of one field only");
+    Field* f = sfield(ctx, ra.field);
+    if (!f || f->n != s->n) return sfail(ctx, CC_ERR_INVALID_ARG, "field does not match");
+    if ((uint64_t)ra.np * rb.np >= (1ull << 32))
+        return sfail(ctx, CC_ERR_INVALID_ARG, "|A| * |B| must be below 2^32");
+    cudaStream_t st = ctx->stream;
+    const int n = s->n;
+    const SurOff& o = s->off;
+    const int64_t na = ra.np, nb = rb.np;
+    cc_status r = ensure_batch(ctx, s, (std::max(na, nb) + 1) / 2);
+    if (r) return r;
+    DevMem Ea, Eb, Ua, Vb, pred, aux;
+    SK(Ea.alloc(4 * na * kE));
+    SK(Eb.alloc(4 * nb * kE));
+    SK(Ua.alloc(4 * na * kH3));
+    SK(Vb.alloc(4 * nb * kH3));
+    SK(pred.alloc(4 * (size_t)na * nb));
+    const float* w = s->w.as<float>();
+    // per-point encoder (bf16 weights, as in training) and head projections
+    for (int side = 0; side < 2; ++side) {
+        const Region& rg = side ? rb : ra;
+        const int64_t np = rg.np;
+        float* E = side ? Eb.as<float>() : Ea.as<float>();
+        note_launch(2);
+        k_sur_gather_z<<<grid1(np * n), 256, 0, st>>>(f->zhat.as<float>(), n, f->n_pad,
+                                                      sqrtf((float)(n - 1)),
+                                                      rg.pts.as<uint32_t>(), np, s->X0.as<bf16>());
+        SK(mm(s->X0.as<bf16>(), n, 1, s->wb.as<bf16>() + o.W1, 1, n, s->A1.as<float>(), kH1,
+              (int)np, kH1, n, 0, st));
+        k_sur_bias_gelu<<<grid1(np * kH1), 256, 0, st>>>(s->A1.as<float>(), w + o.b1, np, kH1,
+                                                         s->H1.as<bf16>());
+        SK(mm(s->H1.as<bf16>(), kH1, 1, s->wb.as<bf16>() + o.W2, 1, kH1, E, kE, (int)np, kE, kH1,
+              0, st));
+        note_launch();
+        k_sur_add_bias<<<grid1(np * kE), 256, 0, st>>>(E, w + o.b2, np, kE);
+        float* UV = side ? Vb.as<float>() : Ua.as<float>();
+        SK(mm(E, kE, 1, w + o.W3 + side * kE, 1, kHeadIn, UV, kH3, (int)np, kH3, kE, 0, st));
+        if (!side) {
+            note_launch();
+            k_sur_add_bias<<<grid1(np * kH3), 256, 0, st>>>(UV, w + o.b3, np, kH3);
+        }
+    }
+    const size_t smem = 4 * (size_t)(kH3 * kE + kH3 * 3 + kH3 + kScrI * kE + kScrJ * kE +
+                                     kScrI * kH3 + kScrJ * kH3);
+    SK(cudaFuncSetAttribute(k_sur_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((nb + kScrJ - 1) / kScrJ), (unsigned)((na + kScrI - 1) / kScrI));
+    note_launch();
+    k_sur_screen<<<grid, 256, smem, st>>>(Ea.as<float>(), Ua.as<float>(), Eb.as<float>(),
+                                          Vb.as<float>(), w, o.W3, o.w4, o.b4,
+                                          ra.pts.as<uint32_t>(), rb.pts.as<uint32_t>(), na, nb,
+                                          region_a == region_b, f->X, f->Y, f->Z, s->tmean,
+                                          s->tsd, pred.as<float>());
+    SK(cudaGetLastError());
+    // top-k by histogram selection, then one sorting CTA
+    const size_t o_hist = 0, o_sel = 4 * 4096, o_idx = o_sel + 256, o_tv = o_idx + 4 * 8192,
+                 o_ti = o_tv + 4 * 8192;
+    SK(aux.alloc(o_ti + 8 * 8192));
+    unsigned char* ab = aux.as<unsigned char>();
+    SK(cudaMemsetAsync(ab, 0, o_idx, st));
+    const int64_t N = na * nb;
+    SK(launch_select_top(pred.as<float>(), N, 1.f, (unsigned)topk, (unsigned*)(ab + o_hist),
+                         (Select*)(ab + o_sel), (uint32_t*)(ab + o_idx), 8192, st));
+    // candidate indices are the linear pair indices a * nb + b themselves
+    SK(launch_sort_top_ids(pred.as<float>(), (const uint32_t*)(ab + o_idx),
+                           &((Select*)(ab + o_sel))->count, 8192, topk, (float*)(ab + o_tv),
+                           (unsigned long long*)(ab + o_ti), st));
+    SK(cudaMemcpyAsync(preds, ab + o_tv, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
+    SK(cudaMemcpyAsync(ids, ab + o_ti, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
+    SK(cudaStreamSynchronize(st));
+    return CC_OK;
+}
+
+cc_status cc_sur_destroy(cc_ctx* ctx, cc_sur* s) {
+    if (!s) return CC_ERR_INVALID_ARG;
+    if (ctx) cudaStreamSynchronize(ctx->stream);
+    delete s;
+    return CC_OK;
+}
+
+}  // extern "C"
