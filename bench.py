@@ -395,13 +395,112 @@ def run_ours(args, rank, world, local_rank):
             "ksg_pairs_per_s": PRE["sampled_pairs"] / (st2["ksg"] * 1e-3),
             "results": wl2.results, "stage_roofline": roof2, "gpu_launches": int(l2),
             "e2e_ms_per_step": e2e2}
+    sur = None
+    if not args.skip_surrogate:
+        line["surrogate"], sur = run_surrogate(args, cc, dev, stream, rank)
     if not args.skip_context:
-        line["context"] = run_context(args, cc, dev, stream, rank)
+        line["context"] = run_context(args, cc, dev, stream, rank, sur)
+    if sur is not None:
+        sur.close()
     cc.close()
     return line
 
 
-def run_context(args, cc, dev, stream, rank):
+def run_surrogate(args, cc, dev, stream, rank):
+    """Learned surrogate: train on exact KSG values, screen a focus region pair."""
+    import torch
+    import paper_2309_03308_gb300 as pg
+    from paper_2309_03308_gb300 import Params, Surrogate
+    cfg = configs.SURROGATE
+    n_train = cfg["train_pairs"] if not args.quick_surrogate else 400_000
+    Ft = gen.field(cfg["train_seed"], cfg["X"], cfg["Y"], cfg["Z"], cfg["n"])
+    ft = cc.load_field(torch.from_numpy(Ft).to(dev))
+    (whole,) = cc.define_regions(ft, [(0, 0, 0, cfg["X"], cfg["Y"], cfg["Z"])])
+    pa = torch.empty(n_train, dtype=torch.int32, device=dev)
+    pb = torch.empty(n_train, dtype=torch.int32, device=dev)
+    tgt = torch.empty(n_train, device=dev)
+    cc.sample_pairs(whole, whole, 21 + rank, n_train, pa=pa, pb=pb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cc.eval_pairs(ft, ft, Params(pg.CC_MI_KSG, k=cfg["k"]), pa, pb, out=tgt)
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - t0
+    n_fit = int(n_train * 0.95)
+    sur = Surrogate(cc, cfg["n"], seed=5)
+    epochs = 3
+    t0 = time.perf_counter()
+    losses = sur.train(ft, pa[:n_fit], pb[:n_fit], tgt[:n_fit], epochs=epochs, batch=4096,
+                       lr=2e-3, seed=6)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    held = sur.predict(ft, pa[n_fit:], pb[n_fit:], out=torch.empty(n_train - n_fit, device=dev))
+    h_pred, h_true = held.cpu().numpy(), tgt[n_fit:].cpu().numpy()
+    r_held = float(np.corrcoef(h_pred, h_true)[0, 1])
+    cc.free_field(ft)
+    # held-out field, focus geometry: screen all pairs, verify the top list exactly
+    Fe = gen.field(cfg["eval_seed"], cfg["X"], cfg["Y"], cfg["Z"], cfg["n"])
+    fe = cc.load_field(torch.from_numpy(Fe).to(dev))
+    ra, rb = cc.define_regions(fe, [cfg["box_a"], cfg["box_b"]])
+    K = cfg["screen_topk"]
+    sur.screen(ra, rb, K)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ids, preds = sur.screen(ra, rb, K)
+    screen_s = time.perf_counter() - t0
+    boxa, boxb = cfg["box_a"], cfg["box_b"]
+
+    def pts(box):
+        x0, y0, z0, x1, y1, z1 = box
+        zz, yy, xx = np.meshgrid(np.arange(z0, z1), np.arange(y0, y1), np.arange(x0, x1),
+                                 indexing="ij")
+        return (xx + cfg["X"] * (yy + cfg["Y"] * zz)).astype(np.uint32).ravel()
+    A, B = pts(boxa), pts(boxb)
+    ia, ib = np.divmod(ids.astype(np.int64), len(B))
+    exact_top = cc.eval_pairs(fe, fe, Params(pg.CC_MI_KSG, k=cfg["k"]), A[ia], B[ib])
+    rpa, rpb = cc.sample_pairs(ra, rb, 33, K)
+    exact_rand = cc.eval_pairs(fe, fe, Params(pg.CC_MI_KSG, k=cfg["k"]), rpa, rpb)
+    out = {"workload": cfg["name"], "train_pairs": n_fit, "epochs": epochs,
+           "label_s": label_s, "train_s": train_s,
+           "train_samples_per_s": epochs * n_fit / train_s,
+           "train_loss_per_epoch": [float(x) for x in losses],
+           "heldout_corr": r_held, "screen_pairs": 20480 * 20480, "screen_s": screen_s,
+           "screen_pairs_per_s": 20480 * 20480 / screen_s,
+           "top_k": K, "topk_exact_ksg_max": float(exact_top.max()),
+           "random_k_exact_ksg_max": float(exact_rand.max())}
+    if args.recall:
+        # exhaustive KSG over all 419M pairs of the region pair, in slices
+        t0 = time.perf_counter()
+        best = -np.inf
+        rows = 2048
+        for a0 in range(0, len(A), rows):
+            qa = torch.from_numpy(np.repeat(A[a0:a0 + rows], len(B)).astype(np.int32)).to(dev)
+            qb = torch.from_numpy(np.tile(B, min(rows, len(A) - a0)).astype(np.int32)).to(dev)
+            r = cc.segment_extremes(fe, Params(pg.CC_MI_KSG, k=cfg["k"]), qa, qb,
+                                    [0, qa.shape[0]])[0]
+            best = max(best, r["max"])
+        out["exhaustive_ksg_max"] = float(best)
+        out["exhaustive_ksg_s"] = time.perf_counter() - t0
+        out["screen_recall_0.01"] = bool(exact_top.max() >= best - 0.01)
+        out["random_recall_0.01"] = bool(exact_rand.max() >= best - 0.01)
+    cc.free_field(fe)
+    return out, sur
+
+
+def surrogate_prior(cc, sur, fid, X, Y, rp_a, rp_b, pools):
+    """Surrogate predictions at the voxel nearest to every pool entry: [n_rp][Q]."""
+    pa, pb = [], []
+    for i, pool in enumerate(pools):
+        ba = cc.region_info(rp_a[i])[1]
+        bb = cc.region_info(rp_b[i])[1]
+        v = np.rint(pool).astype(np.int64)
+        pa.append((ba[0] + v[:, 0]) + X * ((ba[1] + v[:, 1]) + Y * (ba[2] + v[:, 2])))
+        pb.append((bb[0] + v[:, 3]) + X * ((bb[1] + v[:, 4]) + Y * (bb[2] + v[:, 5])))
+    pa = np.concatenate(pa).astype(np.uint32)
+    pb = np.concatenate(pb).astype(np.uint32)
+    return sur.predict(fid, pa, pb).reshape(len(pools), -1)
+
+
+def run_context(args, cc, dev, stream, rank, sur=None):
     """Context view: batched BOS over all 3916 region pairs of a 340x250x20 field."""
     import torch
     import paper_2309_03308_gb300 as pg
@@ -460,6 +559,25 @@ def run_context(args, cc, dev, stream, rank):
     torch.cuda.synchronize()
     plain_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
     ksg_best = np.array([r["max"] for r in res[3]])
+    prior_stats = {}
+    if sur is not None:
+        # the same BOS with the surrogate's prediction as prior mean, equal budget
+        probe = cc.bos_create(fid, rp_a, rp_b, **kw)
+        pools = [probe.inspect(i)["pool"] for i in range(n_rp)]
+        probe.close()
+        t0 = time.perf_counter()
+        prior = surrogate_prior(cc, sur, fid, cfg["X"], cfg["Y"], rp_a, rp_b, pools)
+        prior_s = time.perf_counter() - t0
+        bs = cc.bos_create(fid, rp_a, rp_b, **kw)
+        bs.set_prior(np.ascontiguousarray(prior, np.float32))
+        bs.run(T, True)
+        rs = bs.results()
+        bs.close()
+        sbest = np.array([r["max"] for r in rs[3]])
+        prior_stats = {"surrogate_prior_s": prior_s,
+                       "ksg_best_mean_surrogate_prior": float(sbest.mean()),
+                       "surrogate_prior_wins": float(np.mean(sbest > ksg_best)),
+                       "surrogate_prior_ties": float(np.mean(sbest == ksg_best))}
     out = {"workload": cfg["name"], "region_pairs": n_rp, "rounds": T, "per_round": R,
            "pool": kw["pool"], "shortlist": kw["shortlist"],
            "bos_ms_graph": ms_graph, "bos_ms_direct": ms_direct,
@@ -468,7 +586,8 @@ def run_context(args, cc, dev, stream, rank):
            "measure_evals_per_s": 4 * n_rp * R * T / (ms_graph * 1e-3),
            "plain_eval_ms_per_round": plain_ms,
            "speedup_round_vs_plain_eval": plain_ms / (ms_graph / T),
-           "ksg_best_mean": float(ksg_best.mean()), "ksg_best_max": float(ksg_best.max())}
+           "ksg_best_mean": float(ksg_best.mean()), "ksg_best_max": float(ksg_best.max()),
+           **prior_stats}
     if args.recall:
         # recall of the Pearson maximum per region pair against exhaustive
         # evaluation (BF16 tensor-core all-pairs with certified exact extremes)
@@ -583,6 +702,10 @@ def main():
                     help="do not time the n = 1000 workload")
     ap.add_argument("--skip-context", action="store_true",
                     help="do not time the batched BOS context view")
+    ap.add_argument("--skip-surrogate", action="store_true",
+                    help="do not train and time the learned surrogate")
+    ap.add_argument("--quick-surrogate", action="store_true",
+                    help="train the surrogate on 400k instead of 4M pairs")
     ap.add_argument("--recall", action="store_true",
                     help="also measure BOS recall against exhaustive Pearson maxima")
     ap.add_argument("--workload", default="focus", choices=["focus", "focus-regions"],
