@@ -321,7 +321,7 @@ __global__ void k_bos_eval(BosDev d, int warps_per_block) {
     const int n = d.n, n_pad = d.n_pad, B = d.bins;
     long long* psi = reinterpret_cast<long long*>(es);
     long long* clogc = psi + ((n + 2) & ~1);
-    const size_t slot = ksg_slot_bytes(n_pad);
+    const size_t slot = ksg_slot_bytes(n_pad, KMAX);
     unsigned char* wbase = reinterpret_cast<unsigned char*>(clogc + ((n + 2) & ~1)) +
                            (size_t)warp * (slot + 256 * sizeof(int));
     int* hist = reinterpret_cast<int*>(wbase + slot);
@@ -342,8 +342,8 @@ __global__ void k_bos_eval(BosDev d, int warps_per_block) {
         const int64_t ra = (int64_t)p * n_pad, rb = (int64_t)q * n_pad;
         float value = 0.f;
         if (measure == CC_MI_KSG) {
-            ksg_stage(wbase, n, n_pad, d.sorted + ra, d.perm + ra, d.fvals + ra, d.sorted + rb,
-                      d.perm + rb, d.fvals + rb);
+            ksg_stage<KMAX>(wbase, n, n_pad, d.sorted + ra, d.perm + ra, d.fvals + ra,
+                            d.sorted + rb, d.perm + rb, d.fvals + rb);
             long long acc = 0;
             for (int ti = lane; ti < n; ti += 32)
                 acc += ksg_sample<KMAX>(wbase, n, n_pad, d.k, ti, psi, nullptr, nullptr, nullptr);
@@ -625,7 +625,7 @@ size_t condition_smem(const BosDev& d) {
 }
 size_t eval_smem(const BosDev& d, int warps) {
     const int pl = (d.n + 2) & ~1;
-    return 2 * pl * 8 + (size_t)warps * (ksg_slot_bytes(d.n_pad) + 256 * 4);
+    return 2 * pl * 8 + (size_t)warps * (ksg_slot_bytes(d.n_pad, ksg_kmax(d.k)) + 256 * 4);
 }
 
 // set_attr: raise the kernel's dynamic shared-memory limit first (not while

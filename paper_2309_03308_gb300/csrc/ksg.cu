@@ -15,16 +15,20 @@
 //   gathers only. The samples of the group's pairs form one stream that the
 //   lanes take 32 at a time, so fewer lanes idle at the end of a pair.
 //
-//   eps_i: walk outward from i along ONE axis in non-decreasing axis distance
-//   (two pointers over that axis's sorted order); every visited j offers d_ij.
-//   The first k visited are taken unconditionally and sorted once; later ones
-//   enter a sorted register list of the k smallest. When the next axis
-//   distance is not below the current k-th value no later j can enter, so the
-//   walk stops with the exact k-th smallest. The walk length is about the
-//   number of samples within eps_i along the axis, large where that axis is
-//   locally dense; each lane walks along the axis whose local spacing
-//   (8-neighbour span in sorted order) is wider. The step is branch-free and
-//   all lanes run the same code on lane-selected arrays.
+//   eps_i: walk outward from i along ONE axis, over that axis's sorted order,
+//   on both sides at once; every visited j offers d_ij. The first k
+//   positions are taken unconditionally and sorted by a fixed network; each
+//   later step offers the next two positions of each side to a sorted register
+//   list of the k smallest (four values merged at once: sorted, folded into
+//   the list's top four, bitonic merger) and passes the positions whose axis
+//   distance was below the list's k-th value. When both next axis distances
+//   are not below the k-th value no unvisited j can enter, so the walk stops
+//   with the exact k-th smallest. The walk length is about the number of
+//   samples within eps_i along the axis, large where that axis is locally
+//   dense; each lane walks along the axis whose local spacing (8-neighbour
+//   span in sorted order) is wider. Sentinels (+-inf) around the staged arrays
+//   keep the step free of bounds checks, and all lanes run the same code on
+//   lane-selected arrays.
 //
 //   Counts: the walk's final window holds every j with axis distance below
 //   eps_i (trimmed at its ends); the other axis is counted with two binary
@@ -57,7 +61,7 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
     long long* psi = reinterpret_cast<long long*>(ksg_smem);
     const int psi_len = (n + 2) & ~1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t slot_bytes = ksg_slot_bytes(n_pad);
+    const size_t slot_bytes = ksg_slot_bytes(n_pad, KMAX);
     unsigned char* wbase = ksg_smem + psi_len * sizeof(long long) + (size_t)warp * G * slot_bytes;
     for (int i = threadIdx.x; i <= n; i += blockDim.x) psi[i] = psi_fix[i];
     __syncthreads();
@@ -79,8 +83,8 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
             }
             valid |= 1u << sl;
             const int64_t ra = (int64_t)p * n_pad, rb = (int64_t)q * n_pad;
-            ksg_stage(wbase + sl * slot_bytes, n, n_pad, sorted_a + ra, perm_a + ra, vals_a + ra,
-                      sorted_b + rb, perm_b + rb, vals_b + rb);
+            ksg_stage<KMAX>(wbase + sl * slot_bytes, n, n_pad, sorted_a + ra, perm_a + ra,
+                            vals_a + ra, sorted_b + rb, perm_b + rb, vals_b + rb);
         }
 
         long long acc[kMaxGroup];
@@ -126,7 +130,8 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
     // (more pairs per warp costs occupancy through shared memory)
     const int G = fa.n_pad <= 128 ? 2 : 1;
     const int psi_len = (fa.n + 2) & ~1;
-    const size_t smem = psi_len * sizeof(long long) + kKsgWarps * G * ksg_slot_bytes(fa.n_pad);
+    const size_t smem =
+        psi_len * sizeof(long long) + kKsgWarps * G * ksg_slot_bytes(fa.n_pad, KMAX);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_ksg_pairs<KMAX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,

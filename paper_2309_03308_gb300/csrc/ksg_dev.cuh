@@ -21,17 +21,98 @@ __device__ __forceinline__ void topk_insert(float (&top)[KMAX], float d) {
     top[0] = fminf(top[0], d);
 }
 
-// ascending odd-even transposition sort of a register array
-template <int KMAX>
-__device__ __forceinline__ void sort_net(float (&t)[KMAX]) {
+// compare-exchange: a <- min, b <- max
+__device__ __forceinline__ void ce(float& a, float& b) {
+    const float lo = fminf(a, b);
+    b = fmaxf(a, b);
+    a = lo;
+}
+
+__host__ __device__ constexpr int ksg_pow2_at_least(int v) {
+    int q = 1;
+    while (q < v) q <<= 1;
+    return q;
+}
+
+// ascending sort of a small register array. Fixed networks for the common
+// sizes (4: 5 comparators; 8: 19; 10: 29, Waksman's network), a bitonic
+// sorter for other powers of two, odd-even transposition otherwise. Each
+// network is checked against all 0/1 inputs by a host test.
+template <int N>
+__device__ __forceinline__ void sort_small(float (&t)[N]) {
+    if constexpr (N == 2) {
+        ce(t[0], t[1]);
+    } else if constexpr (N == 4) {
+        ce(t[0], t[1]); ce(t[2], t[3]); ce(t[0], t[2]); ce(t[1], t[3]); ce(t[1], t[2]);
+    } else if constexpr (N == 8) {
+        ce(t[0], t[2]); ce(t[1], t[3]); ce(t[4], t[6]); ce(t[5], t[7]);
+        ce(t[0], t[4]); ce(t[1], t[5]); ce(t[2], t[6]); ce(t[3], t[7]);
+        ce(t[0], t[1]); ce(t[2], t[3]); ce(t[4], t[5]); ce(t[6], t[7]);
+        ce(t[2], t[4]); ce(t[3], t[5]); ce(t[1], t[4]); ce(t[3], t[6]);
+        ce(t[1], t[2]); ce(t[3], t[4]); ce(t[5], t[6]);
+    } else if constexpr (N == 10) {
+        ce(t[4], t[9]); ce(t[3], t[8]); ce(t[2], t[7]); ce(t[1], t[6]); ce(t[0], t[5]);
+        ce(t[1], t[4]); ce(t[6], t[9]); ce(t[0], t[3]); ce(t[5], t[8]); ce(t[0], t[2]);
+        ce(t[3], t[6]); ce(t[7], t[9]); ce(t[0], t[1]); ce(t[2], t[4]); ce(t[5], t[7]);
+        ce(t[8], t[9]); ce(t[1], t[2]); ce(t[4], t[6]); ce(t[7], t[8]); ce(t[3], t[5]);
+        ce(t[2], t[5]); ce(t[6], t[8]); ce(t[1], t[3]); ce(t[4], t[7]); ce(t[2], t[3]);
+        ce(t[6], t[7]); ce(t[3], t[4]); ce(t[5], t[6]); ce(t[4], t[5]);
+    } else if constexpr (ksg_pow2_at_least(N) == N) {
 #pragma unroll
-    for (int r = 0; r < KMAX; ++r) {
+        for (int size = 2; size <= N; size *= 2) {
 #pragma unroll
-        for (int i = r & 1; i + 1 < KMAX; i += 2) {
-            const float a = t[i], b = t[i + 1];
-            t[i] = fminf(a, b);
-            t[i + 1] = fmaxf(a, b);
+            for (int stride = size / 2; stride > 0; stride /= 2) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    const int j = i ^ stride;
+                    if (j > i) {
+                        if ((i & size) == 0) ce(t[i], t[j]);
+                        else ce(t[j], t[i]);
+                    }
+                }
+            }
         }
+    } else {
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+#pragma unroll
+            for (int i = r & 1; i + 1 < N; i += 2) ce(t[i], t[i + 1]);
+        }
+    }
+}
+
+// Sort a bitonic register array (ascending then descending) ascending: the
+// bitonic merger of the next power of two Q, with Q - KMAX virtual -inf
+// entries in front (comparators touching them are no-ops and are dropped).
+template <int KMAX>
+__device__ __forceinline__ void bitonic_merge(float (&t)[KMAX]) {
+    constexpr int Q = ksg_pow2_at_least(KMAX), PADN = Q - KMAX;
+#pragma unroll
+    for (int d = Q / 2; d > 0; d /= 2) {
+#pragma unroll
+        for (int q = PADN; q < Q; ++q)
+            if ((q & d) == 0) ce(t[q - PADN], t[q + d - PADN]);
+    }
+}
+
+// The KMAX smallest of the sorted list t and four new values, sorted: the
+// new values are sorted, the i-th largest list entry is replaced by the
+// minimum of itself and the i-th smallest new value (the result holds the
+// KMAX smallest and is bitonic), and a bitonic merger restores the order.
+template <int KMAX>
+__device__ __forceinline__ void topk_merge4(float (&t)[KMAX], float c0, float c1, float c2,
+                                            float c3) {
+    if constexpr (KMAX < 4) {
+        topk_insert<KMAX>(t, c0);
+        topk_insert<KMAX>(t, c1);
+        topk_insert<KMAX>(t, c2);
+        topk_insert<KMAX>(t, c3);
+    } else {
+        float c[4] = {c0, c1, c2, c3};
+        sort_small<4>(c);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[KMAX - 1 - j] = fminf(t[KMAX - 1 - j], c[j]);
+        bitonic_merge<KMAX>(t);
     }
 }
 
@@ -46,57 +127,27 @@ __device__ __forceinline__ int lower_search(int lo, int hi, Pred pred) {
     return lo;
 }
 
-__host__ __device__ constexpr size_t ksg_slot_bytes(int n_pad) {
-    return (size_t)n_pad * (2 * sizeof(float2) + 2 * sizeof(uint16_t));
+// KMAX instantiated for a given k (the list length rounded up to a template size)
+__host__ __device__ constexpr int ksg_kmax(int k) {
+    return k <= 1 ? 1 : k == 2 ? 2 : k == 3 ? 3 : k <= 4 ? 4 : k <= 8 ? 8 : k <= 10 ? 10
+           : k <= 16 ? 16 : 32;
 }
 
-// Walk along sorted pairs W (walk value, other value) from position s.
-// L / R = next unvisited positions on each side, dL / dR their axis distances
-// (inf when exhausted), cL / cR their entries.
-struct KsgWalk {
-    const float2* W;
-    int n, L, R;
-    float pv, ov, dL, dR;
-    float2 cL, cR;
-    __device__ __forceinline__ void init(const float2* w, int n_, int s, float p, float o) {
-        W = w;
-        n = n_;
-        pv = p;
-        ov = o;
-        L = s - 1;
-        R = s + 1;
-        cL = W[L >= 0 ? L : s];
-        cR = W[R < n ? R : s];
-        dL = L >= 0 ? __fsub_rn(pv, cL.x) : CUDART_INF_F;
-        dR = R < n ? __fsub_rn(cR.x, pv) : CUDART_INF_F;
-    }
-    __device__ __forceinline__ float next_axis() const { return fminf(dL, dR); }
-    // visit the nearer side's candidate (branch free); returns its Chebyshev distance
-    __device__ __forceinline__ float step() {
-        const bool right = dR < dL;
-        const float da = right ? dR : dL;
-        const float oj = right ? cR.y : cL.y;
-        const float d = fmaxf(da, fabsf(__fsub_rn(ov, oj)));
-        const int np = right ? R + 1 : L - 1;
-        const bool inb = right ? np < n : np >= 0;
-        const float2 c = W[inb ? np : (right ? R : L)];
-        const float nd = !inb ? CUDART_INF_F : (right ? __fsub_rn(c.x, pv) : __fsub_rn(pv, c.x));
-        if (right) {
-            R = np;
-            dR = nd;
-            cR = c;
-        } else {
-            L = np;
-            dL = nd;
-            cL = c;
-        }
-        return d;
-    }
-};
+// sentinel entries on each side of a staged sorted array: the first walk
+// step reads up to ceil(KMAX/2) positions out, a later step two more
+__host__ __device__ constexpr int ksg_pad(int kmax) { return (kmax + 1) / 2 + 2; }
+
+__host__ __device__ constexpr size_t ksg_slot_bytes(int n_pad, int kmax) {
+    return (size_t)(n_pad + 2 * ksg_pad(kmax)) * 2 * sizeof(float2) +
+           (size_t)n_pad * 2 * sizeof(uint16_t);
+}
 
 // Warp-cooperative staging of one pair into a slot (ends with __syncwarp).
 // sa/pa/va: sorted values, argsort and member values of point p (x);
-// sb/pb/vb: the same for point q (y).
+// sb/pb/vb: the same for point q (y). Both sorted arrays get ksg_pad(KMAX)
+// sentinels per side, -inf on the left and +inf on the right, so that every
+// axis distance to a sentinel is +inf.
+template <int KMAX>
 __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
                                           const float* __restrict__ sa,
                                           const uint16_t* __restrict__ pa,
@@ -104,11 +155,19 @@ __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
                                           const float* __restrict__ sb,
                                           const uint16_t* __restrict__ pb,
                                           const float* __restrict__ vb) {
+    constexpr int pad = ksg_pad(KMAX);
     const int lane = threadIdx.x & 31;
-    float2* XO = reinterpret_cast<float2*>(slot);
-    float2* YO = XO + n_pad;
-    uint16_t* upos = reinterpret_cast<uint16_t*>(YO + n_pad);
+    float2* XO = reinterpret_cast<float2*>(slot) + pad;
+    float2* YO = XO + n_pad + 2 * pad;
+    uint16_t* upos = reinterpret_cast<uint16_t*>(YO + n_pad + pad);
     uint16_t* invq = upos + n_pad;
+    if (lane < pad) {
+        const float2 lo = make_float2(-CUDART_INF_F, 0.f), hi = make_float2(CUDART_INF_F, 0.f);
+        XO[lane - pad] = lo;
+        YO[lane - pad] = lo;
+        XO[n + lane] = hi;
+        YO[n + lane] = hi;
+    }
     for (int m = lane; m < n; m += 32) {
         const int mq = pb[m];
         invq[mq] = (uint16_t)m;
@@ -125,13 +184,28 @@ __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
 
 // One sample (x-sorted position ti) of a staged pair: eps and the two counts;
 // returns psi[n_x] + psi[n_y] from the fixed-point table.
+//
+// The walk runs along one axis (W: that axis's sorted (value, other value)
+// entries), from the sample's position s outwards on both sides at once.
+// L / R are the next unvisited positions on each side. The first k
+// positions (ceil(k/2) left, floor(k/2) right) are visited unconditionally
+// and sorted; every later step offers the next two positions of each side
+// and advances a side past the positions whose axis distance was below the
+// k-th smallest value before the step. A position that is offered but not
+// passed has a Chebyshev distance not below that value, so it cannot change
+// the list (and it is offered again only under the same condition). The
+// walk ends when both next axis distances are not below the k-th smallest
+// value; every position not passed then has a distance not below it, so the
+// list's last entry is eps exactly.
 template <int KMAX>
 __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n, int n_pad, int k,
                                                 int ti, const long long* __restrict__ psi,
                                                 int* cx_out, int* cy_out, float* eps_out) {
-    const float2* XO = reinterpret_cast<const float2*>(slot);
-    const float2* YO = XO + n_pad;
-    const uint16_t* upos = reinterpret_cast<const uint16_t*>(YO + n_pad);
+    constexpr int pad = ksg_pad(KMAX);
+    constexpr int P1 = (KMAX + 1) / 2, NP1 = 2 * P1;
+    const float2* XO = reinterpret_cast<const float2*>(slot) + pad;
+    const float2* YO = XO + n_pad + 2 * pad;
+    const uint16_t* upos = reinterpret_cast<const uint16_t*>(YO + n_pad + pad);
     const float2 zi = XO[ti];
     const int ui = upos[ti];
     // walk along the axis with the wider local spacing
@@ -139,25 +213,47 @@ __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n
     const float span_x = __fsub_rn(XO[min(ti + h, n - 1)].x, XO[max(ti - h, 0)].x);
     const float span_y = __fsub_rn(YO[min(ui + h, n - 1)].x, YO[max(ui - h, 0)].x);
     const bool on_y = span_y > span_x;
+    const float2* W = on_y ? YO : XO;
     const float2* O = on_y ? XO : YO;  // other axis order (sorted in .x)
     const int s = on_y ? ui : ti;
-    KsgWalk w;
-    w.init(on_y ? YO : XO, n, s, on_y ? zi.y : zi.x, on_y ? zi.x : zi.y);
+    const float pv = on_y ? zi.y : zi.x, ov = on_y ? zi.x : zi.y;
+    // the first k positions, alternating left / right; unused slots are -inf
     float top[KMAX];
+    {
+        float c[NP1];
 #pragma unroll
-    for (int m = 0; m < KMAX; ++m)
-        top[m] = m >= KMAX - k ? w.step() : -CUDART_INF_F;  // the k axis-nearest
-    sort_net<KMAX>(top);
-    while (w.next_axis() < top[KMAX - 1]) {
-        const float d = w.step();
-        if (d < top[KMAX - 1]) topk_insert<KMAX>(top, d);
+        for (int t = 0; t < P1; ++t) {
+            const float2 l = W[s - 1 - t], r = W[s + 1 + t];
+            const float dl = fmaxf(__fsub_rn(pv, l.x), fabsf(__fsub_rn(ov, l.y)));
+            const float dr = fmaxf(__fsub_rn(r.x, pv), fabsf(__fsub_rn(ov, r.y)));
+            c[2 * t] = 2 * t < k ? dl : -CUDART_INF_F;
+            c[2 * t + 1] = 2 * t + 1 < k ? dr : -CUDART_INF_F;
+        }
+        sort_small<NP1>(c);
+#pragma unroll
+        for (int m = 0; m < KMAX; ++m) top[m] = c[m + NP1 - KMAX];
+    }
+    int L = s - (k + 1) / 2 - 1, R = s + k / 2 + 1;
+    while (true) {
+        const float2 l0 = W[L], l1 = W[L - 1], r0 = W[R], r1 = W[R + 1];
+        const float al0 = __fsub_rn(pv, l0.x), al1 = __fsub_rn(pv, l1.x);
+        const float ar0 = __fsub_rn(r0.x, pv), ar1 = __fsub_rn(r1.x, pv);
+        const float kth = top[KMAX - 1];
+        if (!(fminf(al0, ar0) < kth)) break;
+        const float d0 = fmaxf(al0, fabsf(__fsub_rn(ov, l0.y)));
+        const float d1 = fmaxf(al1, fabsf(__fsub_rn(ov, l1.y)));
+        const float d2 = fmaxf(ar0, fabsf(__fsub_rn(ov, r0.y)));
+        const float d3 = fmaxf(ar1, fabsf(__fsub_rn(ov, r1.y)));
+        L -= (int)(al0 < kth) + (int)(al1 < kth);
+        R += (int)(ar0 < kth) + (int)(ar1 < kth);
+        topk_merge4<KMAX>(top, d0, d1, d2, d3);
     }
     const float eps = top[KMAX - 1];
-    const float pv = w.pv, ov = w.ov;
-    int L = w.L, R = w.R;
-    // walk axis: trim the visited window (L, R) to axis distance < eps
-    while (L + 1 < s && !(__fsub_rn(pv, w.W[L + 1].x) < eps)) ++L;
-    while (R - 1 > s && !(__fsub_rn(w.W[R - 1].x, pv) < eps)) --R;
+    // walk axis: the passed window (L, R), trimmed to axis distance < eps
+    L = max(L, -1);
+    R = min(R, n);
+    while (L + 1 < s && !(__fsub_rn(pv, W[L + 1].x) < eps)) ++L;
+    while (R - 1 > s && !(__fsub_rn(W[R - 1].x, pv) < eps)) --R;
     const int c_walk = eps > 0.f ? R - L - 1 : 1;
     // other axis: [a, b) with a = first j with fl(ov - O[j].x) < eps,
     // b = first j with fl(O[j].x - ov) >= eps
