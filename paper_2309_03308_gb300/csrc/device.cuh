@@ -17,6 +17,32 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
+// Knuth's TwoSum: s = fl(a + b) and the exact rounding error e (a + b = s + e)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// float-float accumulation (ah, al) += (bh, bl): TwoSum of the leading parts,
+// low parts added, renormalised so |al| <= ulp(ah) / 2. Symmetric in its
+// operands, so a butterfly reduction leaves every lane with the same value.
+__device__ __forceinline__ void ff_add(float& ah, float& al, float bh, float bl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    two_sum(s, e, ah, al);
+}
+
+__device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        ff_add(h, l, oh, ol);
+    }
+}
+
 __device__ __forceinline__ long long warp_sum_i64(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -180,12 +180,6 @@ __global__ void k_compact(const float* __restrict__ v, int64_t N, float sign,
 // addresses cm[chunk][row] = i, i.e. chunk = i / na_pad, row = i % na_pad.
 // One warp per chunk: the warp holds row a's member vector (n <= 1024) in
 // registers and evaluates its 32 pairs (a, 32 * chunk + j).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
 __device__ __forceinline__ float dot2_warp(const float (&x)[32], const float* __restrict__ y,
                                            int n) {
     const int lane = threadIdx.x & 31;

@@ -49,8 +49,13 @@ cudaError_t launch_ingest(const float* in, int n, int64_t P, int n_pad, float* v
 // ----------------------------------------------------------------------------
 // One warp per grid point, member vector in registers in blocked layout
 // (lane l holds members l*E .. l*E+E-1, E = n_pad / 32):
-//   mean, ss      FP64 (sum, then sum of squared deviations about the mean)
-//   zhat          (v - mean) / sqrt(ss) rounded to fp32 (0 when ss == 0)
+//   mean, ss      sum, then sum of squared deviations about the mean, each
+//                 accumulated in float-float (TwoSum / exact FMA products, ~2^-44
+//                 relative) and finalised in FP64 (the per-point FP64 work is a
+//                 few instructions: this GPU's FP64 rate is a small fraction of
+//                 its FP32 rate)
+//   zhat          (v - mean) / sqrt(ss) rounded to fp32 (0 when ss == 0); the
+//                 FP64 reciprocal square root is shared with rhat's
 //   sorted, perm  ascending order, stable: a warp bitonic sort of the unique
 //                 64-bit keys (order-preserving bits of v + 0.0f, member index),
 //                 so -0.0 and +0.0 tie and equal values keep member order
@@ -68,9 +73,23 @@ __device__ __forceinline__ float unorder_bits(unsigned o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
+__device__ __forceinline__ float warp_max_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// power of two s with m * s in [1, 2) for finite m > 0 (1 for m == 0)
+__device__ __forceinline__ float pow2_scale(float m) {
+    if (!(m > 0.f)) return 1.f;
+    int ex;
+    frexpf(m, &ex);  // m = f * 2^ex, f in [0.5, 1)
+    return ldexpf(1.f, 1 - ex);
+}
+
 template <int E>
 __global__ void __launch_bounds__(kPrepWarps * 32)
-    k_point_prep(const float* __restrict__ vals, int64_t P, int n, double inv_n,
+    k_point_prep(const float* __restrict__ vals, int64_t P, int n, float nf,
                  float* __restrict__ sorted,
                  uint16_t* __restrict__ perm, int16_t* __restrict__ rank2,
                  float* __restrict__ zhat, float* __restrict__ rhat,
@@ -83,38 +102,60 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
     const int g0 = lane * E;
 
     unsigned long long key[E];
-    double s = 0.0;
+    float dev[E];  // v - mean rounded to fp32, times 2^-ed; scaled to z below
+    float ss_h = 0.f, ss_l = 0.f;
+    float mean_h, mean_l, vscale, dscale;
     {
         float v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = vals[row + g0 + e];
 #pragma unroll
         for (int e = 0; e < E; ++e)
-            if (g0 + e < n) s += (double)v[e];
-        const double mean = warp_sum_f64(s) * inv_n;
-        double q = 0.0;
-        float dev[E];  // v - mean, centred in FP64, then rounded to fp32
+            key[e] = g0 + e < n ? ((unsigned long long)order_bits(v[e]) << 32) | (unsigned)(g0 + e)
+                                : (0xffffffffull << 32) | (unsigned)(g0 + e);
+        // exact power-of-two scaling to max |v| in [1, 2): the float-float
+        // sums below neither overflow nor lose their low parts to underflow
+        float mv = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (g0 + e < n) mv = fmaxf(mv, fabsf(v[e]));
+        vscale = pow2_scale(warp_max_f32(mv));
+        // sum in float-float (error-free transformations; ~2^-44 relative)
+        float sh = 0.f, sl = 0.f;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const double d = (double)v[e] - mean;
-            dev[e] = (float)d;
-            if (g0 + e < n) q = fma(d, d, q);
+            v[e] *= vscale;
+            if (g0 + e < n) ff_add(sh, sl, v[e], 0.f);
         }
-        const double ss = warp_sum_f64(q);
-        // one FP64 reciprocal square root per point; the per-member scaling
-        // is an fp32 multiply (relative error <= 3 fp32 roundings)
-        const float inv = ss > 0.0 ? (float)rsqrt(ss) : 0.f;
+        warp_sum_ff(sh, sl);
+        // mean = (sh + sl) / n as mean_h + mean_l: the remainder of a rounded
+        // quotient is exact under FMA
+        mean_h = __fdiv_rn(sh, nf);
+        const float rem = __fadd_rn(fmaf(-mean_h, nf, sh), sl);
+        mean_l = __fdiv_rn(rem, nf);
+        // deviations dh + dl = v - mean (TwoSum; dh is v - mean rounded)
+        float dl[E], md = 0.f;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const int g = g0 + e;
-            zhat[row + g] = g < n ? dev[e] * inv : 0.f;
-            key[e] = g < n ? ((unsigned long long)order_bits(v[e]) << 32) | (unsigned)g
-                           : (0xffffffffull << 32) | (unsigned)g;
+            float a, ea;
+            two_sum(v[e], -mean_h, a, ea);
+            two_sum(a, __fsub_rn(ea, mean_l), dev[e], dl[e]);
+            if (g0 + e < n) md = fmaxf(md, fabsf(dev[e]));
         }
-        if (lane == 0) {
-            mean_out[p] = mean;
-            ss_out[p] = ss;
+        // second exact scaling, max |dh| in [1, 2), then the sum of squares
+        // in float-float (exact products, the dl term to first order)
+        dscale = pow2_scale(warp_max_f32(md));
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float dh = dev[e] * dscale, dle = dl[e] * dscale;
+            dev[e] = dh;
+            if (g0 + e < n) {
+                const float p = __fmul_rn(dh, dh);
+                const float pe = fmaf(dh, dh, -p) + 2.f * dh * dle;
+                ff_add(ss_h, ss_l, p, pe);
+            }
         }
+        warp_sum_ff(ss_h, ss_l);
     }
 
     // bitonic sort, ascending, over NP keys
@@ -199,7 +240,23 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
         }
     }
     c2 = warp_sum_i64(c2);
-    const float rinv = c2 > 0 ? (float)rsqrt((double)c2) : 0.f;
+    // FP64 finalisation, one instruction stream for both norms: lane 0 the
+    // sum of squared deviations, lane 1 the sum of squared centred ranks
+    const double ss_s = (double)ss_h + (double)ss_l;  // in units of (vscale dscale)^2
+    const double x = lane == 0 ? ss_s : (double)c2;
+    const double r = x > 0.0 ? rsqrt(x) : 0.0;
+    const float inv = (float)__shfl_sync(0xffffffffu, r, 0);
+    const float rinv = (float)__shfl_sync(0xffffffffu, r, 1);
+    if (lane == 0) {  // undo the power-of-two scalings (exact)
+        const double s2 = (double)vscale * (double)dscale;
+        mean_out[p] = ((double)mean_h + (double)mean_l) / (double)vscale;
+        ss_out[p] = ss_s / (s2 * s2);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int g = g0 + e;
+        zhat[row + g] = g < n ? dev[e] * inv : 0.f;  // fp32 scale (<= 3 roundings)
+    }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int g = g0 + e;
@@ -219,7 +276,7 @@ cudaError_t launch_point_prep(const Field& f, cudaStream_t st) {
     note_launch();
 #define CC_PREP(E)                                                                               \
     k_point_prep<E><<<blocks, kPrepWarps * 32, 0, st>>>(                                         \
-        f.vals.as<float>(), f.P, f.n, 1.0 / f.n, f.sorted.as<float>(), f.perm.as<uint16_t>(),   \
+        f.vals.as<float>(), f.P, f.n, (float)f.n, f.sorted.as<float>(), f.perm.as<uint16_t>(),   \
         f.rank2.as<int16_t>(), f.zhat.as<float>(), f.rhat.as<float>(), f.mean.as<double>(),      \
         f.ss.as<double>())
     switch (f.n_pad / 32) {  // n_pad is a power of two >= 32

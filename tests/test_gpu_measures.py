@@ -76,6 +76,24 @@ def test_planes_with_ties(cc, orc):
     assert np.all(z == 0)
 
 
+@pytest.mark.parametrize("offset,scale", [(0.0, 1.0), (1e4, 1e-2), (-3e5, 7.0), (1e-30, 1e-33)])
+def test_zhat_standardisation_accuracy(cc, offset, scale):
+    """The unit-norm centred member vectors are within a few fp32 roundings of
+    (v - mean) / sqrt(sum (v - mean)^2) evaluated in FP64, also when the mean
+    is large against the spread (cancellation in the centring)."""
+    rng = np.random.default_rng(11)
+    for n in (32, 100, 1000):
+        F = (offset + scale * rng.standard_normal((n, 2, 3, 4))).astype(np.float32)
+        fid = cc.load_field(F)
+        pts = np.arange(24, dtype=np.uint32)
+        z = cc.get_plane(fid, 3, pts, n).astype(np.float64)
+        V = F.reshape(n, -1).T.astype(np.float64)
+        d = V - V.mean(axis=1, keepdims=True)
+        ref = d / np.sqrt((d * d).sum(axis=1, keepdims=True))
+        assert np.abs(z - ref).max() < 4 * 2.0 ** -24 * np.abs(ref).max(), (n, offset)
+        cc.free_field(fid)
+
+
 # ---------------------------------------------------------------- small config, all pairs
 @pytest.mark.parametrize("kind,kw", [(oracle.PEARSON, {}), (oracle.SPEARMAN, {}),
                                      (oracle.MI_BINNED, {"bins": 8}), (oracle.MI_KSG, {"k": 3})],
