@@ -85,6 +85,8 @@ struct BosDev {
     const long long* psi_fix;
     const long long* clogc_fix;
     double psi_nk;
+    double fix_over_n;  // 1 / (2^40 n): fixed-point sum -> mean
+    double logn;
 };
 
 __device__ __forceinline__ unsigned okey32(float v) {
@@ -348,19 +350,28 @@ __global__ void k_bos_eval(BosDev d, int warps_per_block) {
             for (int ti = lane; ti < n; ti += 32)
                 acc += ksg_sample<KMAX>(wbase, n, n_pad, d.k, ti, psi, nullptr, nullptr, nullptr);
             acc = warp_sum_i64(acc);
-            value = (float)(d.psi_nk - ((double)acc / kFixScale) / (double)n);
+            value = (float)(d.psi_nk - (double)acc * d.fix_over_n);
         } else if (measure == CC_MI_BINNED) {
             const uint8_t* ba = d.bins_p + ra;
             const uint8_t* bb = d.bins_p + rb;
-            for (int m = lane; m < n; m += 32) atomicAdd(&hist[ba[m] * B + bb[m]], 1);
+            // the member whose increment finds its cell empty owns the cell:
+            // it adds the cell's c ln c once the counts are complete and clears it
+            unsigned own = 0;  // bit j: member lane + 32 j (n <= 1024)
+            for (int m = lane, j = 0; m < n; m += 32, ++j)
+                if (atomicAdd(&hist[ba[m] * B + bb[m]], 1) == 0) own |= 1u << j;
             __syncwarp();
             long long s = 0;
-            for (int c = lane; c < B * B; c += 32) {
-                s += clogc[hist[c]];
-                hist[c] = 0;
+            for (unsigned o = own; o; o &= o - 1) {
+                const int m = lane + 32 * (__ffs(o) - 1);
+                s += clogc[hist[ba[m] * B + bb[m]]];
+            }
+            __syncwarp();
+            for (unsigned o = own; o; o &= o - 1) {
+                const int m = lane + 32 * (__ffs(o) - 1);
+                hist[ba[m] * B + bb[m]] = 0;
             }
             s = warp_sum_i64(s);
-            value = (float)(log((double)n) + ((double)(s - d.hmarg[p] - d.hmarg[q]) / kFixScale) / n);
+            value = (float)(d.logn + (double)(s - d.hmarg[p] - d.hmarg[q]) * d.fix_over_n);
         } else {
             const float* A = (measure == CC_SPEARMAN ? d.rhat : d.zhat) + ra;
             const float* Bp = (measure == CC_SPEARMAN ? d.rhat : d.zhat) + rb;
@@ -926,6 +937,8 @@ cc_status cc_bos_run(cc_ctx* ctx, cc_bos* b, int rounds, int use_graph) {
         b->d.psi_fix = (const long long*)ctx->psi_fix[f.n]->as<int64_t>();
         b->d.clogc_fix = (const long long*)ctx->clogc_fix[f.n]->as<int64_t>();
         b->d.psi_nk = digamma_int_host(f.n) + digamma_int_host(b->d.k);
+        b->d.fix_over_n = 1.0 / (kFixScale * f.n);
+        b->d.logn = std::log((double)f.n);
         b->field_version = f.version;
     }
     cudaStream_t st = ctx->stream;

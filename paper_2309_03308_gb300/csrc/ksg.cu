@@ -54,8 +54,9 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
                 const float* __restrict__ vals_a, int64_t Pa, const float* __restrict__ sorted_b,
                 const uint16_t* __restrict__ perm_b, const float* __restrict__ vals_b, int64_t Pb,
                 int n, int n_pad, int k, int G, const long long* __restrict__ psi_fix,
-                double psi_nk, const uint32_t* __restrict__ pa, const uint32_t* __restrict__ pb,
-                int64_t N, float* __restrict__ out, int32_t* __restrict__ nx_out,
+                double psi_nk, double fix_over_n, const uint32_t* __restrict__ pa,
+                const uint32_t* __restrict__ pb, int64_t N, float* __restrict__ out,
+                int32_t* __restrict__ nx_out,
                 int32_t* __restrict__ ny_out, float* __restrict__ eps_out, int* status) {
     extern __shared__ __align__(16) unsigned char ksg_smem[];
     long long* psi = reinterpret_cast<long long*>(ksg_smem);
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
             if (u < gc) {
                 const long long sum = warp_sum_i64(acc[u]);
                 if (lane == 0 && ((valid >> u) & 1u))
-                    out[t0 + u] = (float)(psi_nk - ((double)sum / kFixScale) / (double)n);
+                    out[t0 + u] = (float)(psi_nk - (double)sum * fix_over_n);
             }
         }
         __syncwarp();
@@ -148,7 +149,8 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
     k_ksg_pairs<KMAX><<<(unsigned)blocks, kKsgWarps * 32, smem, st>>>(
         fa.sorted.as<float>(), fa.perm.as<uint16_t>(), fa.vals.as<float>(), fa.P,
         fb.sorted.as<float>(), fb.perm.as<uint16_t>(), fb.vals.as<float>(), fb.P, fa.n, fa.n_pad,
-        k, G, (const long long*)psi_fix, psi_nk, pa, pb, N, out, nx, ny, eps, status);
+        k, G, (const long long*)psi_fix, psi_nk, 1.0 / (kFixScale * fa.n), pa, pb, N, out, nx, ny,
+        eps, status);
     return cudaGetLastError();
 }
 

@@ -79,23 +79,27 @@ cudaError_t launch_pearson_pairs(const float* plane_a, int64_t Pa, const float* 
 //   MI = ln n + (1/n) [sum c_xy ln c_xy - sum c_x ln c_x - sum c_y ln c_y].
 // The marginal sums are precomputed per point; c ln c comes from a
 // fixed-point table so the sum is exact and order independent.
-// One warp per pair; the B x B histogram lives in shared memory.
+// One warp per pair; the B x B histogram lives in shared memory. Each lane
+// reads four members' bins as one 32-bit word per side; the sample whose
+// atomic increment found its cell empty owns the cell and, once the counts
+// are complete, adds that cell's c ln c and clears it, so every occupied cell
+// is summed once and no sweep over the B^2 cells is needed.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_hist_pairs(const uint8_t* __restrict__ bins_a, const long long* __restrict__ hm_a,
                  int64_t Pa, const uint8_t* __restrict__ bins_b,
                  const long long* __restrict__ hm_b, int64_t Pb, int n, int n_pad, int B,
-                 const long long* __restrict__ clogc_fix, const uint32_t* __restrict__ pa,
-                 const uint32_t* __restrict__ pb, int64_t N, float* __restrict__ out,
-                 int* status) {
+                 const long long* __restrict__ clogc_fix, double logn, double fix_over_n,
+                 const uint32_t* __restrict__ pa, const uint32_t* __restrict__ pb, int64_t N,
+                 float* __restrict__ out, int* status) {
     __shared__ int hist[kWarpsPerBlock][256];
+    extern __shared__ long long clogc[];  // [n + 1]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* h = hist[warp];
-    const int cells = B * B;
-    const double logn = log((double)n);
+    for (int c = threadIdx.x; c < 256 * kWarpsPerBlock; c += blockDim.x) (&hist[0][0])[c] = 0;
+    for (int c = threadIdx.x; c <= n; c += blockDim.x) clogc[c] = clogc_fix[c];
+    __syncthreads();
     const int64_t w0 = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int c = lane; c < cells; c += 32) h[c] = 0;
-    __syncwarp();
     for (int64_t t = w0; t < N; t += stride) {
         const uint32_t p = pa[t], q = pb[t];
         if (p >= Pa || q >= Pb) {
@@ -105,21 +109,51 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             }
             continue;
         }
-        const uint8_t* ba = bins_a + (int64_t)p * n_pad;
-        const uint8_t* bb = bins_b + (int64_t)q * n_pad;
-        for (int m = lane; m < n; m += 32) atomicAdd(&h[ba[m] * B + bb[m]], 1);
+        const uint32_t* ba = reinterpret_cast<const uint32_t*>(bins_a + (int64_t)p * n_pad);
+        const uint32_t* bb = reinterpret_cast<const uint32_t*>(bins_b + (int64_t)q * n_pad);
+        // n <= 1024: at most 8 chunks of 128 members, 4 per lane each; the
+        // first chunk's words stay in registers, later ones are re-read (L1)
+        uint32_t wa0 = 0, wb0 = 0;
+        if (4 * lane < n) {
+            wa0 = __ldg(ba + lane);
+            wb0 = __ldg(bb + lane);
+        }
+        auto cell_of = [&](int c, int j) {
+            const int w = (c * 128 >> 2) + lane;
+            const uint32_t wa = c ? __ldg(ba + w) : wa0, wb = c ? __ldg(bb + w) : wb0;
+            return (int)((wa >> (8 * j)) & 0xffu) * B + (int)((wb >> (8 * j)) & 0xffu);
+        };
+        unsigned own = 0;  // bit 4c + j: this lane's member 128c + 4 lane + j owns its cell
+        for (int c = 0; c * 128 < n; ++c) {
+            const int m = c * 128 + 4 * lane;
+            if (m < n) {
+                const uint32_t wa = c ? __ldg(ba + (m >> 2)) : wa0;
+                const uint32_t wb = c ? __ldg(bb + (m >> 2)) : wb0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int cell =
+                        (int)((wa >> (8 * j)) & 0xffu) * B + (int)((wb >> (8 * j)) & 0xffu);
+                    if (m + j < n && atomicAdd(&h[cell], 1) == 0) own |= 1u << (4 * c + j);
+                }
+            }
+        }
         __syncwarp();
         long long s = 0;
-        for (int c = lane; c < cells; c += 32) {
-            s += clogc_fix[h[c]];
-            h[c] = 0;
+        for (unsigned o = own; o; o &= o - 1) {
+            const int bit = __ffs(o) - 1;
+            s += clogc[h[cell_of(bit >> 2, bit & 3)]];
         }
+        __syncwarp();
+        for (unsigned o = own; o; o &= o - 1) {
+            const int bit = __ffs(o) - 1;
+            h[cell_of(bit >> 2, bit & 3)] = 0;
+        }
+        __syncwarp();
         s = warp_sum_i64(s);
         if (lane == 0) {
             const long long d = s - hm_a[p] - hm_b[q];
-            out[t] = (float)(logn + ((double)d / kFixScale) / (double)n);
+            out[t] = (float)(logn + (double)d * fix_over_n);
         }
-        __syncwarp();
     }
 }
 
@@ -131,9 +165,10 @@ cudaError_t launch_hist_pairs(const uint8_t* bins_a, const int64_t* hm_a, int64_
     if (N <= 0) return cudaSuccess;
     const unsigned g = pair_grid(N, kWarpsPerBlock);
     note_launch();
-    k_hist_pairs<<<g, kWarpsPerBlock * 32, 0, st>>>(
+    k_hist_pairs<<<g, kWarpsPerBlock * 32, (n + 1) * sizeof(long long), st>>>(
         bins_a, (const long long*)hm_a, Pa, bins_b, (const long long*)hm_b, Pb, n, n_pad, B,
-        (const long long*)clogc_fix, pa, pb, N, out, status);
+        (const long long*)clogc_fix, std::log((double)n), 1.0 / (kFixScale * n), pa, pb, N, out,
+        status);
     return cudaGetLastError();
 }
 

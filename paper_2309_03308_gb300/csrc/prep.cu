@@ -79,12 +79,12 @@ __device__ __forceinline__ float warp_max_f32(float v) {
     return v;
 }
 
-// power of two s with m * s in [1, 2) for finite m > 0 (1 for m == 0)
+// power of two s with m * s in [1, 2) for finite normal m > 0 (1 for m == 0)
 __device__ __forceinline__ float pow2_scale(float m) {
     if (!(m > 0.f)) return 1.f;
     int ex;
     frexpf(m, &ex);  // m = f * 2^ex, f in [0.5, 1)
-    return ldexpf(1.f, 1 - ex);
+    return ldexpf(1.f, min(1 - ex, 126));  // below 2^-126 (subnormal m): 2^126
 }
 
 template <int E>
@@ -247,10 +247,10 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
     const double r = x > 0.0 ? rsqrt(x) : 0.0;
     const float inv = (float)__shfl_sync(0xffffffffu, r, 0);
     const float rinv = (float)__shfl_sync(0xffffffffu, r, 1);
-    if (lane == 0) {  // undo the power-of-two scalings (exact)
-        const double s2 = (double)vscale * (double)dscale;
-        mean_out[p] = ((double)mean_h + (double)mean_l) / (double)vscale;
-        ss_out[p] = ss_s / (s2 * s2);
+    if (lane == 0) {  // undo the power-of-two scalings (exact reciprocals)
+        const double rv = (double)__frcp_rn(vscale), rs = rv * (double)__frcp_rn(dscale);
+        mean_out[p] = ((double)mean_h + (double)mean_l) * rv;
+        ss_out[p] = ss_s * (rs * rs);
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
