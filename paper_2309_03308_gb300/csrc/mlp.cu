@@ -55,27 +55,36 @@ __device__ __forceinline__ float gelu_grad(float x) {
            x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-// ---------------------------------------------------------------------------
-// C[m][n] (+)= sum_k A(m, k) B(k, n); A(m, k) = A[m * sam + k * sak],
-// B(k, n) = B[k * sbk + n * sbn]; C row stride ldc. 64 x 64 tiles, 256
-// threads with 4 x 4 outputs, K staged 16 at a time through shared memory.
+// Generic strided GEMM C (+)= A B with A[m][k] = A[m * sam + k * sak] and
+// B[k][n] = B[k * sbk + n * sbn] (fp32 or bf16 inputs, fp32 accumulation).
+// 64 x 64 output tile per CTA, 256 threads with 4 x 4 outputs, K staged 16 at
+// a time through shared memory; each operand tile is read along its
+// unit-stride dimension. Split-K over gridDim.z: slice z covers k in
+// [z kc, (z + 1) kc) and writes a dense partial [M][N] that k_mm_reduce sums
+// in slice order (deterministic), so the weight gradients (M x N small, K =
+// the batch) still fill the GPU.
 template <class TA, class TB>
 __global__ void __launch_bounds__(256)
     k_mm(const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
          int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc, int M, int N, int K,
-         int accumulate) {
+         int kc, int accumulate, float* __restrict__ part) {
     __shared__ float As[16][64 + 1];
     __shared__ float Bs[16][64 + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    const bool a_k = sak == 1, b_k = sbk == 1;
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = kb; k0 < ke; k0 += 16) {
         for (int e = tid; e < 16 * 64; e += 256) {
-            const int kk = e / 64, mm = e % 64;
+            const int kk = a_k ? (e & 15) : (e >> 6), mm = a_k ? (e >> 4) : (e & 63);
             const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? ld(A + m * sam + k * sak) : 0.f;
-            const int n = n0 + mm;
-            Bs[kk][mm] = (n < N && k < K) ? ld(B + k * sbk + n * sbn) : 0.f;
+            As[kk][mm] = (m < M && k < ke) ? ld(A + m * sam + k * sak) : 0.f;
+        }
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int kk = b_k ? (e & 15) : (e >> 6), nn = b_k ? (e >> 4) : (e & 63);
+            const int n = n0 + nn, k = k0 + kk;
+            Bs[kk][nn] = (n < N && k < ke) ? ld(B + k * sbk + n * sbn) : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -100,18 +109,50 @@ __global__ void __launch_bounds__(256)
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tx + 16 * j;
             if (n >= N) continue;
-            float* c = C + (int64_t)m * ldc + n;
-            *c = accumulate ? *c + acc[i][j] : acc[i][j];
+            if (part) {
+                part[((int64_t)blockIdx.z * M + m) * N + n] = acc[i][j];
+            } else {
+                float* c = C + (int64_t)m * ldc + n;
+                *c = accumulate ? *c + acc[i][j] : acc[i][j];
+            }
         }
+    }
+}
+
+__global__ void k_mm_reduce(const float* __restrict__ part, int S, int M, int N,
+                            float* __restrict__ C, int64_t ldc, int accumulate) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)M * N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < S; ++z) s += part[(int64_t)z * M * N + e];
+        float* c = C + (e / N) * ldc + e % N;
+        *c = accumulate ? *c + s : s;
     }
 }
 
 template <class TA, class TB>
 static cudaError_t mm(const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk, int64_t sbn,
-                      float* C, int64_t ldc, int M, int N, int K, int acc, cudaStream_t st) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
+                      float* C, int64_t ldc, int M, int N, int K, int acc, cudaStream_t st,
+                      DevMem* ws = nullptr) {
+    const int gx = (N + 63) / 64, gy = (M + 63) / 64;
+    // split K when the output tiles alone would leave most SMs idle
+    int S = 1, kc = ((K + 15) / 16) * 16;
+    if (ws && gx * gy < 152 && K >= 512) {
+        S = std::min((2 * 152 + gx * gy - 1) / (gx * gy), K / 128);
+        kc = ((K + S - 1) / S + 15) / 16 * 16;
+        S = (K + kc - 1) / kc;
+        cudaError_t e = ws->ensure(sizeof(float) * (size_t)S * M * N);
+        if (e != cudaSuccess) return e;
+    }
     note_launch();
-    k_mm<TA, TB><<<grid, 256, 0, st>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, acc);
+    k_mm<TA, TB><<<dim3(gx, gy, S), 256, 0, st>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kc,
+                                                  acc, S > 1 ? ws->as<float>() : nullptr);
+    if (S > 1) {
+        note_launch();
+        const int64_t MN = (int64_t)M * N;
+        k_mm_reduce<<<(unsigned)std::min<int64_t>((MN + 255) / 256, 1024), 256, 0, st>>>(
+            ws->as<float>(), S, M, N, C, ldc, acc);
+    }
     return cudaGetLastError();
 }
 
@@ -391,6 +432,7 @@ struct cc_sur {
     int64_t cap = 0;
     DevMem pts, tb, X0, A1, H1, Ef, E, X3, A3, H3, y, dy, dA3, dX3, dE, dH1, dA1, loss;
     DevMem order;
+    DevMem ws;  // split-K partials of the weight-gradient GEMMs
 };
 
 namespace {
@@ -491,14 +533,15 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
     const bf16* wb = s->wb.as<bf16>();
     float* g = s->g.as<float>();
     // head output layer
-    SK(mm(s->H3.as<bf16>(), 1, kH3, s->dy.as<float>(), 1, 0, g + o.w4, 1, kH3, 1, (int)B, 0, st));
+    SK(mm(s->H3.as<bf16>(), 1, kH3, s->dy.as<float>(), 1, 0, g + o.w4, 1, kH3, 1, (int)B, 0, st,
+          &s->ws));
     note_launch(5);
     k_sur_colsum<<<1, 256, 0, st>>>(s->dy.as<float>(), B, 1, g + o.b4);
     k_sur_gelu_bwd<<<grid1(B * kH3), 256, 0, st>>>(s->A3.as<float>(), s->dy.as<float>(),
                                                    s->w.as<float>() + o.w4, nullptr, B, kH3,
                                                    s->dA3.as<float>());
     SK(mm(s->dA3.as<float>(), 1, kH3, s->X3.as<bf16>(), kHeadIn, 1, g + o.W3, kHeadIn, kH3, kHeadIn,
-          (int)B, 0, st));
+          (int)B, 0, st, &s->ws));
     k_sur_colsum<<<kH3, 256, 0, st>>>(s->dA3.as<float>(), B, kH3, g + o.b3);
     SK(mm(s->dA3.as<float>(), kH3, 1, wb + o.W3, kHeadIn, 1, s->dX3.as<float>(), kHeadIn, (int)B,
           kHeadIn, kH3, 0, st));
@@ -506,7 +549,7 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
                                                s->dE.as<float>());
     // encoder
     SK(mm(s->dE.as<float>(), 1, kE, s->H1.as<bf16>(), kH1, 1, g + o.W2, kH1, kE, kH1, (int)(2 * B),
-          0, st));
+          0, st, &s->ws));
     note_launch(3);
     k_sur_colsum<<<kE, 256, 0, st>>>(s->dE.as<float>(), 2 * B, kE, g + o.b2);
     SK(mm(s->dE.as<float>(), kE, 1, wb + o.W2, kH1, 1, s->dH1.as<float>(), kH1, (int)(2 * B), kH1,
@@ -515,7 +558,7 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
                                                        s->dH1.as<float>(), 2 * B, kH1,
                                                        s->dA1.as<float>());
     SK(mm(s->dA1.as<float>(), 1, kH1, s->X0.as<bf16>(), n, 1, g + o.W1, n, kH1, n, (int)(2 * B), 0,
-          st));
+          st, &s->ws));
     k_sur_colsum<<<kH1, 256, 0, st>>>(s->dA1.as<float>(), 2 * B, kH1, g + o.b1);
     SK(cudaGetLastError());
     return CC_OK;
