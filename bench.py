@@ -4,7 +4,8 @@ Headline workload (focus refinement at paper scale): a 352x256x20 ensemble
 with n = 100 members (seeded synthetic stand-in for the paper's weather
 ensemble) and two 32x32x20 regions (20,480 points each). One step runs every
 built stage of the path on the resident field:
-  ingest      per-point planes (FP64 stats, z-scores, ranks, sorted values)
+  ingest      per-point planes (float-float stats finalised in FP64, z-scores,
+              ranks, sorted values)
   fp32 x2     all 419,430,400 cross pairs, Pearson and Spearman, FP32 SIMT,
               every value stored, extremes fused
   bf16, fp8   the same Pearson pairs on the tensor cores, certified exact
