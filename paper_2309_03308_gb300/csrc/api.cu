@@ -649,6 +649,11 @@ cc_status cc_all_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, const cc
 namespace {
 
 // Reduced-precision plane of a region (rows padded to 256, K to 128 bytes).
+// BF16 Spearman with n <= 257 contracts the integer centred ranks exactly
+// (see k_quantize_ranks); the approximate values then differ from the exact
+// ones only by the epilogue's two fp32 scalings.
+bool rank_exact(bool sp, bool fp8, int n) { return sp && !fp8 && n <= 257; }
+
 cc_status ensure_qplane(cc_ctx* ctx, Region& r, bool sp, bool fp8, Region::QPlane** out) {
     Field& f = *ctx->fields[r.field];
     auto& slot = r.qplanes[(sp ? 2 : 0) + (fp8 ? 1 : 0)];
@@ -664,9 +669,14 @@ cc_status ensure_qplane(cc_ctx* ctx, Region& r, bool sp, bool fp8, Region::QPlan
         CK(qp.emax.alloc(sizeof(unsigned)));
     }
     CK(cudaMemsetAsync(qp.emax.p, 0, sizeof(unsigned), ctx->stream));
-    CK(launch_quantize(fp8, sp ? f.rhat.as<float>() : f.zhat.as<float>(), f.n_pad, f.n,
-                       r.pts.as<uint32_t>(), r.np, qp.rows_pad, qp.kbytes, qp.q.p,
-                       qp.inv.as<float>(), qp.emax.as<unsigned>(), ctx->stream));
+    if (rank_exact(sp, fp8, f.n))  // integer ranks: exact operands, e_p = 0
+        CK(launch_quantize_ranks(f.rank2.as<int16_t>(), f.n_pad, f.n, r.pts.as<uint32_t>(), r.np,
+                                 qp.rows_pad, qp.kbytes, qp.q.p, qp.inv.as<float>(),
+                                 ctx->stream));
+    else
+        CK(launch_quantize(fp8, sp ? f.rhat.as<float>() : f.zhat.as<float>(), f.n_pad, f.n,
+                           r.pts.as<uint32_t>(), r.np, qp.rows_pad, qp.kbytes, qp.q.p,
+                           qp.inv.as<float>(), qp.emax.as<unsigned>(), ctx->stream));
     unsigned bits = 0;
     CK(cudaMemcpyAsync(&bits, qp.emax.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -741,7 +751,9 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
     unsigned long long* tids = (unsigned long long*)(base + o_ti);
     cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(hist, 0, 4 * 4096, st));
-    CK(launch_tc_chunk_extremes(fp8, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad, qa->kbytes, self,
+    const bool exact = rank_exact(sp, fp8, fa.n);
+    CK(launch_tc_chunk_extremes(fp8, fp8 || exact, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad,
+                                qa->kbytes, self,
                                 qa->inv.as<float>(), qb->inv.as<float>(), cmax, cmin,
                                 ctx->status.as<int>(), st));
     const float emax = std::max(qa->emax_host, qb->emax_host);
@@ -763,7 +775,11 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
                                 sign, rvals, rpids, best, st));
         Select h1;
         CK(cudaMemcpyAsync(&h1, sel, sizeof h1, cudaMemcpyDeviceToHost, st));
-        CK(launch_second_threshold(best, emax, 1.f / 4096.f, thr, thr + 1, st));
+        // relative error of the approximate values beyond the quantization
+        // error: FP32 accumulation (2^-12, conservative), or for exact integer
+        // ranks the two fp32 scalings of the epilogue (2^-22 covers them)
+        CK(launch_second_threshold(best, emax, exact ? 1.f / 4194304.f : 1.f / 4096.f, thr,
+                                   thr + 1, st));
         CK(cudaStreamSynchronize(st));
         const unsigned c1 = std::min(h1.count, cap);
         bool certified = h1.overflow == 0;

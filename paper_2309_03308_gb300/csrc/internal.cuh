@@ -159,13 +159,16 @@ struct Select {
     unsigned count;      // compacted candidates
     unsigned overflow;   // candidates beyond capacity
 };
-cudaError_t launch_tc_chunk_extremes(bool fp8, const void* qa, int64_t na, int64_t na_pad,
-                                     const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
+cudaError_t launch_tc_chunk_extremes(bool fp8, bool scaled, const void* qa, int64_t na,
+                                     int64_t na_pad, const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
                                      int self, const float* inv_sa, const float* inv_sb,
                                      float* cmax, float* cmin, int* status, cudaStream_t st);
 cudaError_t launch_quantize(bool fp8, const float* plane, int n_pad, int n, const uint32_t* pts,
                             int64_t np, int64_t np_pad, int kbytes, void* q, float* inv_scale,
                             unsigned* emax_bits, cudaStream_t st);
+cudaError_t launch_quantize_ranks(const int16_t* rank2, int n_pad, int n, const uint32_t* pts,
+                                  int64_t np, int64_t np_pad, int kbytes, void* q,
+                                  float* inv_scale, cudaStream_t st);
 cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned want,
                               unsigned* hist, Select* sel, uint32_t* out, unsigned cap,
                               cudaStream_t st);

@@ -89,6 +89,37 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// 1b. Spearman, n <= 257: the centred doubled ranks c = rank2 - (n + 1) are
+// integers with |c| <= n - 1 <= 256, exact in BF16, and every partial sum of
+// their products is an integer below 2^24 (sum |c_a c_b| <= sum c^2 <= n^3 / 3),
+// exact in FP32. The operand is c itself with the per-point scale
+// 1 / sqrt(sum c^2) applied in the epilogue, so the contraction has no
+// quantization error (e_p = 0).
+__global__ void __launch_bounds__(256)
+    k_quantize_ranks(const int16_t* __restrict__ rank2, int n_pad, int n,
+                     const uint32_t* __restrict__ pts, int64_t np, int64_t np_pad, int kbytes,
+                     unsigned char* __restrict__ q, float* __restrict__ inv_scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= np_pad) return;
+    unsigned char* qrow = q + r * kbytes;
+    if (r >= np) {
+        for (int b = lane * 4; b < kbytes; b += 128) *reinterpret_cast<uint32_t*>(qrow + b) = 0;
+        if (lane == 0) inv_scale[r] = 0.f;
+        return;
+    }
+    const int16_t* c2 = rank2 + (int64_t)pts[r] * n_pad;
+    long long ss = 0;
+    for (int k = lane * 2; k < kbytes / 2; k += 64) {
+        const int c0 = k < n ? c2[k] - (n + 1) : 0, c1 = k + 1 < n ? c2[k + 1] - (n + 1) : 0;
+        *reinterpret_cast<__nv_bfloat162*>(qrow + 2 * k) =
+            __floats2bfloat162_rn((float)c0, (float)c1);
+        ss += (long long)(c0 * c0 + c1 * c1);
+    }
+    ss = warp_sum_i64(ss);
+    if (lane == 0) inv_scale[r] = ss > 0 ? (float)rsqrt((double)ss) : 0.f;
+}
+
 // ---------------------------------------------------------------------------
 // 3a. two-pass histogram select on order-preserving keys of sign * value.
 // Pass `level` 0 bins the top 12 bits, pass 1 the next 12 among keys whose
@@ -322,6 +353,16 @@ cudaError_t launch_quantize(bool fp8, const float* plane, int n_pad, int n, cons
     else
         k_quantize<false><<<blocks, 256, 0, st>>>(plane, n_pad, n, pts, np, np_pad, kbytes,
                                                   (unsigned char*)q, inv_scale, emax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_ranks(const int16_t* rank2, int n_pad, int n, const uint32_t* pts,
+                                  int64_t np, int64_t np_pad, int kbytes, void* q,
+                                  float* inv_scale, cudaStream_t st) {
+    if (n > 257) return cudaErrorInvalidValue;
+    note_launch();
+    k_quantize_ranks<<<(unsigned)((np_pad + 7) / 8), 256, 0, st>>>(
+        rank2, n_pad, n, pts, np, np_pad, kbytes, (unsigned char*)q, inv_scale);
     return cudaGetLastError();
 }
 

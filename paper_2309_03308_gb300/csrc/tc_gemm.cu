@@ -9,8 +9,8 @@
 // (M = 128, N = 256, FP32 accumulation in TMEM, two accumulator buffers so the
 // epilogue of one tile overlaps the MMAs of the next). Four epilogue warps
 // read TMEM with tcgen05.ld and emit, per output row and 32-column chunk, the
-// max and min of the approximate correlations (FP8: rescaled by the two
-// per-point inverse scales). No per-pair value is stored: the chunk extremes
+// max and min of the approximate correlations (FP8, and BF16 integer ranks:
+// rescaled by the two per-point inverse scales). No per-pair value is stored: the chunk extremes
 // select the candidates that are re-evaluated exactly afterwards.
 //
 // Warp roles (192 threads, one CTA per SM, persistent over tiles):
@@ -148,7 +148,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <bool FP8>
+template <bool FP8, bool SCALED>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_chunk_extremes(const __grid_constant__ CUtensorMap tma,
                         const __grid_constant__ CUtensorMap tmb, int num_kb, int64_t na,
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
             const int acc = tc & 1;
             const int m0 = (t / tiles_n) * TM, n0 = (t % tiles_n) * TN;
-            if (FP8) {
+            if (SCALED) {
                 for (int c = et; c < TN; c += 128)
                     colscale[c] = n0 + c < nb ? inv_sb[n0 + c] : 0.f;
                 asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_after();
             const int64_t row = m0 + 32 * q + lane;
             const bool row_ok = row < na;
-            const float rs = FP8 ? (row_ok ? inv_sa[row] : 0.f) : 1.f;
+            const float rs = SCALED ? (row_ok ? inv_sa[row] : 0.f) : 1.f;
 #pragma unroll 1
             for (int c = 0; c < TN / 32; ++c) {
                 float v[32];
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int64_t col = col0 + j;
-                    const float val = FP8 ? v[j] * rs * colscale[c * 32 + j] : v[j];
+                    const float val = SCALED ? v[j] * rs * colscale[c * 32 + j] : v[j];
                     const bool ok = row_ok && col < nb && (!self || col > row);
                     mx = ok ? fmaxf(mx, val) : mx;
                     mn = ok ? fminf(mn, val) : mn;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
-            if (FP8) asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (SCALED) asm volatile("bar.sync 1, 128;" ::: "memory");
         }
     }
     tc_fence_before();
@@ -345,7 +345,7 @@ static cudaError_t make_map(CUtensorMap* m, const void* base, bool fp8, int64_t 
 
 // qa: [na_pad][kbytes] operand A (rows padded to 256), qb likewise; kbytes a
 // multiple of 128. Writes cmax/cmin [nb_pad/32][na_pad].
-cudaError_t launch_tc_chunk_extremes(bool fp8, const void* qa, int64_t na, int64_t na_pad,
+cudaError_t launch_tc_chunk_extremes(bool fp8, bool scaled, const void* qa, int64_t na, int64_t na_pad,
                                      const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
                                      int self, const float* inv_sa, const float* inv_sb,
                                      float* cmax, float* cmin, int* status, cudaStream_t st) {
@@ -362,7 +362,10 @@ cudaError_t launch_tc_chunk_extremes(bool fp8, const void* qa, int64_t na, int64
     const int tiles = tiles_m * tiles_n;
     const int grid = tiles < sms ? tiles : sms;
     const size_t smem = tc::smem_bytes();
-    auto kern = fp8 ? tc::k_tc_chunk_extremes<true> : tc::k_tc_chunk_extremes<false>;
+    if (fp8 && !scaled) return cudaErrorInvalidValue;  // FP8 operands always carry scales
+    auto kern = fp8      ? tc::k_tc_chunk_extremes<true, true>
+                : scaled ? tc::k_tc_chunk_extremes<false, true>
+                         : tc::k_tc_chunk_extremes<false, false>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launch();

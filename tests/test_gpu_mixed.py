@@ -86,6 +86,26 @@ def test_self_pair_bf16(cc, orc):
     assert np.abs(full[ids.astype(np.int64)] - vals).max() < TOL_REFINED
 
 
+@pytest.mark.parametrize("n", [32, 100, 257])
+def test_spearman_bf16_integer_ranks_exact(cc, orc, n):
+    """n <= 257: the BF16 contraction of integer centred ranks is exact, so the
+    certificate bound is only the epilogue's fp32 scaling (~1e-6) and the
+    refined extremes and top list match the FP64 Spearman values, with ties."""
+    from paper_2309_03308_gb300 import CC_BF16, CC_SPEARMAN, Params
+    Fa, Fb = two_fields(n, (64, 64, 0, 96, 80, 2), (256, 160, 0, 280, 176, 1))  # 1024 x 384
+    Fa = np.round(Fa * 2) / 2  # heavy ties: average ranks, odd doubled ranks
+    fa, fb = cc.load_field(Fa.astype(np.float32)), cc.load_field(Fb)
+    (ra,) = cc.define_regions(fa, [(0, 0, 0, 32, 16, 2)])
+    (rb,) = cc.define_regions(fb, [(0, 0, 0, 24, 16, 1)])
+    full = all_values(orc, oracle.SPEARMAN, Fa.astype(np.float32), Fb)
+    res, ids, vals, cert = cc.all_pairs_topk(ra, rb, Params(CC_SPEARMAN, precision=CC_BF16),
+                                             topk=512)
+    assert cert["bound"] < 2e-6, cert
+    check(res, ids, vals, cert, full, full.size, 512)
+    cc.free_field(fa)
+    cc.free_field(fb)
+
+
 def test_spearman_n100_and_cc_all_pairs_route(cc, orc):
     from paper_2309_03308_gb300 import CC_BF16, CC_FP8_E4M3, CC_SPEARMAN, Params
     Fa, Fb = two_fields(100, (64, 64, 0, 96, 96, 2), (256, 160, 0, 288, 176, 1))  # 2048 x 512
