@@ -9,7 +9,8 @@ built stage of the path on the resident field:
   fp32 x2     all 419,430,400 cross pairs, Pearson and Spearman, FP32 SIMT,
               every value stored, extremes fused
   bf16, fp8   the same Pearson pairs on the tensor cores, certified exact
-              extremes (Dot2 re-evaluation) and the top-4096 list
+              extremes (Dot2 re-evaluation) and the top-4096 list; Spearman in
+              BF16 on the integer ranks (an exact contraction for n <= 257)
   sample      2,000,000 seeded uniform cross pairs
   ksg, hist   KSG MI (k = 10) and 16x16-bin MI on them, with extremes
 `value` counts point-pair measure evaluations per second over the step.
@@ -188,6 +189,12 @@ class Workload:
                                     f"pearson_{tag}", Params(P.CC_PEARSON, precision=prec),
                                     topk))(prec, tag),
                                 N_ALL, kind, 2.0 * n * N_ALL))
+        if n <= 257:  # Spearman on the exact integer-rank BF16 path
+            self.stages.append(("allpairs_spearman_bf16",
+                                lambda i, h: self._topk("spearman_bf16",
+                                                        Params(P.CC_SPEARMAN, precision=P.CC_BF16),
+                                                        topk),
+                                N_ALL, "bf16", 2.0 * n * N_ALL))
         self.stages.append(("sample", self._sample, 0, None, 0))
         self.stages.append(("ksg", lambda i, h: self._eval("ksg", Params(P.CC_MI_KSG, k=k),
                                                            self.ksg),

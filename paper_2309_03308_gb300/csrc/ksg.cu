@@ -122,6 +122,93 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
     }
 }
 
+// Sample-stream form for 32 <= n <= 256: warp w owns the contiguous pairs
+// [w P_w, (w + 1) P_w) and walks their samples as one stream, 32 per round
+// (lane l takes stream position 32 r + l), so no lane idles at the end of a
+// pair. A round spans at most two pairs, so two slots per warp suffice: pair
+// p is staged into slot p & 1 before the first round that reaches it, and
+// its slot is reused for pair p + 2, whose first sample lies more than 32
+// positions after p's last. At most one pair ends per round; its digamma sum
+// is reduced over the warp and written at the end of that round.
+template <int KMAX>
+__global__ void __launch_bounds__(kKsgWarps * 32)
+    k_ksg_stream(const float* __restrict__ sorted_a, const uint16_t* __restrict__ perm_a,
+                 const float* __restrict__ vals_a, int64_t Pa, const float* __restrict__ sorted_b,
+                 const uint16_t* __restrict__ perm_b, const float* __restrict__ vals_b, int64_t Pb,
+                 int n, int n_pad, int k, int64_t per_warp, const long long* __restrict__ psi_fix,
+                 double psi_nk, double fix_over_n, const uint32_t* __restrict__ pa,
+                 const uint32_t* __restrict__ pb, int64_t N, float* __restrict__ out,
+                 int32_t* __restrict__ nx_out, int32_t* __restrict__ ny_out,
+                 float* __restrict__ eps_out, int* status) {
+    extern __shared__ __align__(16) unsigned char ksg_smem[];
+    long long* psi = reinterpret_cast<long long*>(ksg_smem);
+    const int psi_len = (n + 2) & ~1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t slot_bytes = ksg_slot_bytes(n_pad, KMAX);
+    unsigned char* wbase = ksg_smem + psi_len * sizeof(long long) + (size_t)warp * 2 * slot_bytes;
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) psi[i] = psi_fix[i];
+    __syncthreads();
+
+    const int64_t p0 = ((int64_t)blockIdx.x * kKsgWarps + warp) * per_warp;
+    const int64_t p1 = min(N, p0 + per_warp);
+    if (p0 >= p1) return;
+    const int64_t total = (p1 - p0) * n;  // stream length
+    int64_t staged = p0;                   // next pair to stage
+    unsigned valid = 0;                    // bit (p & 1): pair in that slot is valid
+    long long acc[2] = {0, 0};
+    for (int64_t r0 = 0; r0 < total; r0 += 32) {
+        const int64_t last = min(total, r0 + 32) - 1;
+        const int64_t p_last = p0 + last / n;
+        for (; staged <= p_last; ++staged) {  // warp-uniform
+            const int sl = (int)(staged & 1);
+            const uint32_t p = pa[staged], q = pb[staged];
+            if (p >= Pa || q >= Pb) {
+                valid &= ~(1u << sl);
+                if (lane == 0) {
+                    out[staged] = CUDART_NAN_F;
+                    set_status(status, DEV_BAD_INDEX);
+                }
+                continue;
+            }
+            valid |= 1u << sl;
+            const int64_t ra = (int64_t)p * n_pad, rb = (int64_t)q * n_pad;
+            ksg_stage<KMAX>(wbase + sl * slot_bytes, n, n_pad, sorted_a + ra, perm_a + ra,
+                            vals_a + ra, sorted_b + rb, perm_b + rb, vals_b + rb);
+        }
+        const int64_t s = r0 + lane;
+        if (s <= last) {
+            const int64_t t = p0 + s / n;
+            const int ti = (int)(s % n), sl = (int)(t & 1);
+            if ((valid >> sl) & 1u) {
+                int cx, cy;
+                float eps;
+                const long long v = ksg_sample<KMAX>(wbase + sl * slot_bytes, n, n_pad, k, ti,
+                                                     psi, nx_out ? &cx : nullptr, &cy, &eps);
+                if (sl) acc[1] += v;
+                else acc[0] += v;
+                if (nx_out) {
+                    const int orig = perm_a[(int64_t)pa[t] * n_pad + ti];
+                    nx_out[t * n + orig] = cx;
+                    ny_out[t * n + orig] = cy;
+                    if (eps_out) eps_out[t * n + orig] = eps;
+                }
+            }
+        }
+        // the pair whose last sample is in this round (at most one, n >= 32)
+        const int64_t ended = (last + 1) / n;  // pairs of this warp complete after the round
+        if (ended > 0 && ended * n - 1 >= r0) {
+            const int64_t te = p0 + ended - 1;
+            const int sl = (int)(te & 1);
+            const long long sum = warp_sum_i64(sl ? acc[1] : acc[0]);
+            if (lane == 0 && ((valid >> sl) & 1u))
+                out[te] = (float)(psi_nk - (double)sum * fix_over_n);
+            if (sl) acc[1] = 0;
+            else acc[0] = 0;
+        }
+        __syncwarp();
+    }
+}
+
 template <int KMAX>
 static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int64_t* psi_fix,
                               double psi_nk, const uint32_t* pa, const uint32_t* pb, int64_t N,
@@ -142,6 +229,27 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (fa.n >= 32 && fa.n_pad <= 256) {  // sample stream, two slots per warp
+        const size_t smem2 =
+            psi_len * sizeof(long long) + kKsgWarps * 2 * ksg_slot_bytes(fa.n_pad, KMAX);
+        if (smem2 > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_ksg_stream<KMAX>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem2);
+            if (e != cudaSuccess) return e;
+        }
+        const int64_t want_warps = (int64_t)sms * 16 * kKsgWarps;
+        const int64_t per_warp = (N + want_warps - 1) / want_warps;
+        const int64_t warps = (N + per_warp - 1) / per_warp;
+        const int64_t blocks = (warps + kKsgWarps - 1) / kKsgWarps;
+        note_launch();
+        k_ksg_stream<KMAX><<<(unsigned)blocks, kKsgWarps * 32, smem2, st>>>(
+            fa.sorted.as<float>(), fa.perm.as<uint16_t>(), fa.vals.as<float>(), fa.P,
+            fb.sorted.as<float>(), fb.perm.as<uint16_t>(), fb.vals.as<float>(), fb.P, fa.n,
+            fa.n_pad, k, per_warp, (const long long*)psi_fix, psi_nk, 1.0 / (kFixScale * fa.n),
+            pa, pb, N, out, nx, ny, eps, status);
+        return cudaGetLastError();
+    }
     const int64_t groups = (N + G - 1) / G;
     int64_t blocks = (groups + kKsgWarps - 1) / kKsgWarps;
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
