@@ -677,11 +677,7 @@ cc_status ensure_qplane(cc_ctx* ctx, Region& r, bool sp, bool fp8, Region::QPlan
         CK(launch_quantize(fp8, sp ? f.rhat.as<float>() : f.zhat.as<float>(), f.n_pad, f.n,
                            r.pts.as<uint32_t>(), r.np, qp.rows_pad, qp.kbytes, qp.q.p,
                            qp.inv.as<float>(), qp.emax.as<unsigned>(), ctx->stream));
-    unsigned bits = 0;
-    CK(cudaMemcpyAsync(&bits, qp.emax.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    memcpy(&qp.emax_host, &bits, sizeof(float));
-    qp.version = f.version;
+    qp.version = f.version;  // the error norm stays on the device (read by the threshold)
     return CC_OK;
 }
 
@@ -729,18 +725,24 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
         off += (bytes + 255) / 256 * 256;
         return o;
     };
+    // per side: the record that the host reads once at the end
+    struct SideOut {
+        Select sel;               // first and second pass counts, overflow, threshold
+        unsigned pad;
+        unsigned long long best;  // (key of best value, inverted pair index)
+        float thr[2];             // second-pass threshold, bound
+    };
     const size_t o_cmax = take(4 * N), o_cmin = take(4 * N), o_hist = take(4 * 4096),
-                 o_sel = take(sizeof(Select) * 2), o_cnt = take(16), o_best = take(8),
-                 o_thr = take(8), o_ids = take(4ull * cap), o_vals = take(4ull * cap * 32),
+                 o_sel = take(sizeof(Select) * 2), o_best = take(8), o_thr = take(8),
+                 o_ids = take(4ull * cap), o_vals = take(4ull * cap * 32),
                  o_pids = take(8ull * cap * 32), o_sidx = take(4 * 8192), o_tv = take(4 * 4096),
-                 o_ti = take(8 * 4096);
+                 o_ti = take(8 * 4096), o_out = take(sizeof(SideOut) * 2);
     CK(ctx->mixed.ensure(off));
     unsigned char* base = ctx->mixed.as<unsigned char>();
     float* cmax = (float*)(base + o_cmax);
     float* cmin = (float*)(base + o_cmin);
     unsigned* hist = (unsigned*)(base + o_hist);
     Select* sel = (Select*)(base + o_sel);
-    unsigned* cnt2 = (unsigned*)(base + o_cnt);  // [count, overflow] of the second pass
     unsigned long long* best = (unsigned long long*)(base + o_best);
     float* thr = (float*)(base + o_thr);  // [threshold, bound]
     uint32_t* cids = (uint32_t*)(base + o_ids);
@@ -749,83 +751,75 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
     uint32_t* sidx = (uint32_t*)(base + o_sidx);
     float* tvals = (float*)(base + o_tv);
     unsigned long long* tids = (unsigned long long*)(base + o_ti);
+    SideOut* dout = (SideOut*)(base + o_out);
     cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(hist, 0, 4 * 4096, st));
     const bool exact = rank_exact(sp, fp8, fa.n);
     CK(launch_tc_chunk_extremes(fp8, fp8 || exact, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad,
-                                qa->kbytes, self,
-                                qa->inv.as<float>(), qb->inv.as<float>(), cmax, cmin,
-                                ctx->status.as<int>(), st));
-    const float emax = std::max(qa->emax_host, qb->emax_host);
+                                qa->kbytes, self, qa->inv.as<float>(), qb->inv.as<float>(), cmax,
+                                cmin, ctx->status.as<int>(), st));
     const float* plane_a = sp ? fa.rhat.as<float>() : fa.zhat.as<float>();
     const float* plane_b = sp ? fb.rhat.as<float>() : fb.zhat.as<float>();
-    cc_mixed_info inf{};
-    float ext_val[2] = {-INFINITY, -INFINITY};
-    uint64_t ext_id[2] = {~0ull, ~0ull};
+    // relative error of the approximate values beyond the quantization error:
+    // FP32 accumulation (2^-12, conservative), or for exact integer ranks the
+    // two fp32 scalings of the epilogue (2^-22 covers them)
+    const float acc_rel = exact ? 1.f / 4194304.f : 1.f / 4096.f;
+    // Both passes are decided on the device (no host round trip): the second
+    // compaction appends the chunks in [r* - B, first threshold) after the
+    // first pass's, unless the first pass took every chunk or overflowed.
     for (int side = 0; side < 2; ++side) {
         const float sign = side == 0 ? 1.f : -1.f;
         const float* v = side == 0 ? cmax : cmin;
         CK(cudaMemsetAsync(sel, 0, sizeof(Select) * 2, st));
-        CK(cudaMemsetAsync(cnt2, 0, 16, st));
         CK(cudaMemsetAsync(best, 0, 8, st));
         const unsigned want = side == 0 ? (unsigned)std::max(topk, 256) : 256u;
         CK(launch_select_top(v, N, sign, want, hist, sel, cids, cap, st));
         CK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
-                                rb->pts.as<uint32_t>(), nb, self, na_pad, cids, &sel->count, cap,
-                                sign, rvals, rpids, best, st));
-        Select h1;
-        CK(cudaMemcpyAsync(&h1, sel, sizeof h1, cudaMemcpyDeviceToHost, st));
-        // relative error of the approximate values beyond the quantization
-        // error: FP32 accumulation (2^-12, conservative), or for exact integer
-        // ranks the two fp32 scalings of the epilogue (2^-22 covers them)
-        CK(launch_second_threshold(best, emax, exact ? 1.f / 4194304.f : 1.f / 4096.f, thr,
-                                   thr + 1, st));
-        CK(cudaStreamSynchronize(st));
-        const unsigned c1 = std::min(h1.count, cap);
-        bool certified = h1.overflow == 0;
-        unsigned c2 = 0;
-        if (certified && h1.threshold != 0 && c1 < cap) {
-            CK(launch_compact_range(v, N, sign, thr, &sel->threshold, cids + c1, cap - c1, cnt2,
-                                    cnt2 + 1, st));
-            CK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
-                                    rb->pts.as<uint32_t>(), nb, self, na_pad, cids + c1, cnt2,
-                                    cap - c1, sign, rvals + (size_t)c1 * 32,
-                                    rpids + (size_t)c1 * 32, best, st));
-            unsigned h2[2];
-            CK(cudaMemcpyAsync(h2, cnt2, sizeof h2, cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            c2 = std::min(h2[0], cap - c1);
-            certified = h2[1] == 0;
-        } else if (h1.threshold != 0) {
-            certified = false;
-        }
-        unsigned long long hb = 0;
-        float ht[2];
-        CK(cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(ht, thr, 8, cudaMemcpyDeviceToHost, st));
-        if (side == 0 && topk > 0) {
-            const int64_t n2 = (int64_t)(c1 + c2) * 32;
-            CK(cudaMemsetAsync(sel + 1, 0, sizeof(Select), st));
-            CK(launch_select_top(rvals, n2, 1.f, (unsigned)topk, hist, sel + 1, sidx, 8192, st));
+                                rb->pts.as<uint32_t>(), nb, self, na_pad, cids, nullptr,
+                                &sel->count, cap, sign, rvals, rpids, best, st));
+        CK(launch_second_threshold(best, qa->emax.as<unsigned>(), qb->emax.as<unsigned>(),
+                                   acc_rel, sel, thr, st));
+        CK(launch_compact_second(v, N, sign, thr, sel, cids, cap, st));
+        CK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
+                                rb->pts.as<uint32_t>(), nb, self, na_pad, cids, &sel->pass1,
+                                &sel->count, cap, sign, rvals, rpids, best, st));
+        if (side == 0 && topk > 0) {  // top-K of every refined value
+            CK(launch_select_top(rvals, (int64_t)cap * 32, 1.f, (unsigned)topk, hist, sel + 1,
+                                 sidx, 8192, st, &sel->count));
             CK(launch_sort_top(rvals, rpids, sidx, &sel[1].count, 8192, 1.f, topk, tvals, tids,
                                st));
-            CK(cudaMemcpyAsync(vals, tvals, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(ids, tids, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
         }
-        if ((s = take_status(ctx))) return s;
-        if (hb != 0) {
-            ext_val[side] = unorder_key((unsigned)(hb >> 32));
-            ext_id[side] = 0xffffffffull - (hb & 0xffffffffull);
+        CK(cudaMemcpyAsync(&dout[side].sel, sel, sizeof(Select), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(&dout[side].best, best, 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(dout[side].thr, thr, 8, cudaMemcpyDeviceToDevice, st));
+    }
+    SideOut hout[2];
+    CK(cudaMemcpyAsync(hout, dout, sizeof hout, cudaMemcpyDeviceToHost, st));
+    if (topk > 0) {
+        CK(cudaMemcpyAsync(vals, tvals, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ids, tids, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    if ((s = take_status(ctx))) return s;
+    cc_mixed_info inf{};
+    float ext_val[2] = {-INFINITY, -INFINITY};
+    uint64_t ext_id[2] = {~0ull, ~0ull};
+    for (int side = 0; side < 2; ++side) {
+        const SideOut& o = hout[side];
+        const bool certified = o.sel.overflow == 0;  // both passes fit (or pass 1 took all)
+        if (o.best != 0) {
+            ext_val[side] = unorder_key((unsigned)(o.best >> 32));
+            ext_id[side] = 0xffffffffull - (o.best & 0xffffffffull);
         }
-        inf.bound = ht[1];
+        inf.bound = o.thr[1];
         if (side == 0) {
-            inf.threshold_max = ht[0];
+            inf.threshold_max = o.thr[0];
             inf.certified_max = certified;
         } else {
-            inf.threshold_min = -ht[0];
+            inf.threshold_min = -o.thr[0];
             inf.certified_min = certified;
         }
-        inf.refined_pairs += (int64_t)(c1 + c2) * 32;
+        inf.refined_pairs += (int64_t)std::min(o.sel.count, cap) * 32;
     }
     const uint64_t count = self ? (uint64_t)na * (na - 1) / 2 : (uint64_t)na * nb;
     *out = cc_rp_result{ext_val[0], -ext_val[1], ext_id[0], ext_id[1], count};

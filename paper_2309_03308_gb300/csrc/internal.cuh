@@ -86,7 +86,6 @@ struct Region {
         DevMem q, inv, emax;
         int64_t rows_pad = 0;
         int kbytes = 0;
-        float emax_host = 0.f;
         uint64_t version = ~0ull;
     };
     std::map<int, std::unique_ptr<QPlane>> qplanes;
@@ -158,6 +157,7 @@ struct Select {
     unsigned threshold;  // order-preserving key threshold; 0 = every key
     unsigned count;      // compacted candidates
     unsigned overflow;   // candidates beyond capacity
+    unsigned pass1;      // candidates of the first pass (the second appends after them)
 };
 cudaError_t launch_tc_chunk_extremes(bool fp8, bool scaled, const void* qa, int64_t na,
                                      int64_t na_pad, const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
@@ -171,18 +171,18 @@ cudaError_t launch_quantize_ranks(const int16_t* rank2, int n_pad, int n, const 
                                   float* inv_scale, cudaStream_t st);
 cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned want,
                               unsigned* hist, Select* sel, uint32_t* out, unsigned cap,
-                              cudaStream_t st);
-cudaError_t launch_compact_range(const float* v, int64_t N, float sign, const float* lo_val,
-                                 const unsigned* hi_key, uint32_t* out, unsigned cap,
-                                 unsigned* count, unsigned* ovf, cudaStream_t st);
+                              cudaStream_t st, const unsigned* nchunks = nullptr);
+cudaError_t launch_compact_second(const float* v, int64_t N, float sign, const float* lo_val,
+                                  Select* sel, uint32_t* out, unsigned cap, cudaStream_t st);
 cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int n_pad, int n,
                                  const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
                                  int64_t nb, int self, int64_t na_pad, const uint32_t* ids,
-                                 const unsigned* count, unsigned cap, float sign, float* vals,
-                                 unsigned long long* pair_ids, unsigned long long* best,
-                                 cudaStream_t st);
-cudaError_t launch_second_threshold(const unsigned long long* best, float emax, float acc_rel,
-                                    float* thr, float* bound, cudaStream_t st);
+                                 const unsigned* start, const unsigned* count, unsigned cap,
+                                 float sign, float* vals, unsigned long long* pair_ids,
+                                 unsigned long long* best, cudaStream_t st);
+cudaError_t launch_second_threshold(const unsigned long long* best, const unsigned* emax_a,
+                                    const unsigned* emax_b, float acc_rel, Select* sel,
+                                    float* thr, cudaStream_t st);
 cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,
                             const uint32_t* sel_idx, const unsigned* count, unsigned cap,
                             float sign, int topk, float* out_vals, unsigned long long* out_ids,

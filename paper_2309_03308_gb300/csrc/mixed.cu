@@ -126,8 +126,10 @@ __global__ void __launch_bounds__(256)
 // top 12 bits equal sel->prefix. Values of -inf (empty chunks) are skipped.
 
 __global__ void k_hist12(const float* __restrict__ v, int64_t N, float sign, int level,
-                         const Select* __restrict__ sel, unsigned* __restrict__ hist) {
+                         const Select* __restrict__ sel, unsigned* __restrict__ hist,
+                         const unsigned* __restrict__ nchunks) {
     __shared__ unsigned h[4096];
+    if (nchunks) N = min(N, (int64_t)*nchunks * 32);
     for (int i = threadIdx.x; i < 4096; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const unsigned prefix = level ? sel->prefix : 0u;
@@ -187,12 +189,17 @@ __global__ void k_pick_bin(unsigned* __restrict__ hist, int level, unsigned want
 }
 
 // 3b. compact chunk ids whose key lies in [lo_key, hi_key) (hi_key 0 = no cap).
+// First pass (lo_val null): keys >= sel->threshold. Second pass: keys in
+// [okey(*lo_val), sel->threshold), appended after the first pass's; skipped
+// when the first pass took every key (threshold 0) or overflowed.
 __global__ void k_compact(const float* __restrict__ v, int64_t N, float sign,
                           const Select* __restrict__ sel, const float* __restrict__ lo_val,
-                          const unsigned* __restrict__ hi_key_p, uint32_t* __restrict__ out,
-                          unsigned cap, unsigned* __restrict__ count, unsigned* __restrict__ ovf) {
+                          uint32_t* __restrict__ out, unsigned cap, unsigned* __restrict__ count,
+                          unsigned* __restrict__ ovf, const unsigned* __restrict__ nchunks) {
+    if (nchunks) N = min(N, (int64_t)*nchunks * 32);
+    if (lo_val && (sel->threshold == 0u || sel->overflow)) return;
     const unsigned lo = lo_val ? okey(*lo_val) : sel->threshold;
-    const unsigned hi = hi_key_p ? *hi_key_p : 0u;
+    const unsigned hi = lo_val ? sel->threshold : 0u;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float x = sign * v[i];
@@ -211,12 +218,15 @@ __global__ void k_compact(const float* __restrict__ v, int64_t N, float sign,
 // addresses cm[chunk][row] = i, i.e. chunk = i / na_pad, row = i % na_pad.
 // One warp per chunk: the warp holds row a's member vector (n <= 1024) in
 // registers and evaluates its 32 pairs (a, 32 * chunk + j).
-__device__ __forceinline__ float dot2_warp(const float (&x)[32], const float* __restrict__ y,
+// R = member slices of 32 in use (ceil(n / 32) rounded up to a power of two),
+// a template parameter so every load of a row is issued before the sums.
+template <int R>
+__device__ __forceinline__ float dot2_warp(const float (&x)[R], const float* __restrict__ y,
                                            int n) {
     const int lane = threadIdx.x & 31;
     float s = 0.f, c = 0.f;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
+    for (int r = 0; r < R; ++r) {
         const int k = r * 32 + lane;
         if (k < n) {
             const float p = __fmul_rn(x[r], y[k]);
@@ -239,25 +249,27 @@ __device__ __forceinline__ float dot2_warp(const float (&x)[32], const float* __
     return __fadd_rn(s, c);
 }
 
+template <int R>
 __global__ void __launch_bounds__(256)
     k_refine_chunks(const float* __restrict__ plane_a, const float* __restrict__ plane_b,
                     int n_pad, int n, const uint32_t* __restrict__ pts_a, int64_t na,
                     const uint32_t* __restrict__ pts_b, int64_t nb, int self, int64_t na_pad,
-                    const uint32_t* __restrict__ ids, const unsigned* __restrict__ count_p,
-                    unsigned cap, float sign, float* __restrict__ vals,
-                    unsigned long long* __restrict__ pair_ids,
+                    const uint32_t* __restrict__ ids, const unsigned* __restrict__ start_p,
+                    const unsigned* __restrict__ count_p, unsigned cap, float sign,
+                    float* __restrict__ vals, unsigned long long* __restrict__ pair_ids,
                     unsigned long long* __restrict__ best) {
     const int lane = threadIdx.x & 31;
     const unsigned count = min(*count_p, cap);
-    for (int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); w < count;
+    const unsigned start = start_p ? min(*start_p, cap) : 0u;
+    for (int64_t w = start + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); w < count;
          w += (int64_t)gridDim.x * 8) {
         const uint32_t id = ids[w];
         const int64_t chunk = id / na_pad, a = id % na_pad;
         if (a >= na) continue;
-        float x[32];
+        float x[R];
         const float* xa = plane_a + (int64_t)pts_a[a] * n_pad;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
+        for (int r = 0; r < R; ++r) {
             const int k = r * 32 + lane;
             x[r] = k < n ? xa[k] : 0.f;
         }
@@ -267,7 +279,7 @@ __global__ void __launch_bounds__(256)
             const int64_t b = chunk * 32 + j;
             const bool ok = b < nb && (!self || b > a);
             float r = -CUDART_INF_F;
-            if (ok) r = sign * dot2_warp(x, plane_b + (int64_t)pts_b[b] * n_pad, n);
+            if (ok) r = sign * dot2_warp<R>(x, plane_b + (int64_t)pts_b[b] * n_pad, n);
             if (lane == j) {
                 mine = r;
                 mine_id = ok ? (unsigned long long)(a * nb + b) : ~0ull;
@@ -283,61 +295,117 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// r* - B as a value threshold for the second pass (sign-adjusted domain).
-__global__ void k_second_threshold(const unsigned long long* best, float e, float acc_rel,
-                                   float* out_thr, float* out_bound) {
+// r* - B as a value threshold for the second pass (sign-adjusted domain);
+// records where the first pass's candidates end.
+__global__ void k_second_threshold(const unsigned long long* best, const unsigned* emax_a,
+                                   const unsigned* emax_b, float acc_rel, Select* sel,
+                                   float* thr) {
+    const float e = fmaxf(__uint_as_float(*emax_a), __uint_as_float(*emax_b));
     const float B = 2.f * e + e * e + (1.f + e) * (1.f + e) * acc_rel + 1e-6f;
     const float rstar = okey_inv((unsigned)(*best >> 32));
-    *out_thr = rstar - B;
-    *out_bound = B;
+    thr[0] = rstar - B;
+    thr[1] = B;
+    sel->pass1 = sel->count;
 }
 
 // 5. top-K: bitonic sort (descending) of up to 8192 (value, pair) entries in
-// one CTA, taken from the compacted refined values.
+// one CTA, taken from the compacted refined values. Thread t holds entries
+// 8t .. 8t+7 in registers: exchanges at distance < 8 stay in registers, at
+// distance 8 .. 255 go through warp shuffles, and only the 15 stages at
+// distance >= 256 pass through shared memory.
+__device__ __forceinline__ void sort_keep(unsigned long long& k, unsigned long long& p,
+                                          unsigned long long ok, unsigned long long op,
+                                          bool keep_max) {
+    const bool take = keep_max ? ok > k : ok < k;
+    k = take ? ok : k;
+    p = take ? op : p;
+}
+
+template <int D>
+__device__ __forceinline__ void sort_regs(unsigned long long (&key)[8], unsigned long long (&pid)[8],
+                                          int i0, int size) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        constexpr int dd = D;
+        const int e2 = e ^ dd;
+        if (e2 > e) {
+            const bool desc = ((i0 + e) & size) == 0;
+            if ((key[e] < key[e2]) == desc) {
+                const unsigned long long tk = key[e], tp = pid[e];
+                key[e] = key[e2];
+                pid[e] = pid[e2];
+                key[e2] = tk;
+                pid[e2] = tp;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(1024)
     k_sort_top(const float* __restrict__ vals, const unsigned long long* __restrict__ pids,
                const uint32_t* __restrict__ sel_idx, const unsigned* __restrict__ count_p,
                unsigned cap, float sign, int topk, float* __restrict__ out_vals,
                unsigned long long* __restrict__ out_ids) {
     extern __shared__ unsigned long long sort_smem[];
-    unsigned long long* key = sort_smem;
-    unsigned long long* pid = sort_smem + 8192;
+    unsigned long long* skey = sort_smem;
+    unsigned long long* spid = sort_smem + 8192;
+    constexpr int E = 8;
+    const int t = threadIdx.x;
     const unsigned count = min(*count_p, cap);
-    for (int i = threadIdx.x; i < 8192; i += 1024) {
+    unsigned long long key[E], pid[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = t * E + e;
         if ((unsigned)i < count) {
             const uint32_t j = sel_idx[i];
             const unsigned long long id = pids ? pids[j] : (unsigned long long)j;
-            key[i] = ((unsigned long long)okey(vals[j]) << 32) | (0xffffffffull - (id & 0xffffffffull));
-            pid[i] = id;
+            key[e] = ((unsigned long long)okey(vals[j]) << 32) | (0xffffffffull - (id & 0xffffffffull));
+            pid[e] = id;
         } else {
-            key[i] = 0;
-            pid[i] = ~0ull;
+            key[e] = 0;
+            pid[e] = ~0ull;
         }
     }
-    __syncthreads();
     for (int size = 2; size <= 8192; size <<= 1) {
         for (int d = size >> 1; d > 0; d >>= 1) {
-            for (int i = threadIdx.x; i < 8192; i += 1024) {
-                const int p = i ^ d;
-                if (p > i) {
-                    const bool desc = (i & size) == 0;
-                    if ((key[i] < key[p]) == desc) {
-                        const unsigned long long tk = key[i];
-                        key[i] = key[p];
-                        key[p] = tk;
-                        const unsigned long long tp = pid[i];
-                        pid[i] = pid[p];
-                        pid[p] = tp;
-                    }
+            if (d >= 256) {  // partner in another warp
+                __syncthreads();
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    skey[t * E + e] = key[e];
+                    spid[t * E + e] = pid[e];
                 }
+                __syncthreads();
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int i = t * E + e, q = i ^ d;
+                    sort_keep(key[e], pid[e], skey[q], spid[q], (i < q) == ((i & size) == 0));
+                }
+            } else if (d >= E) {  // partner lane t ^ (d / E) of the same warp
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int i = t * E + e, q = i ^ d;
+                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key[e], d / E);
+                    const unsigned long long op = __shfl_xor_sync(0xffffffffu, pid[e], d / E);
+                    sort_keep(key[e], pid[e], ok, op, (i < q) == ((i & size) == 0));
+                }
+            } else if (d == 4) {  // partner in this thread's registers
+                sort_regs<4>(key, pid, t * E, size);
+            } else if (d == 2) {
+                sort_regs<2>(key, pid, t * E, size);
+            } else {
+                sort_regs<1>(key, pid, t * E, size);
             }
-            __syncthreads();
         }
     }
-    for (int i = threadIdx.x; i < topk; i += 1024) {
-        const bool ok = (unsigned)i < count;
-        out_vals[i] = ok ? sign * okey_inv((unsigned)(key[i] >> 32)) : -sign * CUDART_INF_F;
-        out_ids[i] = ok ? pid[i] : ~0ull;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = t * E + e;
+        if (i < topk) {
+            const bool ok = (unsigned)i < count;
+            out_vals[i] = ok ? sign * okey_inv((unsigned)(key[e] >> 32)) : -sign * CUDART_INF_F;
+            out_ids[i] = ok ? pid[e] : ~0ull;
+        }
     }
 }
 
@@ -377,43 +445,52 @@ static unsigned grid_for(int64_t N, int per_block) {
 // their indices into out (capacity cap). scratch: hist[4096] zeroed, sel.
 cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned want,
                               unsigned* hist, Select* sel, uint32_t* out, unsigned cap,
-                              cudaStream_t st) {
+                              cudaStream_t st, const unsigned* nchunks) {
     note_launch(5);
-    k_hist12<<<grid_for(N, 256 * 16), 256, 0, st>>>(v, N, sign, 0, sel, hist);
+    k_hist12<<<grid_for(N, 256 * 16), 256, 0, st>>>(v, N, sign, 0, sel, hist, nchunks);
     k_pick_bin<<<1, 1024, 0, st>>>(hist, 0, want, sel);
-    k_hist12<<<grid_for(N, 256 * 16), 256, 0, st>>>(v, N, sign, 1, sel, hist);
+    k_hist12<<<grid_for(N, 256 * 16), 256, 0, st>>>(v, N, sign, 1, sel, hist, nchunks);
     k_pick_bin<<<1, 1024, 0, st>>>(hist, 1, want, sel);
-    k_compact<<<grid_for(N, 256 * 8), 256, 0, st>>>(v, N, sign, sel, nullptr, nullptr, out, cap,
-                                                    &sel->count, &sel->overflow);
+    k_compact<<<grid_for(N, 256 * 8), 256, 0, st>>>(v, N, sign, sel, nullptr, out, cap,
+                                                    &sel->count, &sel->overflow, nchunks);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_range(const float* v, int64_t N, float sign, const float* lo_val,
-                                 const unsigned* hi_key, uint32_t* out, unsigned cap,
-                                 unsigned* count, unsigned* ovf, cudaStream_t st) {
+cudaError_t launch_compact_second(const float* v, int64_t N, float sign, const float* lo_val,
+                                  Select* sel, uint32_t* out, unsigned cap, cudaStream_t st) {
     note_launch();
-    k_compact<<<grid_for(N, 256 * 8), 256, 0, st>>>(v, N, sign, nullptr, lo_val, hi_key, out, cap,
-                                                    count, ovf);
+    k_compact<<<grid_for(N, 256 * 8), 256, 0, st>>>(v, N, sign, sel, lo_val, out, cap,
+                                                    &sel->count, &sel->overflow, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int n_pad, int n,
                                  const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
                                  int64_t nb, int self, int64_t na_pad, const uint32_t* ids,
-                                 const unsigned* count, unsigned cap, float sign, float* vals,
-                                 unsigned long long* pair_ids, unsigned long long* best,
-                                 cudaStream_t st) {
+                                 const unsigned* start, const unsigned* count, unsigned cap,
+                                 float sign, float* vals, unsigned long long* pair_ids,
+                                 unsigned long long* best, cudaStream_t st) {
     note_launch();
-    k_refine_chunks<<<152 * 8, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, nb,
-                                             self, na_pad, ids, count, cap, sign, vals, pair_ids,
-                                             best);
+#define CC_REFINE(R)                                                                           \
+    k_refine_chunks<R><<<152 * 8, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, \
+                                                nb, self, na_pad, ids, start, count, cap,      \
+                                                sign, vals, pair_ids, best)
+    const int slices = (n + 31) / 32;
+    if (slices <= 1) CC_REFINE(1);
+    else if (slices <= 2) CC_REFINE(2);
+    else if (slices <= 4) CC_REFINE(4);
+    else if (slices <= 8) CC_REFINE(8);
+    else if (slices <= 16) CC_REFINE(16);
+    else CC_REFINE(32);
+#undef CC_REFINE
     return cudaGetLastError();
 }
 
-cudaError_t launch_second_threshold(const unsigned long long* best, float emax, float acc_rel,
-                                    float* thr, float* bound, cudaStream_t st) {
+cudaError_t launch_second_threshold(const unsigned long long* best, const unsigned* emax_a,
+                                    const unsigned* emax_b, float acc_rel, Select* sel,
+                                    float* thr, cudaStream_t st) {
     note_launch();
-    k_second_threshold<<<1, 1, 0, st>>>(best, emax, acc_rel, thr, bound);
+    k_second_threshold<<<1, 1, 0, st>>>(best, emax_a, emax_b, acc_rel, sel, thr);
     return cudaGetLastError();
 }
 
@@ -439,6 +516,7 @@ cudaError_t launch_sort_top_ids(const float* vals, const uint32_t* sel_idx, cons
 }
 
 // 3c for a plain pair batch: Dot2 Pearson/Spearman (precision CC_FP32_DOT2).
+template <int R>
 __global__ void __launch_bounds__(256)
     k_dot2_pairs(const float* __restrict__ A, int64_t Pa, const float* __restrict__ B, int64_t Pb,
                  int n_pad, int n, const uint32_t* __restrict__ pa, const uint32_t* __restrict__ pb,
@@ -454,14 +532,14 @@ __global__ void __launch_bounds__(256)
             }
             continue;
         }
-        float x[32];
+        float x[R];
         const float* xa = A + (int64_t)p * n_pad;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
+        for (int r = 0; r < R; ++r) {
             const int k = r * 32 + lane;
             x[r] = k < n ? xa[k] : 0.f;
         }
-        const float r = dot2_warp(x, B + (int64_t)q * n_pad, n);
+        const float r = dot2_warp<R>(x, B + (int64_t)q * n_pad, n);
         if (lane == 0) out[t] = r;
     }
 }
@@ -471,7 +549,16 @@ cudaError_t launch_dot2_pairs(const float* A, int64_t Pa, const float* B, int64_
                               int* status, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     note_launch();
-    k_dot2_pairs<<<grid_for(N, 8), 256, 0, st>>>(A, Pa, B, Pb, n_pad, n, pa, pb, N, out, status);
+#define CC_DOT2(R) \
+    k_dot2_pairs<R><<<grid_for(N, 8), 256, 0, st>>>(A, Pa, B, Pb, n_pad, n, pa, pb, N, out, status)
+    const int slices = (n + 31) / 32;
+    if (slices <= 1) CC_DOT2(1);
+    else if (slices <= 2) CC_DOT2(2);
+    else if (slices <= 4) CC_DOT2(4);
+    else if (slices <= 8) CC_DOT2(8);
+    else if (slices <= 16) CC_DOT2(16);
+    else CC_DOT2(32);
+#undef CC_DOT2
     return cudaGetLastError();
 }
 
