@@ -95,8 +95,38 @@ __global__ void __launch_bounds__(NT, 2)
     }
     cp_async_wait<0>();
 
-    // epilogue: store and reduce
+    // epilogue: store and reduce. A tile inside both regions and clear of the
+    // self-pair diagonal reduces without per-value checks: value extremes
+    // with the thread-local position (compile-time), first position on ties,
+    // which is the smallest linear pair index (rows, then columns, ascend).
     Ext e = ext_empty();
+    const bool interior = a0 + BM <= PA && b0 + BN <= PB && (!self || b0 >= a0 + BM);
+    if (interior) {
+        float vmax = -CUDART_INF_F, vmin = CUDART_INF_F;
+        int pmax = 0, pmin = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int hj = 0; hj < 8; ++hj) {
+                const float v = acc[i][hj];
+                pmax = v > vmax ? i * 8 + hj : pmax;
+                vmax = fmaxf(vmax, v);
+                pmin = v < vmin ? i * 8 + hj : pmin;
+                vmin = fminf(vmin, v);
+            }
+        }
+        auto lin = [&](int pos) {
+            const int i = pos >> 3, hj = pos & 7;
+            const int64_t row = a0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+            const int64_t col = b0 + (hj >> 2) * 64 + tx * 4 + (hj & 3);
+            return (unsigned long long)(row * PB + col);
+        };
+        e.vmax = vmax;
+        e.vmin = vmin;
+        e.imax = lin(pmax);
+        e.imin = lin(pmin);
+        e.count = 64;
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t row = a0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
@@ -116,11 +146,13 @@ __global__ void __launch_bounds__(NT, 2)
                         if (col0 + j < PB) __stcs(dst + j, acc[i][h * 4 + j]);
                 }
             }
+            if (!interior) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int64_t col = col0 + j;
-                if (col < PB && (!self || row < col))
-                    ext_add(e, acc[i][h * 4 + j], (unsigned long long)(row * PB + col));
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t col = col0 + j;
+                    if (col < PB && (!self || row < col))
+                        ext_add(e, acc[i][h * 4 + j], (unsigned long long)(row * PB + col));
+                }
             }
         }
     }

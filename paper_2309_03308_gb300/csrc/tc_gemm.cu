@@ -280,14 +280,26 @@ __global__ void __launch_bounds__(THREADS, 1)
                 float v[32];
                 tmem_ld32(tmem + (uint32_t)(acc * TN + c * 32) + ((uint32_t)(32 * q) << 16), v);
                 const int64_t col0 = n0 + c * 32;
-                float mx = -CUDART_INF_F, mn = CUDART_INF_F;
+                if (SCALED) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = col0 + j;
-                    const float val = SCALED ? v[j] * rs * colscale[c * 32 + j] : v[j];
-                    const bool ok = row_ok && col < nb && (!self || col > row);
-                    mx = ok ? fmaxf(mx, val) : mx;
-                    mn = ok ? fminf(mn, val) : mn;
+                    for (int j = 0; j < 32; ++j) v[j] = v[j] * rs * colscale[c * 32 + j];
+                }
+                float mx = -CUDART_INF_F, mn = CUDART_INF_F;
+                if (row_ok && col0 + 31 < nb && (!self || col0 > row)) {
+                    // every pair of the chunk counts: no per-value checks
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        mx = fmaxf(mx, fmaxf(v[j], v[j + 1]));
+                        mn = fminf(mn, fminf(v[j], v[j + 1]));
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t col = col0 + j;
+                        const bool ok = row_ok && col < nb && (!self || col > row);
+                        mx = ok ? fmaxf(mx, v[j]) : mx;
+                        mn = ok ? fminf(mn, v[j]) : mn;
+                    }
                 }
                 const int64_t chunk = (n0 >> 5) + c;
                 if (row < na_pad) {
