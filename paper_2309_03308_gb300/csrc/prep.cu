@@ -10,39 +10,60 @@
 namespace cc {
 
 // ----------------------------------------------------------------------------
-// [n][P] member-major input -> [P][n_pad] point-major values, via a 32x32
-// shared-memory tile (both global sides coalesced). Padding members are 0.
-// Non-finite inputs set DEV_NONFINITE.
-__global__ void k_ingest(const float* __restrict__ in, int n, int64_t P, int n_pad,
-                         float* __restrict__ vals, int* status) {
-    __shared__ float tile[32][33];
-    const int64_t p0 = (int64_t)blockIdx.x * 32;
-    const int m0 = blockIdx.y * 32;
+// [n][P] member-major input -> [P][n_pad] point-major values. A CTA moves 32
+// points x all members through a shared-memory tile: every row of 32 input
+// floats is one coalesced 128-byte read (a thread keeps up to 16 in flight),
+// every point row is written as coalesced float4 stores. Padding members are
+// 0. Non-finite inputs set DEV_NONFINITE.
+constexpr int kIngestPts = 32;
+
+__global__ void __launch_bounds__(256)
+    k_ingest(const float* __restrict__ in, int n, int64_t P, int n_pad, float* __restrict__ vals,
+             int* status) {
+    extern __shared__ float tile[];  // [n_pad][kIngestPts + 1]
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t p0 = (int64_t)blockIdx.x * kIngestPts;
+    const int64_t p = p0 + tx;
     bool bad = false;
-    for (int r = threadIdx.y; r < 32; r += 8) {
-        const int m = m0 + r;
-        const int64_t p = p0 + threadIdx.x;
-        float v = 0.f;
-        if (m < n && p < P) {
-            v = __ldcs(in + (int64_t)m * P + p);
-            bad |= !isfinite(v);
+    for (int m0 = 0; m0 < n_pad; m0 += 8 * 16) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int m = m0 + 8 * u + ty;
+            v[u] = (m < n && p < P) ? __ldcs(in + (int64_t)m * P + p) : 0.f;
         }
-        tile[r][threadIdx.x] = v;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int m = m0 + 8 * u + ty;
+            bad |= !isfinite(v[u]);
+            if (m < n_pad) tile[m * (kIngestPts + 1) + tx] = v[u];
+        }
     }
     if (bad) set_status(status, DEV_NONFINITE);
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += 8) {
-        const int64_t p = p0 + r;
-        const int m = m0 + threadIdx.x;
-        if (p < P && m < n_pad) vals[p * n_pad + m] = tile[threadIdx.x][r];
+    const int q = n_pad / 4;  // float4 per point row
+    for (int e = threadIdx.x; e < kIngestPts * q; e += blockDim.x) {
+        const int pt = e / q, m = 4 * (e % q);
+        if (p0 + pt >= P) continue;
+        const float4 o = make_float4(tile[m * (kIngestPts + 1) + pt],
+                                     tile[(m + 1) * (kIngestPts + 1) + pt],
+                                     tile[(m + 2) * (kIngestPts + 1) + pt],
+                                     tile[(m + 3) * (kIngestPts + 1) + pt]);
+        *reinterpret_cast<float4*>(vals + (p0 + pt) * n_pad + m) = o;
     }
 }
 
 cudaError_t launch_ingest(const float* in, int n, int64_t P, int n_pad, float* vals, int* status,
                           cudaStream_t st) {
-    dim3 grid((unsigned)((P + 31) / 32), (unsigned)(n_pad / 32));
+    const size_t smem = sizeof(float) * (size_t)n_pad * (kIngestPts + 1);
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_ingest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     note_launch();
-    k_ingest<<<grid, dim3(32, 8), 0, st>>>(in, n, P, n_pad, vals, status);
+    k_ingest<<<(unsigned)((P + kIngestPts - 1) / kIngestPts), 256, smem, st>>>(in, n, P, n_pad,
+                                                                              vals, status);
     return cudaGetLastError();
 }
 
@@ -311,18 +332,25 @@ __global__ void __launch_bounds__(128)
     const float hi = sorted[p * n_pad + n - 1];
     const bool flat = !(hi > lo);
     const float w = __fsub_rn(hi, lo);
-    for (int m = lane; m < n_pad; m += 32) {
-        int b = 0;
-        if (m < n && !flat) {
-            const float v = vals[p * n_pad + m];
-            const float t = __fsub_rn(v, lo);
-            const float r = __fdiv_rn(t, w);
-            const float sc = __fmul_rn(r, (float)B);
-            b = (int)floorf(sc);
-            b = b < 0 ? 0 : (b > B - 1 ? B - 1 : b);
+    // four members per lane per 128-member slice: one float4 in, one word out
+    for (int m = 4 * lane; m < n_pad; m += 128) {
+        const float4 v4 = *reinterpret_cast<const float4*>(vals + p * n_pad + m);
+        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+        uint32_t word = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int b = 0;
+            if (m + j < n && !flat) {
+                const float t = __fsub_rn(v[j], lo);
+                const float r = __fdiv_rn(t, w);
+                const float sc = __fmul_rn(r, (float)B);
+                b = (int)floorf(sc);
+                b = b < 0 ? 0 : (b > B - 1 ? B - 1 : b);
+            }
+            word |= (uint32_t)b << (8 * j);
+            if (m + j < n) atomicAdd(&hist[warp][b], 1);
         }
-        bins[p * n_pad + m] = (uint8_t)b;
-        if (m < n) atomicAdd(&hist[warp][b], 1);
+        *reinterpret_cast<uint32_t*>(bins + p * n_pad + m) = word;
     }
     __syncwarp();
     long long s = lane < B ? clogc_fix[hist[warp][lane]] : 0;
