@@ -179,18 +179,21 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
         warp_sum_ff(ss_h, ss_l);
     }
 
-    // bitonic sort, ascending, over NP keys
+    // bitonic sort, ascending, over NP keys (unique: the member index is in
+    // the low word). Exchange across lanes: the element takes its partner's
+    // key when (partner < own) equals "this element keeps the minimum", one
+    // 64-bit comparison; the keep-minimum flag depends on the lane only, since
+    // e < E <= d leaves the bits d and size of g0 + e to g0.
 #pragma unroll
     for (int size = 2; size <= NP; size <<= 1) {
 #pragma unroll
         for (int d = size >> 1; d > 0; d >>= 1) {
             if (d >= E) {
+                const bool keep_min = ((g0 & d) == 0) == ((g0 & size) == 0);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const int g = g0 + e;
                     const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[e], d / E);
-                    const bool keep_min = ((g & d) == 0) == ((g & size) == 0);
-                    key[e] = keep_min ? (o < key[e] ? o : key[e]) : (o > key[e] ? o : key[e]);
+                    key[e] = ((o < key[e]) == keep_min) ? o : key[e];
                 }
             } else {
 #pragma unroll
@@ -198,10 +201,10 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
                     const int e2 = e ^ d;
                     if (e2 > e) {
                         const bool asc = ((g0 + e) & size) == 0;
-                        const unsigned long long lo = key[e] < key[e2] ? key[e] : key[e2];
-                        const unsigned long long hi = key[e] < key[e2] ? key[e2] : key[e];
-                        key[e] = asc ? lo : hi;
-                        key[e2] = asc ? hi : lo;
+                        const bool swap = (key[e2] < key[e]) == asc;
+                        const unsigned long long a = key[e], b = key[e2];
+                        key[e] = swap ? b : a;
+                        key[e2] = swap ? a : b;
                     }
                 }
             }
