@@ -256,9 +256,14 @@ __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n
     while (R - 1 > s && !(__fsub_rn(W[R - 1].x, pv) < eps)) --R;
     const int c_walk = eps > 0.f ? R - L - 1 : 1;
     // other axis: [a, b) with a = first j with fl(ov - O[j].x) < eps,
-    // b = first j with fl(O[j].x - ov) >= eps
-    const int a = lower_search(0, n, [&](int j) { return __fsub_rn(ov, O[j].x) < eps; });
-    const int b = lower_search(0, n, [&](int j) { return !(__fsub_rn(O[j].x, ov) < eps); });
+    // b = first j with fl(O[j].x - ov) >= eps; both found by one branch-free
+    // binary search over power-of-two steps (a and b interleaved)
+    int a = 0, b = 0;
+    for (int step = 1 << (31 - __clz(n)); step > 0; step >>= 1) {
+        const int ja = a + step - 1, jb = b + step - 1;
+        if (ja < n && !(__fsub_rn(ov, O[ja].x) < eps)) a += step;
+        if (jb < n && __fsub_rn(O[jb].x, ov) < eps) b += step;
+    }
     const int c_oth = max(b - a, 1);
     const int cx = on_y ? c_oth : c_walk;
     const int cy = on_y ? c_walk : c_oth;
