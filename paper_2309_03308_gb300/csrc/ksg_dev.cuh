@@ -252,8 +252,16 @@ __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n
     // walk axis: the passed window (L, R), trimmed to axis distance < eps
     L = max(L, -1);
     R = min(R, n);
-    while (L + 1 < s && !(__fsub_rn(pv, W[L + 1].x) < eps)) ++L;
-    while (R - 1 > s && !(__fsub_rn(W[R - 1].x, pv) < eps)) --R;
+    {  // trim both ends at once by branch-free binary lifting over the window
+        const int wl = s - 1 - L, wr = R - 1 - s;
+        int tl = 0, tr = 0;
+        for (int step = 1 << (31 - __clz(max(wl, wr) | 1)); step > 0; step >>= 1) {
+            if (tl + step <= wl && !(__fsub_rn(pv, W[L + tl + step].x) < eps)) tl += step;
+            if (tr + step <= wr && !(__fsub_rn(W[R - tr - step].x, pv) < eps)) tr += step;
+        }
+        L += tl;
+        R -= tr;
+    }
     const int c_walk = eps > 0.f ? R - L - 1 : 1;
     // other axis: [a, b) with a = first j with fl(ov - O[j].x) < eps,
     // b = first j with fl(O[j].x - ov) >= eps; both found by one branch-free
