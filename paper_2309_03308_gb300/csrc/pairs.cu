@@ -73,6 +73,41 @@ cudaError_t launch_pearson_pairs(const float* plane_a, int64_t Pa, const float* 
     return cudaGetLastError();
 }
 
+// Joint-histogram sum of c ln c over the occupied cells for n > 128 members:
+// up to 8 slices of 128 members, 4 per lane each; cells are recomputed from
+// the (L1-resident) bin words when the owners read and clear them.
+__device__ __forceinline__ long long hist_slices(const uint32_t* __restrict__ ba,
+                                                 const uint32_t* __restrict__ bb, int n, int B,
+                                                 int* h, const long long* clogc, int lane) {
+    auto cell_of = [&](int c, int j) {
+        const int w = (c * 128 >> 2) + lane;
+        const uint32_t wa = __ldg(ba + w), wb = __ldg(bb + w);
+        return (int)((wa >> (8 * j)) & 0xffu) * B + (int)((wb >> (8 * j)) & 0xffu);
+    };
+    unsigned own = 0;  // bit 4c + j: member 128c + 4 lane + j owns its cell
+    for (int c = 0; c * 128 < n; ++c) {
+        const int m = c * 128 + 4 * lane;
+        if (m < n) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (m + j < n && atomicAdd(&h[cell_of(c, j)], 1) == 0) own |= 1u << (4 * c + j);
+        }
+    }
+    __syncwarp();
+    long long s = 0;
+    for (unsigned o = own; o; o &= o - 1) {
+        const int bit = __ffs(o) - 1;
+        s += clogc[h[cell_of(bit >> 2, bit & 3)]];
+    }
+    __syncwarp();
+    for (unsigned o = own; o; o &= o - 1) {
+        const int bit = __ffs(o) - 1;
+        h[cell_of(bit >> 2, bit & 3)] = 0;
+    }
+    __syncwarp();
+    return s;
+}
+
 // ----------------------------------------------------------------------------
 // Joint-histogram MI (Section 3.2, binning; Eq. 1 on the empirical
 // distribution): with joint counts c_xy and marginals c_x, c_y,
@@ -111,44 +146,33 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
         const uint32_t* ba = reinterpret_cast<const uint32_t*>(bins_a + (int64_t)p * n_pad);
         const uint32_t* bb = reinterpret_cast<const uint32_t*>(bins_b + (int64_t)q * n_pad);
-        // n <= 1024: at most 8 chunks of 128 members, 4 per lane each; the
-        // first chunk's words stay in registers, later ones are re-read (L1)
-        uint32_t wa0 = 0, wb0 = 0;
-        if (4 * lane < n) {
-            wa0 = __ldg(ba + lane);
-            wb0 = __ldg(bb + lane);
-        }
-        auto cell_of = [&](int c, int j) {
-            const int w = (c * 128 >> 2) + lane;
-            const uint32_t wa = c ? __ldg(ba + w) : wa0, wb = c ? __ldg(bb + w) : wb0;
-            return (int)((wa >> (8 * j)) & 0xffu) * B + (int)((wb >> (8 * j)) & 0xffu);
-        };
-        unsigned own = 0;  // bit 4c + j: this lane's member 128c + 4 lane + j owns its cell
-        for (int c = 0; c * 128 < n; ++c) {
-            const int m = c * 128 + 4 * lane;
-            if (m < n) {
-                const uint32_t wa = c ? __ldg(ba + (m >> 2)) : wa0;
-                const uint32_t wb = c ? __ldg(bb + (m >> 2)) : wb0;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int cell =
-                        (int)((wa >> (8 * j)) & 0xffu) * B + (int)((wb >> (8 * j)) & 0xffu);
-                    if (m + j < n && atomicAdd(&h[cell], 1) == 0) own |= 1u << (4 * c + j);
-                }
-            }
-        }
-        __syncwarp();
         long long s = 0;
-        for (unsigned o = own; o; o &= o - 1) {
-            const int bit = __ffs(o) - 1;
-            s += clogc[h[cell_of(bit >> 2, bit & 3)]];
+        if (n <= 128) {  // one slice: cells stay in registers
+            const int m = 4 * lane;
+            uint32_t wa = 0, wb = 0;
+            if (m < n) {
+                wa = __ldg(ba + lane);
+                wb = __ldg(bb + lane);
+            }
+            int cell[4];
+            unsigned own = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                cell[j] = (int)((wa >> (8 * j)) & 0xffu) * B + (int)((wb >> (8 * j)) & 0xffu);
+                if (m + j < n && atomicAdd(&h[cell[j]], 1) == 0) own |= 1u << j;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((own >> j) & 1u) s += clogc[h[cell[j]]];
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((own >> j) & 1u) h[cell[j]] = 0;
+            __syncwarp();
+        } else {
+            s = hist_slices(ba, bb, n, B, h, clogc, lane);
         }
-        __syncwarp();
-        for (unsigned o = own; o; o &= o - 1) {
-            const int bit = __ffs(o) - 1;
-            h[cell_of(bit >> 2, bit & 3)] = 0;
-        }
-        __syncwarp();
         s = warp_sum_i64(s);
         if (lane == 0) {
             const long long d = s - hm_a[p] - hm_b[q];
