@@ -355,8 +355,22 @@ cc_status cc_update_field(cc_ctx* ctx, int32_t field_id, const float* data, int 
     }
     CK(launch_ingest(src, f->n, f->P, f->n_pad, f->vals.as<float>(), ctx->status.as<int>(),
                      ctx->stream));
-    CK(launch_point_prep(*f, ctx->stream));
+    // bin planes already in use are rebuilt in the same pass (two bin counts)
+    PrepBins pb;
+    for (auto& kv : f->bins) {
+        if (pb.count == 2) break;
+        const int64_t* clogc = nullptr;
+        cc_status s = table(ctx, ctx->clogc_fix, f->n, false, &clogc);
+        if (s) return s;
+        pb.clogc = (const long long*)clogc;
+        pb.B[pb.count] = kv.first;
+        pb.bins[pb.count] = kv.second->as<uint8_t>();
+        pb.hmarg[pb.count] = f->hmarg[kv.first]->as<long long>();
+        ++pb.count;
+    }
+    CK(launch_point_prep(*f, ctx->stream, pb));
     f->version++;
+    for (int i = 0; i < pb.count; ++i) f->bins_version[pb.B[i]] = f->version;
     return CC_OK;
 }
 

@@ -120,7 +120,15 @@ void note_launch(int kernels = 1);
 // Kernel launchers (defined in the .cu files), all on `st`.
 cudaError_t launch_ingest(const float* in, int n, int64_t P, int n_pad, float* vals, int* status,
                           cudaStream_t st);
-cudaError_t launch_point_prep(const Field& f, cudaStream_t st);
+// bin planes rebuilt inside the per-point pass (at most two bin counts)
+struct PrepBins {
+    int count = 0;
+    int B[2] = {0, 0};
+    uint8_t* bins[2] = {nullptr, nullptr};
+    long long* hmarg[2] = {nullptr, nullptr};
+    const long long* clogc = nullptr;
+};
+cudaError_t launch_point_prep(const Field& f, cudaStream_t st, const PrepBins& pb = PrepBins());
 cudaError_t launch_bins(const Field& f, int B, const int64_t* clogc_fix, uint8_t* bins,
                         int64_t* hmarg, cudaStream_t st);
 cudaError_t launch_region_planes(const Field& f, const Region& r, cudaStream_t st);

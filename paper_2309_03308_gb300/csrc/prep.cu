@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
                  float* __restrict__ sorted,
                  uint16_t* __restrict__ perm, int16_t* __restrict__ rank2,
                  float* __restrict__ zhat, float* __restrict__ rhat,
-                 double* __restrict__ mean_out, double* __restrict__ ss_out) {
+                 double* __restrict__ mean_out, double* __restrict__ ss_out, PrepBins pb) {
+    __shared__ int bin_hist[kPrepWarps][16];
     constexpr int NP = 32 * E;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t p = (int64_t)blockIdx.x * kPrepWarps + warp;
@@ -220,6 +221,51 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
         sorted[row + g] = g < n ? sv[e] : CUDART_INF_F;
         perm[row + g] = (uint16_t)(key[e] & 0xffffu);
     }
+    // bin planes of the requested bin counts (same fp32 steps as k_bins)
+    if (pb.count > 0) {
+        __syncwarp();  // the sorted row written above is visible to the warp
+        const float lo = sorted[row], hi = sorted[row + n - 1];
+        const bool flat = !(hi > lo);
+        const float w = __fsub_rn(hi, lo);
+        float vm[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) vm[e] = vals[row + g0 + e];
+        int* hh = bin_hist[warp];
+        auto build = [&](const int B, uint8_t* brow, long long* hmarg) {
+            if (lane < 16) hh[lane] = 0;
+            __syncwarp();
+            uint32_t word = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int g = g0 + e;
+                int b = 0;
+                if (g < n && !flat) {
+                    const float t = __fsub_rn(vm[e], lo);
+                    const float r = __fdiv_rn(t, w);
+                    const float sc = __fmul_rn(r, (float)B);
+                    b = (int)floorf(sc);
+                    b = b < 0 ? 0 : (b > B - 1 ? B - 1 : b);
+                }
+                if (g < n) atomicAdd(&hh[b], 1);
+                if (E % 4 == 0) {
+                    word |= (uint32_t)b << (8 * (e & 3));
+                    if ((e & 3) == 3) {
+                        *reinterpret_cast<uint32_t*>(brow + g - 3) = word;
+                        word = 0;
+                    }
+                } else {
+                    brow[g] = (uint8_t)b;
+                }
+            }
+            __syncwarp();
+            long long sm = lane < B ? pb.clogc[hh[lane]] : 0;
+            sm = warp_sum_i64(sm);
+            if (lane == 0) hmarg[p] = sm;
+            __syncwarp();
+        };
+        build(pb.B[0], pb.bins[0] + row, pb.hmarg[0]);
+        if (pb.count > 1) build(pb.B[1], pb.bins[1] + row, pb.hmarg[1]);
+    }
     // run start a: prefix max of (start ? g : 0); run end b: suffix min of (end ? g : NP)
     const float prev_last = __shfl_up_sync(0xffffffffu, sv[E - 1], 1);
     const float next_first = __shfl_down_sync(0xffffffffu, sv[0], 1);
@@ -295,14 +341,14 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
     }
 }
 
-cudaError_t launch_point_prep(const Field& f, cudaStream_t st) {
+cudaError_t launch_point_prep(const Field& f, cudaStream_t st, const PrepBins& pb) {
     const unsigned blocks = (unsigned)((f.P + kPrepWarps - 1) / kPrepWarps);
     note_launch();
 #define CC_PREP(E)                                                                               \
     k_point_prep<E><<<blocks, kPrepWarps * 32, 0, st>>>(                                         \
         f.vals.as<float>(), f.P, f.n, (float)f.n, f.sorted.as<float>(), f.perm.as<uint16_t>(),   \
         f.rank2.as<int16_t>(), f.zhat.as<float>(), f.rhat.as<float>(), f.mean.as<double>(),      \
-        f.ss.as<double>())
+        f.ss.as<double>(), pb)
     switch (f.n_pad / 32) {  // n_pad is a power of two >= 32
         case 1: CC_PREP(1); break;
         case 2: CC_PREP(2); break;

@@ -76,6 +76,36 @@ def test_planes_with_ties(cc, orc):
     assert np.all(z == 0)
 
 
+def test_update_field_rebuilds_every_plane(cc, orc):
+    """After cc_update_field the planes, including the bin planes of the bin
+    counts already in use (rebuilt in the per-point pass) and of a new bin
+    count (built lazily), equal the oracle's for the new values."""
+    import torch
+    from paper_2309_03308_gb300 import CC_MI_BINNED, Params
+    X, Y, Z, n = 12, 10, 3, 100
+    F1 = gen.field(31, X, Y, Z, n)
+    F2 = gen.field(32, X, Y, Z, n)
+    F2[:, 0, 0, 0] = 2.5  # a constant member vector
+    fid = cc.load_field(F1)
+    pts = np.arange(X * Y * Z, dtype=np.uint32)
+    for B in (8, 16):
+        cc.get_plane(fid, 1, pts[:4], n, bins=B)  # bins for 8 and 16 are now in use
+    for src in (F2, torch.from_numpy(F2).cuda()):
+        cc.update_field(fid, src)
+        for B in (8, 16, 5):
+            assert np.array_equal(cc.get_plane(fid, 1, pts, n, bins=B), orc.bins(F2, pts, B)), B
+        assert np.array_equal(cc.get_plane(fid, 0, pts, n), orc.rank2(F2, pts))
+        srt = cc.get_plane(fid, 2, pts, n)
+        assert np.array_equal(srt, np.sort(F2.reshape(n, -1)[:, pts].T, axis=1))
+        pa, pb = all_unique_pairs(X * Y * Z)
+        pa, pb = pa[::37].copy(), pb[::37].copy()
+        for B in (8, 16):
+            got = cc.eval_pairs(fid, fid, Params(CC_MI_BINNED, bins=B), pa, pb)
+            ref = orc.eval_pairs(F2, oracle.MI_BINNED, pa, pb, bins=B)
+            assert np.abs(got - ref).max() < TOL
+    cc.free_field(fid)
+
+
 @pytest.mark.parametrize("offset,scale", [(0.0, 1.0), (1e4, 1e-2), (-3e5, 7.0), (1e-30, 1e-33)])
 def test_zhat_standardisation_accuracy(cc, offset, scale):
     """The unit-norm centred member vectors are within a few fp32 roundings of
