@@ -420,9 +420,9 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     const int rp = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     const int r = *d.round, R = d.R, Q = d.Q, S = R * d.T;
     const int s = r * R;
-    double* Lf = reinterpret_cast<double*>(cs);            // R x R (fp64 Cholesky)
-    float* G = reinterpret_cast<float*>(Lf + R * R);       // 32 rows x R of V[:, P]
-    float* covP = G + 32 * R;                              // R x R
+    float* G = reinterpret_cast<float*>(cs);               // 32 rows x 32 of V[:, P] (0-padded)
+    double* Lf = reinterpret_cast<double*>(G + 32 * 32);   // R x R (fp64 Cholesky)
+    float* covP = reinterpret_cast<float*>(Lf + R * R);    // R x R
     float* L = covP + R * R;                               // R x R fp32 copy
     float* gb = L + R * R;                        // R: V[:, P]^T beta
     float* b2 = gb + R;                           // R: new beta
@@ -467,24 +467,27 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     // covP = V[:, P]^T V[:, P] and gb = V[:, P]^T beta over the s old rows
     float cacc[4] = {0.f, 0.f, 0.f, 0.f};  // entries tid, tid+256, ... of R x R
     float gacc = 0.f;
-    for (int t0 = 0; t0 < s; t0 += 32) {
-        for (int e = tid; e < 32 * R; e += blockDim.x) {
-            const int t = t0 + e / R, j = e % R;
-            G[e] = t < s ? Vr[(int64_t)t * Q + P[j]] : 0.f;
+    auto gather = [&](int t0) {  // G[t][j] = V[t0 + t][P[j]], zero beyond s and R
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            const int t = t0 + (e >> 5), j = e & 31;
+            G[e] = (t < s && j < R) ? Vr[(int64_t)t * Q + P[j]] : 0.f;
         }
+    };
+    for (int t0 = 0; t0 < s; t0 += 32) {
+        gather(t0);
         __syncthreads();
         for (int q = 0; q < 4; ++q) {
             const int e = tid + q * blockDim.x;
             if (e < R * R) {
                 const int i = e / R, j = e % R;
                 float a = cacc[q];
-                for (int t = 0; t < 32; ++t) a = fmaf(G[t * R + i], G[t * R + j], a);
+                for (int t = 0; t < 32; ++t) a = fmaf(G[t * 32 + i], G[t * 32 + j], a);
                 cacc[q] = a;
             }
         }
         if (tid < R)
             for (int t = 0; t < 32 && t0 + t < s; ++t)
-                gacc = fmaf(G[t * R + tid], d.beta[(int64_t)rp * S + t0 + t], gacc);
+                gacc = fmaf(G[t * 32 + tid], d.beta[(int64_t)rp * S + t0 + t], gacc);
         __syncthreads();
     }
     for (int q = 0; q < 4; ++q) {
@@ -526,29 +529,52 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
         }
     }
     __syncthreads();
-    // new rows: V2 = L22^-1 (K(P, pool) - V[:, P]^T V), then mu, var updates
-    for (int c0 = 0; c0 < Q; c0 += blockDim.x) {
-        const int c = c0 + tid;
-        float w[32];
+    // new rows: V2 = L22^-1 (K(P, pool) - V[:, P]^T V), then mu, var updates.
+    // W = V[:, P]^T V over panels of 2 x 256 pool columns: a thread keeps the
+    // 32 x 2 block of W for its columns c and c + 256 in registers; per old row
+    // t it reads G[t][0..31] as eight broadcast float4 and two values of V
+    // (64 FMAs per 8 shared + 2 global loads), loading eight rows at a time.
+    constexpr int kPanel = 2 * kBosThreads;
+    for (int c0 = 0; c0 < Q; c0 += kPanel) {
+        const int cA = c0 + tid, cB = c0 + kBosThreads + tid;
+        float wA[32], wB[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) w[i] = 0.f;
+        for (int i = 0; i < 32; ++i) wA[i] = wB[i] = 0.f;
         for (int t0 = 0; t0 < s; t0 += 32) {
             __syncthreads();
-            for (int e = tid; e < 32 * R; e += blockDim.x) {
-                const int t = t0 + e / R, j = e % R;
-                G[e] = t < s ? Vr[(int64_t)t * Q + P[j]] : 0.f;
-            }
+            gather(t0);
             __syncthreads();
-            if (c < Q) {
-                for (int t = 0; t < 32 && t0 + t < s; ++t) {
-                    const float v = Vr[(int64_t)(t0 + t) * Q + c];
+            const int tn = min(32, s - t0);
+            // eight rows per step: their 16 loads of V are in flight together
+            for (int tb = 0; tb < tn; tb += 8) {
+                float vA[8], vB[8];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (i < R) w[i] = fmaf(G[t * R + i], v, w[i]);
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t row = (int64_t)(t0 + tb + u) * Q;
+                    const bool ok = tb + u < tn;
+                    vA[u] = ok && cA < Q ? __ldcs(Vr + row + cA) : 0.f;
+                    vB[u] = ok && cB < Q ? __ldcs(Vr + row + cB) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float4* g4 = reinterpret_cast<const float4*>(G + (tb + u) * 32);
+#pragma unroll
+                    for (int i4 = 0; i4 < 8; ++i4) {
+                        const float4 g = g4[i4];
+                        wA[4 * i4 + 0] = fmaf(g.x, vA[u], wA[4 * i4 + 0]);
+                        wA[4 * i4 + 1] = fmaf(g.y, vA[u], wA[4 * i4 + 1]);
+                        wA[4 * i4 + 2] = fmaf(g.z, vA[u], wA[4 * i4 + 2]);
+                        wA[4 * i4 + 3] = fmaf(g.w, vA[u], wA[4 * i4 + 3]);
+                        wB[4 * i4 + 0] = fmaf(g.x, vB[u], wB[4 * i4 + 0]);
+                        wB[4 * i4 + 1] = fmaf(g.y, vB[u], wB[4 * i4 + 1]);
+                        wB[4 * i4 + 2] = fmaf(g.z, vB[u], wB[4 * i4 + 2]);
+                        wB[4 * i4 + 3] = fmaf(g.w, vB[u], wB[4 * i4 + 3]);
+                    }
                 }
             }
         }
-        if (c < Q) {
+        auto finish = [&](int c, float (&w)[32]) {
+            if (c >= Q) return;
             const float* pc = d.pool + ((int64_t)rp * Q + c) * 6;
             float pcl[6];
 #pragma unroll
@@ -558,6 +584,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
             for (int i = 0; i < 32; ++i) {
                 if (i < R) {
                     float x = matern52(pp + i * 6, pcl, inv_ell, sf2) - w[i];
+#pragma unroll
                     for (int q = 0; q < i; ++q) x = fmaf(-L[i * R + q], w[q], x);
                     x /= L[i * R + i];
                     w[i] = x;
@@ -568,7 +595,9 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
             }
             var[c] -= dv;
             mu[c] += dm;
-        }
+        };
+        finish(cA, wA);
+        finish(cB, wB);
     }
     if (tid < R) {
         d.obs[(int64_t)rp * S + s + tid] = P[tid];
@@ -632,7 +661,7 @@ size_t propose_smem(const BosDev& d) {
 }
 size_t condition_smem(const BosDev& d) {
     const int R = d.R;
-    return 32 * R * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 + R * 6 * 4 + 2 * R * 4 + 16;
+    return 32 * 32 * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 + R * 6 * 4 + 2 * R * 4 + 16;
 }
 size_t eval_smem(const BosDev& d, int warps) {
     const int pl = (d.n + 2) & ~1;
