@@ -153,8 +153,8 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
     float* cov = reinterpret_cast<float*>(SL + M);
     float* pos = cov + M * M;
     float* msl = pos + M * 6;
-    float* rowbuf = msl + M;        // 8 rows x M
-    float* red_v = rowbuf + 8 * M;  // per-warp argmax
+    float* rowbuf = msl + M;         // 16 rows x M
+    float* red_v = rowbuf + 16 * M;  // per-warp argmax
     int* red_i = reinterpret_cast<int*>(red_v + 32);
     const float* mu = d.mu + (int64_t)rp * Q;
     const float* var = d.var + (int64_t)rp * Q;
@@ -201,23 +201,25 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
     const float* Vr = d.V + (int64_t)rp * (R * d.T) * Q;
-    for (int t0 = 0; t0 < s; t0 += 8) {
-        for (int e = tid; e < 8 * M; e += blockDim.x) {
+    // 16 gathered rows per barrier; per row a thread reads its 2 x per
+    // operands once and updates its per x per block (per <= 8)
+    for (int t0 = 0; t0 < s; t0 += 16) {
+        for (int e = tid; e < 16 * M; e += blockDim.x) {
             const int t = t0 + e / M, i = e % M;
             rowbuf[e] = t < s ? Vr[(int64_t)t * Q + SL[i]] : 0.f;
         }
         __syncthreads();
-        for (int t = 0; t < 8; ++t) {
+        for (int t = 0; t < 16; ++t) {
+            float a[8], b[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                if (i >= per) break;
-                const float a = rowbuf[t * M + ti * per + i];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (j >= per) break;
-                    acc[i][j] = fmaf(a, rowbuf[t * M + tj * per + j], acc[i][j]);
-                }
+                a[i] = i < per ? rowbuf[t * M + ti * per + i] : 0.f;
+                b[i] = i < per ? rowbuf[t * M + tj * per + i] : 0.f;
             }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -657,7 +659,7 @@ cc_status bfail(cc_ctx* c, cc_status s, const char* fmt, ...) {
 
 size_t propose_smem(const BosDev& d) {
     const int M = d.M;
-    return (size_t)d.Q * 8 + M * 4 + (size_t)M * M * 4 + M * 6 * 4 + M * 4 + 8 * M * 4 + 32 * 8;
+    return (size_t)d.Q * 8 + M * 4 + (size_t)M * M * 4 + M * 6 * 4 + M * 4 + 16 * M * 4 + 32 * 8;
 }
 size_t condition_smem(const BosDev& d) {
     const int R = d.R;
