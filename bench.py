@@ -18,6 +18,9 @@ built stage of the path on the resident field:
 A second workload with n = 1000 (the same two regions, only those boxes
 generated) is timed in the same run and reported under "m1000": FP32 SIMT vs
 BF16 vs FP8 all-pairs extremes and KSG on 1,000,000 sampled pairs.
+"one_to_all" times the paper's Table 1 workload (one reference point against
+all 1.76 M points of a 352 x 250 x 20 field, Pearson and KSG, n = 100 and
+1000), with the paper's RTX 3090 times as context.
 
 Multi-GPU (torchrun): every rank runs its own replica with its own sampler
 stream (weak scaling); the only collectives are the timing barrier and max.
@@ -403,6 +406,9 @@ def run_ours(args, rank, world, local_rank):
             "ksg_pairs_per_s": PRE["sampled_pairs"] / (st2["ksg"] * 1e-3),
             "results": wl2.results, "stage_roofline": roof2, "gpu_launches": int(l2),
             "e2e_ms_per_step": e2e2}
+    if not args.skip_one_to_all:
+        line["one_to_all"] = [run_one_to_all(args, cc, dev, stream, n)
+                              for n in ((100,) if args.skip_m1000 else (100, 1000))]
     sur = None
     if not args.skip_surrogate:
         line["surrogate"], sur = run_surrogate(args, cc, dev, stream, rank)
@@ -412,6 +418,46 @@ def run_ours(args, rank, world, local_rank):
         sur.close()
     cc.close()
     return line
+
+
+# The paper's own timing workload (Table 1): correlations from one reference
+# point to all 1.76 M points of a 250 x 352 x 20 grid, at n = 100 and 1000; the
+# paper's RTX 3090 times are quoted as context (other hardware).
+PAPER_TABLE1_GPU_S = {100: {"pearson": 0.002, "ksg": 0.672}, 1000: {"pearson": 0.21, "ksg": 35.9}}
+
+
+def run_one_to_all(args, cc, dev, stream, n):
+    import torch
+    import paper_2309_03308_gb300 as pg
+    from paper_2309_03308_gb300 import Params
+    X, Y, Z = 352, 250, 20
+    P = X * Y * Z
+    F = gen.field(5, X, Y, Z, n)
+    fid = cc.load_field(torch.from_numpy(F).to(dev))
+    del F
+    ref = X // 2 + X * (Y // 2 + Y * (Z // 2))
+    pa = torch.full((P,), ref, dtype=torch.int32, device=dev)
+    pb = torch.arange(P, dtype=torch.int32, device=dev)
+    out = torch.empty(P, device=dev)
+    res = {"workload": f"one-to-all-{X}x{Y}x{Z}-n{n}", "pairs": P}
+    for name, prm in (("pearson", Params(pg.CC_PEARSON)), ("ksg", Params(pg.CC_MI_KSG, k=10))):
+        ms = []
+        for rep in range(4):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cc.eval_pairs(fid, fid, prm, pa, pb, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep:  # the first is a warm-up
+                ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms) * 1e-3
+        res[name] = {"s": t, "pairs_per_s": P / t,
+                     "paper_rtx3090_s": PAPER_TABLE1_GPU_S[n][name],
+                     "speedup_vs_paper_gpu": PAPER_TABLE1_GPU_S[n][name] / t}
+    cc.free_field(fid)
+    return res
 
 
 def run_surrogate(args, cc, dev, stream, rank):
@@ -475,19 +521,78 @@ def run_surrogate(args, cc, dev, stream, rank):
            "screen_pairs_per_s": 20480 * 20480 / screen_s,
            "top_k": K, "topk_exact_ksg_max": float(exact_top.max()),
            "random_k_exact_ksg_max": float(exact_rand.max())}
+    # screen-and-verify: exact KSG on the surrogate's top `budget` pairs,
+    # against exact KSG on `budget` uniform pairs of the same region pair
+    kp = Params(pg.CC_MI_KSG, k=cfg["k"])
+    sv = []
+    for bud in (2_000_000, 8_000_000):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = sur.screen_verify(ra, rb, bud, kp)
+        t_sv = time.perf_counter() - t0
+        qa, qb = cc.sample_pairs(ra, rb, 41, bud, pa=torch.empty(bud, dtype=torch.int32,
+                                                                 device=dev),
+                                 pb=torch.empty(bud, dtype=torch.int32, device=dev))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rr = cc.segment_extremes(fe, kp, qa, qb, [0, bud])[0]
+        t_rand = time.perf_counter() - t0
+        sv.append({"budget": bud, "exact_pairs": r["count"], "screen_verify_s": t_sv,
+                   "screen_verify_ksg_max": r["max"], "random_ksg_max": rr["max"],
+                   "random_s": t_rand})
+    out["screen_verify"] = sv
+
+    def exhaustive_ksg(rga, rgb, Aa, Bb):
+        best, best_pair = -np.inf, None
+        rows = 2048
+        for a0 in range(0, len(Aa), rows):
+            qa = torch.from_numpy(np.repeat(Aa[a0:a0 + rows], len(Bb)).astype(np.int32)).to(dev)
+            qb = torch.from_numpy(np.tile(Bb, min(rows, len(Aa) - a0)).astype(np.int32)).to(dev)
+            r = cc.segment_extremes(fe, kp, qa, qb, [0, qa.shape[0]])[0]
+            if r["max"] > best:
+                best = r["max"]
+                best_pair = (Aa[a0 + r["argmax"] // len(Bb)], Bb[r["argmax"] % len(Bb)])
+        return best, best_pair
+
+    if args.recall:
+        # more region pairs of the held-out field: recall of the exhaustive KSG
+        # maximum (within 0.01) by screen-and-verify and by random sampling at
+        # the same exact-evaluation budget
+        extra = [((32, 32, 0, 64, 64, 20), (288, 192, 0, 320, 224, 20)),
+                 ((160, 96, 0, 192, 128, 20), (96, 200, 0, 128, 232, 20)),
+                 ((0, 0, 0, 32, 32, 20), (320, 224, 0, 352, 256, 20))]
+        rec = []
+        for bx_a, bx_b in [(boxa, boxb)] + extra:
+            xa, xb = cc.define_regions(fe, [bx_a, bx_b])
+            t0 = time.perf_counter()
+            best, _ = exhaustive_ksg(xa, xb, pts(bx_a), pts(bx_b))
+            t_ex = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            r = sur.screen_verify(xa, xb, 8_000_000, kp)
+            t_sv = time.perf_counter() - t0
+            qa, qb = cc.sample_pairs(xa, xb, 43, 8_000_000)
+            rr = cc.segment_extremes(fe, kp, qa, qb, [0, len(qa)])[0]
+            rec.append({"boxes": [bx_a, bx_b], "exhaustive_ksg_max": best, "exhaustive_s": t_ex,
+                        "screen_verify_ksg_max": r["max"], "screen_verify_s": t_sv,
+                        "screen_verify_recall_0.01": bool(r["max"] >= best - 0.01),
+                        "random_ksg_max": rr["max"],
+                        "random_recall_0.01": bool(rr["max"] >= best - 0.01)})
+        out["recall_8M_budget"] = rec
     if args.recall:
         # exhaustive KSG over all 419M pairs of the region pair, in slices
         t0 = time.perf_counter()
-        best = -np.inf
-        rows = 2048
-        for a0 in range(0, len(A), rows):
-            qa = torch.from_numpy(np.repeat(A[a0:a0 + rows], len(B)).astype(np.int32)).to(dev)
-            qb = torch.from_numpy(np.tile(B, min(rows, len(A) - a0)).astype(np.int32)).to(dev)
-            r = cc.segment_extremes(fe, Params(pg.CC_MI_KSG, k=cfg["k"]), qa, qb,
-                                    [0, qa.shape[0]])[0]
-            best = max(best, r["max"])
+        best, best_pair = exhaustive_ksg(ra, rb, A, B)
         out["exhaustive_ksg_max"] = float(best)
         out["exhaustive_ksg_s"] = time.perf_counter() - t0
+        # where the exhaustive maximum ranks in the surrogate's ordering, from
+        # the predictions of 4M uniform pairs of the region pair
+        pbest = sur.predict(fe, np.array([best_pair[0]], np.uint32),
+                            np.array([best_pair[1]], np.uint32))[0]
+        rng = np.random.default_rng(9)
+        sa = A[rng.integers(0, len(A), 4_000_000)]
+        sb = B[rng.integers(0, len(B), 4_000_000)]
+        frac = float(np.mean(sur.predict(fe, sa, sb) > pbest))
+        out["surrogate_rank_of_exhaustive_max_est"] = frac * len(A) * len(B)
         out["screen_recall_0.01"] = bool(exact_top.max() >= best - 0.01)
         out["random_recall_0.01"] = bool(exact_rand.max() >= best - 0.01)
     cc.free_field(fe)
@@ -710,6 +815,8 @@ def main():
                     help="do not time the n = 1000 workload")
     ap.add_argument("--skip-context", action="store_true",
                     help="do not time the batched BOS context view")
+    ap.add_argument("--skip-one-to-all", action="store_true",
+                    help="do not time the one-to-all volume (the paper's Table 1 workload)")
     ap.add_argument("--skip-surrogate", action="store_true",
                     help="do not train and time the learned surrogate")
     ap.add_argument("--quick-surrogate", action="store_true",

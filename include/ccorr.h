@@ -447,6 +447,20 @@ cc_status cc_sur_predict(cc_ctx* ctx, cc_sur* sur, int32_t field_id, const uint3
 cc_status cc_sur_screen(cc_ctx* ctx, cc_sur* sur, int32_t region_a, int32_t region_b, int topk,
                         uint64_t* ids, float* preds);
 
+/*
+ * Surrogate-screened region-pair extremes: screen all pairs of two regions
+ * (as cc_sur_screen), keep the `budget` pairs with the largest predictions
+ * (ties at the cut may add a few; budget in [1, 2^24]), evaluate exactly those
+ * pairs with `params` (any measure, as cc_eval_pairs) and return their exact
+ * max / argmax / min / argmin in *out; argmax and argmin are linear pair
+ * indices a * |B| + b, count is the number of pairs evaluated exactly. The
+ * surrogate only chooses which pairs are evaluated: every reported value is
+ * an exact evaluation. The maximum over the whole region pair is found
+ * whenever its pair ranks within the budget in the surrogate's ordering.
+ */
+cc_status cc_sur_screen_verify(cc_ctx* ctx, cc_sur* sur, int32_t region_a, int32_t region_b,
+                               int64_t budget, const cc_params* params, cc_rp_result* out);
+
 /* Release the surrogate. */
 cc_status cc_sur_destroy(cc_ctx* ctx, cc_sur* sur);
 

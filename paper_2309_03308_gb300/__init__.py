@@ -336,6 +336,14 @@ class Surrogate:
                                                    ids.ctypes.data, preds.ctypes.data))
         return ids, preds
 
+    def screen_verify(self, ra: int, rb: int, budget: int, params: Params):
+        """Exact extremes over the `budget` pairs the surrogate ranks highest."""
+        res = _lib.cc_rp_result()
+        prm = params.c()
+        self.ctx._check(self.ctx.lib.cc_sur_screen_verify(self.ctx.h, self.h, ra, rb, budget,
+                                                          ctypes.byref(prm), ctypes.byref(res)))
+        return _res(res)
+
     def close(self):
         if self.h:
             self.ctx.lib.cc_sur_destroy(self.ctx.h, self.h)

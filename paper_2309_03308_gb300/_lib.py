@@ -97,6 +97,8 @@ SIGNATURES = {
     "cc_sur_train": (_S, [_P, _P, _I32, _P, _P, _P, _I64, _I, _I, _I, ctypes.c_float, _U64, _P]),
     "cc_sur_predict": (_S, [_P, _P, _I32, _P, _P, _I64, _I, _P, _I]),
     "cc_sur_screen": (_S, [_P, _P, _I32, _I32, _I, _P, _P]),
+    "cc_sur_screen_verify": (_S, [_P, _P, _I32, _I32, _I64, ctypes.POINTER(cc_params),
+                                  ctypes.POINTER(cc_rp_result)]),
     "cc_sur_destroy": (_S, [_P, _P]),
     "cc_all_pairs_static": (_S, [_P, _I64, _P, _I64, _I, _I64, _I64, _I, _P, _I64, _P, _P]),
     "cc_launch_count": (_S, [ctypes.POINTER(_U64)]),

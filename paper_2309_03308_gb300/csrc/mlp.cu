@@ -417,6 +417,19 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// linear pair index a * nb + b -> point ids of the pair
+__global__ void k_sur_ids_to_pairs(const uint32_t* __restrict__ ids, int64_t count,
+                                   const uint32_t* __restrict__ pts_a,
+                                   const uint32_t* __restrict__ pts_b, int64_t nb,
+                                   uint32_t* __restrict__ pa, uint32_t* __restrict__ pb) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t id = ids[i];
+        pa[i] = pts_a[id / nb];
+        pb[i] = pts_b[id % nb];
+    }
+}
+
 }  // namespace cc
 
 // ============================================================================
@@ -567,6 +580,73 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
 Field* sfield(cc_ctx* ctx, int32_t id) {
     if (id < 0 || id >= (int32_t)ctx->fields.size()) return nullptr;
     return ctx->fields[id].get();
+}
+
+// Predictions for every pair of two regions of one field into pred [|A|][|B|]
+// (self region pairs: -inf for b <= a).
+cc_status screen_predict(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t region_b,
+                         DevMem& pred, Region** ra_out, Region** rb_out) {
+    if (region_a < 0 || region_a >= (int)ctx->regions.size() || !ctx->regions[region_a] ||
+        region_b < 0 || region_b >= (int)ctx->regions.size() || !ctx->regions[region_b])
+        return sfail(ctx, CC_ERR_INVALID_ARG, "unknown region");
+    Region& ra = *ctx->regions[region_a];
+    Region& rb = *ctx->regions[region_b];
+    if (ra.field != rb.field) return sfail(ctx, CC_ERR_INVALID_ARG, "regions of one field only");
+    Field* f = sfield(ctx, ra.field);
+    if (!f || f->n != s->n) return sfail(ctx, CC_ERR_INVALID_ARG, "field does not match");
+    if ((uint64_t)ra.np * rb.np >= (1ull << 32))
+        return sfail(ctx, CC_ERR_INVALID_ARG, "|A| * |B| must be below 2^32");
+    cudaStream_t st = ctx->stream;
+    const int n = s->n;
+    const SurOff& o = s->off;
+    const int64_t na = ra.np, nb = rb.np;
+    cc_status r = ensure_batch(ctx, s, (std::max(na, nb) + 1) / 2);
+    if (r) return r;
+    DevMem Ea, Eb, Ua, Vb;
+    SK(Ea.alloc(4 * na * kE));
+    SK(Eb.alloc(4 * nb * kE));
+    SK(Ua.alloc(4 * na * kH3));
+    SK(Vb.alloc(4 * nb * kH3));
+    SK(pred.alloc(4 * (size_t)na * nb));
+    const float* w = s->w.as<float>();
+    // per-point encoder (bf16 weights, as in training) and head projections
+    for (int side = 0; side < 2; ++side) {
+        const Region& rg = side ? rb : ra;
+        const int64_t np = rg.np;
+        float* E = side ? Eb.as<float>() : Ea.as<float>();
+        note_launch(2);
+        k_sur_gather_z<<<grid1(np * n), 256, 0, st>>>(f->zhat.as<float>(), n, f->n_pad,
+                                                      sqrtf((float)(n - 1)),
+                                                      rg.pts.as<uint32_t>(), np, s->X0.as<bf16>());
+        SK(mm(s->X0.as<bf16>(), n, 1, s->wb.as<bf16>() + o.W1, 1, n, s->A1.as<float>(), kH1,
+              (int)np, kH1, n, 0, st));
+        k_sur_bias_gelu<<<grid1(np * kH1), 256, 0, st>>>(s->A1.as<float>(), w + o.b1, np, kH1,
+                                                         s->H1.as<bf16>());
+        SK(mm(s->H1.as<bf16>(), kH1, 1, s->wb.as<bf16>() + o.W2, 1, kH1, E, kE, (int)np, kE, kH1,
+              0, st));
+        note_launch();
+        k_sur_add_bias<<<grid1(np * kE), 256, 0, st>>>(E, w + o.b2, np, kE);
+        float* UV = side ? Vb.as<float>() : Ua.as<float>();
+        SK(mm(E, kE, 1, w + o.W3 + side * kE, 1, kHeadIn, UV, kH3, (int)np, kH3, kE, 0, st));
+        if (!side) {
+            note_launch();
+            k_sur_add_bias<<<grid1(np * kH3), 256, 0, st>>>(UV, w + o.b3, np, kH3);
+        }
+    }
+    const size_t smem = 4 * (size_t)(kH3 * kE + kH3 * 3 + kH3 + kScrI * kE + kScrJ * kE +
+                                     kScrI * kH3 + kScrJ * kH3);
+    SK(cudaFuncSetAttribute(k_sur_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((nb + kScrJ - 1) / kScrJ), (unsigned)((na + kScrI - 1) / kScrI));
+    note_launch();
+    k_sur_screen<<<grid, 256, smem, st>>>(Ea.as<float>(), Ua.as<float>(), Eb.as<float>(),
+                                          Vb.as<float>(), w, o.W3, o.w4, o.b4,
+                                          ra.pts.as<uint32_t>(), rb.pts.as<uint32_t>(), na, nb,
+                                          region_a == region_b, f->X, f->Y, f->Z, s->tmean,
+                                          s->tsd, pred.as<float>());
+    SK(cudaGetLastError());
+    *ra_out = &ra;
+    *rb_out = &rb;
+    return CC_OK;
 }
 
 }  // namespace
@@ -810,64 +890,12 @@ cc_status cc_sur_screen(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t region
                         uint64_t* ids, float* preds) {
     if (!ctx || !s || topk < 1 || topk > 8192 || !ids || !preds)
         return sfail(ctx, CC_ERR_INVALID_ARG, "bad arguments (1 <= topk <= 8192)");
-    if (region_a < 0 || region_a >= (int)ctx->regions.size() || !ctx->regions[region_a] ||
-        region_b < 0 || region_b >= (int)ctx->regions.size() || !ctx->regions[region_b])
-        return sfail(ctx, CC_ERR_INVALID_ARG, "unknown region");
-    Region& ra = *ctx->regions[region_a];
-    Region& rb = *ctx->regions[region_b];
-    if (ra.field != rb.field) return sfail(ctx, CC_ERR_INVALID_ARG, "regions of one field only");
-    Field* f = sfield(ctx, ra.field);
-    if (!f || f->n != s->n) return sfail(ctx, CC_ERR_INVALID_ARG, "field does not match");
-    if ((uint64_t)ra.np * rb.np >= (1ull << 32))
-        return sfail(ctx, CC_ERR_INVALID_ARG, "|A| * |B| must be below 2^32");
-    cudaStream_t st = ctx->stream;
-    const int n = s->n;
-    const SurOff& o = s->off;
-    const int64_t na = ra.np, nb = rb.np;
-    cc_status r = ensure_batch(ctx, s, (std::max(na, nb) + 1) / 2);
+    DevMem pred, aux;
+    Region *pra = nullptr, *prb = nullptr;
+    cc_status r = screen_predict(ctx, s, region_a, region_b, pred, &pra, &prb);
     if (r) return r;
-    DevMem Ea, Eb, Ua, Vb, pred, aux;
-    SK(Ea.alloc(4 * na * kE));
-    SK(Eb.alloc(4 * nb * kE));
-    SK(Ua.alloc(4 * na * kH3));
-    SK(Vb.alloc(4 * nb * kH3));
-    SK(pred.alloc(4 * (size_t)na * nb));
-    const float* w = s->w.as<float>();
-    // per-point encoder (bf16 weights, as in training) and head projections
-    for (int side = 0; side < 2; ++side) {
-        const Region& rg = side ? rb : ra;
-        const int64_t np = rg.np;
-        float* E = side ? Eb.as<float>() : Ea.as<float>();
-        note_launch(2);
-        k_sur_gather_z<<<grid1(np * n), 256, 0, st>>>(f->zhat.as<float>(), n, f->n_pad,
-                                                      sqrtf((float)(n - 1)),
-                                                      rg.pts.as<uint32_t>(), np, s->X0.as<bf16>());
-        SK(mm(s->X0.as<bf16>(), n, 1, s->wb.as<bf16>() + o.W1, 1, n, s->A1.as<float>(), kH1,
-              (int)np, kH1, n, 0, st));
-        k_sur_bias_gelu<<<grid1(np * kH1), 256, 0, st>>>(s->A1.as<float>(), w + o.b1, np, kH1,
-                                                         s->H1.as<bf16>());
-        SK(mm(s->H1.as<bf16>(), kH1, 1, s->wb.as<bf16>() + o.W2, 1, kH1, E, kE, (int)np, kE, kH1,
-              0, st));
-        note_launch();
-        k_sur_add_bias<<<grid1(np * kE), 256, 0, st>>>(E, w + o.b2, np, kE);
-        float* UV = side ? Vb.as<float>() : Ua.as<float>();
-        SK(mm(E, kE, 1, w + o.W3 + side * kE, 1, kHeadIn, UV, kH3, (int)np, kH3, kE, 0, st));
-        if (!side) {
-            note_launch();
-            k_sur_add_bias<<<grid1(np * kH3), 256, 0, st>>>(UV, w + o.b3, np, kH3);
-        }
-    }
-    const size_t smem = 4 * (size_t)(kH3 * kE + kH3 * 3 + kH3 + kScrI * kE + kScrJ * kE +
-                                     kScrI * kH3 + kScrJ * kH3);
-    SK(cudaFuncSetAttribute(k_sur_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((nb + kScrJ - 1) / kScrJ), (unsigned)((na + kScrI - 1) / kScrI));
-    note_launch();
-    k_sur_screen<<<grid, 256, smem, st>>>(Ea.as<float>(), Ua.as<float>(), Eb.as<float>(),
-                                          Vb.as<float>(), w, o.W3, o.w4, o.b4,
-                                          ra.pts.as<uint32_t>(), rb.pts.as<uint32_t>(), na, nb,
-                                          region_a == region_b, f->X, f->Y, f->Z, s->tmean,
-                                          s->tsd, pred.as<float>());
-    SK(cudaGetLastError());
+    cudaStream_t st = ctx->stream;
+    const int64_t na = pra->np, nb = prb->np;
     // top-k by histogram selection, then one sorting CTA
     const size_t o_hist = 0, o_sel = 4 * 4096, o_idx = o_sel + 256, o_tv = o_idx + 4 * 8192,
                  o_ti = o_tv + 4 * 8192;
@@ -884,6 +912,56 @@ cc_status cc_sur_screen(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t region
     SK(cudaMemcpyAsync(preds, ab + o_tv, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
     SK(cudaMemcpyAsync(ids, ab + o_ti, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
     SK(cudaStreamSynchronize(st));
+    return CC_OK;
+}
+
+cc_status cc_sur_screen_verify(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t region_b,
+                               int64_t budget, const cc_params* params, cc_rp_result* out) {
+    if (!ctx || !s || !params || !out || budget < 1 || budget > (1 << 24))
+        return sfail(ctx, CC_ERR_INVALID_ARG, "bad arguments (1 <= budget <= 2^24)");
+    DevMem pred, aux, pairs;
+    Region *pra = nullptr, *prb = nullptr;
+    cc_status r = screen_predict(ctx, s, region_a, region_b, pred, &pra, &prb);
+    if (r) return r;
+    cudaStream_t st = ctx->stream;
+    const int64_t na = pra->np, nb = prb->np, N = na * nb;
+    // the budget's largest predictions (threshold selection; ties at the cut
+    // fill up to a quarter more before the rest is dropped)
+    const int64_t cap = std::min<int64_t>(N, budget + std::max<int64_t>(budget / 4, 4096));
+    const size_t o_hist = 0, o_sel = 4 * 4096, o_idx = o_sel + 256;
+    SK(aux.alloc(o_idx + 4 * (size_t)cap));
+    unsigned char* ab = aux.as<unsigned char>();
+    SK(cudaMemsetAsync(ab, 0, o_idx, st));
+    uint32_t* idx = (uint32_t*)(ab + o_idx);
+    SK(launch_select_top(pred.as<float>(), N, 1.f, (unsigned)budget, (unsigned*)(ab + o_hist),
+                         (Select*)(ab + o_sel), idx, (unsigned)cap, st));
+    Select hs;
+    SK(cudaMemcpyAsync(&hs, ab + o_sel, sizeof hs, cudaMemcpyDeviceToHost, st));
+    SK(cudaStreamSynchronize(st));
+    const int64_t cnt = std::min<int64_t>(hs.count, cap);
+    if (cnt == 0) {
+        *out = cc_rp_result{-INFINITY, INFINITY, ~0ull, ~0ull, 0};
+        return CC_OK;
+    }
+    SK(pairs.alloc(8 * (size_t)cnt));
+    uint32_t* pa = pairs.as<uint32_t>();
+    uint32_t* pb = pa + cnt;
+    note_launch();
+    k_sur_ids_to_pairs<<<grid1(cnt), 256, 0, st>>>(idx, cnt, pra->pts.as<uint32_t>(),
+                                                   prb->pts.as<uint32_t>(), nb, pa, pb);
+    SK(cudaGetLastError());
+    const int64_t offs[2] = {0, cnt};
+    r = cc_segment_extremes(ctx, pra->field, params, pa, pb, 1, offs, 1, nullptr, out);
+    if (r) return r;
+    // list positions -> linear pair indices of the region pair
+    uint32_t lin[2] = {0, 0};
+    if (out->argmax < (uint64_t)cnt)
+        SK(cudaMemcpyAsync(&lin[0], idx + out->argmax, 4, cudaMemcpyDeviceToHost, st));
+    if (out->argmin < (uint64_t)cnt)
+        SK(cudaMemcpyAsync(&lin[1], idx + out->argmin, 4, cudaMemcpyDeviceToHost, st));
+    SK(cudaStreamSynchronize(st));
+    if (out->argmax < (uint64_t)cnt) out->argmax = lin[0];
+    if (out->argmin < (uint64_t)cnt) out->argmin = lin[1];
     return CC_OK;
 }
 

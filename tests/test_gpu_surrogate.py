@@ -123,3 +123,37 @@ def test_screen_beats_random_at_equal_budget(env, orc):
     assert np.mean(gains) > 0, gains
     assert recall_s >= recall_r
     sur.close()
+
+
+def test_screen_verify_is_exact_on_the_screened_pairs(env, orc):
+    """Screen-and-verify: every reported value is an exact evaluation. With a
+    budget covering all pairs it equals exhaustive evaluation; with a small
+    budget it equals the exact maximum over the screen's own top list."""
+    from paper_2309_03308_gb300 import CC_MI_KSG, CC_PEARSON, Params, Surrogate
+    ctx, F, fid = env
+    P = X * Y * Z
+    rng = np.random.default_rng(8)
+    pa = rng.integers(0, P, 30000).astype(np.uint32)
+    pb = rng.integers(0, P, 30000).astype(np.uint32)
+    t = ctx.eval_pairs(fid, fid, Params(CC_MI_KSG, k=5), pa, pb)
+    sur = Surrogate(ctx, N, seed=9)
+    sur.train(fid, pa, pb, t, epochs=3, batch=2048, lr=2e-3, seed=10)
+    boxes = [(0, 0, 0, 12, 10, 3), (12, 10, 3, 24, 20, 6)]
+    ra, rb = ctx.define_regions(fid, boxes)
+    A = oracle.box_points(X, Y, Z, boxes[0])
+    B = oracle.box_points(X, Y, Z, boxes[1])
+    allpa, allpb = np.repeat(A, len(B)), np.tile(B, len(A))
+    for prm, kind in ((Params(CC_MI_KSG, k=5), oracle.MI_KSG), (Params(CC_PEARSON), oracle.PEARSON)):
+        full = orc.eval_pairs(F, kind, allpa, allpb, k=5)
+        res = sur.screen_verify(ra, rb, len(full), prm)
+        assert res["count"] == len(full)
+        assert abs(res["max"] - full.max()) < 1e-5 and abs(res["min"] - full.min()) < 1e-5
+        assert abs(full[res["argmax"]] - full.max()) < 1e-5
+        assert abs(full[res["argmin"]] - full.min()) < 1e-5
+        ids, _ = sur.screen(ra, rb, 256)
+        small = sur.screen_verify(ra, rb, 256, prm)
+        assert 256 <= small["count"] <= 256 + 4096
+        sub = full[ids.astype(np.int64)]
+        assert small["max"] >= sub.max() - 1e-5  # the screened set contains the top list
+        assert abs(full[small["argmax"]] - small["max"]) < 1e-5
+    sur.close()
