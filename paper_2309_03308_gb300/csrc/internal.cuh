@@ -167,6 +167,12 @@ struct Select {
     unsigned overflow;   // candidates beyond capacity
     unsigned pass1;      // candidates of the first pass (the second appends after them)
 };
+cudaError_t launch_sur_screen_tc(const float* Ea, const float* Ua, const float* Eb,
+                                 const void* wb, const float* w, int64_t oW3, int64_t ow4,
+                                 int64_t ob4, const uint32_t* pts_a, const uint32_t* pts_b,
+                                 int64_t na, int64_t nb, int self, int X, int Y, int Z,
+                                 float tmean, float tsd, float* pred, int* status,
+                                 cudaStream_t st);
 cudaError_t launch_tc_chunk_extremes(bool fp8, bool scaled, const void* qa, int64_t na,
                                      int64_t na_pad, const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
                                      int self, const float* inv_sa, const float* inv_sb,

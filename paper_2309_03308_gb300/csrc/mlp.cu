@@ -341,82 +341,6 @@ __global__ void k_sur_batch(const uint32_t* __restrict__ pa, const uint32_t* __r
     }
 }
 
-// ---------------------------------------------------------------------------
-// All-pairs screen: pred[a][b] = head(e_a, e_b) with U = Wa e + b3 and
-// Vb = Wb e precomputed per point (fp32). One CTA per 16 rows x 64 columns.
-constexpr int kScrI = 16, kScrJ = 64;
-
-__global__ void __launch_bounds__(256)
-    k_sur_screen(const float* __restrict__ Ea, const float* __restrict__ Ua,
-                 const float* __restrict__ Eb, const float* __restrict__ Vb,
-                 const float* __restrict__ w, int64_t oW3, int64_t ow4, int64_t ob4,
-                 const uint32_t* __restrict__ pts_a, const uint32_t* __restrict__ pts_b,
-                 int64_t na, int64_t nb, int self, int X, int Y, int Z, float tmean, float tsd,
-                 float* __restrict__ pred) {
-    extern __shared__ float sm[];
-    float* Wc = sm;                          // [128][64]
-    float* Wd = Wc + kH3 * kE;               // [128][3]
-    float* w4 = Wd + kH3 * 3;                // [128]
-    float* ea = w4 + kH3;                    // [16][64]
-    float* eb = ea + kScrI * kE;             // [64][64]
-    float* ua = eb + kScrJ * kE;             // [16][128]
-    float* vb = ua + kScrI * kH3;            // [64][128]
-    const int tid = threadIdx.x;
-    const int64_t a0 = (int64_t)blockIdx.y * kScrI, b0 = (int64_t)blockIdx.x * kScrJ;
-    for (int e = tid; e < kH3 * kE; e += 256) {
-        const int h = e / kE, q = e % kE;
-        Wc[e] = w[oW3 + (int64_t)h * kHeadIn + 2 * kE + q];
-    }
-    for (int e = tid; e < kH3 * 3; e += 256)
-        Wd[e] = w[oW3 + (int64_t)(e / 3) * kHeadIn + 3 * kE + e % 3];
-    for (int e = tid; e < kH3; e += 256) w4[e] = w[ow4 + e];
-    for (int e = tid; e < kScrI * kE; e += 256) {
-        const int64_t a = a0 + e / kE;
-        ea[e] = a < na ? Ea[a * kE + e % kE] : 0.f;
-    }
-    for (int e = tid; e < kScrJ * kE; e += 256) {
-        const int64_t b = b0 + e / kE;
-        eb[e] = b < nb ? Eb[b * kE + e % kE] : 0.f;
-    }
-    for (int e = tid; e < kScrI * kH3; e += 256) {
-        const int64_t a = a0 + e / kH3;
-        ua[e] = a < na ? Ua[a * kH3 + e % kH3] : 0.f;
-    }
-    for (int e = tid; e < kScrJ * kH3; e += 256) {
-        const int64_t b = b0 + e / kH3;
-        vb[e] = b < nb ? Vb[b * kH3 + e % kH3] : 0.f;
-    }
-    __syncthreads();
-    const float b4 = w[ob4];
-    // 1024 pairs per CTA, 4 per thread
-    for (int pidx = tid; pidx < kScrI * kScrJ; pidx += 256) {
-        const int li = pidx / kScrJ, lj = pidx % kScrJ;
-        const int64_t a = a0 + li, b = b0 + lj;
-        if (a >= na || b >= nb) continue;
-        float d[kE];
-#pragma unroll
-        for (int q = 0; q < kE; ++q) d[q] = fabsf(ea[li * kE + q] - eb[lj * kE + q]);
-        const int64_t p = pts_a[a], qq = pts_b[b];
-        const float o0 = (float)((qq % X) - (p % X)) / (float)X;
-        const float o1 = (float)(((qq / X) % Y) - ((p / X) % Y)) / (float)Y;
-        const float o2 = (float)((qq / ((int64_t)X * Y)) - (p / ((int64_t)X * Y))) / (float)Z;
-        float y = b4;
-        for (int h = 0; h < kH3; ++h) {
-            float s = ua[li * kH3 + h] + vb[lj * kH3 + h];
-            s = fmaf(Wd[h * 3 + 0], o0, s);
-            s = fmaf(Wd[h * 3 + 1], o1, s);
-            s = fmaf(Wd[h * 3 + 2], o2, s);
-            const float* wr = Wc + h * kE;
-#pragma unroll
-            for (int q = 0; q < kE; ++q) s = fmaf(wr[q], d[q], s);
-            y = fmaf(w4[h], gelu(s), y);
-        }
-        float v = y * tsd + tmean;
-        if (self && b <= a) v = -CUDART_INF_F;  // each unordered pair once
-        pred[a * nb + b] = v;
-    }
-}
-
 // linear pair index a * nb + b -> point ids of the pair
 __global__ void k_sur_ids_to_pairs(const uint32_t* __restrict__ ids, int64_t count,
                                    const uint32_t* __restrict__ pts_a,
@@ -582,6 +506,17 @@ Field* sfield(cc_ctx* ctx, int32_t id) {
     return ctx->fields[id].get();
 }
 
+// device status word after a screen (the tensor-core kernel's bounded waits)
+cc_status screen_status(cc_ctx* ctx) {
+    int st = 0;
+    SK(cudaMemcpyAsync(&st, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SK(cudaStreamSynchronize(ctx->stream));
+    if (st == DEV_OK) return CC_OK;
+    SK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), ctx->stream));
+    return sfail(ctx, st == DEV_TIMEOUT ? CC_ERR_TIMEOUT : CC_ERR_CUDA,
+                 "surrogate screen: device status %d", st);
+}
+
 // Predictions for every pair of two regions of one field into pred [|A|][|B|]
 // (self region pairs: -inf for b <= a).
 cc_status screen_predict(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t region_b,
@@ -602,11 +537,10 @@ cc_status screen_predict(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t regio
     const int64_t na = ra.np, nb = rb.np;
     cc_status r = ensure_batch(ctx, s, (std::max(na, nb) + 1) / 2);
     if (r) return r;
-    DevMem Ea, Eb, Ua, Vb;
+    DevMem Ea, Eb, Ua;
     SK(Ea.alloc(4 * na * kE));
     SK(Eb.alloc(4 * nb * kE));
     SK(Ua.alloc(4 * na * kH3));
-    SK(Vb.alloc(4 * nb * kH3));
     SK(pred.alloc(4 * (size_t)na * nb));
     const float* w = s->w.as<float>();
     // per-point encoder (bf16 weights, as in training) and head projections
@@ -626,23 +560,18 @@ cc_status screen_predict(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t regio
               0, st));
         note_launch();
         k_sur_add_bias<<<grid1(np * kE), 256, 0, st>>>(E, w + o.b2, np, kE);
-        float* UV = side ? Vb.as<float>() : Ua.as<float>();
-        SK(mm(E, kE, 1, w + o.W3 + side * kE, 1, kHeadIn, UV, kH3, (int)np, kH3, kE, 0, st));
-        if (!side) {
+        if (!side) {  // Wa e_a + b3 per point of A (Wb e_b is part of the contraction)
+            SK(mm(E, kE, 1, w + o.W3, 1, kHeadIn, Ua.as<float>(), kH3, (int)np, kH3, kE, 0, st));
             note_launch();
-            k_sur_add_bias<<<grid1(np * kH3), 256, 0, st>>>(UV, w + o.b3, np, kH3);
+            k_sur_add_bias<<<grid1(np * kH3), 256, 0, st>>>(Ua.as<float>(), w + o.b3, np, kH3);
         }
     }
-    const size_t smem = 4 * (size_t)(kH3 * kE + kH3 * 3 + kH3 + kScrI * kE + kScrJ * kE +
-                                     kScrI * kH3 + kScrJ * kH3);
-    SK(cudaFuncSetAttribute(k_sur_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((nb + kScrJ - 1) / kScrJ), (unsigned)((na + kScrI - 1) / kScrI));
-    note_launch();
-    k_sur_screen<<<grid, 256, smem, st>>>(Ea.as<float>(), Ua.as<float>(), Eb.as<float>(),
-                                          Vb.as<float>(), w, o.W3, o.w4, o.b4,
-                                          ra.pts.as<uint32_t>(), rb.pts.as<uint32_t>(), na, nb,
-                                          region_a == region_b, f->X, f->Y, f->Z, s->tmean,
-                                          s->tsd, pred.as<float>());
+    SK(launch_sur_screen_tc(Ea.as<float>(), Ua.as<float>(), Eb.as<float>(), s->wb.p, w, o.W3,
+                            o.w4, o.b4, ra.pts.as<uint32_t>(), rb.pts.as<uint32_t>(), na, nb,
+                            region_a == region_b, f->X, f->Y, f->Z, s->tmean, s->tsd,
+                            pred.as<float>(), ctx->status.as<int>(), st));
+    cc_status sr = screen_status(ctx);
+    if (sr) return sr;
     SK(cudaGetLastError());
     *ra_out = &ra;
     *rb_out = &rb;
