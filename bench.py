@@ -713,6 +713,10 @@ def run_context(args, cc, dev, stream, rank, sur=None):
         rpb = torch.empty(budget, dtype=torch.int32, device=dev)
         hit = hit_rand = 0
         nerr, nerr_rand = [], []
+        # the quasi-random sequences the paper also tried (Section 3.1), same budget
+        lds_kinds = {"halton": pg.CC_LDS_HALTON, "r6": pg.CC_LDS_R6}
+        lds_hit = {k: 0 for k in lds_kinds}
+        lds_err = {k: [] for k in lds_kinds}
         t0 = time.perf_counter()
         for i in range(n_rp):
             ex = cc.all_pairs(rp_a[i], rp_b[i], Params(pg.CC_PEARSON, precision=pg.CC_BF16))
@@ -723,10 +727,18 @@ def run_context(args, cc, dev, stream, rank, sur=None):
             hit_rand += rnd["max"] >= ex["max"] - 0.005
             nerr.append((ex["max"] - rb[i]["max"]) / span)
             nerr_rand.append((ex["max"] - rnd["max"]) / span)
+            for name, kind in lds_kinds.items():
+                cc.sample_pairs_lds(rp_a[i], rp_b[i], kind, budget, pa=rpa, pb=rpb)
+                q = cc.segment_extremes(fid, Params(pg.CC_PEARSON), rpa, rpb, [0, budget])[0]
+                lds_hit[name] += q["max"] >= ex["max"] - 0.005
+                lds_err[name].append((ex["max"] - q["max"]) / span)
         out["pearson_recall_0.005"] = hit / n_rp
         out["pearson_recall_0.005_random"] = hit_rand / n_rp
         out["pearson_normalized_error_mean"] = float(np.mean(nerr))
         out["pearson_normalized_error_mean_random"] = float(np.mean(nerr_rand))
+        for name in lds_kinds:
+            out[f"pearson_recall_0.005_{name}"] = lds_hit[name] / n_rp
+            out[f"pearson_normalized_error_mean_{name}"] = float(np.mean(lds_err[name]))
         out["exhaustive_pearson_s"] = time.perf_counter() - t0
     cc.free_field(fid)
     return out

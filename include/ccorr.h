@@ -201,6 +201,31 @@ cc_status cc_sample_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, uint6
                           uint64_t stream, uint64_t first, int64_t n_pairs, uint32_t* pa,
                           uint32_t* pb, int out_is_device);
 
+/*
+ * Quasi-random (low-discrepancy) point pairs between two box regions (Section
+ * 3.1 names Halton and plastic-type low-discrepancy sequences as alternatives
+ * to uniform random samples in the 6D space of a brick pair). Pair t takes the
+ * point index j = first + t + 1 (first + n_pairs < 2^40) and a 6D point u:
+ *   CC_LDS_HALTON  u_d = radical inverse of j in base (2, 3, 5, 7, 11, 13)[d]:
+ *                  u_d = N_d / b^K with N_d the K base-b digits of j reversed;
+ *                  c_d = floor(N_d * ext_d / b^K) in exact integer arithmetic.
+ *   CC_LDS_R6      alpha_d = phi^-(d+1), phi the real root of x^7 = x + 1 (the
+ *                  6D generalisation of the plastic number), as the nearest
+ *                  doubles; u_d = frac(0.5 + j * alpha_d) and c_d = min(floor(
+ *                  u_d * ext_d), ext_d - 1), each IEEE double operation rounded
+ *                  once (no fused multiply-add).
+ * ext_0..2 are the extents of region A's box and ext_3..5 of region B's; the
+ * region-local indices are a = c_0 + ext_0 (c_1 + ext_1 c_2) and b likewise
+ * from c_3..5. For region_a == region_b: if a == b then b = (b + 1) mod |A|,
+ * then (a, b) is ordered so that a < b. pa[t], pb[t] receive the grid point
+ * ids; device or host memory (out_is_device).
+ */
+#define CC_LDS_HALTON 1
+#define CC_LDS_R6 2
+cc_status cc_sample_pairs_lds(cc_ctx* ctx, int32_t region_a, int32_t region_b, int kind,
+                              uint64_t first, int64_t n_pairs, uint32_t* pa, uint32_t* pb,
+                              int out_is_device);
+
 /* ------------------------------------------------------------------ evaluation */
 
 /*

@@ -14,12 +14,13 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from ._lib import (CC_BF16, CC_FP8_E4M3, CC_FP32, CC_FP32_DOT2, CC_MI_BINNED, CC_MI_KSG,
-                   CC_PEARSON, CC_PLANE_BINS, CC_PLANE_RANK2, CC_PLANE_SORTED, CC_PLANE_ZHAT,
-                   CC_SPEARMAN, CCError)
+from ._lib import (CC_BF16, CC_FP8_E4M3, CC_FP32, CC_FP32_DOT2, CC_LDS_HALTON, CC_LDS_R6,
+                   CC_MI_BINNED, CC_MI_KSG, CC_PEARSON, CC_PLANE_BINS, CC_PLANE_RANK2,
+                   CC_PLANE_SORTED, CC_PLANE_ZHAT, CC_SPEARMAN, CCError)
 
 __all__ = ["Context", "Params", "CCError", "CC_PEARSON", "CC_SPEARMAN", "CC_MI_BINNED",
-           "CC_MI_KSG", "CC_FP32", "CC_BF16", "CC_FP8_E4M3", "CC_FP32_DOT2"]
+           "CC_MI_KSG", "CC_FP32", "CC_BF16", "CC_FP8_E4M3", "CC_FP32_DOT2", "CC_LDS_HALTON",
+           "CC_LDS_R6"]
 
 
 @dataclass
@@ -142,6 +143,17 @@ class Context:
         b, _ = _ptr(pb)
         self._check(self.lib.cc_sample_pairs(self.h, ra, rb, seed, stream, first, n_pairs, a, b,
                                              dev))
+        return pa, pb
+
+    def sample_pairs_lds(self, ra: int, rb: int, kind: int, n_pairs: int, first: int = 0,
+                         pa=None, pb=None):
+        """Quasi-random pairs (kind CC_LDS_HALTON or CC_LDS_R6); numpy when pa is None."""
+        if pa is None:
+            pa = np.empty(n_pairs, np.uint32)
+            pb = np.empty(n_pairs, np.uint32)
+        a, dev = _ptr(pa)
+        b, _ = _ptr(pb)
+        self._check(self.lib.cc_sample_pairs_lds(self.h, ra, rb, kind, first, n_pairs, a, b, dev))
         return pa, pb
 
     def eval_pairs(self, fa: int, fb: int, params: Params, pa, pb, out=None):

@@ -24,6 +24,7 @@ CC_ERR_UNSUPPORTED = -6
 CC_PEARSON, CC_SPEARMAN, CC_MI_BINNED, CC_MI_KSG = 0, 1, 2, 3
 CC_FP32, CC_BF16, CC_FP8_E4M3, CC_FP32_DOT2 = 0, 1, 2, 3
 CC_PLANE_RANK2, CC_PLANE_BINS, CC_PLANE_SORTED, CC_PLANE_ZHAT = 0, 1, 2, 3
+CC_LDS_HALTON, CC_LDS_R6 = 1, 2
 
 
 class cc_params(ctypes.Structure):
@@ -74,6 +75,7 @@ SIGNATURES = {
     "cc_partition_regular": (_S, [_P, _I32, _I, _I, _I, _P, _I, ctypes.POINTER(_I)]),
     "cc_region_info": (_S, [_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(cc_box)]),
     "cc_sample_pairs": (_S, [_P, _I32, _I32, _U64, _U64, _U64, _I64, _P, _P, _I]),
+    "cc_sample_pairs_lds": (_S, [_P, _I32, _I32, _I, _U64, _I64, _P, _P, _I]),
     "cc_eval_pairs": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _P, _P, _I64, _I, _P, _I]),
     "cc_ksg_counts": (_S, [_P, _I32, _I32, _I32, _P, _P, _I64, _P, _P, _P, _P]),
     "cc_segment_extremes": (_S, [_P, _I32, ctypes.POINTER(cc_params), _P, _P, _I, _P, _I, _P,

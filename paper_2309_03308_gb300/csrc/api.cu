@@ -497,6 +497,56 @@ cc_status cc_sample_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, uint6
     return CC_OK;
 }
 
+cc_status cc_sample_pairs_lds(cc_ctx* ctx, int32_t region_a, int32_t region_b, int kind,
+                              uint64_t first, int64_t n_pairs, uint32_t* pa, uint32_t* pb,
+                              int out_is_device) {
+    if (!ctx) return CC_ERR_INVALID_ARG;
+    Region* ra = get_region(ctx, region_a);
+    Region* rb = get_region(ctx, region_b);
+    if (!ra || !rb || !pa || !pb || n_pairs < 0 || (kind != CC_LDS_HALTON && kind != CC_LDS_R6))
+        return fail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    if (first + (uint64_t)n_pairs >= (1ull << 40))
+        return fail(ctx, CC_ERR_INVALID_ARG, "first + n_pairs must be below 2^40");
+    const int self = region_a == region_b;
+    if (self && ra->np < 2) return fail(ctx, CC_ERR_INVALID_ARG, "self pair needs >= 2 points");
+    const cc_box& A = ra->box;
+    const cc_box& B = rb->box;
+    const int ext[6] = {A.x1 - A.x0, A.y1 - A.y0, A.z1 - A.z0,
+                        B.x1 - B.x0, B.y1 - B.y0, B.z1 - B.z0};
+    // alpha_d = phi^-(d+1), phi the real root of x^7 = x + 1: bisection in
+    // extended precision, then rounded to double
+    double alpha[6];
+    {
+        long double lo = 1.0L, hi = 2.0L;
+        for (int i = 0; i < 200; ++i) {
+            const long double mid = 0.5L * (lo + hi);
+            const long double f = mid * mid * mid * mid * mid * mid * mid - mid - 1.0L;
+            (f > 0.0L ? hi : lo) = mid;
+        }
+        const long double phi = 0.5L * (lo + hi);
+        long double p = 1.0L;
+        for (int d = 0; d < 6; ++d) {
+            p /= phi;
+            alpha[d] = (double)p;
+        }
+    }
+    uint32_t *da = pa, *db = pb;
+    if (!out_is_device) {
+        CK(ctx->pair_a.ensure(4 * (size_t)std::max<int64_t>(n_pairs, 1)));
+        CK(ctx->pair_b.ensure(4 * (size_t)std::max<int64_t>(n_pairs, 1)));
+        da = ctx->pair_a.as<uint32_t>();
+        db = ctx->pair_b.as<uint32_t>();
+    }
+    CK(launch_sample_lds(kind, ext, alpha, self, ra->pts.as<uint32_t>(), rb->pts.as<uint32_t>(),
+                         first, n_pairs, da, db, ctx->stream));
+    if (!out_is_device && n_pairs > 0) {
+        CK(cudaMemcpyAsync(pa, da, 4 * n_pairs, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(pb, db, 4 * n_pairs, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return CC_OK;
+}
+
 cc_status cc_eval_pairs(cc_ctx* ctx, int32_t field_a, int32_t field_b, const cc_params* params,
                         const uint32_t* pa, const uint32_t* pb, int64_t n_pairs,
                         int pairs_on_device, float* out, int out_on_device) {

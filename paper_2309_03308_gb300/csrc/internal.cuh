@@ -144,6 +144,9 @@ cudaError_t launch_hist_pairs(const uint8_t* bins_a, const int64_t* hm_a, int64_
 cudaError_t launch_ksg_pairs(const Field& fa, const Field& fb, int k, const int64_t* psi_fix,
                              const uint32_t* pa, const uint32_t* pb, int64_t N, float* out,
                              int32_t* nx, int32_t* ny, float* eps, int* status, cudaStream_t st);
+cudaError_t launch_sample_lds(int kind, const int* ext, const double* alpha, int self,
+                              const uint32_t* pts_a, const uint32_t* pts_b, uint64_t first,
+                              int64_t N, uint32_t* pa, uint32_t* pb, cudaStream_t st);
 cudaError_t launch_sample_pairs(const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
                                 int64_t nb, int self, uint64_t seed, uint64_t stream,
                                 uint64_t first, int64_t N, uint32_t* pa, uint32_t* pb,

@@ -223,6 +223,75 @@ __global__ void k_sample_pairs(const uint32_t* __restrict__ pts_a, int64_t na,
     }
 }
 
+// Quasi-random pair samplers (Section 3.1): Halton radical inverses in exact
+// integer arithmetic, or the R6 Kronecker sequence in IEEE double; the exact
+// mapping to voxels is stated with cc_sample_pairs_lds in the header.
+struct LdsArgs {
+    int kind, self;
+    int ext[6];
+    double alpha[6];
+};
+
+__global__ void k_sample_lds(LdsArgs g, const uint32_t* __restrict__ pts_a,
+                             const uint32_t* __restrict__ pts_b, uint64_t first, int64_t N,
+                             uint32_t* __restrict__ pa, uint32_t* __restrict__ pb) {
+    const int bases[6] = {2, 3, 5, 7, 11, 13};
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t j = first + (uint64_t)t + 1;
+        int64_t c[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            if (g.kind == 1) {
+                const uint64_t b = (uint64_t)bases[d];
+                uint64_t jj = j, num = 0, den = 1;
+                while (jj > 0) {
+                    num = num * b + jj % b;
+                    jj /= b;
+                    den *= b;
+                }
+                c[d] = (int64_t)((num * (uint64_t)g.ext[d]) / den);
+            } else {
+                double u = __dadd_rn(0.5, __dmul_rn((double)j, g.alpha[d]));
+                u = u - floor(u);
+                const int64_t v = (int64_t)floor(__dmul_rn(u, (double)g.ext[d]));
+                c[d] = v < g.ext[d] - 1 ? v : g.ext[d] - 1;
+            }
+        }
+        const int64_t na = (int64_t)g.ext[0] * g.ext[1] * g.ext[2];
+        int64_t a = c[0] + g.ext[0] * (c[1] + g.ext[1] * c[2]);
+        int64_t b = c[3] + g.ext[3] * (c[4] + g.ext[4] * c[5]);
+        if (g.self) {
+            if (a == b) b = (b + 1) % na;
+            if (b < a) {
+                const int64_t tmp = a;
+                a = b;
+                b = tmp;
+            }
+        }
+        pa[t] = pts_a[a];
+        pb[t] = pts_b[b];
+    }
+}
+
+cudaError_t launch_sample_lds(int kind, const int* ext, const double* alpha, int self,
+                              const uint32_t* pts_a, const uint32_t* pts_b, uint64_t first,
+                              int64_t N, uint32_t* pa, uint32_t* pb, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    LdsArgs g;
+    g.kind = kind;
+    g.self = self;
+    for (int d = 0; d < 6; ++d) {
+        g.ext[d] = ext[d];
+        g.alpha[d] = alpha[d];
+    }
+    int64_t blocks = (N + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    note_launch();
+    k_sample_lds<<<(unsigned)blocks, 256, 0, st>>>(g, pts_a, pts_b, first, N, pa, pb);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sample_pairs(const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
                                 int64_t nb, int self, uint64_t seed, uint64_t stream,
                                 uint64_t first, int64_t N, uint32_t* pa, uint32_t* pb,
