@@ -717,9 +717,34 @@ def run_context(args, cc, dev, stream, rank, sur=None):
         lds_kinds = {"halton": pg.CC_LDS_HALTON, "r6": pg.CC_LDS_R6}
         lds_hit = {k: 0 for k in lds_kinds}
         lds_err = {k: [] for k in lds_kinds}
+        # mean-tree level (Section 3.3): the same region pairs on 2 x 2 x 2 block means
+        t0 = time.perf_counter()
+        gid = cc.aggregate_field(fid, 2, 2, 2, pg.CC_AGG_MEAN)
+        bx, by, bz = cfg["region"]
+        gids = cc.partition_regular(gid, bx // 2, by // 2, bz // 2)
+        assert len(gids) == len(rids)
+        gpos = {r: k for k, r in enumerate(rids)}
+        agg_max = []
+        for i in range(n_rp):
+            ex = cc.all_pairs(gids[gpos[rp_a[i]]], gids[gpos[rp_b[i]]],
+                              Params(pg.CC_PEARSON, precision=pg.CC_BF16))
+            agg_max.append(ex["max"])
+        agg_s = time.perf_counter() - t0
+        # BOS on the means (Section 3.3: the context view samples the mean-tree)
+        t0 = time.perf_counter()
+        ga = [gids[gpos[r]] for r in rp_a]
+        gb = [gids[gpos[r]] for r in rp_b]
+        bg = cc.bos_create(gid, ga, gb, **dict(kw, objective=pg.CC_PEARSON))
+        bg.run(T, True)
+        bos_agg = [r["max"] for r in bg.results()[0]]
+        bg.close()
+        bos_agg_s = time.perf_counter() - t0
+        cc.free_field(gid)
+        full_max = []
         t0 = time.perf_counter()
         for i in range(n_rp):
             ex = cc.all_pairs(rp_a[i], rp_b[i], Params(pg.CC_PEARSON, precision=pg.CC_BF16))
+            full_max.append(ex["max"])
             cc.sample_pairs(rp_a[i], rp_b[i], 17, budget, stream=i, pa=rpa, pb=rpb)
             rnd = cc.segment_extremes(fid, Params(pg.CC_PEARSON), rpa, rpb, [0, budget])[0]
             span = max(ex["max"] - ex["min"], 1e-12)
@@ -739,6 +764,17 @@ def run_context(args, cc, dev, stream, rank, sur=None):
         for name in lds_kinds:
             out[f"pearson_recall_0.005_{name}"] = lds_hit[name] / n_rp
             out[f"pearson_normalized_error_mean_{name}"] = float(np.mean(lds_err[name]))
+        dev = np.array(full_max) - np.array(agg_max)
+        dev_bos = np.array(full_max) - np.array(bos_agg)
+        dev_bos_full = np.array(full_max) - np.array([r["max"] for r in rb])
+        out["mean_tree_2x2x2"] = {"exhaustive_on_means_s": agg_s,
+                                  "max_deviation_mean": float(np.mean(dev)),
+                                  "max_deviation_p95": float(np.percentile(dev, 95)),
+                                  "within_0.05": float(np.mean(np.abs(dev) <= 0.05)),
+                                  "bos_on_means_s": bos_agg_s,
+                                  "bos_on_means_deviation_mean": float(np.mean(dev_bos)),
+                                  "bos_full_resolution_deviation_mean": float(
+                                      np.mean(dev_bos_full))}
         out["exhaustive_pearson_s"] = time.perf_counter() - t0
     cc.free_field(fid)
     return out

@@ -144,6 +144,21 @@ cc_status cc_load_field(cc_ctx* ctx, const float* data, int data_is_device, int 
  */
 cc_status cc_update_field(cc_ctx* ctx, int32_t field_id, const float* data, int data_is_device);
 
+/*
+ * Spatial aggregate of a field (Section 3.3: mean-tree / max-tree levels that
+ * let sampling run on a coarser copy when the full ensemble does not fit):
+ * blocks of bx x by x bz grid points (the last block of an axis is smaller
+ * when the extent is not a multiple) become one grid point of a new field of
+ * ceil(X/bx) x ceil(Y/by) x ceil(Z/bz) points with the same n members. Per
+ * block and member: CC_AGG_MEAN the mean (FP64 sum of the block's fp32
+ * values divided by its point count, rounded to fp32), CC_AGG_MAX the
+ * maximum. The new field (with all its planes) is returned in *out_field_id.
+ */
+#define CC_AGG_MEAN 0
+#define CC_AGG_MAX 1
+cc_status cc_aggregate_field(cc_ctx* ctx, int32_t field_id, int bx, int by, int bz, int mode,
+                             int32_t* out_field_id);
+
 /* Drop a field and its regions' device planes. */
 cc_status cc_free_field(cc_ctx* ctx, int32_t field_id);
 

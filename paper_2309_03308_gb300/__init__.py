@@ -14,13 +14,14 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from ._lib import (CC_BF16, CC_FP8_E4M3, CC_FP32, CC_FP32_DOT2, CC_LDS_HALTON, CC_LDS_R6,
+from ._lib import (CC_AGG_MAX, CC_AGG_MEAN, CC_BF16, CC_FP8_E4M3, CC_FP32, CC_FP32_DOT2,
+                   CC_LDS_HALTON, CC_LDS_R6,
                    CC_MI_BINNED, CC_MI_KSG, CC_PEARSON, CC_PLANE_BINS, CC_PLANE_RANK2,
                    CC_PLANE_SORTED, CC_PLANE_ZHAT, CC_SPEARMAN, CCError)
 
 __all__ = ["Context", "Params", "CCError", "CC_PEARSON", "CC_SPEARMAN", "CC_MI_BINNED",
            "CC_MI_KSG", "CC_FP32", "CC_BF16", "CC_FP8_E4M3", "CC_FP32_DOT2", "CC_LDS_HALTON",
-           "CC_LDS_R6"]
+           "CC_LDS_R6", "CC_AGG_MEAN", "CC_AGG_MAX"]
 
 
 @dataclass
@@ -99,6 +100,12 @@ class Context:
         """Replace a loaded field's values (same shape) and recompute its planes in place."""
         p, dev = _ptr(data)
         self._check(self.lib.cc_update_field(self.h, fid, p, dev))
+
+    def aggregate_field(self, fid: int, bx: int, by: int, bz: int, mode: int = 0) -> int:
+        """New field of block means (mode CC_AGG_MEAN) or maxima (CC_AGG_MAX)."""
+        out = ctypes.c_int32()
+        self._check(self.lib.cc_aggregate_field(self.h, fid, bx, by, bz, mode, ctypes.byref(out)))
+        return out.value
 
     def free_field(self, fid: int):
         self._check(self.lib.cc_free_field(self.h, fid))

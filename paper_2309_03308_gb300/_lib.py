@@ -25,6 +25,7 @@ CC_PEARSON, CC_SPEARMAN, CC_MI_BINNED, CC_MI_KSG = 0, 1, 2, 3
 CC_FP32, CC_BF16, CC_FP8_E4M3, CC_FP32_DOT2 = 0, 1, 2, 3
 CC_PLANE_RANK2, CC_PLANE_BINS, CC_PLANE_SORTED, CC_PLANE_ZHAT = 0, 1, 2, 3
 CC_LDS_HALTON, CC_LDS_R6 = 1, 2
+CC_AGG_MEAN, CC_AGG_MAX = 0, 1
 
 
 class cc_params(ctypes.Structure):
@@ -69,6 +70,7 @@ SIGNATURES = {
     "cc_sync": (_S, [_P]),
     "cc_load_field": (_S, [_P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(_I32)]),
     "cc_update_field": (_S, [_P, _I32, _P, _I]),
+    "cc_aggregate_field": (_S, [_P, _I32, _I, _I, _I, _I, ctypes.POINTER(_I32)]),
     "cc_free_field": (_S, [_P, _I32]),
     "cc_get_plane": (_S, [_P, _I32, _I, _I, _P, _I64, _P]),
     "cc_define_regions": (_S, [_P, _I32, _P, _I, _P]),

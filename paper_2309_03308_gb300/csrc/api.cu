@@ -341,6 +341,23 @@ cc_status cc_load_field(cc_ctx* ctx, const float* data, int data_is_device, int 
     return CC_OK;
 }
 
+cc_status cc_aggregate_field(cc_ctx* ctx, int32_t field_id, int bx, int by, int bz, int mode,
+                             int32_t* out_field_id) {
+    if (!ctx) return CC_ERR_INVALID_ARG;
+    Field* f = get_field(ctx, field_id);
+    if (!f || !out_field_id || bx < 1 || by < 1 || bz < 1 ||
+        (mode != CC_AGG_MEAN && mode != CC_AGG_MAX))
+        return fail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    CK(cudaSetDevice(ctx->device));
+    const int Xc = (f->X + bx - 1) / bx, Yc = (f->Y + by - 1) / by, Zc = (f->Z + bz - 1) / bz;
+    const int64_t Pc = (int64_t)Xc * Yc * Zc;
+    DevMem agg;
+    CK(agg.alloc(sizeof(float) * (size_t)Pc * f->n));
+    CK(launch_aggregate(*f, bx, by, bz, Xc, Yc, Pc, mode, agg.as<float>(), ctx->stream));
+    const int n = f->n;  // f may move when the field list grows
+    return cc_load_field(ctx, agg.as<float>(), 1, Xc, Yc, Zc, n, out_field_id);
+}
+
 cc_status cc_update_field(cc_ctx* ctx, int32_t field_id, const float* data, int data_is_device) {
     if (!ctx) return CC_ERR_INVALID_ARG;
     Field* f = get_field(ctx, field_id);

@@ -128,6 +128,8 @@ struct PrepBins {
     long long* hmarg[2] = {nullptr, nullptr};
     const long long* clogc = nullptr;
 };
+cudaError_t launch_aggregate(const Field& f, int bx, int by, int bz, int Xc, int Yc, int64_t Pc,
+                             int mode, float* out, cudaStream_t st);
 cudaError_t launch_point_prep(const Field& f, cudaStream_t st, const PrepBins& pb = PrepBins());
 cudaError_t launch_bins(const Field& f, int B, const int64_t* clogc_fix, uint8_t* bins,
                         int64_t* hmarg, cudaStream_t st);

@@ -363,6 +363,43 @@ cudaError_t launch_point_prep(const Field& f, cudaStream_t st, const PrepBins& p
 }
 
 // ----------------------------------------------------------------------------
+// Spatial aggregate (Section 3.3): one warp per block of the source grid,
+// lanes over members (coalesced point rows); mean (FP64 sum, rounded once)
+// or maximum per block and member, written member-major [n][Pc].
+__global__ void __launch_bounds__(256)
+    k_aggregate(const float* __restrict__ vals, int X, int Y, int Z, int n, int n_pad, int bx,
+                int by, int bz, int Xc, int Yc, int64_t Pc, int mode, float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= Pc) return;
+    const int ci = (int)(c % Xc), cj = (int)((c / Xc) % Yc), ck = (int)(c / ((int64_t)Xc * Yc));
+    const int x0 = ci * bx, y0 = cj * by, z0 = ck * bz;
+    const int x1 = min(x0 + bx, X), y1 = min(y0 + by, Y), z1 = min(z0 + bz, Z);
+    const double cnt = (double)(x1 - x0) * (y1 - y0) * (z1 - z0);
+    for (int m = lane; m < n; m += 32) {
+        double s = 0.0;
+        float mx = -CUDART_INF_F;
+        for (int z = z0; z < z1; ++z)
+            for (int y = y0; y < y1; ++y)
+                for (int x = x0; x < x1; ++x) {
+                    const float v = vals[((int64_t)x + (int64_t)X * (y + (int64_t)Y * z)) * n_pad + m];
+                    s += (double)v;
+                    mx = fmaxf(mx, v);
+                }
+        out[(int64_t)m * Pc + c] = mode == 0 ? (float)(s / cnt) : mx;
+    }
+}
+
+cudaError_t launch_aggregate(const Field& f, int bx, int by, int bz, int Xc, int Yc, int64_t Pc,
+                             int mode, float* out, cudaStream_t st) {
+    note_launch();
+    k_aggregate<<<(unsigned)((Pc + 7) / 8), 256, 0, st>>>(f.vals.as<float>(), f.X, f.Y, f.Z, f.n,
+                                                         f.n_pad, bx, by, bz, Xc, Yc, Pc, mode,
+                                                         out);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
 // Bins for B bins per variable (Section 3.2, binning): over the point's own
 // [lo, hi] = [min, max], b = floor(((v - lo) / (hi - lo)) * B) with each step
 // an IEEE fp32 operation, clamped to [0, B-1]; hi == lo gives bin 0.

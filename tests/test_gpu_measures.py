@@ -297,3 +297,32 @@ def test_device_buffers_and_torch_stream(small, orc):
         ctx.close()
     ref = orc.eval_pairs(F, oracle.MI_KSG, pa[:20000], pb[:20000], k=3)
     assert np.abs(got[:20000] - ref).max() < TOL
+
+
+@pytest.mark.parametrize("mode", ["mean", "max"])
+def test_aggregate_field(cc, orc, mode):
+    """Block means / maxima of a field (Section 3.3) against the aggregate
+    oracle, ragged boundary blocks included; the new field's planes and
+    measures follow."""
+    from oracle import agg
+    from paper_2309_03308_gb300 import CC_AGG_MAX, CC_AGG_MEAN, CC_PEARSON, Params
+    X, Y, Z, n = 37, 23, 9, 48
+    F = gen.field(8, X, Y, Z, n)
+    fid = cc.load_field(F)
+    gid = cc.aggregate_field(fid, 4, 3, 2, CC_AGG_MEAN if mode == "mean" else CC_AGG_MAX)
+    G = agg.aggregate(F, 4, 3, 2, mode)
+    Pc = G[0].size
+    pts = np.arange(Pc, dtype=np.uint32)
+    got = cc.get_plane(gid, 2, pts, n)
+    ref = np.sort(G.reshape(n, -1).T, axis=1)
+    if mode == "max":
+        assert np.array_equal(got, ref)
+    else:
+        ulp = np.spacing(np.abs(ref).astype(np.float32))
+        assert np.all(np.abs(got - ref) <= ulp)
+    pa, pb = all_unique_pairs(Pc)
+    pa, pb = pa[::13].copy(), pb[::13].copy()
+    vals = cc.eval_pairs(gid, gid, Params(CC_PEARSON), pa, pb)
+    assert np.abs(vals - orc.eval_pairs(G, oracle.PEARSON, pa, pb)).max() < TOL
+    cc.free_field(gid)
+    cc.free_field(fid)
