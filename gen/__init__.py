@@ -64,6 +64,18 @@ def field(seed: int, X: int, Y: int, Z: int, n: int, box=None) -> np.ndarray:
     return out
 
 
+def coupled_field(F: np.ndarray, seed: int, shift: tuple[int, int], w_shift: float = 0.6,
+                  w_noise: float = 0.8) -> np.ndarray:
+    """A second variable on the grid of F ([n][Z][Y][X]): w_shift times F moved
+    by shift = (dx, dy) voxels (periodic) plus w_noise times an independent
+    field of the given seed. Stands in for a pair of physical variables (wind
+    components) whose dependence is offset in space."""
+    n, Z, Y, X = F.shape
+    G = field(seed, X, Y, Z, n)
+    return (w_shift * np.roll(F, shift=(shift[1], shift[0]), axis=(2, 3)) +
+            w_noise * G).astype(np.float32)
+
+
 def clusters(seed: int, X: int, Y: int, Z: int, n: int, centres) -> np.ndarray:
     """Cluster fixture (l-infinity decaying blend of one shared sequence and noise).
 

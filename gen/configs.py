@@ -30,6 +30,12 @@ PRECISION = dict(name="precision-2x32x32x20-n1000", seed=2, X=352, Y=256, Z=20, 
 CONTEXT = dict(name="context-340x250x20-n100", seed=3, X=340, Y=250, Z=20, n=100, k=10,
                bins=16, region=(32, 32, 20), rounds=30, per_round=32)
 
+# Inter-variable matrix on the context grid: the second variable is 0.6 x the
+# first moved by (40, 0) voxels plus 0.8 x an independent seed-5 field; BOS
+# over all 88 x 88 ordered region pairs (7744 entries, none symmetric).
+INTER_VARIABLE = dict(name="intervar-340x250x20-n100", second_seed=5, shift=(40, 0),
+                      rounds=30, per_round=32, check_entries=64)
+
 # Learned surrogate: trained on a seed-2 352x256x20 n=100 field, evaluated on a
 # seed-4 field with the focus geometry.
 SURROGATE = dict(name="surrogate-352x256x20-n100", train_seed=2, eval_seed=4, X=352, Y=256,

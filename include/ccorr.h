@@ -283,6 +283,16 @@ cc_status cc_segment_extremes(cc_ctx* ctx, int32_t field_id, const cc_params* pa
                               cc_rp_result* out);
 
 /*
+ * Two-variable form (Section 4.3): pa[t] indexes field_id and pb[t]
+ * field_b_id (same ensemble size). cc_segment_extremes(ctx, f, ...) equals
+ * cc_segment_extremes2(ctx, f, f, ...).
+ */
+cc_status cc_segment_extremes2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id,
+                               const cc_params* params, const uint32_t* pa, const uint32_t* pb,
+                               int pairs_on_device, const int64_t* seg_offsets, int n_seg,
+                               float* values, cc_rp_result* out);
+
+/*
  * All pairs between two regions (Section 4.2: exhaustive focus refinement of
  * a brick pair; Section 3: maximum per brick pair). Pair (a, b) has linear
  * index a * |B| + b with a, b region-local indices. When region_a ==
@@ -383,6 +393,20 @@ typedef struct {
  */
 cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, const int32_t* rp_b,
                         int n_rp, const cc_bos_params* params, cc_bos** out);
+
+/*
+ * Two-variable form (Section 4.3: sampling runs as for one field, but each
+ * point pair takes its first point from field_id and its second from
+ * field_b_id). Regions rp_a[i] belong to field_id, rp_b[i] to field_b_id; the
+ * two fields need the same grid and ensemble size. Because the measure is no
+ * longer symmetric in the two regions, the search of (A, B) and of (B, A)
+ * are different entries of the inter-variable matrix, and no region pair is
+ * a self pair (a voxel may pair with itself: its two variables differ).
+ * cc_bos_create(ctx, f, ...) equals cc_bos_create2(ctx, f, f, ...).
+ */
+cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, const int32_t* rp_a,
+                         const int32_t* rp_b, int n_rp, const cc_bos_params* params,
+                         cc_bos** out);
 
 /*
  * Prior mean per pool entry, float [n_rp][pool] (e.g. a surrogate's

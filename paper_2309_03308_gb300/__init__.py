@@ -188,7 +188,10 @@ class Context:
                                            eps.ctypes.data))
         return out, nx, ny, eps
 
-    def segment_extremes(self, fid: int, params: Params, pa, pb, seg_offsets, values=None):
+    def segment_extremes(self, fid: int, params: Params, pa, pb, seg_offsets, values=None,
+                         field_b: int | None = None):
+        """Per-segment extremes of pairs (pa[t] of field fid, pb[t] of field_b,
+        default fid)."""
         offs = np.ascontiguousarray(seg_offsets, np.int64)
         n_seg = offs.shape[0] - 1
         a, pdev = _ptr(pa)
@@ -196,8 +199,9 @@ class Context:
         v = _ptr(values)[0] if values is not None else None
         res = (_lib.cc_rp_result * max(n_seg, 1))()
         prm = params.c()
-        self._check(self.lib.cc_segment_extremes(self.h, fid, ctypes.byref(prm), a, b, pdev,
-                                                 offs.ctypes.data, n_seg, v, res))
+        fb = fid if field_b is None else field_b
+        self._check(self.lib.cc_segment_extremes2(self.h, fid, fb, ctypes.byref(prm), a, b, pdev,
+                                                  offs.ctypes.data, n_seg, v, res))
         return [_res(r) for r in res[:n_seg]]
 
     def all_pairs(self, ra: int, rb: int, params: Params, values=None, ld: int = 0):
@@ -227,15 +231,19 @@ class Context:
         return _res(res), ids[:topk], vals[:topk], cert
 
     def bos_create(self, fid: int, rp_a, rp_b, pool=2048, per_round=32, rounds=30,
-                   shortlist=128, kappa=0.5, objective=CC_MI_KSG, k=10, bins=16, seed=3):
-        """Batched BOS state over region pairs (rp_a[i], rp_b[i]) of field fid."""
+                   shortlist=128, kappa=0.5, objective=CC_MI_KSG, k=10, bins=16, seed=3,
+                   field_b: int | None = None):
+        """Batched BOS state over region pairs (rp_a[i], rp_b[i]) of field fid;
+        with field_b, the second point of each pair is read from that field
+        (regions rp_b[i] belong to it): the inter-variable matrix."""
         a = np.ascontiguousarray(rp_a, np.int32)
         b = np.ascontiguousarray(rp_b, np.int32)
         prm = _lib.cc_bos_params(pool, per_round, rounds, shortlist, kappa, objective, k, bins,
                                  seed)
         h = ctypes.c_void_p()
-        self._check(self.lib.cc_bos_create(self.h, fid, a.ctypes.data, b.ctypes.data, len(a),
-                                           ctypes.byref(prm), ctypes.byref(h)))
+        fb = fid if field_b is None else field_b
+        self._check(self.lib.cc_bos_create2(self.h, fid, fb, a.ctypes.data, b.ctypes.data,
+                                            len(a), ctypes.byref(prm), ctypes.byref(h)))
         return Bos(self, h, len(a), prm)
 
     def sync(self):

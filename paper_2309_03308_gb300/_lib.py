@@ -82,9 +82,13 @@ SIGNATURES = {
     "cc_ksg_counts": (_S, [_P, _I32, _I32, _I32, _P, _P, _I64, _P, _P, _P, _P]),
     "cc_segment_extremes": (_S, [_P, _I32, ctypes.POINTER(cc_params), _P, _P, _I, _P, _I, _P,
                                  _P]),
+    "cc_segment_extremes2": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _P, _P, _I, _P,
+                                  _I, _P, _P]),
     "cc_all_pairs": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _P, _I64, _P]),
     "cc_all_pairs_topk": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _I, _P, _P, _P, _P]),
     "cc_bos_create": (_S, [_P, _I32, _P, _P, _I, ctypes.POINTER(cc_bos_params),
+                           ctypes.POINTER(_P)]),
+    "cc_bos_create2": (_S, [_P, _I32, _I32, _P, _P, _I, ctypes.POINTER(cc_bos_params),
                            ctypes.POINTER(_P)]),
     "cc_bos_set_prior": (_S, [_P, _P, _P, _I]),
     "cc_bos_run": (_S, [_P, _P, _I, _I]),

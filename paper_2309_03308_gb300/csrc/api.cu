@@ -629,14 +629,16 @@ cc_status cc_ksg_counts(cc_ctx* ctx, int32_t field_a, int32_t field_b, int32_t k
     return take_status(ctx);
 }
 
-cc_status cc_segment_extremes(cc_ctx* ctx, int32_t field_id, const cc_params* params,
-                              const uint32_t* pa, const uint32_t* pb, int pairs_on_device,
-                              const int64_t* seg_offsets, int n_seg, float* values,
-                              cc_rp_result* out) {
+cc_status cc_segment_extremes2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id,
+                               const cc_params* params, const uint32_t* pa, const uint32_t* pb,
+                               int pairs_on_device, const int64_t* seg_offsets, int n_seg,
+                               float* values, cc_rp_result* out) {
     if (!ctx) return CC_ERR_INVALID_ARG;
     Field* f = get_field(ctx, field_id);
-    if (!f || !pa || !pb || !seg_offsets || !out || n_seg < 0)
+    Field* g = get_field(ctx, field_b_id);
+    if (!f || !g || !pa || !pb || !seg_offsets || !out || n_seg < 0)
         return fail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    if (f->n != g->n) return fail(ctx, CC_ERR_INVALID_ARG, "fields differ in member count");
     for (int s = 0; s < n_seg; ++s)
         if (seg_offsets[s + 1] < seg_offsets[s] || seg_offsets[0] != 0)
             return fail(ctx, CC_ERR_INVALID_ARG, "segment offsets must start at 0 and not decrease");
@@ -652,7 +654,7 @@ cc_status cc_segment_extremes(cc_ctx* ctx, int32_t field_id, const cc_params* pa
         CK(ctx->vals_out.ensure(4 * (size_t)std::max<int64_t>(N, 1)));
         dv = ctx->vals_out.as<float>();
     }
-    if ((s = eval_device(ctx, *f, *f, params, k, da, db, N, dv))) return s;
+    if ((s = eval_device(ctx, *f, *g, params, k, da, db, N, dv))) return s;
     // chunk table: [start, end) per chunk, first chunk per segment
     std::vector<int64_t> table_h;
     std::vector<int64_t> first_h(n_seg + 1);
@@ -683,6 +685,14 @@ cc_status cc_segment_extremes(cc_ctx* ctx, int32_t field_id, const cc_params* pa
     for (int i = 0; i < n_seg; ++i)
         out[i] = cc_rp_result{h[i].max, h[i].min, h[i].argmax, h[i].argmin, h[i].count};
     return CC_OK;
+}
+
+cc_status cc_segment_extremes(cc_ctx* ctx, int32_t field_id, const cc_params* params,
+                              const uint32_t* pa, const uint32_t* pb, int pairs_on_device,
+                              const int64_t* seg_offsets, int n_seg, float* values,
+                              cc_rp_result* out) {
+    return cc_segment_extremes2(ctx, field_id, field_id, params, pa, pb, pairs_on_device,
+                                seg_offsets, n_seg, values, out);
 }
 
 cc_status cc_all_pairs(cc_ctx* ctx, int32_t region_a, int32_t region_b, const cc_params* params,

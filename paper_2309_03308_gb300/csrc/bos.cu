@@ -75,13 +75,20 @@ struct BosDev {
     int* queue;
     int* status;
     // field planes
-    const float* zhat;
+    const float* zhat;  // planes of the field of the first regions ...
     const float* rhat;
     const float* fvals;
     const float* sorted;
     const uint16_t* perm;
     const uint8_t* bins_p;
     const long long* hmarg;
+    const float* zhat_b;  // ... and of the second regions (the same field, or a second
+    const float* rhat_b;  // variable on the same grid: Section 4.3)
+    const float* fvals_b;
+    const float* sorted_b;
+    const uint16_t* perm_b;
+    const uint8_t* bins_b;
+    const long long* hmarg_b;
     const long long* psi_fix;
     const long long* clogc_fix;
     double psi_nk;
@@ -347,7 +354,7 @@ __global__ void k_bos_eval(BosDev d, int warps_per_block) {
         float value = 0.f;
         if (measure == CC_MI_KSG) {
             ksg_stage<KMAX>(wbase, n, n_pad, d.sorted + ra, d.perm + ra, d.fvals + ra,
-                            d.sorted + rb, d.perm + rb, d.fvals + rb);
+                            d.sorted_b + rb, d.perm_b + rb, d.fvals_b + rb);
             long long acc = 0;
             for (int ti = lane; ti < n; ti += 32)
                 acc += ksg_sample<KMAX>(wbase, n, n_pad, d.k, ti, psi, nullptr, nullptr, nullptr);
@@ -355,7 +362,7 @@ __global__ void k_bos_eval(BosDev d, int warps_per_block) {
             value = (float)(d.psi_nk - (double)acc * d.fix_over_n);
         } else if (measure == CC_MI_BINNED) {
             const uint8_t* ba = d.bins_p + ra;
-            const uint8_t* bb = d.bins_p + rb;
+            const uint8_t* bb = d.bins_b + rb;
             // the member whose increment finds its cell empty owns the cell:
             // it adds the cell's c ln c once the counts are complete and clears it
             unsigned own = 0;  // bit j: member lane + 32 j (n <= 1024)
@@ -373,10 +380,10 @@ __global__ void k_bos_eval(BosDev d, int warps_per_block) {
                 hist[ba[m] * B + bb[m]] = 0;
             }
             s = warp_sum_i64(s);
-            value = (float)(d.logn + (double)(s - d.hmarg[p] - d.hmarg[q]) * d.fix_over_n);
+            value = (float)(d.logn + (double)(s - d.hmarg[p] - d.hmarg_b[q]) * d.fix_over_n);
         } else {
             const float* A = (measure == CC_SPEARMAN ? d.rhat : d.zhat) + ra;
-            const float* Bp = (measure == CC_SPEARMAN ? d.rhat : d.zhat) + rb;
+            const float* Bp = (measure == CC_SPEARMAN ? d.rhat_b : d.zhat_b) + rb;
             float acc = 0.f;
             for (int m = lane; m < n_pad; m += 32) acc = fmaf(A[m], Bp[m], acc);
             value = warp_sum_f32(acc);
@@ -621,8 +628,8 @@ using namespace cc;
 
 struct cc_bos {
     BosDev d{};
-    int field = -1;
-    uint64_t field_version = ~0ull;
+    int field = -1, field_b = -1;
+    uint64_t field_version = ~0ull, field_b_version = ~0ull;
     DevMem box, self, pool, V, mu, var, sel, obs, y, beta, hyp, prior, picks, pa, pb, vals, best,
         counters;
     int eval_warps = 8, eval_blocks_per_sm = 4;
@@ -802,14 +809,19 @@ void tune_store(const std::string& key, int w, int b) {
 
 extern "C" {
 
-cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, const int32_t* rp_b,
-                        int n_rp, const cc_bos_params* prm, cc_bos** out) {
+cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, const int32_t* rp_a,
+                         const int32_t* rp_b, int n_rp, const cc_bos_params* prm, cc_bos** out) {
     if (!ctx) return CC_ERR_INVALID_ARG;
     if (!rp_a || !rp_b || !prm || !out || n_rp < 1)
         return bfail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
-    if (field_id < 0 || field_id >= (int)ctx->fields.size() || !ctx->fields[field_id])
+    if (field_id < 0 || field_id >= (int)ctx->fields.size() || !ctx->fields[field_id] ||
+        field_b_id < 0 || field_b_id >= (int)ctx->fields.size() || !ctx->fields[field_b_id])
         return bfail(ctx, CC_ERR_INVALID_ARG, "unknown field");
     Field& f = *ctx->fields[field_id];
+    const Field& fb = *ctx->fields[field_b_id];
+    if (fb.X != f.X || fb.Y != f.Y || fb.Z != f.Z || fb.n != f.n)
+        return bfail(ctx, CC_ERR_INVALID_ARG,
+                     "the two fields need the same grid and the same ensemble size");
     const int Q = prm->pool, R = prm->per_round, T = prm->rounds, M = prm->shortlist;
     if (Q < 256 || Q > 8192 || (Q & (Q - 1)) || R < 1 || R > 32 || T < 1 ||
         M < 16 || M > 128 || M % 16 || (int64_t)R * T + M > Q)
@@ -826,7 +838,7 @@ cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, cons
         const int ids[2] = {rp_a[i], rp_b[i]};
         for (int s = 0; s < 2; ++s) {
             if (ids[s] < 0 || ids[s] >= (int)ctx->regions.size() || !ctx->regions[ids[s]] ||
-                ctx->regions[ids[s]]->field != field_id)
+                ctx->regions[ids[s]]->field != (s ? field_b_id : field_id))
                 return bfail(ctx, CC_ERR_INVALID_ARG, "region pair %d: bad region", i);
             const cc_box& bx = ctx->regions[ids[s]]->box;
             int* o = &box[12 * i + 6 * s];
@@ -837,7 +849,7 @@ cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, cons
             o[4] = bx.y1 - bx.y0;
             o[5] = bx.z1 - bx.z0;
         }
-        self[i] = rp_a[i] == rp_b[i];
+        self[i] = field_id == field_b_id && rp_a[i] == rp_b[i];
         if (self[i] && box[12 * i + 3] * box[12 * i + 4] * box[12 * i + 5] < 2)
             return bfail(ctx, CC_ERR_INVALID_ARG, "self pair needs two points");
     }
@@ -845,6 +857,7 @@ cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, cons
     if (!b) return CC_ERR_OOM;
     std::unique_ptr<cc_bos> guard(b);
     b->field = field_id;
+    b->field_b = field_b_id;
     b->rp_a.assign(rp_a, rp_a + n_rp);
     b->rp_b.assign(rp_b, rp_b + n_rp);
     BosDev& d = b->d;
@@ -918,6 +931,11 @@ cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, cons
     return CC_OK;
 }
 
+cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, const int32_t* rp_b,
+                        int n_rp, const cc_bos_params* prm, cc_bos** out) {
+    return cc_bos_create2(ctx, field_id, field_id, rp_a, rp_b, n_rp, prm, out);
+}
+
 cc_status cc_bos_set_prior(cc_ctx* ctx, cc_bos* b, const float* prior, int prior_is_device) {
     if (!ctx || !b) return CC_ERR_INVALID_ARG;
     if (b->rounds_done > 0)
@@ -945,19 +963,24 @@ cc_status cc_bos_run(cc_ctx* ctx, cc_bos* b, int rounds, int use_graph) {
     if (!ctx || !b || rounds < 0) return CC_ERR_INVALID_ARG;
     if (b->rounds_done + rounds > b->d.T)
         return bfail(ctx, CC_ERR_INVALID_ARG, "only %d rounds were provisioned", b->d.T);
+    if (b->field >= (int)ctx->fields.size() || !ctx->fields[b->field] ||
+        b->field_b >= (int)ctx->fields.size() || !ctx->fields[b->field_b])
+        return bfail(ctx, CC_ERR_INVALID_ARG, "a field of this search was freed");
     Field& f = *ctx->fields[b->field];
+    Field& fb = *ctx->fields[b->field_b];
     // field planes (bins for the binned measure, tables) are bound at the first round
-    if (b->field_version != f.version) {
+    if (b->field_version != f.version || b->field_b_version != fb.version) {
         if (b->rounds_done > 0)
             return bfail(ctx, CC_ERR_INVALID_ARG, "the field changed during sampling");
         cc_params p{CC_MI_BINNED, b->d.k, b->d.bins, 0, 0};
-        // evaluate one in-range pair so the bins and tables of the field exist
+        // evaluate one in-range pair so the bins and tables of both fields exist
         uint32_t one = 0;
         float tmp = 0.f;
-        cc_status s = cc_eval_pairs(ctx, b->field, b->field, &p, &one, &one, 1, 0, &tmp, 0);
+        cc_status s = cc_eval_pairs(ctx, b->field, b->field_b, &p, &one, &one, 1, 0, &tmp, 0);
         if (s) return s;
         p.measure = CC_MI_KSG;
-        if ((s = cc_eval_pairs(ctx, b->field, b->field, &p, &one, &one, 1, 0, &tmp, 0))) return s;
+        if ((s = cc_eval_pairs(ctx, b->field, b->field_b, &p, &one, &one, 1, 0, &tmp, 0)))
+            return s;
         b->d.zhat = f.zhat.as<float>();
         b->d.rhat = f.rhat.as<float>();
         b->d.fvals = f.vals.as<float>();
@@ -965,12 +988,20 @@ cc_status cc_bos_run(cc_ctx* ctx, cc_bos* b, int rounds, int use_graph) {
         b->d.perm = f.perm.as<uint16_t>();
         b->d.bins_p = f.bins[b->d.bins]->as<uint8_t>();
         b->d.hmarg = (const long long*)f.hmarg[b->d.bins]->as<int64_t>();
+        b->d.zhat_b = fb.zhat.as<float>();
+        b->d.rhat_b = fb.rhat.as<float>();
+        b->d.fvals_b = fb.vals.as<float>();
+        b->d.sorted_b = fb.sorted.as<float>();
+        b->d.perm_b = fb.perm.as<uint16_t>();
+        b->d.bins_b = fb.bins[b->d.bins]->as<uint8_t>();
+        b->d.hmarg_b = (const long long*)fb.hmarg[b->d.bins]->as<int64_t>();
         b->d.psi_fix = (const long long*)ctx->psi_fix[f.n]->as<int64_t>();
         b->d.clogc_fix = (const long long*)ctx->clogc_fix[f.n]->as<int64_t>();
         b->d.psi_nk = digamma_int_host(f.n) + digamma_int_host(b->d.k);
         b->d.fix_over_n = 1.0 / (kFixScale * f.n);
         b->d.logn = std::log((double)f.n);
         b->field_version = f.version;
+        b->field_b_version = fb.version;
     }
     cudaStream_t st = ctx->stream;
     if (!b->tuned) {

@@ -133,3 +133,83 @@ def test_proposals_and_posterior(setup, orc):
         mu, var = g.posterior(pool[st["obs"]], y, np.full(R * T, m), pool, np.full(Q, m))
         assert np.abs(st["mu"] - mu).max() < 5e-3 * np.sqrt(sf2) + 1e-6
         assert np.abs(st["var"] - var).max() < 5e-3 * sf2 + 1e-9
+
+
+@pytest.fixture(scope="module")
+def setup2():
+    """The same search over two variables on one grid (Section 4.3): the first
+    point of a pair reads field A, the second field B."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_03308_gb300 import Context, build
+    build.build()
+    Fa, Fb = gen.field(31, X, Y, Z, N), gen.field(32, X, Y, Z, N)
+    ctx = Context(0)
+    fa, fb = ctx.load_field(Fa), ctx.load_field(Fb)
+    ra, rb = ctx.partition_regular(fa, 8, 8, 3), ctx.partition_regular(fb, 8, 8, 3)
+    boxes = [ctx.region_info(r)[1] for r in ra]
+    pairs = [(0, 7), (3, 3), (7, 0)]  # (3, 3): one brick, two variables, no self pair
+    bos = ctx.bos_create(fa, [ra[a] for a, _ in pairs], [rb[b] for _, b in pairs], pool=Q,
+                         per_round=R, rounds=T, shortlist=M, kappa=KAPPA, k=K, bins=BINS,
+                         seed=SEED, field_b=fb)
+    bos.run(T)
+    yield Fa, Fb, boxes, pairs, [bos.inspect(i) for i in range(len(pairs))], bos.results()
+    bos.close()
+    ctx.close()
+
+
+def test_two_field_observations(setup2, orc):
+    Fa, Fb, boxes, pairs, states, res = setup2
+    for rp, (pair, st) in enumerate(zip(pairs, states)):
+        ba, bb = boxes[pair[0]], boxes[pair[1]]
+        assert np.array_equal(st["pool"], ogp.pool_positions(orc, SEED, rp, Q, ext_of(ba),
+                                                             ext_of(bb)))
+        pa, pb = [], []
+        for i, c in enumerate(st["obs"]):  # no self-pair fix: the variables differ
+            v = ogp.bernoulli_voxels(orc, SEED, rp, i // R, i % R, st["pool"][c])
+            a, b = point_ids(ba, bb, v)
+            pa.append(a)
+            pb.append(b)
+        pa, pb = np.array(pa, np.uint32), np.array(pb, np.uint32)
+        vals = {m: orc.eval_pairs(Fa, m, pa, pb, k=K, bins=BINS, Fb=Fb) for m in range(4)}
+        assert np.abs(st["y"] - vals[oracle.MI_KSG]).max() < 1e-5
+        for m in range(4):
+            assert abs(res[m][rp]["max"] - vals[m].max()) < 1e-5
+            assert abs(res[m][rp]["min"] - vals[m].min()) < 1e-5
+            assert res[m][rp]["count"] == R * T
+
+
+def test_two_field_matrix_is_asymmetric(setup2, orc):
+    """Entries (A at brick 0, B at brick 7) and (A at brick 7, B at brick 0) are
+    different searches: their maxima differ in general."""
+    _, _, _, _, _, res = setup2
+    assert res[oracle.PEARSON][0]["max"] != res[oracle.PEARSON][2]["max"]
+
+
+def test_two_field_segment_extremes(orc):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_03308_gb300 import CC_MI_BINNED, CC_MI_KSG, CC_PEARSON, Context, Params
+    Fa, Fb = gen.field(41, X, Y, Z, 60), gen.field(42, X, Y, Z, 60)
+    ctx = Context(0)
+    fa, fb = ctx.load_field(Fa), ctx.load_field(Fb)
+    rng = np.random.default_rng(5)
+    npts = X * Y * Z
+    pa = rng.integers(0, npts, 5000).astype(np.uint32)
+    pb = rng.integers(0, npts, 5000).astype(np.uint32)
+    pb[:50] = pa[:50]  # the same voxel in both variables
+    offs = [0, 1000, 1000, 3333, 5000]  # an empty segment, ragged sizes
+    for kind in (CC_PEARSON, CC_MI_BINNED, CC_MI_KSG):
+        ref = orc.eval_pairs(Fa, kind, pa, pb, k=5, bins=8, Fb=Fb)
+        out = ctx.segment_extremes(fa, Params(kind, k=5, bins=8), pa, pb, offs, field_b=fb)
+        for s in range(4):
+            seg = ref[offs[s]:offs[s + 1]]
+            assert out[s]["count"] == seg.size
+            if seg.size:
+                assert abs(out[s]["max"] - seg.max()) < 1e-5
+                assert offs[s] <= out[s]["argmax"] < offs[s + 1]
+                assert abs(ref[out[s]["argmax"]] - seg.max()) < 1e-5
+                assert abs(out[s]["min"] - seg.min()) < 1e-5
+    ctx.close()
