@@ -777,7 +777,48 @@ def run_context(args, cc, dev, stream, rank, sur=None):
                                   "bos_full_resolution_deviation_mean": float(
                                       np.mean(dev_bos_full))}
         out["exhaustive_pearson_s"] = time.perf_counter() - t0
+        out["mean_tree_bos_100"] = run_mean_tree_experiment(cc, fid, rids, rp_a, rp_b, kw)
     cc.free_field(fid)
+    return out
+
+
+def run_mean_tree_experiment(cc, fid, rids, rp_a, rp_b, kw):
+    """Section 5.3's accuracy experiment on the context grid: 1000 random
+    region pairs, BOS with 100 samples on the initial values (f = 1) and on
+    means of 2x2x2 (f = 2) and 4x4x4 (f = 4) values, 10 runs each averaged;
+    mean relative deviation of the f = 2, 4 maxima from the f = 1 maxima."""
+    import paper_2309_03308_gb300 as pg
+    cfg = configs.CONTEXT
+    rng = np.random.default_rng(11)
+    sel = rng.choice(len(rp_a), 1000, replace=False)
+    pos = {r: k for k, r in enumerate(rids)}
+    ia, ib = [pos[rp_a[i]] for i in sel], [pos[rp_b[i]] for i in sel]
+    bx, by, bz = cfg["region"]
+    kwm = dict(kw, pool=256, per_round=10, rounds=10, shortlist=16)
+    out = {"region_pairs": len(sel), "samples": 100, "runs": 10}
+    t0 = time.perf_counter()
+    for name, objective, m in (("pearson", pg.CC_PEARSON, 0), ("ksg", pg.CC_MI_KSG, 3)):
+        maxima = {}
+        for f in (1, 2, 4):
+            gid = fid if f == 1 else cc.aggregate_field(fid, f, f, f, pg.CC_AGG_MEAN)
+            g = rids if f == 1 else cc.partition_regular(gid, bx // f, by // f, bz // f)
+            assert len(g) == len(rids)
+            acc = np.zeros(len(sel))
+            for run in range(10):
+                b = cc.bos_create(gid, [g[i] for i in ia], [g[j] for j in ib],
+                                  **dict(kwm, objective=objective, seed=100 + run))
+                b.run(kwm["rounds"], True)
+                acc += np.array([r["max"] for r in b.results()[m]])
+                b.close()
+            maxima[f] = acc / 10
+            if f != 1:
+                cc.free_field(gid)
+        for f in (2, 4):
+            rel = np.abs(maxima[f] - maxima[1]) / np.maximum(np.abs(maxima[1]), 1e-12)
+            out[f"{name}_deviation_f{f}"] = float(rel.mean())
+            out[f"{name}_signed_f{f}"] = float(np.mean(maxima[f] - maxima[1]))
+        out[f"{name}_mean_max_f1"] = float(maxima[1].mean())
+    out["seconds"] = time.perf_counter() - t0
     return out
 
 
