@@ -152,60 +152,68 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
     const int64_t p0 = ((int64_t)blockIdx.x * kKsgWarps + warp) * per_warp;
     const int64_t p1 = min(N, p0 + per_warp);
     if (p0 >= p1) return;
-    const int64_t total = (p1 - p0) * n;  // stream length
-    int64_t staged = p0;                   // next pair to stage
-    unsigned valid = 0;                    // bit (p & 1): pair in that slot is valid
+    // the round's first stream position as (pair tr, sample tir); positions
+    // advance by 32 per round and n >= 32, so a round crosses at most one
+    // pair boundary and no division is needed
+    int64_t tr = p0;
+    int tir = 0;
+    int64_t staged = p0;  // next pair to stage
+    unsigned valid = 0;   // bit (p & 1): pair in that slot is valid
     long long acc[2] = {0, 0};
-    for (int64_t r0 = 0; r0 < total; r0 += 32) {
-        const int64_t last = min(total, r0 + 32) - 1;
-        const int64_t p_last = p0 + last / n;
-        for (; staged <= p_last; ++staged) {  // warp-uniform
+    while (tr < p1) {
+        const int64_t t_last = min(p1 - 1, tr + (tir + 31 >= n ? 1 : 0));
+        for (; staged <= t_last; ++staged) {  // warp-uniform
             const int sl = (int)(staged & 1);
             const uint32_t p = pa[staged], q = pb[staged];
-            if (p >= Pa || q >= Pb) {
+            if (p < Pa && q < Pb) {
+                valid |= 1u << sl;
+                const int64_t ra = (int64_t)p * n_pad, rb = (int64_t)q * n_pad;
+                ksg_stage<KMAX>(wbase + sl * slot_bytes, n, n_pad, sorted_a + ra, perm_a + ra,
+                                vals_a + ra, sorted_b + rb, perm_b + rb, vals_b + rb);
+            } else {
                 valid &= ~(1u << sl);
                 if (lane == 0) {
                     out[staged] = CUDART_NAN_F;
                     set_status(status, DEV_BAD_INDEX);
                 }
-                continue;
-            }
-            valid |= 1u << sl;
-            const int64_t ra = (int64_t)p * n_pad, rb = (int64_t)q * n_pad;
-            ksg_stage<KMAX>(wbase + sl * slot_bytes, n, n_pad, sorted_a + ra, perm_a + ra,
-                            vals_a + ra, sorted_b + rb, perm_b + rb, vals_b + rb);
-        }
-        const int64_t s = r0 + lane;
-        if (s <= last) {
-            const int64_t t = p0 + s / n;
-            const int ti = (int)(s % n), sl = (int)(t & 1);
-            if ((valid >> sl) & 1u) {
-                int cx, cy;
-                float eps;
-                const long long v = ksg_sample<KMAX>(wbase + sl * slot_bytes, n, n_pad, k, ti,
-                                                     psi, nx_out ? &cx : nullptr, &cy, &eps);
-                if (sl) acc[1] += v;
-                else acc[0] += v;
-                if (nx_out) {
-                    const int orig = perm_a[(int64_t)pa[t] * n_pad + ti];
-                    nx_out[t * n + orig] = cx;
-                    ny_out[t * n + orig] = cy;
-                    if (eps_out) eps_out[t * n + orig] = eps;
-                }
             }
         }
-        // the pair whose last sample is in this round (at most one, n >= 32)
-        const int64_t ended = (last + 1) / n;  // pairs of this warp complete after the round
-        if (ended > 0 && ended * n - 1 >= r0) {
-            const int64_t te = p0 + ended - 1;
-            const int sl = (int)(te & 1);
-            const long long sum = warp_sum_i64(sl ? acc[1] : acc[0]);
-            if (lane == 0 && ((valid >> sl) & 1u))
-                out[te] = (float)(psi_nk - (double)sum * fix_over_n);
-            if (sl) acc[1] = 0;
+        int ti = tir + lane;
+        int64_t t = tr;
+        if (ti >= n) {
+            ti -= n;
+            ++t;
+        }
+        const int sl = (int)(t & 1);
+        if (t < p1 && ((valid >> sl) & 1u)) {
+            int cx, cy;
+            float eps;
+            const long long v = ksg_sample<KMAX>(wbase + sl * slot_bytes, n, n_pad, k, ti, psi,
+                                                 nx_out ? &cx : nullptr, &cy, &eps);
+            if (sl) acc[1] += v;
+            else acc[0] += v;
+            if (nx_out) {
+                const int orig = perm_a[(int64_t)pa[t] * n_pad + ti];
+                nx_out[t * n + orig] = cx;
+                ny_out[t * n + orig] = cy;
+                if (eps_out) eps_out[t * n + orig] = eps;
+            }
+        }
+        // pair tr ends in this round when its last sample n - 1 <= tir + 31
+        if (tir + 32 >= n) {
+            const int se = (int)(tr & 1);
+            const long long sum = warp_sum_i64(se ? acc[1] : acc[0]);
+            if (lane == 0 && ((valid >> se) & 1u))
+                out[tr] = (float)(psi_nk - (double)sum * fix_over_n);
+            if (se) acc[1] = 0;
             else acc[0] = 0;
         }
         __syncwarp();
+        tir += 32;
+        if (tir >= n) {
+            tir -= n;
+            ++tr;
+        }
     }
 }
 

@@ -146,7 +146,9 @@ __host__ __device__ constexpr size_t ksg_slot_bytes(int n_pad, int kmax) {
 // sa/pa/va: sorted values, argsort and member values of point p (x);
 // sb/pb/vb: the same for point q (y). Both sorted arrays get ksg_pad(KMAX)
 // sentinels per side, -inf on the left and +inf on the right, so that every
-// axis distance to a sentinel is +inf.
+// axis distance to a sentinel is +inf. Members are taken 128 at a time (four
+// per lane): every global load of a batch is issued before the gathers that
+// depend on it, so a batch costs two memory round trips.
 template <int KMAX>
 __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
                                           const float* __restrict__ sa,
@@ -156,6 +158,7 @@ __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
                                           const uint16_t* __restrict__ pb,
                                           const float* __restrict__ vb) {
     constexpr int pad = ksg_pad(KMAX);
+    constexpr int IT = 4;
     const int lane = threadIdx.x & 31;
     float2* XO = reinterpret_cast<float2*>(slot) + pad;
     float2* YO = XO + n_pad + 2 * pad;
@@ -168,16 +171,48 @@ __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
         XO[n + lane] = hi;
         YO[n + lane] = hi;
     }
-    for (int m = lane; m < n; m += 32) {
-        const int mq = pb[m];
-        invq[mq] = (uint16_t)m;
-        YO[m] = make_float2(sb[m], va[mq]);
+    // y side: invq (inverse argsort of q) and YO = (y sorted, x of that member)
+    for (int base = 0; base < n; base += 32 * IT) {
+        int mq[IT];
+        float y[IT], x[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int m = base + 32 * i + lane;
+            mq[i] = m < n ? pb[m] : 0;
+            y[i] = m < n ? sb[m] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < IT; ++i) x[i] = base + 32 * i + lane < n ? va[mq[i]] : 0.f;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int m = base + 32 * i + lane;
+            if (m < n) {
+                invq[mq[i]] = (uint16_t)m;
+                YO[m] = make_float2(y[i], x[i]);
+            }
+        }
     }
     __syncwarp();
-    for (int m = lane; m < n; m += 32) {
-        const int mp = pa[m];
-        XO[m] = make_float2(sa[m], vb[mp]);
-        upos[m] = invq[mp];
+    // x side: XO = (x sorted, y of that member), upos = y-sorted position
+    for (int base = 0; base < n; base += 32 * IT) {
+        int mp[IT];
+        float x[IT], y[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int m = base + 32 * i + lane;
+            mp[i] = m < n ? pa[m] : 0;
+            x[i] = m < n ? sa[m] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < IT; ++i) y[i] = base + 32 * i + lane < n ? vb[mp[i]] : 0.f;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int m = base + 32 * i + lane;
+            if (m < n) {
+                XO[m] = make_float2(x[i], y[i]);
+                upos[m] = invq[mp[i]];
+            }
+        }
     }
     __syncwarp();
 }
