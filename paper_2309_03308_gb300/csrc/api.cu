@@ -827,7 +827,7 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
                  o_sel = take(sizeof(Select) * 2), o_best = take(8), o_thr = take(8),
                  o_ids = take(4ull * cap), o_vals = take(4ull * cap * 32),
                  o_pids = take(8ull * cap * 32), o_sidx = take(4 * 8192), o_tv = take(4 * 4096),
-                 o_ti = take(8 * 4096), o_out = take(sizeof(SideOut) * 2);
+                 o_ti = take(8 * 4096), o_sk = take(8 * 8192), o_out = take(sizeof(SideOut) * 2);
     CK(ctx->mixed.ensure(off));
     unsigned char* base = ctx->mixed.as<unsigned char>();
     float* cmax = (float*)(base + o_cmax);
@@ -878,7 +878,7 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
             CK(launch_select_top(rvals, (int64_t)cap * 32, 1.f, (unsigned)topk, hist, sel + 1,
                                  sidx, 8192, st, &sel->count));
             CK(launch_sort_top(rvals, rpids, sidx, &sel[1].count, 8192, 1.f, topk, tvals, tids,
-                               st));
+                               (unsigned long long*)(base + o_sk), st));
         }
         CK(cudaMemcpyAsync(&dout[side].sel, sel, sizeof(Select), cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(&dout[side].best, best, 8, cudaMemcpyDeviceToDevice, st));

@@ -202,13 +202,16 @@ cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int
 cudaError_t launch_second_threshold(const unsigned long long* best, const unsigned* emax_a,
                                     const unsigned* emax_b, float acc_rel, Select* sel,
                                     float* thr, cudaStream_t st);
+// top-k (<= 8192) of up to 8192 selected entries, sorted descending by value,
+// then by smallest id; scratch holds 8192 64-bit keys
 cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,
                             const uint32_t* sel_idx, const unsigned* count, unsigned cap,
                             float sign, int topk, float* out_vals, unsigned long long* out_ids,
-                            cudaStream_t st);
+                            unsigned long long* scratch, cudaStream_t st);
 cudaError_t launch_sort_top_ids(const float* vals, const uint32_t* sel_idx, const unsigned* count,
                                 unsigned cap, int topk, float* out_vals,
-                                unsigned long long* out_ids, cudaStream_t st);
+                                unsigned long long* out_ids, unsigned long long* scratch,
+                                cudaStream_t st);
 cudaError_t launch_dot2_pairs(const float* A, int64_t Pa, const float* B, int64_t Pb, int n_pad,
                               int n, const uint32_t* pa, const uint32_t* pb, int64_t N, float* out,
                               int* status, cudaStream_t st);

@@ -206,7 +206,13 @@ __global__ void k_compact(const float* __restrict__ v, int64_t N, float sign,
         if (!(x > -CUDART_INF_F)) continue;
         const unsigned k = okey(x);
         if (k >= lo && (hi == 0u || k < hi)) {
-            const unsigned slot = atomicAdd(count, 1u);
+            // one counter update per warp: the leader takes the warp's slots
+            const unsigned m = __activemask();
+            const int leader = __ffs(m) - 1, lane = threadIdx.x & 31;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+            base = __shfl_sync(m, base, leader);
+            const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
             if (slot < cap) out[slot] = (uint32_t)i;
             else atomicAdd(ovf, 1u);
         }
@@ -249,6 +255,11 @@ __device__ __forceinline__ float dot2_warp(const float (&x)[R], const float* __r
     return __fadd_rn(s, c);
 }
 
+// One warp per chunk, one lane per pair: lane j evaluates (a, 32 * chunk + j)
+// with a sequential Dot2 over the members. The 32 column rows are read 32
+// members at a time, coalesced, into a transposed shared-memory tile (rows
+// padded to 33 words), and row a's member is broadcast from the lane that
+// holds it, so a chunk costs one pass over its rows and no reductions.
 template <int R>
 __global__ void __launch_bounds__(256)
     k_refine_chunks(const float* __restrict__ plane_a, const float* __restrict__ plane_b,
@@ -258,14 +269,16 @@ __global__ void __launch_bounds__(256)
                     const unsigned* __restrict__ count_p, unsigned cap, float sign,
                     float* __restrict__ vals, unsigned long long* __restrict__ pair_ids,
                     unsigned long long* __restrict__ best) {
-    const int lane = threadIdx.x & 31;
+    __shared__ float tile[8][32][33];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float (*T)[33] = tile[wib];
     const unsigned count = min(*count_p, cap);
     const unsigned start = start_p ? min(*start_p, cap) : 0u;
-    for (int64_t w = start + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); w < count;
+    for (int64_t w = start + (int64_t)blockIdx.x * 8 + wib; w < count;
          w += (int64_t)gridDim.x * 8) {
         const uint32_t id = ids[w];
         const int64_t chunk = id / na_pad, a = id % na_pad;
-        if (a >= na) continue;
+        if (a >= na) continue;  // warp-uniform
         float x[R];
         const float* xa = plane_a + (int64_t)pts_a[a] * n_pad;
 #pragma unroll
@@ -273,25 +286,58 @@ __global__ void __launch_bounds__(256)
             const int k = r * 32 + lane;
             x[r] = k < n ? xa[k] : 0.f;
         }
-        float mine = -CUDART_INF_F;
-        unsigned long long mine_id = ~0ull;
-        for (int j = 0; j < 32; ++j) {
-            const int64_t b = chunk * 32 + j;
-            const bool ok = b < nb && (!self || b > a);
-            float r = -CUDART_INF_F;
-            if (ok) r = sign * dot2_warp<R>(x, plane_b + (int64_t)pts_b[b] * n_pad, n);
-            if (lane == j) {
-                mine = r;
-                mine_id = ok ? (unsigned long long)(a * nb + b) : ~0ull;
+        const int64_t b = chunk * 32 + lane;
+        const bool ok = b < nb && (!self || b > a);
+        const int64_t row = ok ? (int64_t)pts_b[b] * n_pad : -1;
+        float s = 0.f, c = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r * 32 < n) {  // warp-uniform
+                // all 32 loads of the slice are issued before the tile is
+                // written, so they are in flight together
+                float v[32];
+                const int k = r * 32 + lane;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t rj = __shfl_sync(0xffffffffu, row, j);
+                    v[j] = rj >= 0 && k < n ? __ldg(plane_b + rj + k) : 0.f;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) T[j][lane] = v[j];
+                __syncwarp();
+                const int kn = min(32, n - r * 32);
+#pragma unroll
+                for (int kk = 0; kk < 32; ++kk) {
+                    if (kk < kn) {
+                        const float xv = __shfl_sync(0xffffffffu, x[r], kk);
+                        const float yv = T[lane][kk];
+                        const float p = __fmul_rn(xv, yv);
+                        const float pe = fmaf(xv, yv, -p);  // TwoProduct error, exact
+                        float t, q;
+                        two_sum(s, p, t, q);
+                        s = t;
+                        c = __fadd_rn(c, __fadd_rn(q, pe));
+                    }
+                }
             }
         }
+        const float mine = ok ? sign * __fadd_rn(s, c) : -CUDART_INF_F;
+        const unsigned long long mine_id = ok ? (unsigned long long)(a * nb + b) : ~0ull;
         vals[w * 32 + lane] = mine;
         pair_ids[w * 32 + lane] = mine_id;
-        if (mine > -CUDART_INF_F) {  // best (signed) value, smallest pair index on ties
-            const unsigned long long key =
-                ((unsigned long long)okey(mine) << 32) | (0xffffffffull - (mine_id & 0xffffffffull));
-            atomicMax(best, key);
+        // best (signed) value, smallest pair index on ties: the warp's maximum
+        // key, then one atomic per chunk (one address is shared by all chunks)
+        unsigned long long key =
+            mine > -CUDART_INF_F
+                ? ((unsigned long long)okey(mine) << 32) | (0xffffffffull - (mine_id & 0xffffffffull))
+                : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+            key = other > key ? other : key;
         }
+        if (lane == 0 && key != 0ull) atomicMax(best, key);
     }
 }
 
@@ -308,104 +354,121 @@ __global__ void k_second_threshold(const unsigned long long* best, const unsigne
     sel->pass1 = sel->count;
 }
 
-// 5. top-K: bitonic sort (descending) of up to 8192 (value, pair) entries in
-// one CTA, taken from the compacted refined values. Thread t holds entries
-// 8t .. 8t+7 in registers: exchanges at distance < 8 stay in registers, at
-// distance 8 .. 255 go through warp shuffles, and only the 15 stages at
-// distance >= 256 pass through shared memory.
-__device__ __forceinline__ void sort_keep(unsigned long long& k, unsigned long long& p,
-                                          unsigned long long ok, unsigned long long op,
-                                          bool keep_max) {
-    const bool take = keep_max ? ok > k : ok < k;
-    k = take ? ok : k;
-    p = take ? op : p;
-}
+// 5. top-K of up to 8192 (value, pair) entries taken from the compacted
+// refined values, sorted descending. An entry is the 64-bit key
+// okey(value) << 32 | (2^32 - 1 - pair id): pair ids are below 2^32, so keys
+// are unique, order by value and then by smallest pair id, and give the id
+// back. Two kernels:
+//   k_topk_chunks  CTA c sorts entries 1024 c .. 1024 c + 1023 (bitonic,
+//                  8 per thread: register, shuffle and shared-memory stages)
+//                  into scratch, descending, missing entries as key 0;
+//   k_topk_rank    every entry's final position is its position in its own
+//                  chunk plus, for each other chunk, the number of its keys
+//                  that are larger (binary search; keys are unique), and
+//                  entries placed below topk are written out.
+constexpr int kTopChunk = 1024, kTopMax = 8192;
 
 template <int D>
-__device__ __forceinline__ void sort_regs(unsigned long long (&key)[8], unsigned long long (&pid)[8],
-                                          int i0, int size) {
+__device__ __forceinline__ void sort_regs(unsigned long long (&key)[8], int i0, int size) {
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         constexpr int dd = D;
         const int e2 = e ^ dd;
         if (e2 > e) {
             const bool desc = ((i0 + e) & size) == 0;
-            if ((key[e] < key[e2]) == desc) {
-                const unsigned long long tk = key[e], tp = pid[e];
-                key[e] = key[e2];
-                pid[e] = pid[e2];
-                key[e2] = tk;
-                pid[e2] = tp;
-            }
+            const unsigned long long a = key[e], b = key[e2];
+            const bool swap = (a < b) == desc;
+            key[e] = swap ? b : a;
+            key[e2] = swap ? a : b;
         }
     }
 }
 
-__global__ void __launch_bounds__(1024)
-    k_sort_top(const float* __restrict__ vals, const unsigned long long* __restrict__ pids,
-               const uint32_t* __restrict__ sel_idx, const unsigned* __restrict__ count_p,
-               unsigned cap, float sign, int topk, float* __restrict__ out_vals,
-               unsigned long long* __restrict__ out_ids) {
-    extern __shared__ unsigned long long sort_smem[];
-    unsigned long long* skey = sort_smem;
-    unsigned long long* spid = sort_smem + 8192;
+__global__ void __launch_bounds__(kTopChunk / 8)
+    k_topk_chunks(const float* __restrict__ vals, const unsigned long long* __restrict__ pids,
+                  const uint32_t* __restrict__ sel_idx, const unsigned* __restrict__ count_p,
+                  unsigned cap, unsigned long long* __restrict__ sorted) {
+    __shared__ unsigned long long skey[kTopChunk];
     constexpr int E = 8;
-    const int t = threadIdx.x;
-    const unsigned count = min(*count_p, cap);
-    unsigned long long key[E], pid[E];
+    const int t = threadIdx.x, c0 = blockIdx.x * kTopChunk;
+    const unsigned count = min(min(*count_p, cap), (unsigned)kTopMax);
+    if ((unsigned)c0 >= count) return;  // block-uniform: an empty chunk is never read
+    unsigned long long key[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int i = t * E + e;
-        if ((unsigned)i < count) {
+        const unsigned i = (unsigned)(c0 + t * E + e);
+        if (i < count) {
             const uint32_t j = sel_idx[i];
             const unsigned long long id = pids ? pids[j] : (unsigned long long)j;
             key[e] = ((unsigned long long)okey(vals[j]) << 32) | (0xffffffffull - (id & 0xffffffffull));
-            pid[e] = id;
         } else {
             key[e] = 0;
-            pid[e] = ~0ull;
         }
     }
-    for (int size = 2; size <= 8192; size <<= 1) {
+    for (int size = 2; size <= kTopChunk; size <<= 1) {
         for (int d = size >> 1; d > 0; d >>= 1) {
             if (d >= 256) {  // partner in another warp
                 __syncthreads();
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    skey[t * E + e] = key[e];
-                    spid[t * E + e] = pid[e];
-                }
+                for (int e = 0; e < E; ++e) skey[t * E + e] = key[e];
                 __syncthreads();
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int i = t * E + e, q = i ^ d;
-                    sort_keep(key[e], pid[e], skey[q], spid[q], (i < q) == ((i & size) == 0));
+                    const unsigned long long o = skey[q];
+                    const bool keep_max = (i < q) == ((i & size) == 0);
+                    key[e] = (keep_max ? o > key[e] : o < key[e]) ? o : key[e];
                 }
             } else if (d >= E) {  // partner lane t ^ (d / E) of the same warp
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int i = t * E + e, q = i ^ d;
-                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key[e], d / E);
-                    const unsigned long long op = __shfl_xor_sync(0xffffffffu, pid[e], d / E);
-                    sort_keep(key[e], pid[e], ok, op, (i < q) == ((i & size) == 0));
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[e], d / E);
+                    const bool keep_max = (i < q) == ((i & size) == 0);
+                    key[e] = (keep_max ? o > key[e] : o < key[e]) ? o : key[e];
                 }
-            } else if (d == 4) {  // partner in this thread's registers
-                sort_regs<4>(key, pid, t * E, size);
+            } else if (d == 4) {
+                sort_regs<4>(key, t * E, size);
             } else if (d == 2) {
-                sort_regs<2>(key, pid, t * E, size);
+                sort_regs<2>(key, t * E, size);
             } else {
-                sort_regs<1>(key, pid, t * E, size);
+                sort_regs<1>(key, t * E, size);
             }
         }
     }
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = t * E + e;
-        if (i < topk) {
-            const bool ok = (unsigned)i < count;
-            out_vals[i] = ok ? sign * okey_inv((unsigned)(key[e] >> 32)) : -sign * CUDART_INF_F;
-            out_ids[i] = ok ? pid[e] : ~0ull;
+    for (int e = 0; e < E; ++e) sorted[c0 + t * E + e] = key[e];
+}
+
+__global__ void __launch_bounds__(256)
+    k_topk_rank(const unsigned long long* __restrict__ sorted, const unsigned* __restrict__ count_p,
+                unsigned cap, float sign, int topk, float* __restrict__ out_vals,
+                unsigned long long* __restrict__ out_ids) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned count = min(min(*count_p, cap), (unsigned)kTopMax);
+    const int nchunks = (int)((count + kTopChunk - 1) / kTopChunk);
+    if ((unsigned)g >= count) {  // positions past the entries: empty
+        if (g < topk) {
+            out_vals[g] = -sign * CUDART_INF_F;
+            out_ids[g] = ~0ull;
         }
+        return;
+    }
+    const int c = g / kTopChunk;
+    const unsigned long long key = sorted[g];  // nonzero: a real entry
+    int rank = g - c * kTopChunk;
+    for (int o = 0; o < nchunks; ++o) {
+        if (o == c) continue;
+        // keys of chunk o are descending: count those above key
+        const unsigned long long* ch = sorted + o * kTopChunk;
+        int lo = 0;
+        for (int step = kTopChunk / 2; step > 0; step >>= 1)
+            if (ch[lo + step - 1] > key) lo += step;
+        rank += lo + (ch[lo] > key ? 1 : 0);
+    }
+    if (rank < topk) {
+        out_vals[rank] = sign * okey_inv((unsigned)(key >> 32));
+        out_ids[rank] = 0xffffffffull - (key & 0xffffffffull);
     }
 }
 
@@ -497,22 +560,23 @@ cudaError_t launch_second_threshold(const unsigned long long* best, const unsign
 cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,
                             const uint32_t* sel_idx, const unsigned* count, unsigned cap,
                             float sign, int topk, float* out_vals, unsigned long long* out_ids,
-                            cudaStream_t st) {
-    const int smem = 2 * 8192 * (int)sizeof(unsigned long long);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_sort_top, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    k_sort_top<<<1, 1024, smem, st>>>(vals, pids, sel_idx, count, cap, sign, topk, out_vals,
-                                      out_ids);
+                            unsigned long long* scratch, cudaStream_t st) {
+    if (topk < 0 || topk > kTopMax) return cudaErrorInvalidValue;
+    note_launch(2);
+    k_topk_chunks<<<kTopMax / kTopChunk, kTopChunk / 8, 0, st>>>(vals, pids, sel_idx, count, cap,
+                                                                 scratch);
+    k_topk_rank<<<kTopMax / 256, 256, 0, st>>>(scratch, count, cap, sign, topk, out_vals,
+                                               out_ids);
     return cudaGetLastError();
 }
 
 // top-k of vals[sel_idx[i]] where the selected index is itself the id
 cudaError_t launch_sort_top_ids(const float* vals, const uint32_t* sel_idx, const unsigned* count,
                                 unsigned cap, int topk, float* out_vals,
-                                unsigned long long* out_ids, cudaStream_t st) {
-    return launch_sort_top(vals, nullptr, sel_idx, count, cap, 1.f, topk, out_vals, out_ids, st);
+                                unsigned long long* out_ids, unsigned long long* scratch,
+                                cudaStream_t st) {
+    return launch_sort_top(vals, nullptr, sel_idx, count, cap, 1.f, topk, out_vals, out_ids,
+                           scratch, st);
 }
 
 // 3c for a plain pair batch: Dot2 Pearson/Spearman (precision CC_FP32_DOT2).

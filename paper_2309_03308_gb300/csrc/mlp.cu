@@ -827,8 +827,8 @@ cc_status cc_sur_screen(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t region
     const int64_t na = pra->np, nb = prb->np;
     // top-k by histogram selection, then one sorting CTA
     const size_t o_hist = 0, o_sel = 4 * 4096, o_idx = o_sel + 256, o_tv = o_idx + 4 * 8192,
-                 o_ti = o_tv + 4 * 8192;
-    SK(aux.alloc(o_ti + 8 * 8192));
+                 o_ti = o_tv + 4 * 8192, o_sk = o_ti + 8 * 8192;
+    SK(aux.alloc(o_sk + 8 * 8192));
     unsigned char* ab = aux.as<unsigned char>();
     SK(cudaMemsetAsync(ab, 0, o_idx, st));
     const int64_t N = na * nb;
@@ -837,7 +837,8 @@ cc_status cc_sur_screen(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t region
     // candidate indices are the linear pair indices a * nb + b themselves
     SK(launch_sort_top_ids(pred.as<float>(), (const uint32_t*)(ab + o_idx),
                            &((Select*)(ab + o_sel))->count, 8192, topk, (float*)(ab + o_tv),
-                           (unsigned long long*)(ab + o_ti), st));
+                           (unsigned long long*)(ab + o_ti), (unsigned long long*)(ab + o_sk),
+                           st));
     SK(cudaMemcpyAsync(preds, ab + o_tv, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
     SK(cudaMemcpyAsync(ids, ab + o_ti, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
     SK(cudaStreamSynchronize(st));
