@@ -10,7 +10,10 @@
 //
 // Tiling: 128 x 128 outputs per CTA, 256 threads with 8 x 8 outputs each
 // (rows ty*4+{0..3} and 64+ty*4+{0..3}, same for columns), K staged through a
-// 3-deep cp.async ring of 8-member slices.
+// 3-deep cp.async ring of 8-member slices. The products accumulate with the
+// packed FP32 FMA (two IEEE fp32 fma.rn per instruction on adjacent columns),
+// which halves the issue slots the FMAs take; the values are those of plain
+// fmaf in the same order.
 #include "device.cuh"
 #include "internal.cuh"
 
@@ -26,6 +29,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// d = a * b + d elementwise on (lo, hi) fp32 pairs, each an IEEE fma.rn
+__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a,
+                                      unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
 
 __global__ void __launch_bounds__(NT, 2)
@@ -61,11 +78,13 @@ __global__ void __launch_bounds__(NT, 2)
         cp_async16(&Bs[s][lrow][lcol], B + (int64_t)k * ldb + b0 + lcol);
     };
 
-    float acc[8][8];
+    // accumulators in column pairs for the packed FP32 FMA (fma.rn.f32x2:
+    // two independent IEEE fp32 FMAs per instruction)
+    unsigned long long acc2[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) acc2[i][j] = 0ull;
 
 #pragma unroll
     for (int s = 0; s < STAGES - 1; ++s) {
@@ -86,14 +105,22 @@ __global__ void __launch_bounds__(NT, 2)
             const float4 bl = *reinterpret_cast<const float4*>(&Bs[s][kk][tx * 4]);
             const float4 bh = *reinterpret_cast<const float4*>(&Bs[s][kk][64 + tx * 4]);
             const float a[8] = {al.x, al.y, al.z, al.w, ah.x, ah.y, ah.z, ah.w};
-            const float b[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
+            const unsigned long long bp[4] = {pack2(bl.x, bl.y), pack2(bl.z, bl.w),
+                                              pack2(bh.x, bh.y), pack2(bh.z, bh.w)};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                const unsigned long long aa = pack2(a[i], a[i]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) ffma2(acc2[i][j], aa, bp[j]);
+            }
         }
     }
     cp_async_wait<0>();
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) unpack2(acc2[i][j], acc[i][2 * j], acc[i][2 * j + 1]);
 
     // epilogue: store and reduce. A tile inside both regions and clear of the
     // self-pair diagonal reduces without per-value checks: value extremes

@@ -341,6 +341,62 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// For n > 128 (more than four member slices) one warp evaluates the chunk's
+// pairs one after another, each with a warp-wide Dot2 (lanes over members,
+// compensated tree reduction): the lane-per-pair form would unroll 32 slices
+// of 32 loads each.
+template <int R>
+__global__ void __launch_bounds__(256)
+    k_refine_chunks_warp(const float* __restrict__ plane_a, const float* __restrict__ plane_b,
+                         int n_pad, int n, const uint32_t* __restrict__ pts_a, int64_t na,
+                         const uint32_t* __restrict__ pts_b, int64_t nb, int self,
+                         int64_t na_pad, const uint32_t* __restrict__ ids,
+                         const unsigned* __restrict__ start_p, const unsigned* __restrict__ count_p,
+                         unsigned cap, float sign, float* __restrict__ vals,
+                         unsigned long long* __restrict__ pair_ids,
+                         unsigned long long* __restrict__ best) {
+    const int lane = threadIdx.x & 31;
+    const unsigned count = min(*count_p, cap);
+    const unsigned start = start_p ? min(*start_p, cap) : 0u;
+    for (int64_t w = start + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); w < count;
+         w += (int64_t)gridDim.x * 8) {
+        const uint32_t id = ids[w];
+        const int64_t chunk = id / na_pad, a = id % na_pad;
+        if (a >= na) continue;  // warp-uniform
+        float x[R];
+        const float* xa = plane_a + (int64_t)pts_a[a] * n_pad;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = r * 32 + lane;
+            x[r] = k < n ? xa[k] : 0.f;
+        }
+        float mine = -CUDART_INF_F;
+        unsigned long long mine_id = ~0ull;
+        for (int j = 0; j < 32; ++j) {
+            const int64_t b = chunk * 32 + j;
+            const bool ok = b < nb && (!self || b > a);
+            float r = -CUDART_INF_F;
+            if (ok) r = sign * dot2_warp<R>(x, plane_b + (int64_t)pts_b[b] * n_pad, n);
+            if (lane == j) {
+                mine = r;
+                mine_id = ok ? (unsigned long long)(a * nb + b) : ~0ull;
+            }
+        }
+        vals[w * 32 + lane] = mine;
+        pair_ids[w * 32 + lane] = mine_id;
+        unsigned long long key =
+            mine > -CUDART_INF_F
+                ? ((unsigned long long)okey(mine) << 32) | (0xffffffffull - (mine_id & 0xffffffffull))
+                : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+            key = other > key ? other : key;
+        }
+        if (lane == 0 && key != 0ull) atomicMax(best, key);
+    }
+}
+
 // r* - B as a value threshold for the second pass (sign-adjusted domain);
 // records where the first pass's candidates end.
 __global__ void k_second_threshold(const unsigned long long* best, const unsigned* emax_a,
@@ -534,17 +590,16 @@ cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int
                                  float sign, float* vals, unsigned long long* pair_ids,
                                  unsigned long long* best, cudaStream_t st) {
     note_launch();
-#define CC_REFINE(R)                                                                           \
-    k_refine_chunks<R><<<152 * 8, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, \
-                                                nb, self, na_pad, ids, start, count, cap,      \
-                                                sign, vals, pair_ids, best)
+#define CC_REFINE(K, R)                                                                   \
+    K<R><<<152 * 8, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, nb, self,  \
+                                  na_pad, ids, start, count, cap, sign, vals, pair_ids, best)
     const int slices = (n + 31) / 32;
-    if (slices <= 1) CC_REFINE(1);
-    else if (slices <= 2) CC_REFINE(2);
-    else if (slices <= 4) CC_REFINE(4);
-    else if (slices <= 8) CC_REFINE(8);
-    else if (slices <= 16) CC_REFINE(16);
-    else CC_REFINE(32);
+    if (slices <= 1) CC_REFINE(k_refine_chunks, 1);
+    else if (slices <= 2) CC_REFINE(k_refine_chunks, 2);
+    else if (slices <= 4) CC_REFINE(k_refine_chunks, 4);
+    else if (slices <= 8) CC_REFINE(k_refine_chunks_warp, 8);
+    else if (slices <= 16) CC_REFINE(k_refine_chunks_warp, 16);
+    else CC_REFINE(k_refine_chunks_warp, 32);
 #undef CC_REFINE
     return cudaGetLastError();
 }
