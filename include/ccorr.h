@@ -140,7 +140,11 @@ cc_status cc_load_field(cc_ctx* ctx, const float* data, int data_is_device, int 
  * allocated on the first such call and kept with the field). Planes of the
  * field's regions and bin planes are rebuilt on their next use. Asynchronous:
  * a NaN or Inf is reported as CC_ERR_NONFINITE by cc_sync or by the next call
- * that returns host data.
+ * that returns host data. From host memory of 64 MB or more the copy runs in
+ * eight point ranges on a second stream of the context, each range's planes
+ * computed on the context's stream as soon as it has arrived; the host
+ * buffer must stay unchanged until the context's stream reaches this call's
+ * work (page-locked memory makes the copy asynchronous).
  */
 cc_status cc_update_field(cc_ctx* ctx, int32_t field_id, const float* data, int data_is_device);
 

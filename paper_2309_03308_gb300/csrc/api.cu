@@ -331,7 +331,7 @@ cc_status cc_load_field(cc_ctx* ctx, const float* data, int data_is_device, int 
                            ctx->stream));
         src = staging.as<float>();
     }
-    CK(launch_ingest(src, n, P, f->n_pad, f->vals.as<float>(), ctx->status.as<int>(),
+    CK(launch_ingest(src, n, P, P, f->n_pad, f->vals.as<float>(), ctx->status.as<int>(),
                      ctx->stream));
     cc_status s = take_status(ctx);  // synchronises: staging may be released after this
     if (s) return s;
@@ -358,20 +358,13 @@ cc_status cc_aggregate_field(cc_ctx* ctx, int32_t field_id, int bx, int by, int 
     return cc_load_field(ctx, agg.as<float>(), 1, Xc, Yc, Zc, n, out_field_id);
 }
 
+constexpr int kUpdateChunks = 8;  // point ranges of a host-data update
+
 cc_status cc_update_field(cc_ctx* ctx, int32_t field_id, const float* data, int data_is_device) {
     if (!ctx) return CC_ERR_INVALID_ARG;
     Field* f = get_field(ctx, field_id);
     if (!f || !data) return fail(ctx, CC_ERR_INVALID_ARG, "unknown field or NULL data");
     CK(cudaSetDevice(ctx->device));
-    const float* src = data;
-    if (!data_is_device) {
-        CK(f->staging.ensure(sizeof(float) * (size_t)f->P * f->n));
-        CK(cudaMemcpyAsync(f->staging.p, data, sizeof(float) * (size_t)f->P * f->n,
-                           cudaMemcpyHostToDevice, ctx->stream));
-        src = f->staging.as<float>();
-    }
-    CK(launch_ingest(src, f->n, f->P, f->n_pad, f->vals.as<float>(), ctx->status.as<int>(),
-                     ctx->stream));
     // bin planes already in use are rebuilt in the same pass (two bin counts)
     PrepBins pb;
     for (auto& kv : f->bins) {
@@ -385,7 +378,49 @@ cc_status cc_update_field(cc_ctx* ctx, int32_t field_id, const float* data, int 
         pb.hmarg[pb.count] = f->hmarg[kv.first]->as<long long>();
         ++pb.count;
     }
-    CK(launch_point_prep(*f, ctx->stream, pb));
+    if (data_is_device) {
+        CK(launch_ingest(data, f->n, f->P, f->P, f->n_pad, f->vals.as<float>(),
+                         ctx->status.as<int>(), ctx->stream));
+        CK(launch_point_prep(*f, ctx->stream, pb));
+    } else {
+        // Host data: the copy is cut into point ranges (one 2D copy of n
+        // member rows each) on a second stream, and each range's ingest and
+        // per-point pass start as soon as its copy has landed, so the
+        // transfer overlaps the computation. The staging buffer keeps the
+        // caller's member-major layout.
+        const size_t bytes = sizeof(float) * (size_t)f->P * f->n;
+        CK(f->staging.ensure(bytes));
+        const int chunks = bytes >= ((size_t)64 << 20) ? kUpdateChunks : 1;
+        if (!ctx->copy_stream)
+            CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        while ((int)ctx->copy_events.size() < kUpdateChunks + 1) {
+            cudaEvent_t e;
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            ctx->copy_events.push_back(e);
+        }
+        // the staging buffer may still be read by work queued before this call
+        CK(cudaEventRecord(ctx->copy_events[kUpdateChunks], ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_events[kUpdateChunks], 0));
+        const int64_t step = (f->P + chunks - 1) / chunks;
+        float* stg = f->staging.as<float>();
+        for (int c = 0; c < chunks; ++c) {
+            const int64_t p0 = c * step, pc = std::min<int64_t>(step, f->P - p0);
+            if (pc <= 0) break;
+            CK(cudaMemcpy2DAsync(stg + p0, sizeof(float) * (size_t)f->P, data + p0,
+                                 sizeof(float) * (size_t)f->P, sizeof(float) * (size_t)pc,
+                                 (size_t)f->n, cudaMemcpyHostToDevice, ctx->copy_stream));
+            CK(cudaEventRecord(ctx->copy_events[c], ctx->copy_stream));
+        }
+        for (int c = 0; c < chunks; ++c) {
+            const int64_t p0 = c * step, pc = std::min<int64_t>(step, f->P - p0);
+            if (pc <= 0) break;
+            CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_events[c], 0));
+            CK(launch_ingest(stg + p0, f->n, pc, f->P, f->n_pad,
+                             f->vals.as<float>() + p0 * f->n_pad, ctx->status.as<int>(),
+                             ctx->stream));
+            CK(launch_point_prep(*f, ctx->stream, pb, p0, p0 + pc));
+        }
+    }
     f->version++;
     for (int i = 0; i < pb.count; ++i) f->bins_version[pb.B[i]] = f->version;
     return CC_OK;

@@ -110,6 +110,14 @@ struct cc_ctx {
     cc::DevMem pair_a, pair_b, vals_out, partials, rp_out, ksg_nx, ksg_ny, ksg_eps, mixed;
     std::map<int, std::unique_ptr<cc::DevMem>> psi_fix;   // n -> int64 [n+1]
     std::map<int, std::unique_ptr<cc::DevMem>> clogc_fix; // n -> int64 [n+1]
+    // host-to-device copies of an update overlap its ingest: a second stream
+    // and one event per chunk (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_events;
+    ~cc_ctx() {
+        for (cudaEvent_t e : copy_events) cudaEventDestroy(e);
+        if (copy_stream) cudaStreamDestroy(copy_stream);
+    }
 };
 
 namespace cc {
@@ -118,8 +126,9 @@ namespace cc {
 void note_launch(int kernels = 1);
 
 // Kernel launchers (defined in the .cu files), all on `st`.
-cudaError_t launch_ingest(const float* in, int n, int64_t P, int n_pad, float* vals, int* status,
-                          cudaStream_t st);
+// in: member-major [n][in_stride] (P points used), vals: point-major [P][n_pad]
+cudaError_t launch_ingest(const float* in, int n, int64_t P, int64_t in_stride, int n_pad,
+                          float* vals, int* status, cudaStream_t st);
 // bin planes rebuilt inside the per-point pass (at most two bin counts)
 struct PrepBins {
     int count = 0;
@@ -130,7 +139,9 @@ struct PrepBins {
 };
 cudaError_t launch_aggregate(const Field& f, int bx, int by, int bz, int Xc, int Yc, int64_t Pc,
                              int mode, float* out, cudaStream_t st);
-cudaError_t launch_point_prep(const Field& f, cudaStream_t st, const PrepBins& pb = PrepBins());
+// per-point planes of points [p_begin, p_end) (p_end < 0: all points)
+cudaError_t launch_point_prep(const Field& f, cudaStream_t st, const PrepBins& pb = PrepBins(),
+                              int64_t p_begin = 0, int64_t p_end = -1);
 cudaError_t launch_bins(const Field& f, int B, const int64_t* clogc_fix, uint8_t* bins,
                         int64_t* hmarg, cudaStream_t st);
 cudaError_t launch_region_planes(const Field& f, const Region& r, cudaStream_t st);

@@ -18,8 +18,8 @@ namespace cc {
 constexpr int kIngestPts = 32;
 
 __global__ void __launch_bounds__(256)
-    k_ingest(const float* __restrict__ in, int n, int64_t P, int n_pad, float* __restrict__ vals,
-             int* status) {
+    k_ingest(const float* __restrict__ in, int n, int64_t P, int64_t in_stride, int n_pad,
+             float* __restrict__ vals, int* status) {
     extern __shared__ float tile[];  // [n_pad][kIngestPts + 1]
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * kIngestPts;
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int m = m0 + 8 * u + ty;
-            v[u] = (m < n && p < P) ? __ldcs(in + (int64_t)m * P + p) : 0.f;
+            v[u] = (m < n && p < P) ? __ldcs(in + (int64_t)m * in_stride + p) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-cudaError_t launch_ingest(const float* in, int n, int64_t P, int n_pad, float* vals, int* status,
-                          cudaStream_t st) {
+cudaError_t launch_ingest(const float* in, int n, int64_t P, int64_t in_stride, int n_pad,
+                          float* vals, int* status, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)n_pad * (kIngestPts + 1);
     if (smem > 48 * 1024) {
         cudaError_t e =
@@ -62,8 +62,8 @@ cudaError_t launch_ingest(const float* in, int n, int64_t P, int n_pad, float* v
         if (e != cudaSuccess) return e;
     }
     note_launch();
-    k_ingest<<<(unsigned)((P + kIngestPts - 1) / kIngestPts), 256, smem, st>>>(in, n, P, n_pad,
-                                                                              vals, status);
+    k_ingest<<<(unsigned)((P + kIngestPts - 1) / kIngestPts), 256, smem, st>>>(
+        in, n, P, in_stride, n_pad, vals, status);
     return cudaGetLastError();
 }
 
@@ -110,7 +110,7 @@ __device__ __forceinline__ float pow2_scale(float m) {
 
 template <int E>
 __global__ void __launch_bounds__(kPrepWarps * 32)
-    k_point_prep(const float* __restrict__ vals, int64_t P, int n, float nf,
+    k_point_prep(const float* __restrict__ vals, int64_t p_begin, int64_t P, int n, float nf,
                  float* __restrict__ sorted,
                  uint16_t* __restrict__ perm, int16_t* __restrict__ rank2,
                  float* __restrict__ zhat, float* __restrict__ rhat,
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
     __shared__ int bin_hist[kPrepWarps][16];
     constexpr int NP = 32 * E;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t p = (int64_t)blockIdx.x * kPrepWarps + warp;
+    const int64_t p = p_begin + (int64_t)blockIdx.x * kPrepWarps + warp;
     if (p >= P) return;
     const int64_t row = p * NP;
     const int g0 = lane * E;
@@ -341,12 +341,16 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
     }
 }
 
-cudaError_t launch_point_prep(const Field& f, cudaStream_t st, const PrepBins& pb) {
-    const unsigned blocks = (unsigned)((f.P + kPrepWarps - 1) / kPrepWarps);
+cudaError_t launch_point_prep(const Field& f, cudaStream_t st, const PrepBins& pb,
+                              int64_t p_begin, int64_t p_end) {
+    if (p_end < 0) p_end = f.P;
+    if (p_end <= p_begin) return cudaSuccess;
+    const unsigned blocks = (unsigned)((p_end - p_begin + kPrepWarps - 1) / kPrepWarps);
     note_launch();
 #define CC_PREP(E)                                                                               \
     k_point_prep<E><<<blocks, kPrepWarps * 32, 0, st>>>(                                         \
-        f.vals.as<float>(), f.P, f.n, (float)f.n, f.sorted.as<float>(), f.perm.as<uint16_t>(),   \
+        f.vals.as<float>(), p_begin, p_end, f.n, (float)f.n, f.sorted.as<float>(),               \
+        f.perm.as<uint16_t>(),                                                                   \
         f.rank2.as<int16_t>(), f.zhat.as<float>(), f.rhat.as<float>(), f.mean.as<double>(),      \
         f.ss.as<double>(), pb)
     switch (f.n_pad / 32) {  // n_pad is a power of two >= 32

@@ -106,6 +106,31 @@ def test_update_field_rebuilds_every_plane(cc, orc):
     cc.free_field(fid)
 
 
+def test_update_from_host_in_overlapped_chunks(cc):
+    """A host-data update above 64 MB is copied and ingested in point ranges
+    on two streams: every plane equals that of the same values loaded from
+    device memory in one pass (bit for bit), including the bin planes rebuilt
+    in the per-point pass and the ragged last range."""
+    import torch
+    from paper_2309_03308_gb300 import CC_PLANE_BINS, CC_PLANE_RANK2, CC_PLANE_SORTED, CC_PLANE_ZHAT
+    X, Y, Z, n = 131, 67, 20, 100  # 175,540 points (not a multiple of 8), 70 MB
+    F1 = gen.field(41, X, Y, Z, n)
+    F2 = gen.field(42, X, Y, Z, n)
+    upd = cc.load_field(F1)
+    ref = cc.load_field(torch.from_numpy(F2).cuda())
+    pts = np.arange(0, X * Y * Z, 7, dtype=np.uint32)
+    for f in (upd, ref):
+        cc.get_plane(f, CC_PLANE_BINS, pts[:4], n, bins=16)  # 16-bin planes in use
+    for _ in range(2):  # twice: the staging buffer is reused
+        cc.update_field(upd, F2)
+    for plane in (CC_PLANE_ZHAT, CC_PLANE_SORTED, CC_PLANE_RANK2):
+        assert np.array_equal(cc.get_plane(upd, plane, pts, n), cc.get_plane(ref, plane, pts, n))
+    assert np.array_equal(cc.get_plane(upd, CC_PLANE_BINS, pts, n, bins=16),
+                          cc.get_plane(ref, CC_PLANE_BINS, pts, n, bins=16))
+    cc.free_field(upd)
+    cc.free_field(ref)
+
+
 @pytest.mark.parametrize("offset,scale", [(0.0, 1.0), (1e4, 1e-2), (-3e5, 7.0), (1e-30, 1e-33)])
 def test_zhat_standardisation_accuracy(cc, offset, scale):
     """The unit-norm centred member vectors are within a few fp32 roundings of
