@@ -31,20 +31,6 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-// d = a * b + d elementwise on (lo, hi) fp32 pairs, each an IEEE fma.rn
-__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a,
-                                      unsigned long long b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
-}
-
 __global__ void __launch_bounds__(NT, 2)
     k_allpairs_f32(const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
                    int64_t ldb, int nk, int64_t PA, int64_t PB, int self, float* __restrict__ C,

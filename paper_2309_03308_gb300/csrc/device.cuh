@@ -18,6 +18,22 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 }
 
 // Knuth's TwoSum: s = fl(a + b) and the exact rounding error e (a + b = s + e)
+// Packed fp32 pairs (lo, hi) in one 64-bit register, for the packed FMA
+// fma.rn.f32x2: two independent IEEE fp32 fma.rn in one instruction.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// d = a * b + d elementwise
+__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a,
+                                      unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
