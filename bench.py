@@ -765,21 +765,68 @@ def run_context(args, cc, dev, stream, rank, sur=None):
         for name in lds_kinds:
             out[f"pearson_recall_0.005_{name}"] = lds_hit[name] / n_rp
             out[f"pearson_normalized_error_mean_{name}"] = float(np.mean(lds_err[name]))
-        dev = np.array(full_max) - np.array(agg_max)
+        dmean = np.array(full_max) - np.array(agg_max)
         dev_bos = np.array(full_max) - np.array(bos_agg)
         dev_bos_full = np.array(full_max) - np.array([r["max"] for r in rb])
         out["mean_tree_2x2x2"] = {"exhaustive_on_means_s": agg_s,
-                                  "max_deviation_mean": float(np.mean(dev)),
-                                  "max_deviation_p95": float(np.percentile(dev, 95)),
-                                  "within_0.05": float(np.mean(np.abs(dev) <= 0.05)),
+                                  "max_deviation_mean": float(np.mean(dmean)),
+                                  "max_deviation_p95": float(np.percentile(dmean, 95)),
+                                  "within_0.05": float(np.mean(np.abs(dmean) <= 0.05)),
                                   "bos_on_means_s": bos_agg_s,
                                   "bos_on_means_deviation_mean": float(np.mean(dev_bos)),
                                   "bos_full_resolution_deviation_mean": float(
                                       np.mean(dev_bos_full))}
         out["exhaustive_pearson_s"] = time.perf_counter() - t0
+        out["ksg_recall_16"] = ksg_recall(cc, dev, fid, cfg, rp_a, rp_b, res[3], R * T)
         out["mean_tree_bos_100"] = run_mean_tree_experiment(cc, fid, rids, rp_a, rp_b, kw)
     cc.free_field(fid)
     return out
+
+
+def region_points(X, Y, box):
+    """Linear point ids x + X (y + Y z) of a half-open box, x fastest."""
+    x0, y0, z0, x1, y1, z1 = box
+    z, y, x = np.meshgrid(np.arange(z0, z1), np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+    return (x + X * (y + Y * z)).ravel().astype(np.int64)
+
+
+def exhaustive_max(cc, dev, fid, prm, Aa, Bb, rows=2048):
+    """Maximum of a measure over all pairs Aa x Bb (batches of rows x |Bb|)."""
+    import torch
+    best = -np.inf
+    for a0 in range(0, len(Aa), rows):
+        qa = torch.from_numpy(np.repeat(Aa[a0:a0 + rows], len(Bb)).astype(np.int32)).to(dev)
+        qb = torch.from_numpy(np.tile(Bb, min(rows, len(Aa) - a0)).astype(np.int32)).to(dev)
+        best = max(best, cc.segment_extremes(fid, prm, qa, qb, [0, qa.shape[0]])[0]["max"])
+    return best
+
+
+def ksg_recall(cc, dev, fid, cfg, rp_a, rp_b, bos_ksg, budget):
+    """Recall of the exhaustive KSG maximum (within 0.01) on 16 seeded
+    region pairs: batched BOS (its running KSG maxima) against uniform random
+    sampling with the same number of exact evaluations."""
+    import paper_2309_03308_gb300 as pg
+    from paper_2309_03308_gb300 import Params
+    prm = Params(pg.CC_MI_KSG, k=cfg["k"])
+    rng = np.random.default_rng(16)
+    cand = [i for i in range(len(rp_a)) if rp_a[i] != rp_b[i]]
+    pick = rng.choice(cand, 16, replace=False)
+    hit = hit_rand = 0
+    gap, gap_rand = [], []
+    t0 = time.perf_counter()
+    for i in pick:
+        Aa = region_points(cfg["X"], cfg["Y"], cc.region_info(rp_a[i])[1])
+        Bb = region_points(cfg["X"], cfg["Y"], cc.region_info(rp_b[i])[1])
+        ex = exhaustive_max(cc, dev, fid, prm, Aa, Bb)
+        qa, qb = cc.sample_pairs(rp_a[i], rp_b[i], 29, budget)
+        rnd = cc.segment_extremes(fid, prm, qa, qb, [0, budget])[0]["max"]
+        hit += bos_ksg[i]["max"] >= ex - 0.01
+        hit_rand += rnd >= ex - 0.01
+        gap.append(ex - bos_ksg[i]["max"])
+        gap_rand.append(ex - rnd)
+    return {"region_pairs": len(pick), "samples": budget, "recall_0.01": hit / len(pick),
+            "recall_0.01_random": hit_rand / len(pick), "gap_mean": float(np.mean(gap)),
+            "gap_mean_random": float(np.mean(gap_rand)), "exhaustive_s": time.perf_counter() - t0}
 
 
 def run_mean_tree_experiment(cc, fid, rids, rp_a, rp_b, kw):
