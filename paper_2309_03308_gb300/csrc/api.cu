@@ -780,6 +780,44 @@ namespace {
 // ones only by the epilogue's two fp32 scalings.
 bool rank_exact(bool sp, bool fp8, int n) { return sp && !fp8 && n <= 257; }
 
+// Replay the graph cached under `key`, or capture `enqueue` on the context's
+// stream into a new one (relaxed capture: the launchers may set function
+// attributes), keep it (at most 16 per cache, the oldest dropped) and launch
+// it. The library's launch counter counts the captured kernels once per run.
+template <class F>
+cudaError_t run_cached_graph(cc_ctx* ctx, std::vector<cc_ctx::CachedGraph>& cache,
+                             const std::vector<uint64_t>& key, F&& enqueue) {
+    cudaStream_t st = ctx->stream;
+    for (auto& g : cache)
+        if (g.key == key) {
+            note_launch(g.kernels);
+            return cudaGraphLaunch(g.exec, st);
+        }
+    const uint64_t before = g_launches.load();
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    const cudaError_t e_run = enqueue();
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    const int kernels = (int)(g_launches.load() - before);
+    g_launches.fetch_sub((uint64_t)kernels);
+    if (e_run != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return e_run != cudaSuccess ? e_run : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    if (cache.size() >= 16) {
+        cudaGraphExecDestroy(cache.front().exec);
+        cache.erase(cache.begin());
+    }
+    cache.push_back({key, exec, kernels});
+    note_launch(kernels);
+    return cudaGraphLaunch(exec, st);
+}
+
 cc_status ensure_qplane(cc_ctx* ctx, Region& r, bool sp, bool fp8, Region::QPlane** out) {
     Field& f = *ctx->fields[r.field];
     auto& slot = r.qplanes[(sp ? 2 : 0) + (fp8 ? 1 : 0)];
@@ -879,46 +917,71 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
     unsigned long long* tids = (unsigned long long*)(base + o_ti);
     SideOut* dout = (SideOut*)(base + o_out);
     cudaStream_t st = ctx->stream;
-    CK(cudaMemsetAsync(hist, 0, 4 * 4096, st));
     const bool exact = rank_exact(sp, fp8, fa.n);
-    CK(launch_tc_chunk_extremes(fp8, fp8 || exact, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad,
-                                qa->kbytes, self, qa->inv.as<float>(), qb->inv.as<float>(), cmax,
-                                cmin, ctx->status.as<int>(), st));
     const float* plane_a = sp ? fa.rhat.as<float>() : fa.zhat.as<float>();
     const float* plane_b = sp ? fb.rhat.as<float>() : fb.zhat.as<float>();
-    // relative error of the approximate values beyond the quantization error:
-    // FP32 accumulation (2^-12, conservative), or for exact integer ranks the
-    // two fp32 scalings of the epilogue (2^-22 covers them)
-    const float acc_rel = exact ? 1.f / 4194304.f : 1.f / 4096.f;
-    // Both passes are decided on the device (no host round trip): the second
-    // compaction appends the chunks in [r* - B, first threshold) after the
-    // first pass's, unless the first pass took every chunk or overflowed.
-    for (int side = 0; side < 2; ++side) {
-        const float sign = side == 0 ? 1.f : -1.f;
-        const float* v = side == 0 ? cmax : cmin;
-        CK(cudaMemsetAsync(sel, 0, sizeof(Select) * 2, st));
-        CK(cudaMemsetAsync(best, 0, 8, st));
-        const unsigned want = side == 0 ? (unsigned)std::max(topk, 256) : 256u;
-        CK(launch_select_top(v, N, sign, want, hist, sel, cids, cap, st));
-        CK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
-                                rb->pts.as<uint32_t>(), nb, self, na_pad, cids, nullptr,
-                                &sel->count, cap, sign, rvals, rpids, best, st));
-        CK(launch_second_threshold(best, qa->emax.as<unsigned>(), qb->emax.as<unsigned>(),
-                                   acc_rel, sel, thr, st));
-        CK(launch_compact_second(v, N, sign, thr, sel, cids, cap, st));
-        CK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
-                                rb->pts.as<uint32_t>(), nb, self, na_pad, cids, &sel->pass1,
-                                &sel->count, cap, sign, rvals, rpids, best, st));
-        if (side == 0 && topk > 0) {  // top-K of every refined value
-            CK(launch_select_top(rvals, (int64_t)cap * 32, 1.f, (unsigned)topk, hist, sel + 1,
-                                 sidx, 8192, st, &sel->count));
-            CK(launch_sort_top(rvals, rpids, sidx, &sel[1].count, 8192, 1.f, topk, tvals, tids,
-                               (unsigned long long*)(base + o_sk), st));
+    // The device work below is ~30 small launches; it is captured once into a
+    // CUDA graph per distinct set of buffers and sizes and replayed, so the
+    // GPU runs the launches back to back instead of waiting on the host.
+    // Every pointer and scalar the launches take is part of the key, so a
+    // replay does exactly what a fresh enqueue would.
+    const std::vector<uint64_t> key = {
+        (uint64_t)(uintptr_t)qa->q.p, (uint64_t)(uintptr_t)qb->q.p,
+        (uint64_t)(uintptr_t)qa->inv.p, (uint64_t)(uintptr_t)qb->inv.p,
+        (uint64_t)(uintptr_t)qa->emax.p, (uint64_t)(uintptr_t)qb->emax.p,
+        (uint64_t)(uintptr_t)plane_a, (uint64_t)(uintptr_t)plane_b,
+        (uint64_t)(uintptr_t)ra->pts.p, (uint64_t)(uintptr_t)rb->pts.p,
+        (uint64_t)(uintptr_t)base, (uint64_t)(uintptr_t)ctx->status.p, (uint64_t)(uintptr_t)st,
+        (uint64_t)na, (uint64_t)nb, (uint64_t)na_pad, (uint64_t)nb_pad, (uint64_t)qa->kbytes,
+        (uint64_t)fa.n, (uint64_t)fa.n_pad, (uint64_t)self, (uint64_t)fp8, (uint64_t)exact,
+        (uint64_t)topk};
+#define EK(call)                                \
+    do {                                        \
+        const cudaError_t _e = (call);          \
+        if (_e != cudaSuccess) return _e;       \
+    } while (0)
+    auto enqueue = [&]() -> cudaError_t {
+        EK(cudaMemsetAsync(hist, 0, 4 * 4096, st));
+        EK(launch_tc_chunk_extremes(fp8, fp8 || exact, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad,
+                                    qa->kbytes, self, qa->inv.as<float>(), qb->inv.as<float>(), cmax,
+                                    cmin, ctx->status.as<int>(), st));
+        // relative error of the approximate values beyond the quantization error:
+        // FP32 accumulation (2^-12, conservative), or for exact integer ranks the
+        // two fp32 scalings of the epilogue (2^-22 covers them)
+        const float acc_rel = exact ? 1.f / 4194304.f : 1.f / 4096.f;
+        // Both passes are decided on the device (no host round trip): the second
+        // compaction appends the chunks in [r* - B, first threshold) after the
+        // first pass's, unless the first pass took every chunk or overflowed.
+        for (int side = 0; side < 2; ++side) {
+            const float sign = side == 0 ? 1.f : -1.f;
+            const float* v = side == 0 ? cmax : cmin;
+            EK(cudaMemsetAsync(sel, 0, sizeof(Select) * 2, st));
+            EK(cudaMemsetAsync(best, 0, 8, st));
+            const unsigned want = side == 0 ? (unsigned)std::max(topk, 256) : 256u;
+            EK(launch_select_top(v, N, sign, want, hist, sel, cids, cap, st));
+            EK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
+                                    rb->pts.as<uint32_t>(), nb, self, na_pad, cids, nullptr,
+                                    &sel->count, cap, sign, rvals, rpids, best, st));
+            EK(launch_second_threshold(best, qa->emax.as<unsigned>(), qb->emax.as<unsigned>(),
+                                       acc_rel, sel, thr, st));
+            EK(launch_compact_second(v, N, sign, thr, sel, cids, cap, st));
+            EK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
+                                    rb->pts.as<uint32_t>(), nb, self, na_pad, cids, &sel->pass1,
+                                    &sel->count, cap, sign, rvals, rpids, best, st));
+            if (side == 0 && topk > 0) {  // top-K of every refined value
+                EK(launch_select_top(rvals, (int64_t)cap * 32, 1.f, (unsigned)topk, hist, sel + 1,
+                                     sidx, 8192, st, &sel->count));
+                EK(launch_sort_top(rvals, rpids, sidx, &sel[1].count, 8192, 1.f, topk, tvals, tids,
+                                   (unsigned long long*)(base + o_sk), st));
+            }
+            EK(cudaMemcpyAsync(&dout[side].sel, sel, sizeof(Select), cudaMemcpyDeviceToDevice, st));
+            EK(cudaMemcpyAsync(&dout[side].best, best, 8, cudaMemcpyDeviceToDevice, st));
+            EK(cudaMemcpyAsync(dout[side].thr, thr, 8, cudaMemcpyDeviceToDevice, st));
         }
-        CK(cudaMemcpyAsync(&dout[side].sel, sel, sizeof(Select), cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(&dout[side].best, best, 8, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(dout[side].thr, thr, 8, cudaMemcpyDeviceToDevice, st));
-    }
+        return cudaSuccess;
+    };
+#undef EK
+    CK(run_cached_graph(ctx, ctx->topk_graphs, key, enqueue));
     SideOut hout[2];
     CK(cudaMemcpyAsync(hout, dout, sizeof hout, cudaMemcpyDeviceToHost, st));
     if (topk > 0) {

@@ -114,7 +114,16 @@ struct cc_ctx {
     // and one event per chunk (created on first use)
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> copy_events;
+    // captured launch sequences of cc_all_pairs_topk, keyed by every buffer
+    // address and size they use
+    struct CachedGraph {
+        std::vector<uint64_t> key;
+        cudaGraphExec_t exec;
+        int kernels;
+    };
+    std::vector<CachedGraph> topk_graphs;
     ~cc_ctx() {
+        for (auto& g : topk_graphs) cudaGraphExecDestroy(g.exec);
         for (cudaEvent_t e : copy_events) cudaEventDestroy(e);
         if (copy_stream) cudaStreamDestroy(copy_stream);
     }
