@@ -36,6 +36,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -93,7 +94,9 @@ class Clocks:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_dev{device}.csv")
+        # raw samples beside the run (CCORR_CLOCKS_DIR, else the system temp dir)
+        self.path = os.path.join(os.environ.get("CCORR_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"ccorr_clocks_dev{device}.csv")
 
     def __enter__(self):
         try:

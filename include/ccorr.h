@@ -453,7 +453,7 @@ cc_status cc_bos_destroy(cc_ctx* ctx, cc_bos* bos);
  * A small pairwise network that predicts a measure (e.g. KSG MI) from two
  * points' member vectors, the network the paper's Section 7 proposes as
  * future work. Used as the BOS prior mean (cc_bos_set_prior) and to screen all
- * pairs of a region pair; exact evaluation stays the judge of every maximum.
+ * pairs of a region pair; every reported maximum comes from exact evaluation.
  *   encoder  z (n) -> h1 = GELU(W1 z + b1) (128) -> e = W2 h1 + b2 (64)
  *   head     x = [e_i, e_j, |e_i - e_j|, off] (195) -> h3 = GELU(W3 x + b3)
  *            (128) -> y = w4 . h3 + b4, prediction = y * sd + mean
