@@ -182,36 +182,56 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int64_t row = m0 + 32 * q + lane;
             const bool row_ok = row < na;
             const float rs = SCALED ? (row_ok ? inv_sa[row] : 0.f) : 1.f;
+            // two 32-column chunks per TMEM round trip (both loads in flight,
+            // one wait). With scales, a value is (acc x col scale) x row scale;
+            // the row scale is positive and rounding is monotone, so it is
+            // applied to the chunk's extremes instead of every value.
 #pragma unroll 1
-            for (int c = 0; c < TN / 32; ++c) {
-                float v[32];
-                tmem_ld32(tmem + (uint32_t)(acc * TN + c * 32) + ((uint32_t)(32 * q) << 16), v);
-                const int64_t col0 = n0 + c * 32;
-                if (SCALED) {
+            for (int c2 = 0; c2 < TN / 32; c2 += 2) {
+                uint32_t r[2][32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = v[j] * rs * colscale[c * 32 + j];
-                }
-                float mx = -CUDART_INF_F, mn = CUDART_INF_F;
-                if (row_ok && col0 + 31 < nb && (!self || col0 > row)) {
-                    // every pair of the chunk counts: no per-value checks
+                for (int h = 0; h < 2; ++h)
+                    tmem_ld32_issue(tmem + (uint32_t)(acc * TN + (c2 + h) * 32) +
+                                        ((uint32_t)(32 * q) << 16),
+                                    r[h]);
+                tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        mx = fmaxf(mx, fmaxf(v[j], v[j + 1]));
-                        mn = fminf(mn, fminf(v[j], v[j + 1]));
+                for (int h = 0; h < 2; ++h) {
+                    const int c = c2 + h;
+                    float v[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[h][j]);
+                    const int64_t col0 = n0 + c * 32;
+                    if (SCALED) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = v[j] * colscale[c * 32 + j];
                     }
-                } else {
+                    float mx = -CUDART_INF_F, mn = CUDART_INF_F;
+                    if (row_ok && col0 + 31 < nb && (!self || col0 > row)) {
+                        // every pair of the chunk counts: no per-value checks
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t col = col0 + j;
-                        const bool ok = row_ok && col < nb && (!self || col > row);
-                        mx = ok ? fmaxf(mx, v[j]) : mx;
-                        mn = ok ? fminf(mn, v[j]) : mn;
+                        for (int j = 0; j < 32; j += 2) {
+                            mx = fmaxf(mx, fmaxf(v[j], v[j + 1]));
+                            mn = fminf(mn, fminf(v[j], v[j + 1]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int64_t col = col0 + j;
+                            const bool ok = row_ok && col < nb && (!self || col > row);
+                            mx = ok ? fmaxf(mx, v[j]) : mx;
+                            mn = ok ? fminf(mn, v[j]) : mn;
+                        }
                     }
-                }
-                const int64_t chunk = (n0 >> 5) + c;
-                if (row < na_pad) {
-                    cmax[chunk * na_pad + row] = mx;
-                    cmin[chunk * na_pad + row] = mn;
+                    if (SCALED) {  // +-inf (no pair of the chunk counts) stays as it is
+                        if (mx > -CUDART_INF_F) mx = mx * rs;
+                        if (mn < CUDART_INF_F) mn = mn * rs;
+                    }
+                    const int64_t chunk = (n0 >> 5) + c;
+                    if (row < na_pad) {
+                        cmax[chunk * na_pad + row] = mx;
+                        cmin[chunk * na_pad + row] = mn;
+                    }
                 }
             }
             tc_fence_before();
