@@ -165,15 +165,30 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else {
         const int q = warp & 3;  // TMEM lane quadrant this warp may access
         const int et = (warp - 2) * 32 + lane;
+        // column scales, double-buffered: the next tile's are loaded while
+        // this tile is reduced and stored before the tile's closing barrier
+        auto col_scales = [&](int t, float (&out)[TN / 128]) {
+            const int n0 = (t % tiles_n) * TN;
+#pragma unroll
+            for (int u = 0; u < TN / 128; ++u) {
+                const int c = et + 128 * u;
+                out[u] = t < tiles && n0 + c < nb ? inv_sb[n0 + c] : 0.f;
+            }
+        };
+        if (SCALED) {
+            float cs[TN / 128];
+            col_scales(blockIdx.x, cs);
+#pragma unroll
+            for (int u = 0; u < TN / 128; ++u) colscale[et + 128 * u] = cs[u];
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
         int tc = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
             const int acc = tc & 1;
             const int m0 = (t / tiles_n) * TM, n0 = (t % tiles_n) * TN;
-            if (SCALED) {
-                for (int c = et; c < TN; c += 128)
-                    colscale[c] = n0 + c < nb ? inv_sb[n0 + c] : 0.f;
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-            }
+            const float* cscale = colscale + (tc & 1) * TN;
+            float cs_next[TN / 128];
+            if (SCALED) col_scales(t + gridDim.x, cs_next);
             if (!mbar_wait(&tfull[acc], (tc >> 1) & 1, abort_flag)) {
                 fail();
                 break;
@@ -204,7 +219,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const int64_t col0 = n0 + c * 32;
                     if (SCALED) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = v[j] * colscale[c * 32 + j];
+                        for (int j = 0; j < 32; ++j) v[j] = v[j] * cscale[c * 32 + j];
                     }
                     float mx = -CUDART_INF_F, mn = CUDART_INF_F;
                     if (row_ok && col0 + 31 < nb && (!self || col0 > row)) {
@@ -237,7 +252,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
-            if (SCALED) asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (SCALED) {  // the other buffer was last read in the previous tile
+                float* nxt = colscale + ((tc + 1) & 1) * TN;
+#pragma unroll
+                for (int u = 0; u < TN / 128; ++u) nxt[et + 128 * u] = cs_next[u];
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
         }
     }
     tc_fence_before();
@@ -249,7 +269,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-constexpr size_t smem_bytes() { return 1024 + STAGES * STAGE_BYTES + 256 + 16 + TN * 4; }
+constexpr size_t smem_bytes() { return 1024 + STAGES * STAGE_BYTES + 256 + 16 + 2 * TN * 4; }
 
 }  // namespace tc
 
