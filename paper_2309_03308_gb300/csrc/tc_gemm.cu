@@ -7,15 +7,17 @@
 // (value * 448 / max|value|), loaded by TMA with 128-byte swizzle into a
 // 4-stage shared-memory ring. One elected thread issues tcgen05.mma
 // (M = 128, N = 256, FP32 accumulation in TMEM, two accumulator buffers so the
-// epilogue of one tile overlaps the MMAs of the next). Four epilogue warps
+// epilogue of one tile overlaps the MMAs of the next). Eight epilogue warps
 // read TMEM with tcgen05.ld and emit, per output row and 32-column chunk, the
 // max and min of the approximate correlations (FP8, and BF16 integer ranks:
-// rescaled by the two per-point inverse scales). No per-pair value is stored: the chunk extremes
-// select the candidates that are re-evaluated exactly afterwards.
+// rescaled by the two per-point inverse scales). No per-pair value is stored:
+// the chunk extremes select the candidates that are re-evaluated exactly
+// afterwards.
 //
-// Warp roles (192 threads, one CTA per SM, persistent over tiles):
+// Warp roles (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0  TMA producer        warp 1  TMEM allocation + MMA issuer
-//   warps 2-5  epilogue (warp w reads TMEM lanes 32*(w%4) .. +31)
+//   warps 2-9  epilogue (warp w reads TMEM lanes 32*(w%4) .. +31, warps 2-5
+//              the tile's first 128 columns, warps 6-9 the last 128)
 // Every mbarrier wait is bounded (wall clock); on timeout the CTA records
 // DEV_TIMEOUT, the other roles leave their loops, in-flight copies and MMAs
 // are drained with bounded waits, and TMEM is freed before returning.
@@ -30,7 +32,8 @@ namespace tc {
 
 constexpr int TM = 128, TN = 256, STAGES = 4;
 constexpr int A_BYTES = TM * 128, B_BYTES = TN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int THREADS = 192;
+constexpr int THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
+constexpr int EPI = 256;      // epilogue threads
 constexpr int TMEM_COLS = 512;  // two 256-column fp32 accumulators
 
 // Instruction descriptor: FP32 accumulator, A/B BF16 (kind::f16) or E4M3
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 4);
+            mbar_init(&tempty[a], EPI / 32);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -163,31 +166,34 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_wait(drain, 0, nullptr);
         }
     } else {
-        const int q = warp & 3;  // TMEM lane quadrant this warp may access
+        // two warps per TMEM lane quadrant (a warp may access the quadrant
+        // warp % 4), each reducing half of the tile's columns
+        const int q = warp & 3;
         const int et = (warp - 2) * 32 + lane;
+        const int half = (warp - 2) >> 2;
         // column scales, double-buffered: the next tile's are loaded while
         // this tile is reduced and stored before the tile's closing barrier
-        auto col_scales = [&](int t, float (&out)[TN / 128]) {
+        auto col_scales = [&](int t, float (&out)[TN / EPI]) {
             const int n0 = (t % tiles_n) * TN;
 #pragma unroll
-            for (int u = 0; u < TN / 128; ++u) {
-                const int c = et + 128 * u;
+            for (int u = 0; u < TN / EPI; ++u) {
+                const int c = et + EPI * u;
                 out[u] = t < tiles && n0 + c < nb ? inv_sb[n0 + c] : 0.f;
             }
         };
         if (SCALED) {
-            float cs[TN / 128];
+            float cs[TN / EPI];
             col_scales(blockIdx.x, cs);
 #pragma unroll
-            for (int u = 0; u < TN / 128; ++u) colscale[et + 128 * u] = cs[u];
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            for (int u = 0; u < TN / EPI; ++u) colscale[et + EPI * u] = cs[u];
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI) : "memory");
         }
         int tc = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
             const int acc = tc & 1;
             const int m0 = (t / tiles_n) * TM, n0 = (t % tiles_n) * TN;
             const float* cscale = colscale + (tc & 1) * TN;
-            float cs_next[TN / 128];
+            float cs_next[TN / EPI];
             if (SCALED) col_scales(t + gridDim.x, cs_next);
             if (!mbar_wait(&tfull[acc], (tc >> 1) & 1, abort_flag)) {
                 fail();
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // the row scale is positive and rounding is monotone, so it is
             // applied to the chunk's extremes instead of every value.
 #pragma unroll 1
-            for (int c2 = 0; c2 < TN / 32; c2 += 2) {
+            for (int c2 = half * (TN / 64); c2 < (half + 1) * (TN / 64); c2 += 2) {
                 uint32_t r[2][32];
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
@@ -255,8 +261,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (SCALED) {  // the other buffer was last read in the previous tile
                 float* nxt = colscale + ((tc + 1) & 1) * TN;
 #pragma unroll
-                for (int u = 0; u < TN / 128; ++u) nxt[et + 128 * u] = cs_next[u];
-                asm volatile("bar.sync 1, 128;" ::: "memory");
+                for (int u = 0; u < TN / EPI; ++u) nxt[et + EPI * u] = cs_next[u];
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI) : "memory");
             }
         }
     }
