@@ -197,6 +197,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (SCALED) col_scales(t + gridDim.x, cs_next);
             if (!mbar_wait(&tfull[acc], (tc >> 1) & 1, abort_flag)) {
                 fail();
+                // epilogue warps whose wait for this tile succeeded meet at the
+                // tile's closing barrier: arrive there without waiting, so they
+                // pass it and then stop at the next wait (the abort flag is set)
+                if (SCALED) asm volatile("bar.arrive 1, %0;" ::"n"(EPI) : "memory");
                 break;
             }
             tc_fence_after();
