@@ -216,17 +216,31 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
             rowbuf[e] = t < s ? Vr[(int64_t)t * Q + SL[i]] : 0.f;
         }
         __syncthreads();
-        for (int t = 0; t < 16; ++t) {
-            float a[8], b[8];
+        if (per == 8) {  // shortlist of 128: the operands are two aligned float4 each
+            for (int t = 0; t < 16; ++t) {
+                const float4* ra = reinterpret_cast<const float4*>(rowbuf + t * M + ti * 8);
+                const float4* rb = reinterpret_cast<const float4*>(rowbuf + t * M + tj * 8);
+                const float4 a0 = ra[0], a1 = ra[1], b0 = rb[0], b1 = rb[1];
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                a[i] = i < per ? rowbuf[t * M + ti * per + i] : 0.f;
-                b[i] = i < per ? rowbuf[t * M + tj * per + i] : 0.f;
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
             }
+        } else {
+            for (int t = 0; t < 16; ++t) {
+                float a[8], b[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 8; ++i) {
+                    a[i] = i < per ? rowbuf[t * M + ti * per + i] : 0.f;
+                    b[i] = i < per ? rowbuf[t * M + tj * per + i] : 0.f;
+                }
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
         }
         __syncthreads();
     }
