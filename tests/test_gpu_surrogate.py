@@ -86,6 +86,13 @@ def test_training_and_screen(env, orc):
     allp = sur.predict(fid, np.repeat(A, len(B)), np.tile(B, len(A)))
     kth = np.sort(allp)[::-1][199]
     assert preds[-1] >= kth - 5e-2 * scale
+    # the tensor-core screen's values against the FP64 forward pass of the
+    # trained parameters (BF16 operands: a few per cent of the target spread)
+    w, m, sd = sur.params()
+    pa_s, pb_s = A[a].astype(np.uint32), B[b].astype(np.uint32)
+    ref_y, _ = mlp.forward(w.astype(np.float64), mlp.zscore(F, pa_s), mlp.zscore(F, pb_s),
+                           mlp.offsets(X, Y, Z, pa_s, pb_s), N)
+    assert np.abs(preds - (ref_y * sd + m)).max() < 5e-2 * scale
     sur.close()
 
 
