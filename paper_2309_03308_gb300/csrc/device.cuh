@@ -65,6 +65,18 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
     return v;
 }
 
+// Warp sum of non-negative 64-bit values below 2^58 (each lane's value):
+// three 32-bit reductions (redux.sync) of the high word and the two 16-bit
+// halves of the low word, none of which can overflow over 32 lanes. Every
+// lane receives the sum.
+__device__ __forceinline__ long long warp_sum_u64_redux(long long v) {
+    const unsigned long long u = (unsigned long long)v;
+    const unsigned hi = __reduce_add_sync(0xffffffffu, (unsigned)(u >> 32));
+    const unsigned mid = __reduce_add_sync(0xffffffffu, (unsigned)(u >> 16) & 0xffffu);
+    const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)u & 0xffffu);
+    return (long long)(((unsigned long long)hi << 32) + ((unsigned long long)mid << 16) + lo);
+}
+
 __device__ __forceinline__ float warp_sum_f32(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         } else {
             s = hist_slices(ba, bb, n, B, h, clogc, lane);
         }
-        s = warp_sum_i64(s);
+        s = warp_sum_u64_redux(s);  // c ln c >= 0: the fixed-point sums are non-negative
         if (lane == 0) {
             const long long d = s - hm_a[p] - hm_b[q];
             out[t] = (float)(logn + (double)d * fix_over_n);
