@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
             }
             __syncwarp();
             long long sm = lane < B ? pb.clogc[hh[lane]] : 0;
-            sm = warp_sum_i64(sm);
+            sm = warp_sum_u64_redux(sm);  // c ln c >= 0
             if (lane == 0) hmarg[p] = sm;
             __syncwarp();
         };
@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
             c2 += c * c;
         }
     }
-    c2 = warp_sum_i64(c2);
+    // each c^2 <= n^2 <= 2^20 and n <= 1024 values: the sum fits 32 bits
+    c2 = (long long)__reduce_add_sync(0xffffffffu, (unsigned)c2);
     // FP64 finalisation, one instruction stream for both norms: lane 0 the
     // sum of squared deviations, lane 1 the sum of squared centred ranks
     const double ss_s = (double)ss_h + (double)ss_l;  // in units of (vscale dscale)^2
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(128)
     }
     __syncwarp();
     long long s = lane < B ? clogc_fix[hist[warp][lane]] : 0;
-    s = warp_sum_i64(s);
+    s = warp_sum_u64_redux(s);  // c ln c >= 0
     if (lane == 0) hmarg[p] = s;
 }
 
