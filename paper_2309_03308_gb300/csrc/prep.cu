@@ -94,10 +94,9 @@ __device__ __forceinline__ float unorder_bits(unsigned o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
+// warp maximum of non-negative floats: their bit patterns order as integers
 __device__ __forceinline__ float warp_max_f32(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
 }
 
 // power of two s with m * s in [1, 2) for finite normal m > 0 (1 for m == 0)
