@@ -46,10 +46,14 @@ namespace cc {
 double digamma_int_host(int m);
 
 constexpr int kKsgWarps = 4;
+// The pair-batch form holds one staged pair per warp in shared memory; for
+// large n the slot, not the register file, limits the warps an SM can run,
+// so a block takes as many warps as leave room for two blocks per SM.
+constexpr int kMaxPairWarps = 16;
 constexpr int kMaxGroup = 4;
 
 template <int KMAX>
-__global__ void __launch_bounds__(kKsgWarps * 32)
+__global__ void __launch_bounds__(kMaxPairWarps * 32)
     k_ksg_pairs(const float* __restrict__ sorted_a, const uint16_t* __restrict__ perm_a,
                 const float* __restrict__ vals_a, int64_t Pa, const float* __restrict__ sorted_b,
                 const uint16_t* __restrict__ perm_b, const float* __restrict__ vals_b, int64_t Pb,
@@ -68,8 +72,9 @@ __global__ void __launch_bounds__(kKsgWarps * 32)
     __syncthreads();
 
     const int64_t ngroups = (N + G - 1) / G;
-    for (int64_t g = (int64_t)blockIdx.x * kKsgWarps + warp; g < ngroups;
-         g += (int64_t)gridDim.x * kKsgWarps) {
+    const int warps = blockDim.x >> 5;
+    for (int64_t g = (int64_t)blockIdx.x * warps + warp; g < ngroups;
+         g += (int64_t)gridDim.x * warps) {
         const int64_t t0 = g * G;
         const int gc = (int)min((int64_t)G, N - t0);
         unsigned valid = 0;
@@ -226,17 +231,29 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
     // (more pairs per warp costs occupancy through shared memory)
     const int G = fa.n_pad <= 128 ? 2 : 1;
     const int psi_len = (fa.n + 2) & ~1;
-    const size_t smem =
-        psi_len * sizeof(long long) + kKsgWarps * G * ksg_slot_bytes(fa.n_pad, KMAX);
+    int dev = 0, sms = 148, smem_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // pair-batch form: as many warps per block as leave room for two blocks
+    // per SM (1 KB per block is reserved by the runtime)
+    const size_t slot = (size_t)G * ksg_slot_bytes(fa.n_pad, KMAX);
+    const size_t psi_b = psi_len * sizeof(long long);
+    int pw = (int)(((size_t)smem_sm / 2 - 1024 - psi_b) / slot);
+    static const int regs = [] {  // and two blocks' registers
+        cudaFuncAttributes fa_attr{};
+        return cudaFuncGetAttributes(&fa_attr, k_ksg_pairs<KMAX>) == cudaSuccess
+                   ? fa_attr.numRegs : 64;
+    }();
+    pw = std::min(pw, 65536 / (2 * 32 * std::max(regs, 1)));
+    pw = pw < 1 ? 1 : (pw > kMaxPairWarps ? kMaxPairWarps : pw);
+    const size_t smem = psi_b + (size_t)pw * slot;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_ksg_pairs<KMAX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (fa.n >= 32 && fa.n_pad <= 256) {  // sample stream, two slots per warp
         const size_t smem2 =
             psi_len * sizeof(long long) + kKsgWarps * 2 * ksg_slot_bytes(fa.n_pad, KMAX);
@@ -259,10 +276,10 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
         return cudaGetLastError();
     }
     const int64_t groups = (N + G - 1) / G;
-    int64_t blocks = (groups + kKsgWarps - 1) / kKsgWarps;
+    int64_t blocks = (groups + pw - 1) / pw;
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
     note_launch();
-    k_ksg_pairs<KMAX><<<(unsigned)blocks, kKsgWarps * 32, smem, st>>>(
+    k_ksg_pairs<KMAX><<<(unsigned)blocks, pw * 32, smem, st>>>(
         fa.sorted.as<float>(), fa.perm.as<uint16_t>(), fa.vals.as<float>(), fa.P,
         fb.sorted.as<float>(), fb.perm.as<uint16_t>(), fb.vals.as<float>(), fb.P, fa.n, fa.n_pad,
         k, G, (const long long*)psi_fix, psi_nk, 1.0 / (kFixScale * fa.n), pa, pb, N, out, nx, ny,
