@@ -57,31 +57,40 @@ __global__ void __launch_bounds__(kMaxPairWarps * 32)
     k_ksg_pairs(const float* __restrict__ sorted_a, const uint16_t* __restrict__ perm_a,
                 const float* __restrict__ vals_a, int64_t Pa, const float* __restrict__ sorted_b,
                 const uint16_t* __restrict__ perm_b, const float* __restrict__ vals_b, int64_t Pb,
-                int n, int n_pad, int k, int G, const long long* __restrict__ psi_fix,
+                int n, int n_pad, int k, int G, int team, const long long* __restrict__ psi_fix,
                 double psi_nk, double fix_over_n, const uint32_t* __restrict__ pa,
                 const uint32_t* __restrict__ pb, int64_t N, float* __restrict__ out,
                 int32_t* __restrict__ nx_out,
                 int32_t* __restrict__ ny_out, float* __restrict__ eps_out, int* status) {
     extern __shared__ __align__(16) unsigned char ksg_smem[];
+    __shared__ long long team_part[kMaxPairWarps][kMaxGroup];
     long long* psi = reinterpret_cast<long long*>(ksg_smem);
     const int psi_len = (n + 2) & ~1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // `team` consecutive warps share one staged group of pairs and split its
+    // samples; the first warp of a team stages and writes the results
+    const int team_id = warp / team, tw = warp % team, tl = tw * 32 + lane;
+    const int teams = (blockDim.x >> 5) / team;
     const size_t slot_bytes = ksg_slot_bytes(n_pad, KMAX);
-    unsigned char* wbase = ksg_smem + psi_len * sizeof(long long) + (size_t)warp * G * slot_bytes;
+    unsigned char* wbase =
+        ksg_smem + psi_len * sizeof(long long) + (size_t)team_id * G * slot_bytes;
+    auto team_sync = [&]() {
+        if (team == 1) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(1 + team_id), "r"(team * 32) : "memory");
+    };
     for (int i = threadIdx.x; i <= n; i += blockDim.x) psi[i] = psi_fix[i];
     __syncthreads();
 
     const int64_t ngroups = (N + G - 1) / G;
-    const int warps = blockDim.x >> 5;
-    for (int64_t g = (int64_t)blockIdx.x * warps + warp; g < ngroups;
-         g += (int64_t)gridDim.x * warps) {
+    for (int64_t g = (int64_t)blockIdx.x * teams + team_id; g < ngroups;
+         g += (int64_t)gridDim.x * teams) {
         const int64_t t0 = g * G;
         const int gc = (int)min((int64_t)G, N - t0);
         unsigned valid = 0;
         for (int sl = 0; sl < gc; ++sl) {
             const uint32_t p = pa[t0 + sl], q = pb[t0 + sl];
             if (p >= Pa || q >= Pb) {
-                if (lane == 0) {
+                if (tl == 0) {
                     out[t0 + sl] = CUDART_NAN_F;
                     set_status(status, DEV_BAD_INDEX);
                 }
@@ -89,15 +98,17 @@ __global__ void __launch_bounds__(kMaxPairWarps * 32)
             }
             valid |= 1u << sl;
             const int64_t ra = (int64_t)p * n_pad, rb = (int64_t)q * n_pad;
-            ksg_stage<KMAX>(wbase + sl * slot_bytes, n, n_pad, sorted_a + ra, perm_a + ra,
-                            vals_a + ra, sorted_b + rb, perm_b + rb, vals_b + rb);
+            if (tw == 0)
+                ksg_stage<KMAX>(wbase + sl * slot_bytes, n, n_pad, sorted_a + ra, perm_a + ra,
+                                vals_a + ra, sorted_b + rb, perm_b + rb, vals_b + rb);
         }
+        team_sync();  // the staged slots are visible to the whole team
 
         long long acc[kMaxGroup];
 #pragma unroll
         for (int u = 0; u < kMaxGroup; ++u) acc[u] = 0;
         const int items = gc * n;
-        for (int it = lane; it < items; it += 32) {
+        for (int it = tl; it < items; it += team * 32) {
             const int sl = it / n, ti = it - sl * n;
             if (!((valid >> sl) & 1u)) continue;
             int cx, cy;
@@ -119,11 +130,20 @@ __global__ void __launch_bounds__(kMaxPairWarps * 32)
         for (int u = 0; u < kMaxGroup; ++u) {
             if (u < gc) {
                 const long long sum = warp_sum_i64(acc[u]);
-                if (lane == 0 && ((valid >> u) & 1u))
-                    out[t0 + u] = (float)(psi_nk - (double)sum * fix_over_n);
+                if (lane == 0) team_part[warp][u] = sum;
             }
         }
-        __syncwarp();
+        // every warp of the team is done with the slots and its part is stored
+        team_sync();
+        if (tw == 0 && lane == 0) {
+            for (int u = 0; u < gc; ++u) {
+                long long sum = 0;
+                for (int w = 0; w < team; ++w) sum += team_part[warp + w][u];
+                if ((valid >> u) & 1u) out[t0 + u] = (float)(psi_nk - (double)sum * fix_over_n);
+            }
+        }
+        // the parts are read before the team's next group overwrites them
+        team_sync();
     }
 }
 
@@ -230,6 +250,9 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
     // two pairs per warp while n is small, so the sample stream fills the lanes
     // (more pairs per warp costs occupancy through shared memory)
     const int G = fa.n_pad <= 128 ? 2 : 1;
+    // for large n two warps share one staged pair, which halves the shared
+    // memory per warp (the slot, not the register file, limits the warps)
+    const int team = fa.n_pad >= 512 ? 2 : 1;
     const int psi_len = (fa.n + 2) & ~1;
     int dev = 0, sms = 148, smem_sm = 0;
     cudaGetDevice(&dev);
@@ -239,15 +262,18 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
     // per SM (1 KB per block is reserved by the runtime)
     const size_t slot = (size_t)G * ksg_slot_bytes(fa.n_pad, KMAX);
     const size_t psi_b = psi_len * sizeof(long long);
-    int pw = (int)(((size_t)smem_sm / 2 - 1024 - psi_b) / slot);
+    const size_t smem_free = (size_t)smem_sm / 2 - 1024 - psi_b -
+                             sizeof(long long) * kMaxPairWarps * kMaxGroup;
+    int pw = team * (int)(smem_free / slot);
     static const int regs = [] {  // and two blocks' registers
         cudaFuncAttributes fa_attr{};
         return cudaFuncGetAttributes(&fa_attr, k_ksg_pairs<KMAX>) == cudaSuccess
                    ? fa_attr.numRegs : 64;
     }();
     pw = std::min(pw, 65536 / (2 * 32 * std::max(regs, 1)));
-    pw = pw < 1 ? 1 : (pw > kMaxPairWarps ? kMaxPairWarps : pw);
-    const size_t smem = psi_b + (size_t)pw * slot;
+    pw = pw < team ? team : (pw > kMaxPairWarps ? kMaxPairWarps : pw);
+    pw -= pw % team;
+    const size_t smem = psi_b + (size_t)(pw / team) * slot;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_ksg_pairs<KMAX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -276,14 +302,14 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
         return cudaGetLastError();
     }
     const int64_t groups = (N + G - 1) / G;
-    int64_t blocks = (groups + pw - 1) / pw;
+    int64_t blocks = (groups + pw / team - 1) / (pw / team);
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
     note_launch();
     k_ksg_pairs<KMAX><<<(unsigned)blocks, pw * 32, smem, st>>>(
         fa.sorted.as<float>(), fa.perm.as<uint16_t>(), fa.vals.as<float>(), fa.P,
         fb.sorted.as<float>(), fb.perm.as<uint16_t>(), fb.vals.as<float>(), fb.P, fa.n, fa.n_pad,
-        k, G, (const long long*)psi_fix, psi_nk, 1.0 / (kFixScale * fa.n), pa, pb, N, out, nx, ny,
-        eps, status);
+        k, G, team, (const long long*)psi_fix, psi_nk, 1.0 / (kFixScale * fa.n), pa, pb, N, out,
+        nx, ny, eps, status);
     return cudaGetLastError();
 }
 
