@@ -250,9 +250,10 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
     // two pairs per warp while n is small, so the sample stream fills the lanes
     // (more pairs per warp costs occupancy through shared memory)
     const int G = fa.n_pad <= 128 ? 2 : 1;
-    // for large n two warps share one staged pair, which halves the shared
-    // memory per warp (the slot, not the register file, limits the warps)
-    const int team = fa.n_pad >= 512 ? 2 : 1;
+    // for large n two (n_pad 512) or four (n_pad 1024) warps share one staged
+    // pair, which divides the shared memory per warp (the slot, not the
+    // register file, limits the warps)
+    const int team = fa.n_pad >= 1024 ? 4 : (fa.n_pad >= 512 ? 2 : 1);
     const int psi_len = (fa.n + 2) & ~1;
     int dev = 0, sms = 148, smem_sm = 0;
     cudaGetDevice(&dev);
