@@ -48,7 +48,7 @@ typedef int32_t cc_status;
 #define CC_ERR_CUDA (-3)         /* a CUDA call failed (message has the CUDA error) */
 #define CC_ERR_NONFINITE (-4)    /* NaN or Inf in a loaded field */
 #define CC_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up */
-#define CC_ERR_UNSUPPORTED (-6)  /* valid request this build or device cannot run */
+#define CC_ERR_UNSUPPORTED (-6)  /* valid request the library or device cannot run */
 
 /* Measures (Section 3.2; Spearman is a project addition). */
 #define CC_PEARSON 0   /* PPMCC of the member vectors */
