@@ -279,7 +279,8 @@ extern "C" cc_status cc_all_pairs_static(const float* za, int64_t lda, const flo
         return CC_ERR_INVALID_ARG;
     if (self && (za != zb || na != nb || lda != ldb)) return CC_ERR_INVALID_ARG;
     if (values && ldv < nb) return CC_ERR_INVALID_ARG;
-    if (ta * tb > kStaticTiles || ta > 65535) return CC_ERR_INVALID_ARG;  // beyond the static scratch
+    // beyond the static scratch (each factor is bounded before the product is formed)
+    if (ta > 65535 || tb > kStaticTiles || ta * tb > kStaticTiles) return CC_ERR_INVALID_ARG;
     cc::Partial* parts = nullptr;
     cudaError_t e = static_partials(&parts);
     if (e == cudaSuccess)

@@ -19,6 +19,15 @@ namespace cc {
 static std::atomic<uint64_t> g_launches{0};
 void note_launch(int kernels) { g_launches.fetch_add((uint64_t)kernels); }
 
+int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+        sms = 1;
+    return sms;
+}
+
 // psi(m) for integer m >= 1 (Eq. 2): psi(1) = -gamma, psi(m+1) = psi(m) + 1/m.
 double digamma_int_host(int m) {
     long double s = -0.577215664901532860606512090082402431L;

@@ -736,13 +736,6 @@ cudaError_t launch_eval(const BosDev& d, int warps, int blocks, bool set_attr, c
     return eval_launch<32>(d, warps, blocks, set_attr, st);
 }
 
-int sm_count() {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
-}
-
 // One round, queued on st (also the body of the captured graph).
 cudaError_t enqueue_round(cc_bos* b, cudaStream_t st) {
     const BosDev& d = b->d;
@@ -753,7 +746,7 @@ cudaError_t enqueue_round(cc_bos* b, cudaStream_t st) {
     note_launch();
     k_bos_round_pairs<<<(d.n_rp * d.R + 255) / 256, 256, 0, st>>>(d);
     if ((e = cudaGetLastError())) return e;
-    if ((e = launch_eval(d, b->eval_warps, sm_count() * b->eval_blocks_per_sm, false, st)))
+    if ((e = launch_eval(d, b->eval_warps, cc::sm_count() * b->eval_blocks_per_sm, false, st)))
         return e;
     note_launch();
     k_bos_extremes<<<(4 * d.n_rp + 255) / 256, 256, 0, st>>>(d);
@@ -1037,7 +1030,7 @@ cc_status cc_bos_run(cc_ctx* ctx, cc_bos* b, int rounds, int use_graph) {
                 for (int rep = 0; rep < 2; ++rep) {
                     BK(cudaMemsetAsync(b->d.queue, 0, 4, st));
                     BK(cudaEventRecord(e0, st));
-                    BK(launch_eval(b->d, sh[0], sm_count() * sh[1], true, st));
+                    BK(launch_eval(b->d, sh[0], cc::sm_count() * sh[1], true, st));
                     BK(cudaEventRecord(e1, st));
                     BK(cudaEventSynchronize(e1));
                     BK(cudaEventElapsedTime(&ms, e0, e1));

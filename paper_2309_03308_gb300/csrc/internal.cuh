@@ -134,6 +134,9 @@ namespace cc {
 // Counts kernel launches of the library (cc_launch_count).
 void note_launch(int kernels = 1);
 
+// Streaming multiprocessors of the current device (grid sizes scale with it).
+int sm_count();
+
 // Kernel launchers (defined in the .cu files), all on `st`.
 // in: member-major [n][in_stride] (P points used), vals: point-major [P][n_pad]
 cudaError_t launch_ingest(const float* in, int n, int64_t P, int64_t in_stride, int n_pad,

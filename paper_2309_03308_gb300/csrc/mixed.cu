@@ -556,7 +556,8 @@ cudaError_t launch_quantize_ranks(const int16_t* rank2, int n_pad, int n, const 
 static unsigned grid_for(int64_t N, int per_block) {
     int64_t b = (N + per_block - 1) / per_block;
     if (b < 1) b = 1;
-    if (b > 152 * 8) b = 152 * 8;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (b > cap) b = cap;
     return (unsigned)b;
 }
 
@@ -591,7 +592,7 @@ cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int
                                  unsigned long long* best, cudaStream_t st) {
     note_launch();
 #define CC_REFINE(K, R)                                                                   \
-    K<R><<<152 * 8, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, nb, self,  \
+    K<R><<<sm_count() * 8, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, nb, self,  \
                                   na_pad, ids, start, count, cap, sign, vals, pair_ids, best)
     const int slices = (n + 31) / 32;
     if (slices <= 1) CC_REFINE(k_refine_chunks, 1);

@@ -137,8 +137,9 @@ static cudaError_t mm(const TA* A, int64_t sam, int64_t sak, const TB* B, int64_
     const int gx = (N + 63) / 64, gy = (M + 63) / 64;
     // split K when the output tiles alone would leave most SMs idle
     int S = 1, kc = ((K + 15) / 16) * 16;
-    if (ws && gx * gy < 152 && K >= 512) {
-        S = std::min((2 * 152 + gx * gy - 1) / (gx * gy), K / 128);
+    const int sms = sm_count();
+    if (ws && gx * gy < sms && K >= 512) {
+        S = std::min((2 * sms + gx * gy - 1) / (gx * gy), K / 128);
         kc = ((K + S - 1) / S + 15) / 16 * 16;
         S = (K + kc - 1) / kc;
         cudaError_t e = ws->ensure(sizeof(float) * (size_t)S * M * N);
@@ -398,7 +399,7 @@ cc_status sfail(cc_ctx* c, cc_status s, const char* fmt, ...) {
 
 unsigned grid1(int64_t n) {
     int64_t b = (n + 255) / 256;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 16));
 }
 
 cc_status ensure_batch(cc_ctx* ctx, cc_sur* s, int64_t B) {

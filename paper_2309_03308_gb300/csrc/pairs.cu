@@ -8,9 +8,7 @@ namespace cc {
 constexpr int kWarpsPerBlock = 8;
 
 static unsigned pair_grid(int64_t N, int warps_per_block) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     int64_t want = (N + warps_per_block - 1) / warps_per_block;
     int64_t cap = (int64_t)sms * 16;
     return (unsigned)(want < cap ? (want < 1 ? 1 : want) : cap);
@@ -286,7 +284,8 @@ cudaError_t launch_sample_lds(int kind, const int* ext, const double* alpha, int
         g.alpha[d] = alpha[d];
     }
     int64_t blocks = (N + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    const int64_t cap = (int64_t)sm_count() * 32;
+    if (blocks > cap) blocks = cap;
     note_launch();
     k_sample_lds<<<(unsigned)blocks, 256, 0, st>>>(g, pts_a, pts_b, first, N, pa, pb);
     return cudaGetLastError();
@@ -298,7 +297,8 @@ cudaError_t launch_sample_pairs(const uint32_t* pts_a, int64_t na, const uint32_
                                 cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     int64_t blocks = (N + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    const int64_t cap = (int64_t)sm_count() * 32;
+    if (blocks > cap) blocks = cap;
     note_launch();
     k_sample_pairs<<<(unsigned)blocks, 256, 0, st>>>(pts_a, na, pts_b, nb, self, seed, stream,
                                                      first, N, pa, pb);

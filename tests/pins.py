@@ -272,4 +272,63 @@ def pin_region_clusters(o):
     assert s["max"] == np.max(vals[iu]) and s["min"] == np.min(vals[iu])
 
 
+# ----------------------------------------------------------------------------- python oracles
+# The GP and MLP oracles are numpy modules; their pins take the oracle function
+# itself so that test_oracle_plants.py can hand them a planted variant.
+def pyo_self_pair_fix(fix):
+    """Section 3.1 reparameterization in a self brick pair (reading: the second
+    voxel of a coinciding sample moves to the next point of the brick in
+    enumeration order, x fastest, wrapping)."""
+    ext = (4, 3, 2)
+    # hand-derived successors: (1,2,0) is point 9 -> point 10 = (2,2,0);
+    # (3,0,0) is point 3 -> point 4 = (0,1,0) (x wraps into the next row);
+    # (3,2,1) is the last point 23 -> point 0 (wraps to the first)
+    for v, want in (((1, 2, 0), (2, 2, 0)), ((3, 0, 0), (0, 1, 0)), ((3, 2, 1), (0, 0, 0)),
+                    ((0, 0, 1), (1, 0, 1))):
+        got = tuple(int(t) for t in fix(list(v) + list(v), ext))
+        assert got == tuple(v) + want, (v, got)
+    pts = [(x, y, z) for z in range(ext[2]) for y in range(ext[1]) for x in range(ext[0])]
+    succ = []
+    for a in pts:
+        for b in pts:
+            got = tuple(int(t) for t in fix(list(a) + list(b), ext))
+            assert got[:3] == a, (a, b, got)  # the first voxel never moves
+            if a != b:
+                assert got[3:] == b, (a, b, got)  # distinct voxels pass unchanged
+            else:
+                assert got[3:] != a and all(0 <= got[3 + d] < ext[d] for d in range(3)), got
+                succ.append(got[3:])
+    # the successors of all points are all points again (one cycle through the brick)
+    assert sorted(succ) == sorted(pts)
+
+
+def pyo_mlp_offsets(offsets):
+    """The pair head's relative position (position_j - position_i) / (X, Y, Z),
+    with point ids x + X (y + Y z)."""
+    X, Y, Z = 10, 5, 4
+    last = 9 + X * (4 + Y * 3)
+    pi = np.array([0, 73, last, 12, 0], np.int64)
+    pj = np.array([73, 0, 0, 12, last], np.int64)
+    want = np.array([[0.3, 0.4, 0.25], [-0.3, -0.4, -0.25], [-0.9, -0.8, -0.75],
+                     [0.0, 0.0, 0.0], [0.9, 0.8, 0.75]])
+    got = offsets(X, Y, Z, pi, pj)
+    assert np.abs(got - want).max() < 1e-15, got
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, X * Y * Z, 200)
+    b = rng.integers(0, X * Y * Z, 200)
+    assert np.array_equal(offsets(X, Y, Z, a, b), -offsets(X, Y, Z, b, a))  # antisymmetry
+    # points enumerated from a box decompose to that box's coordinates
+    box = (2, 1, 1, 6, 4, 3)
+    P = oracle.box_points(X, Y, Z, box)
+    off = offsets(X, Y, Z, np.zeros(len(P), np.int64), P) * np.array([X, Y, Z])
+    zz, yy, xx = np.meshgrid(np.arange(1, 3), np.arange(1, 4), np.arange(2, 6), indexing="ij")
+    assert np.abs(off - np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1)).max() < 1e-12
+
+
+def py_pins():
+    """(pin, oracle function) pairs of the python oracles."""
+    from oracle import gp, mlp
+    return [(pyo_self_pair_fix, gp.self_pair_fix), (pyo_mlp_offsets, mlp.offsets)]
+
+
 ALL = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

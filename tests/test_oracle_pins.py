@@ -7,3 +7,8 @@ import pins
 @pytest.mark.parametrize("pin", pins.ALL, ids=lambda f: f.__name__)
 def test_pin(orc, pin):
     pin(orc)
+
+
+@pytest.mark.parametrize("pin,fn", pins.py_pins(), ids=lambda v: v.__name__)
+def test_python_oracle_pin(pin, fn):
+    pin(fn)

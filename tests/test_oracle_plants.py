@@ -4,6 +4,7 @@ The oracle is rebuilt with a -DPLANT_* define that introduces one plausible
 error (dropped term, wrong comparison, wrong log base, missing centring, ...);
 the named pin must then fail. This shows the pins constrain the oracle.
 """
+import numpy as np
 import pytest
 
 import oracle
@@ -27,3 +28,78 @@ def test_plant_is_caught(define, pin):
     o = oracle.Oracle(defines=(define,))
     with pytest.raises(AssertionError):
         pin(o)
+
+
+# Planted variants of the python oracles' readings: each is the oracle
+# function with one plausible mistake, and its pin must fail on it.
+def _fix_no_wrap(v, ext):
+    v = np.array(v, np.int64)
+    if tuple(v[:3]) == tuple(v[3:]):
+        ex, ey, ez = ext
+        l = v[3] + ex * (v[4] + ey * v[5]) + 1  # planted: no wrap at the last point
+        v[3], v[4], v[5] = l % ex, (l // ex) % ey, l // (ex * ey)
+    return v
+
+
+def _fix_moves_first(v, ext):
+    v = np.array(v, np.int64)
+    if tuple(v[:3]) == tuple(v[3:]):
+        ex, ey, ez = ext
+        l = (v[0] + ex * (v[1] + ey * v[2]) + 1) % (ex * ey * ez)
+        v[0], v[1], v[2] = l % ex, (l // ex) % ey, l // (ex * ey)  # planted: first voxel
+    return v
+
+
+def _fix_backwards(v, ext):
+    v = np.array(v, np.int64)
+    if tuple(v[:3]) == tuple(v[3:]):
+        ex, ey, ez = ext
+        l = (v[3] + ex * (v[4] + ey * v[5]) - 1) % (ex * ey * ez)  # planted: previous point
+        v[3], v[4], v[5] = l % ex, (l // ex) % ey, l // (ex * ey)
+    return v
+
+
+def _fix_y_fastest(v, ext):
+    v = np.array(v, np.int64)
+    if tuple(v[:3]) == tuple(v[3:]):
+        ex, ey, ez = ext
+        l = (v[4] + ey * (v[3] + ex * v[5]) + 1) % (ex * ey * ez)  # planted: y fastest
+        v[4], v[3], v[5] = l % ey, (l // ey) % ex, l // (ex * ey)
+    return v
+
+
+def _pos(X, Y, Z, p):
+    p = np.asarray(p, np.int64)
+    return np.stack([p % X, (p // X) % Y, p // (X * Y)], 1).astype(np.float64)
+
+
+def _off_sign(X, Y, Z, pi, pj):
+    return (_pos(X, Y, Z, pi) - _pos(X, Y, Z, pj)) / np.array([X, Y, Z], np.float64)
+
+
+def _off_extent_minus_one(X, Y, Z, pi, pj):
+    return (_pos(X, Y, Z, pj) - _pos(X, Y, Z, pi)) / np.array([X - 1, Y - 1, Z - 1], np.float64)
+
+
+def _off_yx_swapped(X, Y, Z, pi, pj):
+    def pos(p):
+        p = np.asarray(p, np.int64)
+        return np.stack([(p // Y) % X, p % Y, p // (X * Y)], 1).astype(np.float64)
+    return (pos(pj) - pos(pi)) / np.array([X, Y, Z], np.float64)
+
+
+PY_PLANTS = [
+    (pins.pyo_self_pair_fix, _fix_no_wrap),
+    (pins.pyo_self_pair_fix, _fix_moves_first),
+    (pins.pyo_self_pair_fix, _fix_backwards),
+    (pins.pyo_self_pair_fix, _fix_y_fastest),
+    (pins.pyo_mlp_offsets, _off_sign),
+    (pins.pyo_mlp_offsets, _off_extent_minus_one),
+    (pins.pyo_mlp_offsets, _off_yx_swapped),
+]
+
+
+@pytest.mark.parametrize("pin,planted", PY_PLANTS, ids=lambda v: v.__name__)
+def test_python_plant_is_caught(pin, planted):
+    with pytest.raises(AssertionError):
+        pin(planted)

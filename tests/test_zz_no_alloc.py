@@ -4,8 +4,8 @@ Callers that may not allocate device memory while they run (an interactive
 per-frame loop, or a host application that keeps all device memory in its own
 pool) get the same region-pair extremes as cc_all_pairs from planes they pass
 in, with the scratch held in a static device array. The test compares it with
-cc_all_pairs through the C ABI on two calls in a row, for a cross and a self
-region pair. This file is named so that pytest collects it last.
+cc_all_pairs through the C ABI and with the FP64 oracle's exhaustive extremes,
+on two calls in a row, for a cross and a self region pair. This file is named so that pytest collects it last.
 """
 import ctypes
 
@@ -72,16 +72,22 @@ def test_static_matches_all_pairs_twice(env):
     za, nk, lda = planes(torch, F, A)
     zb, _, ldb = planes(torch, F, B)
     out = torch.zeros(32, dtype=torch.uint8, device="cuda")
+    orc = oracle.get()
     for (r1, r2, z1, l1, z2, l2, P1, P2) in ((ra, rb, za, lda, zb, ldb, A, B),
                                              (ra, ra, za, lda, za, lda, A, A)):
         ref = ctx.all_pairs(r1, r2, Params(0))
+        exact = orc.region_extremes(F, P1, P2, r1 == r2, oracle.PEARSON)
         for _ in range(2):  # the static scratch keeps the previous call's contents
             out.fill_(0xFF)
             assert call_static(lib, z1, l1, z2, l2, nk, len(P1), len(P2), r1 == r2, out) == 0
             torch.cuda.synchronize()
             got = as_result(out)
+            # the same result as the allocating entry point ...
             assert got["count"] == ref["count"]
             assert abs(got["max"] - ref["max"]) < TOL and abs(got["min"] - ref["min"]) < TOL
+            # ... and as the FP64 oracle's exhaustive extremes
+            assert got["count"] == exact["count"]
+            assert abs(got["max"] - exact["max"]) < TOL and abs(got["min"] - exact["min"]) < TOL
             # the reported maximiser and minimiser are valid for the exact measure
             a, b = divmod(got["argmax"], len(P2))
             a2, b2 = divmod(got["argmin"], len(P2))
