@@ -1,9 +1,13 @@
 """Throughput of the correlation hot path on one GB300 (or N independent ranks).
 
-Headline workload (focus refinement at paper scale): a 352x256x20 ensemble
-with n = 100 members (seeded synthetic stand-in for the paper's weather
-ensemble) and two 32x32x20 regions (20,480 points each). One step runs every
-built stage of the path on the resident field:
+Headline (`value`): KSG mutual information (k = 10, Section 3.2) in point-pairs
+per second at n = 100 members, on 2,000,000 seeded uniform cross pairs of two
+32x32x20 regions (20,480 points each) cut from a 352x256x20 ensemble (seeded
+synthetic stand-in for the paper's weather ensemble), fp32 inputs, neighbour
+counts exact, digamma sum in FP64. It is the CUDA-event time of the KSG launch
+inside each step; `roofline` is that kernel's.
+
+One step runs every built stage of the path on the resident field:
   ingest      per-point planes (float-float stats finalised in FP64, z-scores,
               ranks, sorted values)
   fp32 x2     all 419,430,400 cross pairs, Pearson and Spearman, FP32 SIMT,
@@ -13,20 +17,29 @@ built stage of the path on the resident field:
               BF16 on the integer ranks (an exact contraction for n <= 257)
   sample      2,000,000 seeded uniform cross pairs
   ksg, hist   KSG MI (k = 10) and 16x16-bin MI on them, with extremes
-`value` counts point-pair measure evaluations per second over the step.
+Each stage's own rate, dtype and roofline are under "measures"; the count of
+all point-pair evaluations of the step (mixed measures and precisions) over
+the step time is only reported as "step_blend".
 
 A second workload with n = 1000 (the same two regions, only those boxes
-generated) is timed in the same run and reported under "m1000": FP32 SIMT vs
-BF16 vs FP8 all-pairs extremes and KSG on 1,000,000 sampled pairs.
-"one_to_all" times the paper's Table 1 workload (one reference point against
-all 1.76 M points of a 352 x 250 x 20 field, Pearson and KSG, n = 100 and
-1000), with the paper's RTX 3090 times as context.
+generated) is timed in the same run: FP32 SIMT vs BF16 vs FP8 all-pairs
+extremes and KSG on 1,000,000 sampled pairs ("measures" n1000 entries, and
+"m1000" for its stage list). "one_to_all" times the paper's Table 1 workload
+(one reference point against all 1.76 M points of a 352 x 250 x 20 field,
+Pearson and KSG, n = 100 and 1000), with the paper's RTX 3090 times beside it
+as context only.
+
+`e2e`: the headline measure through the public API from host memory: per step
+the field is copied from pinned host memory and re-ingested, the 2,000,000
+pairs go up from pinned host memory, KSG runs, and the values come back to
+pinned host memory.
 
 Multi-GPU (torchrun): every rank runs its own replica with its own sampler
 stream (weak scaling); the only collectives are the timing barrier and max.
 
---impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of each stage and scales it to the step.
+--impl reference times the FP64 CPU oracle's KSG (the paper has no code; the
+oracle is the method's only other executable statement here) on the host
+cores on a bounded sample of the same pairs per step.
 """
 from __future__ import annotations
 
@@ -48,37 +61,61 @@ import gen  # noqa: E402
 from gen import configs  # noqa: E402
 
 METRIC = "KSG-MI & Pearson point-pairs/s at M=100/1000 vs plain FP32 GPU, roofline %"
+HEADLINE = ("KSG MI (k = 10) point-pairs/s at n = 100: 2,000,000 seeded cross pairs of the "
+            "two 32x32x20 focus regions, fp32 inputs, exact neighbour counts, FP64 digamma "
+            "sum; CUDA-event time of the KSG launch inside each step, inputs resident")
 FOC = configs.FOCUS
 PRE = configs.PRECISION
 N_ALL = 20480 * 20480
-N_SMS = 152
-FP32_LANES = 128
+# Dispatch: one warp instruction per clock per SM sub-partition, four per SM.
+# Measured on a GB300 with single-instruction throughput loops (152 SMs, 2 blocks
+# of 1024 threads each, 8 independent chains per thread): FMNMX, FADD, FFMA,
+# IADD and packed 16-bit IMNMX retire 124-125 thread instructions per clock per
+# SM at 2.07 GHz; FSETP (with FSEL), LOP3 and three-input FMNMX half of that.
+ISSUE_LANES = 128   # thread instructions per clock per SM (dispatch limit)
+FFMA_LANES = 128    # FP32 FMA lanes per SM (2 flops each)
 
 
-def peaks():
+def peaks(sms=None):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         d = json.load(open(path))
-        return dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2070.0),
-                    bf16_tflops=d.get("bf16_tflops_sustained", d["bf16_tflops"]),
-                    source="measured")
-    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, bf16_tflops=1700.0, source="fallback")
+        pk = dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2070.0),
+                  bf16_tflops=d["bf16_tflops"],
+                  bf16_tflops_sustained=d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                  source="measured")
+    else:
+        pk = dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, bf16_tflops=1900.0,
+                  bf16_tflops_sustained=1700.0, source="fallback")
+    pk["sms"] = sms if sms else 152
+    return pk
+
+
+def ksg_definition_instr(n):
+    """Instructions of the KSG definition per pair (Section 3.2): n(n-1) Chebyshev
+    distances (two FADD and one FMNMX each) and 2n(n-1) marginal comparisons
+    |x_i - x_j| < eps_i (one FADD and one FSETP each): 6 n (n - 1)."""
+    return 6.0 * n * (n - 1)
 
 
 def peak_of(kind, pk):
     """(peak, unit, source note) of a roofline kind."""
-    alu = N_SMS * FP32_LANES * pk["sm_max_mhz"] * 1e6 / 1e12
+    sms, mhz = pk["sms"], pk["sm_max_mhz"]
     if kind == "fp32_flop":
-        return 2 * alu, "TFLOP/s", f"derived: {N_SMS} SMs x {FP32_LANES} lanes x 2 flop x " \
-                                   f"{pk['sm_max_mhz']:.0f} MHz"
-    if kind == "alu_op":
-        return alu, "Tops/s", f"derived: {N_SMS} SMs x {FP32_LANES} lanes x " \
-                              f"{pk['sm_max_mhz']:.0f} MHz"
-    if kind == "bf16":
-        return pk["bf16_tflops"], "TFLOP/s", f"{pk['source']} sustained bf16"
+        return (sms * FFMA_LANES * 2 * mhz * 1e6 / 1e12, "TFLOP/s",
+                f"derived: {sms} SMs x {FFMA_LANES} FFMA lanes x 2 flop x {mhz:.0f} MHz")
+    if kind == "ksg_instr":
+        return (sms * ISSUE_LANES * mhz * 1e6 / 1e12, "T instr/s",
+                f"derived: {sms} SMs x {ISSUE_LANES} thread instructions per clock (dispatch "
+                f"limit, measured) x {mhz:.0f} MHz; work = the definition's 6n(n-1) "
+                f"instructions per pair (brute-force equivalent, not the instructions the "
+                f"windowed walk executes)")
+    if kind == "bf16":  # timed inside a long step: the sustained figure
+        return (pk["bf16_tflops_sustained"], "TFLOP/s",
+                f"{pk['source']} bf16 sustained (cuBLAS, seconds-long loop)")
     if kind == "fp8":
-        return 2 * pk["bf16_tflops"], "TFLOP/s", f"{pk['source']} sustained bf16 x 2 (nominal " \
-                                                 "fp8/bf16 ratio)"
+        return (2 * pk["bf16_tflops_sustained"], "TFLOP/s",
+                f"{pk['source']} bf16 sustained x 2 (nominal fp8/bf16 ratio)")
     if kind == "hbm":
         return pk["hbm_gbs"], "GB/s", f"{pk['source']} copy bandwidth"
     raise ValueError(kind)
@@ -204,7 +241,7 @@ class Workload:
         self.stages.append(("sample", self._sample, 0, None, 0))
         self.stages.append(("ksg", lambda i, h: self._eval("ksg", Params(P.CC_MI_KSG, k=k),
                                                            self.ksg),
-                            sampled, "alu_op", 3.0 * n * (n - 1) * sampled))
+                            sampled, "ksg_instr", ksg_definition_instr(n) * sampled))
         if n == 100:
             self.stages.append(("hist", lambda i, h: self._eval(
                 "hist", Params(P.CC_MI_BINNED, bins=FOC["bins"]), self.hist),
@@ -321,11 +358,124 @@ def stage_rooflines(wl, stage_ms, pk):
         peak, unit, src = peak_of(kind, pk)
         scale = 1e9 if kind == "hbm" else 1e12
         achieved = work / (stage_ms[name] * 1e-3) / scale
-        out[name] = {"bound": {"fp32_flop": "alu", "alu_op": "alu", "bf16": "tensor",
+        out[name] = {"bound": {"fp32_flop": "alu", "ksg_instr": "alu", "bf16": "tensor",
                                "fp8": "tensor", "hbm": "hbm"}[kind],
                      "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                      "peak_source": src}
     return out
+
+
+def reduced_precision_errors(cc, dev, wl, wl2):
+    """Observed error of the tensor-core path's approximate values against the
+    compensated-fp32 (Dot2) values of the same pairs, beside the bound it
+    certifies with: all pairs between two 16x16x4 sub-boxes (1024 x 1024) of the
+    focus regions, at n = 100 and n = 1000, per (row, 32-column chunk) extreme.
+    Dot2 agrees with the FP64 oracle within 1e-7 on these planes (GPU tests)."""
+    import torch
+    import paper_2309_03308_gb300 as pg
+    from paper_2309_03308_gb300 import Params
+    out = {"pairs": 1024 * 1024, "reference": "compensated fp32 (Dot2) of the fp32 planes"}
+    cases = []
+    if wl is not None:
+        bxa = (64, 64, 0, 80, 80, 4)
+        bxb = (256, 160, 0, 272, 176, 4)
+        cases.append(("n100", wl.fa, wl.fa, bxa, bxb, FOC["X"], FOC["Y"]))
+    if wl2 is not None:
+        cases.append(("n1000", wl2.fa, wl2.fb, (0, 0, 0, 16, 16, 4), (0, 0, 0, 16, 16, 4), 32, 32))
+    for tag, fa, fb, bxa, bxb, X, Y in cases:
+        (ra,) = cc.define_regions(fa, [bxa])
+        (rb,) = cc.define_regions(fb, [bxb])
+        A = region_points(X, Y, bxa)
+        B = region_points(X, Y, bxb)
+        pa = torch.from_numpy(np.repeat(A, len(B)).astype(np.int32)).to(dev)
+        pb = torch.from_numpy(np.tile(B, len(A)).astype(np.int32)).to(dev)
+        ref = cc.eval_pairs(fa, fb, Params(pg.CC_PEARSON, precision=pg.CC_FP32_DOT2), pa, pb,
+                            out=torch.empty(len(A) * len(B), device=dev)).cpu().numpy()
+        ref = ref.reshape(len(A), len(B) // 32, 32)
+        emax, emin = ref.max(2).T, ref.min(2).T
+        for prec, code in (("bf16", pg.CC_BF16), ("fp8", pg.CC_FP8_E4M3)):
+            cmax, cmin, bound = cc.all_pairs_approx(ra, rb, Params(pg.CC_PEARSON, precision=code))
+            err = np.concatenate([np.abs(cmax - emax).ravel(), np.abs(cmin - emin).ravel()])
+            out[f"pearson_{prec}_{tag}"] = {"dtype": prec, "observed_max": float(err.max()),
+                                           "observed_mean": float(err.mean()),
+                                           "bound": float(bound),
+                                           "max_over_bound": float(err.max() / bound)}
+    return out
+
+
+def headline_config(world, boxes_only=False):
+    """The workload of the headline measure (shared by both arms of the bench)."""
+    return {"workload": FOC["name"] + ("-regions-only" if boxes_only else ""),
+            "headline": "ksg_mi_k10_n100",
+            "field": "two 32x32x20 boxes" if boxes_only else "352x256x20",
+            "members": FOC["n"], "regions": "2 x 32x32x20 (20480 points each)",
+            "pairs": FOC["sampled_pairs"], "ksg_k": FOC["k"],
+            "l2": "inputs larger than L2 (field 721 MB rewritten as 4.6 GB of planes every "
+                  "step; stored value matrices 3.4 GB)",
+            "parallelism": f"replicas x{world}"}
+
+
+def kernel_counters(kernel, workload):
+    """ncu counters of a kernel from profiles/kernel_counters.json, or None when
+    the kernel's sources changed since the capture (their hash is recorded)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "kernel_counters.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(workload, {}).get(kernel)
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return rec if h.hexdigest()[:16] == rec["sources_sha16"] else None
+
+
+def measure_entry(dtype, pairs, ms, roof=None, **extra):
+    e = {"dtype": dtype, "pairs": int(pairs), "ms": ms, "pairs_per_s": pairs / (ms * 1e-3)}
+    if roof is not None:
+        e["roofline"] = roof
+    e.update(extra)
+    return e
+
+
+def time_e2e_ksg(wl, args, stream, world, dev):
+    """The headline measure from host memory through the public API: per step the
+    field is updated from pinned host memory (copy + ingest), the step's pairs
+    are read from pinned host memory, KSG runs and the values are written to
+    pinned host memory. Returns (ms per step, h2d bytes, d2h bytes)."""
+    import torch
+    import paper_2309_03308_gb300 as pg
+    from paper_2309_03308_gb300 import Params
+    N = wl.sampled
+    pa_h = torch.empty(N, dtype=torch.int32).pin_memory()
+    pb_h = torch.empty(N, dtype=torch.int32).pin_memory()
+    out_h = torch.empty(N, dtype=torch.float32).pin_memory()
+    pa_h.copy_(wl.pa.cpu())
+    pb_h.copy_(wl.pb.cpu())
+    prm = Params(pg.CC_MI_KSG, k=FOC["k"])
+
+    def step():
+        wl._ingest(0, True)
+        wl.cc.eval_pairs(wl.fa, wl.fb, prm, pa_h.numpy(), pb_h.numpy(), out=out_h.numpy())
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()  # returns once the values are in host memory
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    return ms, int(wl.F_host.nbytes + 8 * N), int(4 * N)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -339,23 +489,59 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
     torch.cuda.set_stream(stream)
     cc = pg.Context(local_rank, stream=stream.cuda_stream)
-    pk = peaks()
+    pk = peaks(torch.cuda.get_device_properties(dev).multi_processor_count)
     boxes_only = args.workload == "focus-regions"
     wl = Workload("focus", cc, dev, rank, 100, boxes_only, FOC["sampled_pairs"], FOC["k"],
                   with_store=True, topk=PRE["topk"])
     with Clocks(local_rank) as clk:
-        ms, stage_ms, e2e_ms, launches = time_workload(wl, args, stream, world, dev)
+        ms, stage_ms, e2e_blend_ms, launches = time_workload(wl, args, stream, world, dev)
     roof = stage_rooflines(wl, stage_ms, pk)
-    dom = max(roof, key=lambda k: stage_ms[k])
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if os.path.exists(tpath):
-        traffic = json.load(open(tpath)).get(FOC["name"], {}).get(dom)
-    dominant = dict(roof[dom], kernel=dom, traffic=traffic)
+    e2e_ms, h2d, d2h = time_e2e_ksg(wl, args, stream, world, dev)
+    ctr = kernel_counters("k_ksg_stream", FOC["name"])
+    head = dict(roof["ksg"], kernel="k_ksg_stream<10>",
+                traffic=ctr["dram_bytes"] if ctr else None,
+                achieved_note="definition instructions (6n(n-1) per pair) per second of the "
+                              "KSG launch; the walk executes a different, smaller work")
+    if ctr:
+        head["ncu"] = {k: ctr[k] for k in ("issue_active_pct", "lanes_active_per_instr",
+                                           "inst_executed_per_pair") if k in ctr}
+    ksg_ms = stage_ms["ksg"]
+    value = FOC["sampled_pairs"] * world / (ksg_ms * 1e-3)
     r = wl.results
+    fp32_ms = stage_ms["allpairs_pearson_fp32"]
+
+    def rp(tag):
+        return {kk: vv for kk, vv in r[tag].items()} if r.get(tag) else None
+
+    measures = {
+        "ksg_mi_k10_n100": measure_entry("f32", FOC["sampled_pairs"], ksg_ms, roof["ksg"],
+                                         result=rp("ksg")),
+        "pearson_all_pairs_fp32_n100": measure_entry(
+            "f32", N_ALL, fp32_ms, roof["allpairs_pearson_fp32"], result=rp("pearson_fp32")),
+        "spearman_all_pairs_fp32_n100": measure_entry(
+            "f32", N_ALL, stage_ms["allpairs_spearman_fp32"], roof["allpairs_spearman_fp32"],
+            result=rp("spearman_fp32")),
+        "hist_mi_b16_n100": measure_entry("f32", FOC["sampled_pairs"], stage_ms["hist"],
+                                          result=rp("hist")),
+        "ingest_n100": {"dtype": "f32 in, f64 stats", "points": 352 * 256 * 20,
+                        "ms": stage_ms["ingest"], "roofline": roof["ingest"]},
+        "pearson_all_pairs_bf16_n100": measure_entry(
+            "bf16", N_ALL, stage_ms["allpairs_pearson_bf16"], roof["allpairs_pearson_bf16"],
+            result=rp("pearson_bf16"), speedup_vs_fp32=fp32_ms / stage_ms["allpairs_pearson_bf16"],
+            output="certified exact max/min (compensated fp32 re-evaluation) and the top 4096"),
+        "pearson_all_pairs_fp8_n100": measure_entry(
+            "fp8", N_ALL, stage_ms["allpairs_pearson_fp8"], roof["allpairs_pearson_fp8"],
+            result=rp("pearson_fp8"), speedup_vs_fp32=fp32_ms / stage_ms["allpairs_pearson_fp8"],
+            output="certified exact max/min (compensated fp32 re-evaluation) and the top 4096"),
+        "spearman_all_pairs_bf16_n100": measure_entry(
+            "bf16", N_ALL, stage_ms["allpairs_spearman_bf16"], roof["allpairs_spearman_bf16"],
+            result=rp("spearman_bf16"),
+            speedup_vs_fp32=stage_ms["allpairs_spearman_fp32"] / stage_ms["allpairs_spearman_bf16"],
+            output="exact integer-rank contraction, certified max/min and the top 4096"),
+    }
     line = {
         "metric": METRIC,
-        "value": wl.pairs_per_step * world / (ms * 1e-3),
+        "value": value,
         "unit": "point-pairs/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -367,28 +553,20 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f32",
         "data": "synthetic (seeded Gaussian random field + latent signal; stand-in for the "
                 "paper's ensembles)",
-        "config": {"workload": FOC["name"] + ("-regions-only" if boxes_only else ""),
-                   "field": "two 32x32x20 boxes" if boxes_only else "352x256x20",
-                   "members": 100, "regions": "2 x 32x32x20 (20480 points each)",
-                   "pairs_per_step": {s[0]: s[2] for s in wl.stages if s[2]},
-                   "ksg_k": FOC["k"], "hist_bins": FOC["bins"], "topk": PRE["topk"],
-                   "l2": "inputs larger than L2 (field 721 MB rewritten as 4.6 GB of planes "
-                         "every step; stored value matrices 3.4 GB)",
-                   "parallelism": f"replicas x{world}"},
+        "headline": HEADLINE,
+        "config": headline_config(world, boxes_only),
+        "sms": pk["sms"],
         "stage_ms": stage_ms,
-        "measures": {
-            "pearson_fp32_pairs_per_s": N_ALL / (stage_ms["allpairs_pearson_fp32"] * 1e-3),
-            "pearson_bf16_pairs_per_s": N_ALL / (stage_ms["allpairs_pearson_bf16"] * 1e-3),
-            "pearson_fp8_pairs_per_s": N_ALL / (stage_ms["allpairs_pearson_fp8"] * 1e-3),
-            "ksg_pairs_per_s": FOC["sampled_pairs"] / (stage_ms["ksg"] * 1e-3),
-            "hist_pairs_per_s": FOC["sampled_pairs"] / (stage_ms["hist"] * 1e-3)},
-        "results": {k: (v if v is None else {kk: vv for kk, vv in v.items()})
-                    for k, v in r.items()},
-        "roofline": dominant,
-        "stage_roofline": roof,
-        "e2e": {"value": wl.pairs_per_step * world / (e2e_ms * 1e-3), "unit": "point-pairs/s",
-                "h2d_bytes_per_step": int(wl.F_host.nbytes),
-                "d2h_bytes_per_step": int(2 * 4 * FOC["sampled_pairs"] + 8 * 40)},
+        "measures": measures,
+        "step_blend": {"point_pair_evals_per_step": wl.pairs_per_step,
+                       "point_pair_evals_per_s": wl.pairs_per_step * world / (ms * 1e-3),
+                       "e2e_ms_per_step": e2e_blend_ms,
+                       "note": "every stage's pairs over the whole step: mixed measures and "
+                               "precisions (fp32, bf16, fp8), not a single-measure rate"},
+        "roofline": head,
+        "e2e": {"value": FOC["sampled_pairs"] * world / (e2e_ms * 1e-3), "unit": "point-pairs/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "what": "field H2D + ingest, pairs H2D, KSG, values D2H (pinned host memory)"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -398,17 +576,29 @@ def run_ours(args, rank, world, local_rank):
         ms2, st2, e2e2, l2 = time_workload(wl2, args, stream, world, dev)
         roof2 = stage_rooflines(wl2, st2, pk)
         fp32 = st2["allpairs_pearson_fp32"]
-        line["m1000"] = {
-            "workload": PRE["name"], "ms_per_step": ms2, "stage_ms": st2,
-            "value": wl2.pairs_per_step * world / (ms2 * 1e-3),
-            "pearson_fp32_pairs_per_s": N_ALL / (fp32 * 1e-3),
-            "pearson_bf16_pairs_per_s": N_ALL / (st2["allpairs_pearson_bf16"] * 1e-3),
-            "pearson_fp8_pairs_per_s": N_ALL / (st2["allpairs_pearson_fp8"] * 1e-3),
-            "speedup_bf16_vs_fp32": fp32 / st2["allpairs_pearson_bf16"],
-            "speedup_fp8_vs_fp32": fp32 / st2["allpairs_pearson_fp8"],
-            "ksg_pairs_per_s": PRE["sampled_pairs"] / (st2["ksg"] * 1e-3),
-            "results": wl2.results, "stage_roofline": roof2, "gpu_launches": int(l2),
-            "e2e_ms_per_step": e2e2}
+        r2 = wl2.results
+        measures["ksg_mi_k10_n1000"] = measure_entry("f32", PRE["sampled_pairs"], st2["ksg"],
+                                                     roof2["ksg"])
+        measures["pearson_all_pairs_fp32_n1000"] = measure_entry(
+            "f32", N_ALL, fp32, roof2["allpairs_pearson_fp32"], result=r2.get("pearson_fp32"))
+        for tag, dt in (("bf16", "bf16"), ("fp8", "fp8")):
+            measures[f"pearson_all_pairs_{tag}_n1000"] = measure_entry(
+                dt, N_ALL, st2[f"allpairs_pearson_{tag}"], roof2[f"allpairs_pearson_{tag}"],
+                result=r2.get(f"pearson_{tag}"),
+                speedup_vs_fp32=fp32 / st2[f"allpairs_pearson_{tag}"],
+                output="certified exact max/min (compensated fp32 re-evaluation) and the top "
+                       "4096")
+        line["m1000"] = {"workload": PRE["name"], "ms_per_step": ms2, "stage_ms": st2,
+                         "gpu_launches": int(l2), "e2e_ms_per_step": e2e2}
+        if not args.skip_errors:
+            line["reduced_precision_error"] = reduced_precision_errors(cc, dev, wl, wl2)
+            for prec in ("bf16", "fp8"):
+                for tag in ("n100", "n1000"):
+                    e = line["reduced_precision_error"].get(f"pearson_{prec}_{tag}")
+                    m = measures.get(f"pearson_all_pairs_{prec}_{tag}")
+                    if e and m:
+                        m["approx_error_vs_fp32"] = {k: e[k] for k in
+                                                     ("observed_max", "observed_mean", "bound")}
     if not args.skip_one_to_all:
         line["one_to_all"] = [run_one_to_all(args, cc, dev, stream, n)
                               for n in ((100,) if args.skip_m1000 else (100, 1000))]
@@ -425,7 +615,8 @@ def run_ours(args, rank, world, local_rank):
 
 # The paper's own timing workload (Table 1): correlations from one reference
 # point to all 1.76 M points of a 250 x 352 x 20 grid, at n = 100 and 1000; the
-# paper's RTX 3090 times are quoted as context (other hardware).
+# paper's RTX 3090 times are quoted beside ours as context only (other hardware,
+# other data), not as a ratio.
 PAPER_TABLE1_GPU_S = {100: {"pearson": 0.002, "ksg": 0.672}, 1000: {"pearson": 0.21, "ksg": 35.9}}
 
 
@@ -457,8 +648,7 @@ def run_one_to_all(args, cc, dev, stream, n):
                 ms.append(e0.elapsed_time(e1))
         t = statistics.median(ms) * 1e-3
         res[name] = {"s": t, "pairs_per_s": P / t,
-                     "paper_rtx3090_s": PAPER_TABLE1_GPU_S[n][name],
-                     "speedup_vs_paper_gpu": PAPER_TABLE1_GPU_S[n][name] / t}
+                     "paper_context_s": PAPER_TABLE1_GPU_S[n][name]}
     cc.free_field(fid)
     return res
 
@@ -944,73 +1134,103 @@ def run_inter_variable(cc, dev, stream, F, fid, rids, kw):
 
 
 # ----------------------------------------------------------------------------- oracle
-STAGE_MEASURE = {"allpairs_pearson_fp32": 0, "allpairs_spearman_fp32": 1,
-                 "allpairs_pearson_bf16": 0, "allpairs_pearson_fp8": 0, "ksg": 3, "hist": 2}
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
-def oracle_sample_rates(F, budget_s=12.0):
-    """Seconds per pair of the FP64 oracle for each measure, on bounded samples."""
+def headline_pairs(m, first=0):
+    """The first m pairs of the headline's sampler stream (rank 0, step 0) as
+    grid point ids, drawn by the oracle's own Philox sampler (bit-identical to
+    the library's cc_sample_pairs for these arguments)."""
     import oracle
     o = oracle.get()
     A = oracle.box_points(FOC["X"], FOC["Y"], FOC["Z"], FOC["box_a"])
     B = oracle.box_points(FOC["X"], FOC["Y"], FOC["Z"], FOC["box_b"])
-    rng = np.random.default_rng(99)
-    plan = [(0, {}, 40000), (1, {}, 20000), (3, {"k": FOC["k"]}, 4000),
-            (2, {"bins": FOC["bins"]}, 40000)]
-    per = budget_s / len(plan)
-    rates, samples = {}, {}
-    for kind, kw, m in plan:
-        ia = A[rng.integers(0, len(A), m)]
-        ib = B[rng.integers(0, len(B), m)]
-        t = time.perf_counter()
-        o.eval_pairs(F, kind, ia[:64], ib[:64], **kw)
-        t64 = (time.perf_counter() - t) / 64
-        m = int(max(64, min(m, per / max(t64, 1e-9))))
-        t = time.perf_counter()
-        o.eval_pairs(F, kind, ia[:m], ib[:m], **kw)
-        rates[kind] = (time.perf_counter() - t) / m
-        samples[["pearson", "spearman", "hist", "ksg"][kind]] = m
-    return rates, samples, o.threads()
+    a, b = o.sample_pairs(FOC["sampler_seed"], 0, first, len(A), len(B), False, m)
+    return A[a], B[b]
 
 
-def oracle_step_seconds(rates):
-    pairs = {"allpairs_pearson_fp32": N_ALL, "allpairs_spearman_fp32": N_ALL,
-             "allpairs_pearson_bf16": N_ALL, "allpairs_pearson_fp8": N_ALL,
-             "ksg": FOC["sampled_pairs"], "hist": FOC["sampled_pairs"]}
-    return sum(rates[STAGE_MEASURE[s]] * p for s, p in pairs.items()), sum(pairs.values())
+def oracle_ksg_seconds(F, pa, pb, threads=None):
+    """Wall seconds of the FP64 oracle's KSG (k = 10) over pairs (pa, pb)."""
+    import oracle
+    o = oracle.get()
+    old = o.threads()
+    if threads:
+        o.set_threads(threads)
+    try:
+        t = time.perf_counter()
+        o.eval_pairs(F, oracle.MI_KSG, pa, pb, k=FOC["k"])
+        return time.perf_counter() - t, o.threads()
+    finally:
+        o.set_threads(old)
+
+
+def sized_sample(F, budget_s, threads=None, cap=2_000_000):
+    """Pairs for about budget_s seconds of oracle KSG, from a 1024-pair calibration."""
+    pa, pb = headline_pairs(1024)
+    t, _ = oracle_ksg_seconds(F, pa, pb, threads)
+    return int(max(64, min(cap, budget_s / max(t / 1024, 1e-9))))
 
 
 def cpu_baseline_line(F):
-    rates, samples, cores = oracle_sample_rates(F)
-    t, pairs = oracle_step_seconds(rates)
-    return {"value": pairs / t, "unit": "point-pairs/s", "cores": cores, "kind": "oracle",
-            "sample": "FP64 oracle timed on " + ", ".join(f"{v} {k} pairs" for k, v in
-                                                         samples.items()) +
-                      " drawn from the step's region pair; per-pair times scaled to the "
-                      "step's pair counts"}
+    """The FP64 oracle's KSG on the headline's pairs, on all host cores and on one."""
+    m = sized_sample(F, 10.0)
+    pa, pb = headline_pairs(m)
+    t, cores = oracle_ksg_seconds(F, pa, pb)
+    m1 = sized_sample(F, 4.0, threads=1)
+    t1, _ = oracle_ksg_seconds(F, pa[:m1], pb[:m1], threads=1) if m1 <= m else \
+        oracle_ksg_seconds(F, *headline_pairs(m1), threads=1)
+    return {"value": m / t, "unit": "point-pairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle KSG (k = {FOC['k']}, n = {FOC['n']}) on {m} pairs of the "
+                      f"headline's sampler (seed {FOC['sampler_seed']}, stream 0) between the "
+                      f"focus regions, {cores} threads ({t:.1f} s)",
+            "one_core": {"value": m1 / t1, "pairs": m1, "seconds": t1},
+            "cpu_model": cpu_model()}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: per step, KSG on a bounded sample of the
+    headline's pairs (consecutive slices of its sampler stream)."""
     F = gen.field(FOC["seed"], FOC["X"], FOC["Y"], FOC["Z"], FOC["n"])
-    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        oracle_sample_rates(F, budget_s=budget)
-    times, samples, cores, pairs = [], None, None, 0
-    for _ in range(args.steps):
-        rates, samples, cores = oracle_sample_rates(F, budget_s=budget)
-        t, pairs = oracle_step_seconds(rates)
-        times.append(t)
+    per_step = min(8.0, 150.0 / max(1, args.steps + args.warmup))
+    m = sized_sample(F, per_step)
+    pa, pb = headline_pairs(m * (args.warmup + args.steps))
+    times, cores = [], None
+    for i in range(args.warmup + args.steps):
+        t, cores = oracle_ksg_seconds(F, pa[i * m:(i + 1) * m], pb[i * m:(i + 1) * m])
+        if i >= args.warmup:
+            times.append(t)
     t = statistics.median(times)
-    value = pairs / t
-    desc = ("FP64 oracle on " + ", ".join(f"{v} {k} pairs" for k, v in samples.items()) +
-            " per step, scaled to the full step")
+    value = m / t
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    desc = (f"FP64 oracle KSG (k = {FOC['k']}, n = {FOC['n']}) on {m} pairs per step, "
+            f"consecutive slices of the headline's sampler (seed {FOC['sampler_seed']}, stream "
+            f"0) between the focus regions, {cores} threads")
     return {"metric": METRIC, "value": value, "unit": "point-pairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": FOC["name"], "members": FOC["n"]},
+            "data": "synthetic (seeded Gaussian random field + latent signal; stand-in for the "
+                    "paper's ensembles)", "impl": "reference",
+            "headline": "the headline's measure and workload (KSG MI, k = 10, n = 100, pairs "
+                        "between the focus regions), timed on the host cores by the FP64 oracle",
+            "config": headline_config(world),
             "cpu_baseline": {"value": value, "unit": "point-pairs/s", "cores": cores,
-                             "kind": "oracle", "sample": desc},
+                             "kind": "oracle", "sample": desc, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "point-pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -1032,6 +1252,8 @@ def main():
                     help="do not train and time the learned surrogate")
     ap.add_argument("--quick-surrogate", action="store_true",
                     help="train the surrogate on 400k instead of 4M pairs")
+    ap.add_argument("--skip-errors", action="store_true",
+                    help="do not measure the reduced-precision errors")
     ap.add_argument("--recall", action="store_true",
                     help="also measure BOS recall against exhaustive Pearson maxima")
     ap.add_argument("--workload", default="focus", choices=["focus", "focus-regions"],

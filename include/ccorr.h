@@ -353,6 +353,22 @@ cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t region_b,
                             const cc_params* params, int topk, uint64_t* ids, float* vals,
                             cc_rp_result* out, cc_mixed_info* info);
 
+/*
+ * The approximate values behind cc_all_pairs_topk, for stating their error
+ * (project addition to Section 4.2's focus refinement). Runs the same
+ * quantization and tensor-core contraction as cc_all_pairs_topk with the same
+ * params and returns, per row a of region A and per chunk c of 32 consecutive
+ * columns b = 32c .. 32c + 31 of region B, the largest and smallest
+ * approximate value r~(a, b) of the chunk: cmax, cmin are host float
+ * [ceil(|B| / 32)][|A|] (chunk-major). For a self region pair only b > a is
+ * included; a chunk with no included pair holds -inf (cmax) and +inf (cmin).
+ * *bound (host) receives the bound B that cc_all_pairs_topk certifies with:
+ * |r~(a, b) - r(a, b)| <= B for every pair, r the value of the fp32 planes,
+ * hence |cmax - max_b r| <= B and |cmin - min_b r| <= B per chunk.
+ */
+cc_status cc_all_pairs_approx(cc_ctx* ctx, int32_t region_a, int32_t region_b,
+                              const cc_params* params, float* cmax, float* cmin, float* bound);
+
 /* ------------------------------------------------- Bayesian optimal sampling (BOS) */
 
 /*

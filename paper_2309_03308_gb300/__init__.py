@@ -230,6 +230,21 @@ class Context:
         cert = {f: getattr(info, f) for f, _ in _lib.cc_mixed_info._fields_}
         return _res(res), ids[:topk], vals[:topk], cert
 
+    def all_pairs_approx(self, ra: int, rb: int, params: Params):
+        """Approximate per-(row, 32-column chunk) extremes of the reduced-precision
+        contraction: (cmax [chunks][|A|], cmin [chunks][|A|], certified bound)."""
+        na, _ = self.region_info(ra)
+        nb, _ = self.region_info(rb)
+        chunks = (nb + 31) // 32
+        cmax = np.empty((chunks, na), np.float32)
+        cmin = np.empty((chunks, na), np.float32)
+        bound = ctypes.c_float()
+        prm = params.c()
+        self._check(self.lib.cc_all_pairs_approx(self.h, ra, rb, ctypes.byref(prm),
+                                                 cmax.ctypes.data, cmin.ctypes.data,
+                                                 ctypes.byref(bound)))
+        return cmax, cmin, bound.value
+
     def bos_create(self, fid: int, rp_a, rp_b, pool=2048, per_round=32, rounds=30,
                    shortlist=128, kappa=0.5, objective=CC_MI_KSG, k=10, bins=16, seed=3,
                    field_b: int | None = None):

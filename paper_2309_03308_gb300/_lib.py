@@ -86,6 +86,7 @@ SIGNATURES = {
                                   _I, _P, _P]),
     "cc_all_pairs": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _P, _I64, _P]),
     "cc_all_pairs_topk": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _I, _P, _P, _P, _P]),
+    "cc_all_pairs_approx": (_S, [_P, _I32, _I32, ctypes.POINTER(cc_params), _P, _P, _P]),
     "cc_bos_create": (_S, [_P, _I32, _P, _P, _I, ctypes.POINTER(cc_bos_params),
                            ctypes.POINTER(_P)]),
     "cc_bos_create2": (_S, [_P, _I32, _I32, _P, _P, _I, ctypes.POINTER(cc_bos_params),

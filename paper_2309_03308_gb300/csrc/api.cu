@@ -1024,3 +1024,55 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
     if (info) *info = inf;
     return CC_OK;
 }
+
+extern "C" cc_status cc_all_pairs_approx(cc_ctx* ctx, int32_t region_a, int32_t region_b,
+                                         const cc_params* params, float* cmax, float* cmin,
+                                         float* bound) {
+    if (!ctx) return CC_ERR_INVALID_ARG;
+    Region* ra = get_region(ctx, region_a);
+    Region* rb = get_region(ctx, region_b);
+    if (!ra || !rb || !cmax || !cmin || !bound) return fail(ctx, CC_ERR_INVALID_ARG, "bad arguments");
+    Field& fa = *ctx->fields[ra->field];
+    Field& fb = *ctx->fields[rb->field];
+    if (fa.n != fb.n) return fail(ctx, CC_ERR_INVALID_ARG, "fields differ in member count");
+    cc_status s = check_params(ctx, params, fa.n, nullptr);
+    if (s) return s;
+    if (params->measure != CC_PEARSON && params->measure != CC_SPEARMAN)
+        return fail(ctx, CC_ERR_UNSUPPORTED, "reduced precision supports Pearson and Spearman");
+    if (params->precision != CC_BF16 && params->precision != CC_FP8_E4M3)
+        return fail(ctx, CC_ERR_INVALID_ARG, "precision must be CC_BF16 or CC_FP8_E4M3");
+    const bool fp8 = params->precision == CC_FP8_E4M3, sp = params->measure == CC_SPEARMAN;
+    const int self = region_a == region_b;
+    Region::QPlane *qa = nullptr, *qb = nullptr;
+    if ((s = ensure_qplane(ctx, *ra, sp, fp8, &qa))) return s;
+    if ((s = ensure_qplane(ctx, *rb, sp, fp8, &qb))) return s;
+    const int64_t na = ra->np, nb = rb->np, na_pad = qa->rows_pad, nb_pad = qb->rows_pad;
+    const int64_t N = (nb_pad / 32) * na_pad, chunks = (nb + 31) / 32;
+    CK(ctx->approx.ensure(8 * (size_t)N + 16));
+    float* dmax = ctx->approx.as<float>();
+    float* dmin = dmax + N;
+    unsigned* demax = reinterpret_cast<unsigned*>(dmin + N);
+    cudaStream_t st = ctx->stream;
+    const bool exact = rank_exact(sp, fp8, fa.n);
+    CK(launch_tc_chunk_extremes(fp8, fp8 || exact, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad,
+                                qa->kbytes, self, qa->inv.as<float>(), qb->inv.as<float>(), dmax,
+                                dmin, ctx->status.as<int>(), st));
+    CK(cudaMemcpyAsync(demax, qa->emax.p, 4, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(demax + 1, qb->emax.p, 4, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpy2DAsync(cmax, sizeof(float) * na, dmax, sizeof(float) * na_pad,
+                         sizeof(float) * na, chunks, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpy2DAsync(cmin, sizeof(float) * na, dmin, sizeof(float) * na_pad,
+                         sizeof(float) * na, chunks, cudaMemcpyDeviceToHost, st));
+    unsigned eb[2] = {0, 0};
+    CK(cudaMemcpyAsync(eb, demax, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((s = take_status(ctx))) return s;
+    // the bound of the certified path (cc_all_pairs_topk), same arithmetic
+    float ea, eb2;
+    memcpy(&ea, &eb[0], 4);
+    memcpy(&eb2, &eb[1], 4);
+    const float e = exact ? 0.f : std::max(ea, eb2);
+    const float acc_rel = exact ? 1.f / 4194304.f : 1.f / 4096.f;
+    *bound = 2.f * e + e * e + (1.f + e) * (1.f + e) * acc_rel + 1e-6f;
+    return CC_OK;
+}

@@ -108,6 +108,7 @@ struct cc_ctx {
     cc::DevMem status;  // int device status word
     // scratch
     cc::DevMem pair_a, pair_b, vals_out, partials, rp_out, ksg_nx, ksg_ny, ksg_eps, mixed;
+    cc::DevMem approx;  // chunk extremes exported by cc_all_pairs_approx
     std::map<int, std::unique_ptr<cc::DevMem>> psi_fix;   // n -> int64 [n+1]
     std::map<int, std::unique_ptr<cc::DevMem>> clogc_fix; // n -> int64 [n+1]
     // host-to-device copies of an update overlap its ingest: a second stream

@@ -270,17 +270,32 @@ __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n
     }
     int L = s - (k + 1) / 2 - 1, R = s + k / 2 + 1;
     while (true) {
-        const float2 l0 = W[L], l1 = W[L - 1], r0 = W[R], r1 = W[R + 1];
-        const float al0 = __fsub_rn(pv, l0.x), al1 = __fsub_rn(pv, l1.x);
-        const float ar0 = __fsub_rn(r0.x, pv), ar1 = __fsub_rn(r1.x, pv);
+        // a side is open while its next axis distance is below the k-th
+        // value; a step offers two positions per open side, or four from
+        // the only open side (a walk near either end of the sorted order
+        // then takes half the steps). Offered positions: L, L-1 (or R+2,
+        // R+3 when the left side is closed) and R, R+1 (or L-2, L-3 when
+        // the right side is closed); an open left side has L >= 0 and an
+        // open right side R <= n - 1, so every index stays within the
+        // sentinels.
         const float kth = top[KMAX - 1];
-        if (!(fminf(al0, ar0) < kth)) break;
-        const float d0 = fmaxf(al0, fabsf(__fsub_rn(ov, l0.y)));
-        const float d1 = fmaxf(al1, fabsf(__fsub_rn(ov, l1.y)));
-        const float d2 = fmaxf(ar0, fabsf(__fsub_rn(ov, r0.y)));
-        const float d3 = fmaxf(ar1, fabsf(__fsub_rn(ov, r1.y)));
-        L -= (int)(al0 < kth) + (int)(al1 < kth);
-        R += (int)(ar0 < kth) + (int)(ar1 < kth);
+        const bool lo = __fsub_rn(pv, W[L].x) < kth;
+        const bool ro = __fsub_rn(W[R].x, pv) < kth;
+        if (!(lo || ro)) break;
+        const float2 z0 = W[lo ? L : R + 2], z1 = W[lo ? L - 1 : R + 3];
+        const float2 z2 = W[ro ? R : L - 2], z3 = W[ro ? R + 1 : L - 3];
+        const float a0 = fabsf(__fsub_rn(pv, z0.x)), a1 = fabsf(__fsub_rn(pv, z1.x));
+        const float a2 = fabsf(__fsub_rn(pv, z2.x)), a3 = fabsf(__fsub_rn(pv, z3.x));
+        const float d0 = fmaxf(a0, fabsf(__fsub_rn(ov, z0.y)));
+        const float d1 = fmaxf(a1, fabsf(__fsub_rn(ov, z1.y)));
+        const float d2 = fmaxf(a2, fabsf(__fsub_rn(ov, z2.y)));
+        const float d3 = fmaxf(a3, fabsf(__fsub_rn(ov, z3.y)));
+        // positions are passed in order of axis distance on each side, so
+        // the passed ones of z0, z1 and of z2, z3 are prefixes
+        const int c01 = (int)(a0 < kth) + (int)(a1 < kth);
+        const int c23 = (int)(a2 < kth) + (int)(a3 < kth);
+        L -= lo ? c01 + (ro ? 0 : c23) : 0;
+        R += ro ? c23 + (lo ? 0 : c01) : 0;
         topk_merge4<KMAX>(top, d0, d1, d2, d3);
     }
     const float eps = top[KMAX - 1];

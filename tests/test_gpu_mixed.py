@@ -7,6 +7,7 @@ import pytest
 
 import gen
 import oracle
+from gen import configs
 
 pytestmark = pytest.mark.gpu
 TOL_REFINED = 1e-6
@@ -146,3 +147,106 @@ def test_mixed_argument_errors(cc):
         cc.all_pairs_topk(r, r, Params(CC_MI_KSG, precision=CC_BF16))
     with pytest.raises(CCError):
         cc.all_pairs_topk(r, r, Params(CC_PEARSON))  # FP32 is not a reduced precision
+
+
+def chunk_extremes(full, na, nb):
+    """Per (32-column chunk, row) max and min of an [na][nb] value matrix, [chunks][na]."""
+    chunks = (nb + 31) // 32
+    pad = np.full((na, chunks * 32), np.nan)
+    pad[:, :nb] = full.reshape(na, nb)
+    v = pad.reshape(na, chunks, 32)
+    return np.nanmax(v, 2).T, np.nanmin(v, 2).T
+
+
+APPROX_CASES = [  # (n, box of field A, box of field B, region A, region B): |A| x |B|
+    (1000, (64, 64, 0, 89, 74, 4), (256, 160, 0, 291, 180, 1), (0, 0, 0, 25, 10, 4),
+     (0, 0, 0, 35, 20, 1)),                                                   # 1000 x 700
+    (100, (64, 64, 0, 96, 96, 2), (256, 160, 0, 288, 176, 1), (0, 0, 0, 32, 32, 2),
+     (0, 0, 0, 32, 16, 1)),                                                   # 2048 x 512
+]
+
+
+@pytest.mark.parametrize("case", range(len(APPROX_CASES)), ids=["n1000_1000x700", "n100_2048x512"])
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_approx_values_within_stated_bound(cc, orc, case, prec):
+    """Every approximate chunk extreme of the tensor-core contraction lies within
+    the certified bound of the FP64 oracle's chunk extreme (the bound is stated
+    for the fp32 planes; their own rounding adds < 1e-6)."""
+    from paper_2309_03308_gb300 import CC_BF16, CC_FP8_E4M3, CC_PEARSON, Params
+    p = {"bf16": CC_BF16, "fp8": CC_FP8_E4M3}[prec]
+    n, bxa, bxb, rga, rgb = APPROX_CASES[case]
+    Fa, Fb = two_fields(n, bxa, bxb)
+    fa, fb = cc.load_field(Fa), cc.load_field(Fb)
+    (ra,) = cc.define_regions(fa, [rga])
+    (rb,) = cc.define_regions(fb, [rgb])
+    na, nb = Fa[0].size, Fb[0].size
+    full = all_values(orc, oracle.PEARSON, Fa, Fb)
+    cmax, cmin, bound = cc.all_pairs_approx(ra, rb, Params(CC_PEARSON, precision=p))
+    emax, emin = chunk_extremes(full, na, nb)
+    err = np.maximum(np.abs(cmax - emax), np.abs(cmin - emin))
+    print(f"n={n} {prec}: observed max {err.max():.3e} mean {err.mean():.3e} bound {bound:.3e}")
+    assert err.max() <= bound + 1e-6, (err.max(), bound)
+    # the bound is the one the certified path uses, and is not vacuous
+    _, _, _, cert = cc.all_pairs_topk(ra, rb, Params(CC_PEARSON, precision=p), topk=0)
+    assert abs(cert["bound"] - bound) <= 1e-6 * bound
+    assert bound < (0.02 if prec == "bf16" else 0.2)
+    cc.free_field(fa)
+    cc.free_field(fb)
+
+
+def test_approx_self_pair_masks_excluded_pairs(cc, orc):
+    """A self region pair: chunk entries with no pair b > a are -inf / +inf and
+    the rest lie within the bound of the oracle's extremes over b > a."""
+    from paper_2309_03308_gb300 import CC_BF16, CC_PEARSON, Params
+    Fa = gen.field(2, 352, 256, 20, 100, box=(100, 100, 0, 132, 116, 2))  # 1024 points
+    fa = cc.load_field(Fa)
+    (ra,) = cc.define_regions(fa, [(0, 0, 0, 32, 16, 2)])
+    full = all_values(orc, oracle.PEARSON, Fa, Fa).reshape(1024, 1024)
+    full = np.where(np.triu(np.ones((1024, 1024), bool), 1), full, np.nan)
+    cmax, cmin, bound = cc.all_pairs_approx(ra, ra, Params(CC_PEARSON, precision=CC_BF16))
+    with np.errstate(all="ignore"):
+        import warnings
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", RuntimeWarning)
+            emax, emin = chunk_extremes(full.ravel(), 1024, 1024)
+    empty = np.isnan(emax)
+    assert np.all(cmax[empty] == -np.inf) and np.all(cmin[empty] == np.inf)
+    assert np.abs(cmax[~empty] - emax[~empty]).max() <= bound + 1e-6
+    assert np.abs(cmin[~empty] - emin[~empty]).max() <= bound + 1e-6
+    cc.free_field(fa)
+
+
+def test_focus_full_size_bf16_certified_against_oracle(cc, orc):
+    """The certified BF16 path on the full 20,480 x 20,480 focus region pair:
+    the reported maximum, minimum and the sorted top 4096 are exact FP64 values
+    of the reported pairs (within the compensated-fp32 tolerance), and no pair
+    of a 100,000-pair uniform sample exceeds them."""
+    from paper_2309_03308_gb300 import CC_BF16, CC_PEARSON, Params
+    c = configs.FOCUS
+    F = gen.field(c["seed"], c["X"], c["Y"], c["Z"], c["n"])
+    fid = cc.load_field(F)
+    ra, rb = cc.define_regions(fid, [c["box_a"], c["box_b"]])
+    A = oracle.box_points(c["X"], c["Y"], c["Z"], c["box_a"])
+    B = oracle.box_points(c["X"], c["Y"], c["Z"], c["box_b"])
+    res, ids, vals, cert = cc.all_pairs_topk(ra, rb, Params(CC_PEARSON, precision=CC_BF16),
+                                             topk=4096)
+    assert cert["certified_max"] == 1 and cert["certified_min"] == 1, cert
+    assert res["count"] == len(A) * len(B)
+    ia, ib = np.divmod(ids.astype(np.int64), len(B))
+    top = orc.eval_pairs(F, oracle.PEARSON, A[ia], B[ib])
+    assert np.abs(top - vals).max() < TOL_REFINED
+    assert np.all(np.diff(vals) <= 0) and vals[0] == res["max"]
+    a, b = divmod(res["argmax"], len(B))
+    a2, b2 = divmod(res["argmin"], len(B))
+    e = orc.eval_pairs(F, oracle.PEARSON, np.array([A[a], A[a2]]), np.array([B[b], B[b2]]))
+    assert abs(e[0] - res["max"]) < TOL_REFINED and abs(e[1] - res["min"]) < TOL_REFINED
+    rng = np.random.default_rng(12)
+    sa = rng.integers(0, len(A), 100000)
+    sb = rng.integers(0, len(B), 100000)
+    ref = orc.eval_pairs(F, oracle.PEARSON, A[sa], B[sb])
+    assert ref.max() <= res["max"] + TOL_REFINED and ref.min() >= res["min"] - TOL_REFINED
+    # sampled pairs above the list's last value are in the list
+    above = ref > vals[-1] + 2 * cert["bound"]
+    listed = set((ia * len(B) + ib).tolist())
+    assert all(int(x) in listed for x in (sa[above] * len(B) + sb[above]))
+    cc.free_field(fid)
