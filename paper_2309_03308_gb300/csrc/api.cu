@@ -898,42 +898,35 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    // per side: the record that the host reads once at the end
-    struct SideOut {
-        Select sel;               // first and second pass counts, overflow, threshold
-        unsigned pad;
-        unsigned long long best;  // (key of best value, inverted pair index)
-        float thr[2];             // second-pass threshold, bound
-    };
-    const size_t o_cmax = take(4 * N), o_cmin = take(4 * N), o_hist = take(4 * 4096),
-                 o_sel = take(sizeof(Select) * 2), o_best = take(8), o_thr = take(8),
-                 o_ids = take(4ull * cap), o_vals = take(4ull * cap * 32),
-                 o_pids = take(8ull * cap * 32), o_sidx = take(4 * 8192), o_tv = take(4 * 4096),
-                 o_ti = take(8 * 4096), o_sk = take(8 * 8192), o_out = take(sizeof(SideOut) * 2);
+    // scratch arena; the 2 x 4096 histogram bins, the two side records and the
+    // top-K selection state are contiguous so one memset clears them
+    const size_t o_hist = take(4 * 2 * 4096 + sizeof(SideState) * 2 + sizeof(Select));
+    const size_t o_cmax = take(4 * N), o_cmin = take(4 * N), o_ids = take(2 * 4ull * cap),
+                 o_vals = take(2 * 4ull * cap * 32), o_pids = take(2 * 8ull * cap * 32),
+                 o_sidx = take(4 * 8192), o_tv = take(4 * 4096), o_ti = take(8 * 4096),
+                 o_sk = take(8 * 8192);
     CK(ctx->mixed.ensure(off));
     unsigned char* base = ctx->mixed.as<unsigned char>();
     float* cmax = (float*)(base + o_cmax);
     float* cmin = (float*)(base + o_cmin);
     unsigned* hist = (unsigned*)(base + o_hist);
-    Select* sel = (Select*)(base + o_sel);
-    unsigned long long* best = (unsigned long long*)(base + o_best);
-    float* thr = (float*)(base + o_thr);  // [threshold, bound]
+    SideState* ss = (SideState*)(hist + 2 * 4096);
+    Select* topsel = (Select*)(ss + 2);
     uint32_t* cids = (uint32_t*)(base + o_ids);
     float* rvals = (float*)(base + o_vals);
     unsigned long long* rpids = (unsigned long long*)(base + o_pids);
     uint32_t* sidx = (uint32_t*)(base + o_sidx);
     float* tvals = (float*)(base + o_tv);
     unsigned long long* tids = (unsigned long long*)(base + o_ti);
-    SideOut* dout = (SideOut*)(base + o_out);
     cudaStream_t st = ctx->stream;
     const bool exact = rank_exact(sp, fp8, fa.n);
     const float* plane_a = sp ? fa.rhat.as<float>() : fa.zhat.as<float>();
     const float* plane_b = sp ? fb.rhat.as<float>() : fb.zhat.as<float>();
-    // The device work below is ~30 small launches; it is captured once into a
-    // CUDA graph per distinct set of buffers and sizes and replayed, so the
-    // GPU runs the launches back to back instead of waiting on the host.
-    // Every pointer and scalar the launches take is part of the key, so a
-    // replay does exactly what a fresh enqueue would.
+    // The device work below is ~20 launches; it is captured once into a CUDA
+    // graph per distinct set of buffers and sizes and replayed, so the GPU
+    // runs the launches back to back instead of waiting on the host. Every
+    // pointer and scalar the launches take is part of the key, so a replay
+    // does exactly what a fresh enqueue would.
     const std::vector<uint64_t> key = {
         (uint64_t)(uintptr_t)qa->q.p, (uint64_t)(uintptr_t)qb->q.p,
         (uint64_t)(uintptr_t)qa->inv.p, (uint64_t)(uintptr_t)qb->inv.p,
@@ -950,7 +943,7 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
         if (_e != cudaSuccess) return _e;       \
     } while (0)
     auto enqueue = [&]() -> cudaError_t {
-        EK(cudaMemsetAsync(hist, 0, 4 * 4096, st));
+        EK(cudaMemsetAsync(hist, 0, 4 * 2 * 4096 + sizeof(SideState) * 2 + sizeof(Select), st));
         EK(launch_tc_chunk_extremes(fp8, fp8 || exact, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad,
                                     qa->kbytes, self, qa->inv.as<float>(), qb->inv.as<float>(), cmax,
                                     cmin, ctx->status.as<int>(), st));
@@ -958,41 +951,34 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
         // FP32 accumulation (2^-12, conservative), or for exact integer ranks the
         // two fp32 scalings of the epilogue (2^-22 covers them)
         const float acc_rel = exact ? 1.f / 4194304.f : 1.f / 4096.f;
-        // Both passes are decided on the device (no host round trip): the second
-        // compaction appends the chunks in [r* - B, first threshold) after the
-        // first pass's, unless the first pass took every chunk or overflowed.
-        for (int side = 0; side < 2; ++side) {
-            const float sign = side == 0 ? 1.f : -1.f;
-            const float* v = side == 0 ? cmax : cmin;
-            EK(cudaMemsetAsync(sel, 0, sizeof(Select) * 2, st));
-            EK(cudaMemsetAsync(best, 0, 8, st));
-            const unsigned want = side == 0 ? (unsigned)std::max(topk, 256) : 256u;
-            EK(launch_select_top(v, N, sign, want, hist, sel, cids, cap, st));
-            EK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
-                                    rb->pts.as<uint32_t>(), nb, self, na_pad, cids, nullptr,
-                                    &sel->count, cap, sign, rvals, rpids, best, st));
-            EK(launch_second_threshold(best, qa->emax.as<unsigned>(), qb->emax.as<unsigned>(),
-                                       acc_rel, sel, thr, st));
-            EK(launch_compact_second(v, N, sign, thr, sel, cids, cap, st));
-            EK(launch_refine_chunks(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
-                                    rb->pts.as<uint32_t>(), nb, self, na_pad, cids, &sel->pass1,
-                                    &sel->count, cap, sign, rvals, rpids, best, st));
-            if (side == 0 && topk > 0) {  // top-K of every refined value
-                EK(launch_select_top(rvals, (int64_t)cap * 32, 1.f, (unsigned)topk, hist, sel + 1,
-                                     sidx, 8192, st, &sel->count));
-                EK(launch_sort_top(rvals, rpids, sidx, &sel[1].count, 8192, 1.f, topk, tvals, tids,
-                                   (unsigned long long*)(base + o_sk), st));
-            }
-            EK(cudaMemcpyAsync(&dout[side].sel, sel, sizeof(Select), cudaMemcpyDeviceToDevice, st));
-            EK(cudaMemcpyAsync(&dout[side].best, best, 8, cudaMemcpyDeviceToDevice, st));
-            EK(cudaMemcpyAsync(dout[side].thr, thr, 8, cudaMemcpyDeviceToDevice, st));
+        // Both sides (maximum: keys of cmax; minimum: keys of -cmin) share every
+        // launch. Both passes are decided on the device (no host round trip):
+        // the second compaction appends the chunks in [r* - B, first threshold)
+        // after the first pass's, unless the first pass took every chunk or
+        // overflowed.
+        EK(launch_select_top2(cmax, cmin, N, (unsigned)std::max(topk, 256), 256u, hist, ss, cids,
+                              cap, st));
+        EK(launch_refine_chunks2(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
+                                 rb->pts.as<uint32_t>(), nb, self, na_pad, cids, cap, ss, true,
+                                 rvals, rpids, fp8, st));
+        EK(launch_second_threshold2(ss, qa->emax.as<unsigned>(), qb->emax.as<unsigned>(), acc_rel,
+                                    st));
+        EK(launch_compact_second2(cmax, cmin, N, ss, cids, cap, st));
+        EK(launch_refine_chunks2(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
+                                 rb->pts.as<uint32_t>(), nb, self, na_pad, cids, cap, ss, false,
+                                 rvals, rpids, fp8, st));
+        if (topk > 0) {  // top-K of every refined value of the maximum side
+            EK(launch_select_top(rvals, (int64_t)cap * 32, 1.f, (unsigned)topk, hist, topsel, sidx,
+                                 8192, st, &ss[0].sel.count));
+            EK(launch_sort_top(rvals, rpids, sidx, &topsel->count, 8192, 1.f, topk, tvals, tids,
+                               (unsigned long long*)(base + o_sk), st));
         }
         return cudaSuccess;
     };
 #undef EK
     CK(run_cached_graph(ctx, ctx->topk_graphs, key, enqueue));
-    SideOut hout[2];
-    CK(cudaMemcpyAsync(hout, dout, sizeof hout, cudaMemcpyDeviceToHost, st));
+    SideState hout[2];
+    CK(cudaMemcpyAsync(hout, ss, sizeof hout, cudaMemcpyDeviceToHost, st));
     if (topk > 0) {
         CK(cudaMemcpyAsync(vals, tvals, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ids, tids, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
@@ -1003,7 +989,7 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
     float ext_val[2] = {-INFINITY, -INFINITY};
     uint64_t ext_id[2] = {~0ull, ~0ull};
     for (int side = 0; side < 2; ++side) {
-        const SideOut& o = hout[side];
+        const SideState& o = hout[side];
         const bool certified = o.sel.overflow == 0;  // both passes fit (or pass 1 took all)
         if (o.best != 0) {
             ext_val[side] = unorder_key((unsigned)(o.best >> 32));

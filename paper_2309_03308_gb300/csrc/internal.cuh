@@ -196,6 +196,14 @@ struct Select {
     unsigned overflow;   // candidates beyond capacity
     unsigned pass1;      // candidates of the first pass (the second appends after them)
 };
+// Device record of one extreme side of a certified all-pairs call, read back
+// by the host once at the end.
+struct SideState {
+    Select sel;               // first and second pass counts, overflow, threshold
+    unsigned pad;
+    unsigned long long best;  // (key of best value, inverted pair index)
+    float thr[2];             // second-pass threshold, bound
+};
 cudaError_t launch_sur_screen_tc(const float* Ea, const float* Ua, const float* Eb,
                                  const void* wb, const float* w, int64_t oW3, int64_t ow4,
                                  int64_t ob4, const uint32_t* pts_a, const uint32_t* pts_b,
@@ -215,17 +223,25 @@ cudaError_t launch_quantize_ranks(const int16_t* rank2, int n_pad, int n, const 
 cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned want,
                               unsigned* hist, Select* sel, uint32_t* out, unsigned cap,
                               cudaStream_t st, const unsigned* nchunks = nullptr);
-cudaError_t launch_compact_second(const float* v, int64_t N, float sign, const float* lo_val,
-                                  Select* sel, uint32_t* out, unsigned cap, cudaStream_t st);
-cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int n_pad, int n,
-                                 const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
-                                 int64_t nb, int self, int64_t na_pad, const uint32_t* ids,
-                                 const unsigned* start, const unsigned* count, unsigned cap,
-                                 float sign, float* vals, unsigned long long* pair_ids,
-                                 unsigned long long* best, cudaStream_t st);
-cudaError_t launch_second_threshold(const unsigned long long* best, const unsigned* emax_a,
-                                    const unsigned* emax_b, float acc_rel, Select* sel,
-                                    float* thr, cudaStream_t st);
+// Both extreme sides at once: keys of +v0 (side 0) and -v1 (side 1); side s
+// selects at least want_s chunk ids into out + s * cap using ss[s].sel; hist
+// holds 2 x 4096 zeroed bins.
+cudaError_t launch_select_top2(const float* v0, const float* v1, int64_t N, unsigned want0,
+                               unsigned want1, unsigned* hist, SideState* ss, uint32_t* out,
+                               unsigned cap, cudaStream_t st);
+// second compaction of both sides (keys in [thr_s, first threshold))
+cudaError_t launch_compact_second2(const float* v0, const float* v1, int64_t N, SideState* ss,
+                                   uint32_t* out, unsigned cap, cudaStream_t st);
+// Dot2 refinement of the candidate chunks of both sides (first_pass: every
+// id from 0, else the ids the second compaction appended); wide: a loose
+// bound (FP8), more blocks per side.
+cudaError_t launch_refine_chunks2(const float* plane_a, const float* plane_b, int n_pad, int n,
+                                  const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
+                                  int64_t nb, int self, int64_t na_pad, const uint32_t* ids,
+                                  unsigned cap, SideState* ss, bool first_pass, float* vals,
+                                  unsigned long long* pair_ids, bool wide, cudaStream_t st);
+cudaError_t launch_second_threshold2(SideState* ss, const unsigned* emax_a,
+                                     const unsigned* emax_b, float acc_rel, cudaStream_t st);
 // top-k (<= 8192) of up to 8192 selected entries, sorted descending by value,
 // then by smallest id; scratch holds 8192 64-bit keys
 cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,

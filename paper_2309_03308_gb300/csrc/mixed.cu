@@ -121,35 +121,71 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// 3a. two-pass histogram select on order-preserving keys of sign * value.
-// Pass `level` 0 bins the top 12 bits, pass 1 the next 12 among keys whose
-// top 12 bits equal sel->prefix. Values of -inf (empty chunks) are skipped.
+// 3a. two-pass histogram select on order-preserving keys of sign * value,
+// for NS = 1 or 2 value arrays at once (the maximum and the minimum side of a
+// region pair share every pass). Pass `level` 0 bins the top 12 bits, pass 1
+// the next 12 among keys whose top 12 bits equal sel->prefix. Values of -inf
+// (empty chunks) are skipped. N is a multiple of 4 (read as float4).
+struct SideVals {
+    const float* v[2];
+    float sign[2];
+    Select* sel[2];
+    const float* lo_val[2];  // second compaction: the side's value threshold (else null)
+};
 
-__global__ void k_hist12(const float* __restrict__ v, int64_t N, float sign, int level,
-                         const Select* __restrict__ sel, unsigned* __restrict__ hist,
-                         const unsigned* __restrict__ nchunks) {
-    __shared__ unsigned h[4096];
+template <int NS>
+__global__ void __launch_bounds__(256)
+    k_hist12(SideVals sv, int64_t N, int level, unsigned* __restrict__ hist,
+             const unsigned* __restrict__ nchunks) {
+    __shared__ unsigned h[NS][4096];
     if (nchunks) N = min(N, (int64_t)*nchunks * 32);
-    for (int i = threadIdx.x; i < 4096; i += blockDim.x) h[i] = 0;
+    for (int i = threadIdx.x; i < NS * 4096; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    const unsigned prefix = level ? sel->prefix : 0u;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+    unsigned prefix[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) prefix[s] = level ? sv.sel[s]->prefix : 0u;
+    const int64_t N4 = N / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N4;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float x = sign * v[i];
-        if (!(x > -CUDART_INF_F)) continue;
-        const unsigned k = okey(x);
-        if (level == 0) atomicAdd(&h[k >> 20], 1u);
-        else if ((k >> 20) == prefix) atomicAdd(&h[(k >> 8) & 0xfffu], 1u);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const float4 q = reinterpret_cast<const float4*>(sv.v[s])[i];
+            const float w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float x = sv.sign[s] * w[j];
+                if (!(x > -CUDART_INF_F)) continue;
+                const unsigned k = okey(x);
+                if (level == 0) atomicAdd(&h[s][k >> 20], 1u);
+                else if ((k >> 20) == prefix[s]) atomicAdd(&h[s][(k >> 8) & 0xfffu], 1u);
+            }
+        }
+    }
+    // the last N % 4 values
+    for (int64_t i = 4 * N4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const float x = sv.sign[s] * sv.v[s][i];
+            if (!(x > -CUDART_INF_F)) continue;
+            const unsigned k = okey(x);
+            if (level == 0) atomicAdd(&h[s][k >> 20], 1u);
+            else if ((k >> 20) == prefix[s]) atomicAdd(&h[s][(k >> 8) & 0xfffu], 1u);
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 4096; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[i], h[i]);
+    for (int i = threadIdx.x; i < NS * 4096; i += blockDim.x)
+        if ((&h[0][0])[i]) atomicAdd(&hist[i], (&h[0][0])[i]);
 }
 
-// One block: scan the 4096 bins from the top until `want` keys are covered.
-__global__ void k_pick_bin(unsigned* __restrict__ hist, int level, unsigned want,
-                           Select* __restrict__ sel) {
+// One block per side: scan the side's 4096 bins from the top until `want`
+// keys are covered.
+__global__ void k_pick_bin(unsigned* __restrict__ hist_all, int level, unsigned want0,
+                           unsigned want1, SideVals sv) {
     __shared__ unsigned part[1024];
+    unsigned* hist = hist_all + 4096 * blockIdx.x;
+    Select* sel = sv.sel[blockIdx.x];
+    const unsigned want = blockIdx.x ? want1 : want0;
     // bins are scanned in descending order: thread t owns bins 4095-4t .. 4092-4t
     const int t = threadIdx.x;
     unsigned s = 0;
@@ -188,34 +224,60 @@ __global__ void k_pick_bin(unsigned* __restrict__ hist, int level, unsigned want
     for (int i = t; i < 4096; i += 1024) hist[i] = 0;  // ready for the next pass
 }
 
-// 3b. compact chunk ids whose key lies in [lo_key, hi_key) (hi_key 0 = no cap).
-// First pass (lo_val null): keys >= sel->threshold. Second pass: keys in
-// [okey(*lo_val), sel->threshold), appended after the first pass's; skipped
-// when the first pass took every key (threshold 0) or overflowed.
-__global__ void k_compact(const float* __restrict__ v, int64_t N, float sign,
-                          const Select* __restrict__ sel, const float* __restrict__ lo_val,
-                          uint32_t* __restrict__ out, unsigned cap, unsigned* __restrict__ count,
-                          unsigned* __restrict__ ovf, const unsigned* __restrict__ nchunks) {
+// 3b. compact chunk ids whose key lies in [lo_key, hi_key) (hi_key 0 = no cap)
+// into out + s * cap for every side s. First pass (lo_val null): keys >=
+// sel->threshold. Second pass: keys in [okey(*lo_val), sel->threshold),
+// appended after the first pass's; skipped for a side whose first pass took
+// every key (threshold 0) or overflowed.
+template <int NS>
+__global__ void __launch_bounds__(256)
+    k_compact(SideVals sv, int64_t N, uint32_t* __restrict__ out, unsigned cap,
+              const unsigned* __restrict__ nchunks) {
     if (nchunks) N = min(N, (int64_t)*nchunks * 32);
-    if (lo_val && (sel->threshold == 0u || sel->overflow)) return;
-    const unsigned lo = lo_val ? okey(*lo_val) : sel->threshold;
-    const unsigned hi = lo_val ? sel->threshold : 0u;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float x = sign * v[i];
-        if (!(x > -CUDART_INF_F)) continue;
+    unsigned lo[NS], hi[NS];
+    bool on[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const Select* sel = sv.sel[s];
+        const float* thr = sv.lo_val[s];
+        on[s] = !(thr && (sel->threshold == 0u || sel->overflow));
+        lo[s] = thr ? okey(*thr) : sel->threshold;
+        hi[s] = thr ? sel->threshold : 0u;
+    }
+    const int lane = threadIdx.x & 31;
+    auto offer = [&](int s, float w, int64_t idx) {
+        const float x = sv.sign[s] * w;
         const unsigned k = okey(x);
-        if (k >= lo && (hi == 0u || k < hi)) {
+        if (x > -CUDART_INF_F && k >= lo[s] && (hi[s] == 0u || k < hi[s])) {
             // one counter update per warp: the leader takes the warp's slots
             const unsigned m = __activemask();
-            const int leader = __ffs(m) - 1, lane = threadIdx.x & 31;
+            const int leader = __ffs(m) - 1;
             unsigned base = 0;
-            if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+            if (lane == leader) base = atomicAdd(&sv.sel[s]->count, (unsigned)__popc(m));
             base = __shfl_sync(m, base, leader);
             const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
-            if (slot < cap) out[slot] = (uint32_t)i;
-            else atomicAdd(ovf, 1u);
+            if (slot < cap) out[(size_t)s * cap + slot] = (uint32_t)idx;
+            else atomicAdd(&sv.sel[s]->overflow, 1u);
         }
+    };
+    const int64_t N4 = N / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (!on[s]) continue;
+            const float4 q = reinterpret_cast<const float4*>(sv.v[s])[i];
+            offer(s, q.x, 4 * i);
+            offer(s, q.y, 4 * i + 1);
+            offer(s, q.z, 4 * i + 2);
+            offer(s, q.w, 4 * i + 3);
+        }
+    }
+    for (int64_t i = 4 * N4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (on[s]) offer(s, sv.v[s][i], i);
     }
 }
 
@@ -260,15 +322,36 @@ __device__ __forceinline__ float dot2_warp(const float (&x)[R], const float* __r
 // members at a time, coalesced, into a transposed shared-memory tile (rows
 // padded to 33 words), and row a's member is broadcast from the lane that
 // holds it, so a chunk costs one pass over its rows and no reductions.
+// The chunks of one side (blockIdx.y) of the refinement: candidate ids,
+// where this pass's ids start (null: 0) and end, the sign of the side, and
+// where the refined values, pair ids and the best key go.
+struct RefineSide {
+    const uint32_t* ids;
+    const unsigned* start;
+    const unsigned* count;
+    float sign;
+    float* vals;
+    unsigned long long* pair_ids;
+    unsigned long long* best;
+};
+struct RefineArgs {
+    RefineSide s[2];
+};
+
 template <int R>
 __global__ void __launch_bounds__(256)
     k_refine_chunks(const float* __restrict__ plane_a, const float* __restrict__ plane_b,
                     int n_pad, int n, const uint32_t* __restrict__ pts_a, int64_t na,
                     const uint32_t* __restrict__ pts_b, int64_t nb, int self, int64_t na_pad,
-                    const uint32_t* __restrict__ ids, const unsigned* __restrict__ start_p,
-                    const unsigned* __restrict__ count_p, unsigned cap, float sign,
-                    float* __restrict__ vals, unsigned long long* __restrict__ pair_ids,
-                    unsigned long long* __restrict__ best) {
+                    unsigned cap, RefineArgs args) {
+    const RefineSide& rs = args.s[blockIdx.y];
+    const uint32_t* __restrict__ ids = rs.ids;
+    const unsigned* __restrict__ start_p = rs.start;
+    const unsigned* __restrict__ count_p = rs.count;
+    const float sign = rs.sign;
+    float* __restrict__ vals = rs.vals;
+    unsigned long long* __restrict__ pair_ids = rs.pair_ids;
+    unsigned long long* __restrict__ best = rs.best;
     __shared__ float tile[8][32][33];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float (*T)[33] = tile[wib];
@@ -350,11 +433,15 @@ __global__ void __launch_bounds__(256)
     k_refine_chunks_warp(const float* __restrict__ plane_a, const float* __restrict__ plane_b,
                          int n_pad, int n, const uint32_t* __restrict__ pts_a, int64_t na,
                          const uint32_t* __restrict__ pts_b, int64_t nb, int self,
-                         int64_t na_pad, const uint32_t* __restrict__ ids,
-                         const unsigned* __restrict__ start_p, const unsigned* __restrict__ count_p,
-                         unsigned cap, float sign, float* __restrict__ vals,
-                         unsigned long long* __restrict__ pair_ids,
-                         unsigned long long* __restrict__ best) {
+                         int64_t na_pad, unsigned cap, RefineArgs args) {
+    const RefineSide& rs = args.s[blockIdx.y];
+    const uint32_t* __restrict__ ids = rs.ids;
+    const unsigned* __restrict__ start_p = rs.start;
+    const unsigned* __restrict__ count_p = rs.count;
+    const float sign = rs.sign;
+    float* __restrict__ vals = rs.vals;
+    unsigned long long* __restrict__ pair_ids = rs.pair_ids;
+    unsigned long long* __restrict__ best = rs.best;
     const int lane = threadIdx.x & 31;
     const unsigned count = min(*count_p, cap);
     const unsigned start = start_p ? min(*start_p, cap) : 0u;
@@ -397,17 +484,18 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// r* - B as a value threshold for the second pass (sign-adjusted domain);
-// records where the first pass's candidates end.
-__global__ void k_second_threshold(const unsigned long long* best, const unsigned* emax_a,
-                                   const unsigned* emax_b, float acc_rel, Select* sel,
-                                   float* thr) {
+// r* - B as a value threshold for the second pass (sign-adjusted domain) of
+// each side; records where the first pass's candidates end.
+__global__ void k_second_threshold(SideState* ss, int nsides, const unsigned* emax_a,
+                                   const unsigned* emax_b, float acc_rel) {
     const float e = fmaxf(__uint_as_float(*emax_a), __uint_as_float(*emax_b));
     const float B = 2.f * e + e * e + (1.f + e) * (1.f + e) * acc_rel + 1e-6f;
-    const float rstar = okey_inv((unsigned)(*best >> 32));
-    thr[0] = rstar - B;
-    thr[1] = B;
-    sel->pass1 = sel->count;
+    for (int s = 0; s < nsides; ++s) {
+        const float rstar = okey_inv((unsigned)(ss[s].best >> 32));
+        ss[s].thr[0] = rstar - B;
+        ss[s].thr[1] = B;
+        ss[s].sel.pass1 = ss[s].sel.count;
+    }
 }
 
 // 5. top-K of up to 8192 (value, pair) entries taken from the compacted
@@ -566,34 +654,78 @@ static unsigned grid_for(int64_t N, int per_block) {
 cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned want,
                               unsigned* hist, Select* sel, uint32_t* out, unsigned cap,
                               cudaStream_t st, const unsigned* nchunks) {
+    SideVals sv{};
+    sv.v[0] = sv.v[1] = v;
+    sv.sign[0] = sv.sign[1] = sign;
+    sv.sel[0] = sv.sel[1] = sel;
     note_launch(5);
-    k_hist12<<<grid_for(N, 256 * 16), 256, 0, st>>>(v, N, sign, 0, sel, hist, nchunks);
-    k_pick_bin<<<1, 1024, 0, st>>>(hist, 0, want, sel);
-    k_hist12<<<grid_for(N, 256 * 16), 256, 0, st>>>(v, N, sign, 1, sel, hist, nchunks);
-    k_pick_bin<<<1, 1024, 0, st>>>(hist, 1, want, sel);
-    k_compact<<<grid_for(N, 256 * 8), 256, 0, st>>>(v, N, sign, sel, nullptr, out, cap,
-                                                    &sel->count, &sel->overflow, nchunks);
+    k_hist12<1><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 0, hist, nchunks);
+    k_pick_bin<<<1, 1024, 0, st>>>(hist, 0, want, want, sv);
+    k_hist12<1><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 1, hist, nchunks);
+    k_pick_bin<<<1, 1024, 0, st>>>(hist, 1, want, want, sv);
+    k_compact<1><<<grid_for(N, 256 * 8), 256, 0, st>>>(sv, N, out, cap, nchunks);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_second(const float* v, int64_t N, float sign, const float* lo_val,
-                                  Select* sel, uint32_t* out, unsigned cap, cudaStream_t st) {
-    note_launch();
-    k_compact<<<grid_for(N, 256 * 8), 256, 0, st>>>(v, N, sign, sel, lo_val, out, cap,
-                                                    &sel->count, &sel->overflow, nullptr);
+static SideVals two_sides(const float* v0, const float* v1, SideState* ss) {
+    SideVals sv{};
+    sv.v[0] = v0;
+    sv.v[1] = v1;
+    sv.sign[0] = 1.f;
+    sv.sign[1] = -1.f;
+    sv.sel[0] = &ss[0].sel;
+    sv.sel[1] = &ss[1].sel;
+    return sv;
+}
+
+cudaError_t launch_select_top2(const float* v0, const float* v1, int64_t N, unsigned want0,
+                               unsigned want1, unsigned* hist, SideState* ss, uint32_t* out,
+                               unsigned cap, cudaStream_t st) {
+    if (N % 4) return cudaErrorInvalidValue;
+    const SideVals sv = two_sides(v0, v1, ss);
+    note_launch(5);
+    k_hist12<2><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 0, hist, nullptr);
+    k_pick_bin<<<2, 1024, 0, st>>>(hist, 0, want0, want1, sv);
+    k_hist12<2><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 1, hist, nullptr);
+    k_pick_bin<<<2, 1024, 0, st>>>(hist, 1, want0, want1, sv);
+    k_compact<2><<<grid_for(N, 256 * 8), 256, 0, st>>>(sv, N, out, cap, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int n_pad, int n,
-                                 const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
-                                 int64_t nb, int self, int64_t na_pad, const uint32_t* ids,
-                                 const unsigned* start, const unsigned* count, unsigned cap,
-                                 float sign, float* vals, unsigned long long* pair_ids,
-                                 unsigned long long* best, cudaStream_t st) {
+cudaError_t launch_compact_second2(const float* v0, const float* v1, int64_t N, SideState* ss,
+                                   uint32_t* out, unsigned cap, cudaStream_t st) {
+    if (N % 4) return cudaErrorInvalidValue;
+    SideVals sv = two_sides(v0, v1, ss);
+    sv.lo_val[0] = &ss[0].thr[0];
+    sv.lo_val[1] = &ss[1].thr[0];
     note_launch();
-#define CC_REFINE(K, R)                                                                   \
-    K<R><<<sm_count() * 8, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, nb, self,  \
-                                  na_pad, ids, start, count, cap, sign, vals, pair_ids, best)
+    k_compact<2><<<grid_for(N, 256 * 8), 256, 0, st>>>(sv, N, out, cap, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_chunks2(const float* plane_a, const float* plane_b, int n_pad, int n,
+                                  const uint32_t* pts_a, int64_t na, const uint32_t* pts_b,
+                                  int64_t nb, int self, int64_t na_pad, const uint32_t* ids,
+                                  unsigned cap, SideState* ss, bool first_pass, float* vals,
+                                  unsigned long long* pair_ids, bool wide, cudaStream_t st) {
+    RefineArgs a{};
+    for (int s = 0; s < 2; ++s) {
+        a.s[s].ids = ids + (size_t)s * cap;
+        a.s[s].start = first_pass ? nullptr : &ss[s].sel.pass1;
+        a.s[s].count = &ss[s].sel.count;
+        a.s[s].sign = s ? -1.f : 1.f;
+        a.s[s].vals = vals + (size_t)s * cap * 32;
+        a.s[s].pair_ids = pair_ids + (size_t)s * cap * 32;
+        a.s[s].best = &ss[s].best;
+    }
+    note_launch();
+    // blocks per side: a loose bound (wide) refines millions of pairs, often on
+    // one side only; a tight one a few thousand chunks, where extra blocks only
+    // add scheduling
+    const dim3 grid((unsigned)sm_count() * (wide ? 8 : 4), 2);
+#define CC_REFINE(K, R)                                                                         \
+    K<R><<<grid, 256, 0, st>>>(plane_a, plane_b, n_pad, n, pts_a, na, pts_b, nb, self, na_pad, \
+                               cap, a)
     const int slices = (n + 31) / 32;
     if (slices <= 1) CC_REFINE(k_refine_chunks, 1);
     else if (slices <= 2) CC_REFINE(k_refine_chunks, 2);
@@ -605,11 +737,10 @@ cudaError_t launch_refine_chunks(const float* plane_a, const float* plane_b, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_second_threshold(const unsigned long long* best, const unsigned* emax_a,
-                                    const unsigned* emax_b, float acc_rel, Select* sel,
-                                    float* thr, cudaStream_t st) {
+cudaError_t launch_second_threshold2(SideState* ss, const unsigned* emax_a,
+                                     const unsigned* emax_b, float acc_rel, cudaStream_t st) {
     note_launch();
-    k_second_threshold<<<1, 1, 0, st>>>(best, emax_a, emax_b, acc_rel, sel, thr);
+    k_second_threshold<<<1, 1, 0, st>>>(ss, 2, emax_a, emax_b, acc_rel);
     return cudaGetLastError();
 }
 
