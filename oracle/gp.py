@@ -19,9 +19,17 @@ READINGS (the paper names the ingredients, not these settings):
     entries are picked greedily from it, each pick followed by the kriging
     believer update (the posterior covariance after observing the pick at its
     posterior mean: cov -= cov[:, c] cov[c, :] / (cov[c, c] + noise)).
+  * Local picks (a project reading, `local_picks` > 0): from the second round
+    on, the first `local_picks` proposals of a round are not taken from the
+    pool but perturb the two best observations so far (by objective value,
+    the earlier one on ties; proposal j uses incumbent j mod 2): theta =
+    clip(theta_inc + local_scale * extent * z, 0, extent - 1) per axis, z
+    standard normal (Box-Muller). They are evaluated, rounded and reduced like
+    every proposal and can become incumbents, but the GP is conditioned on the
+    pool proposals only.
   * Random numbers come from Philox4x64-10 through the oracle's own C
     implementation (`Oracle.philox`), with the counter layout documented in
-    `pool_positions` and `bernoulli_voxels`.
+    `pool_positions`, `bernoulli_voxels` and `local_theta`.
 This module is plain numpy in FP64; scipy's cho_factor/cho_solve serve as the
 Cholesky steps. Only tests and the benchmark's CPU leg may import it.
 """
@@ -71,6 +79,40 @@ def bernoulli_voxels(orc, seed: int, rp: int, rnd: int, j: int, theta: np.ndarra
     f = np.floor(th)
     frac = (th - f).astype(np.float32)
     return (f.astype(np.int64) + (u < frac)).astype(np.int64)
+
+
+def box_muller(words: np.ndarray) -> np.ndarray:
+    """Six standard normals from eight 64-bit words (FP64): for i = 0, 1, 2,
+    u1 = (top 24 bits of w[2i] + 1) / 2^24 in (0, 1], u2 = top 24 bits of
+    w[2i+1] / 2^24, z[2i] = sqrt(-2 ln u1) cos(2 pi u2), z[2i+1] = ... sin."""
+    w = np.asarray(words, np.uint64)
+    top = (w >> np.uint64(40)).astype(np.float64)
+    z = np.empty(6)
+    for i in range(3):
+        u1 = (top[2 * i] + 1.0) * 2.0 ** -24
+        u2 = top[2 * i + 1] * 2.0 ** -24
+        rad = math.sqrt(-2.0 * math.log(u1))
+        z[2 * i] = rad * math.cos(2.0 * math.pi * u2)
+        z[2 * i + 1] = rad * math.sin(2.0 * math.pi * u2)
+    return z
+
+
+def local_theta(orc, seed: int, rp: int, rnd: int, j: int, theta_inc, ext, scale) -> np.ndarray:
+    """Local proposal j of round rnd (a project reading): Philox blocks
+    ctr = {j, rp, 2 + rnd, 2} and {j, rp, 2 + rnd, 3}, key = {seed, ROUND_KEY}
+    give six normals z (`box_muller`); theta_d = clip(theta_inc_d + scale *
+    ext_d * z_d, 0, ext_d - 1), in FP64."""
+    w = np.concatenate([orc.philox([j, rp, 2 + rnd, 2], [seed, ROUND_KEY]),
+                        orc.philox([j, rp, 2 + rnd, 3], [seed, ROUND_KEY])])
+    z = box_muller(w)
+    ext = np.asarray(ext, np.float64)
+    return np.clip(np.asarray(theta_inc, np.float64) + scale * ext * z, 0.0, ext - 1.0)
+
+
+def incumbents(thetas, values, count=2):
+    """Indices of the `count` largest values (the earlier sample on ties)."""
+    order = sorted(range(len(values)), key=lambda i: (-values[i], i))
+    return order[:count]
 
 
 def self_pair_fix(v, ext):
@@ -154,20 +196,23 @@ def shortlist(ucb, selected, M):
 
 
 def bos_run(orc, objective, seed, rp, ext_a, ext_b, Q, per_round, rounds, kappa=0.5, M=128,
-            prior=None):
+            prior=None, local_picks=0, local_scale=0.0625):
     """Plain BOS loop (FP64 GP refit from scratch every round) on one brick pair.
 
     objective(voxels [k][6] int) -> values [k]. Returns the pool, the pool
-    indices observed per round, the observed values and the voxel pairs.
+    indices observed per round (the GP's observations), the observed values,
+    the voxel pairs, and every evaluated sample's theta and value in order.
     """
     pool = pool_positions(orc, seed, rp, Q, ext_a, ext_b)
     ext = np.array(list(ext_a) + list(ext_b), np.float64)
     ell = 0.25 * ext
     obs, ys, vox, rounds_picks = [], [], [], []
+    th_all, y_all = [], []
     picks = list(range(per_round))
     gp = None
     m_pool = None
     for rnd in range(rounds):
+        loc = []
         if rnd > 0:
             X = pool[obs]
             mu, var = gp.posterior(X, np.array(ys), m_pool[obs], pool, m_pool)
@@ -175,11 +220,20 @@ def bos_run(orc, objective, seed, rp, ext_a, ext_b, Q, per_round, rounds, kappa=
             selected[obs] = True
             sl = shortlist(mu + kappa * np.sqrt(np.maximum(var, 0.0)), selected, M)
             cov = gp.posterior_cov(X, pool[sl])
-            picks = [int(sl[i]) for i in believer_picks(mu[sl], cov, kappa, per_round, gp.sn2)]
-        v = np.array([bernoulli_voxels(orc, seed, rp, rnd, j, pool[c]) for j, c in enumerate(picks)])
+            n_gp = per_round - local_picks
+            picks = [int(sl[i]) for i in believer_picks(mu[sl], cov, kappa, n_gp, gp.sn2)]
+            inc = incumbents(th_all, y_all)
+            loc = [local_theta(orc, seed, rp, rnd, j, th_all[inc[j % len(inc)]], ext, local_scale)
+                   for j in range(local_picks)]
+        thetas = [np.asarray(t, np.float64) for t in loc] + [pool[c].astype(np.float64)
+                                                               for c in picks]
+        v = np.array([bernoulli_voxels(orc, seed, rp, rnd, j, np.float32(t))
+                      for j, t in enumerate(thetas)])
         y = np.asarray(objective(v), np.float64)
         obs += picks
-        ys += list(y)
+        ys += list(y[len(loc):])
+        th_all += thetas
+        y_all += list(y)
         vox.append(v)
         rounds_picks.append(picks)
         if rnd == 0:
@@ -188,4 +242,4 @@ def bos_run(orc, objective, seed, rp, ext_a, ext_b, Q, per_round, rounds, kappa=
             gp = GP(ell, sf2, 1e-4 * sf2)
             m_pool = np.full(Q, m) if prior is None else np.asarray(prior, np.float64)
     return dict(pool=pool, picks=rounds_picks, y=np.array(ys), voxels=np.concatenate(vox),
-                gp=gp, m_pool=m_pool)
+                gp=gp, m_pool=m_pool, theta=np.array(th_all), y_all=np.array(y_all))

@@ -325,10 +325,49 @@ def pyo_mlp_offsets(offsets):
     assert np.abs(off - np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1)).max() < 1e-12
 
 
+def pyo_box_muller(bm):
+    """Box-Muller on 24-bit uniforms: hand values and the standard normal's moments."""
+    def words(tops):
+        return np.array([np.uint64(t) << np.uint64(40) for t in tops], np.uint64)
+    # top24 = 2^23 - 1 -> u1 = 1/2; top24 = 0 -> u2 = 0; top24 = 2^22 -> u2 = 1/4
+    z = bm(words([2 ** 23 - 1, 0, 2 ** 23 - 1, 2 ** 22, 2 ** 24 - 1, 2 ** 23, 0, 0]))
+    r = math.sqrt(2.0 * math.log(2.0))
+    want = [r, 0.0, r * math.cos(math.pi / 2), r * math.sin(math.pi / 2), -0.0, 0.0]
+    # u1 = 1 (top24 = 2^24 - 1) gives radius 0; u2 = 1/2 for the last pair
+    assert np.abs(z - np.array(want)).max() < 1e-12, z
+    rng = np.random.default_rng(5)
+    zs = np.concatenate([bm(rng.integers(0, 2 ** 63, 8, dtype=np.int64).astype(np.uint64) * 2)
+                         for _ in range(5000)])
+    assert abs(zs.mean()) < 0.03 and abs(zs.var() - 1.0) < 0.05, (zs.mean(), zs.var())
+
+
+def pyo_incumbents(inc):
+    """The two largest values, the earlier sample on ties."""
+    assert inc(None, [0.1, 0.5, 0.3, 0.5, 0.2]) == [1, 3]
+    assert inc(None, [0.7, 0.1, 0.9]) == [2, 0]
+    assert inc(None, [0.4]) == [0]
+
+
+def pyo_local_theta(lt, orc):
+    """Local proposals: centred on the incumbent, spread scale * extent per axis,
+    clipped to the box."""
+    ext = np.array([32, 32, 20, 20, 26, 20], np.float64)
+    inc = np.array([10.0, 0.5, 18.5, 19.0, 3.0, 7.0])
+    th = np.array([lt(orc, 3, 1, 2, j, inc, ext, 0.0625) for j in range(4000)])
+    assert np.all(th >= 0) and np.all(th <= ext - 1)
+    free = (inc > 4 * 0.0625 * ext) & (inc < ext - 1 - 4 * 0.0625 * ext)  # rarely clipped
+    assert np.abs(th[:, free].mean(0) - inc[free]).max() < 0.1
+    sd = th[:, free].std(0) / (0.0625 * ext[free])
+    assert np.abs(sd - 1.0).max() < 0.06, sd
+    assert np.mean(th[:, 1] == 0.0) > 0.3  # clipped at the low edge
+    assert np.array_equal(lt(orc, 3, 1, 2, 7, inc, ext, 0.0625), lt(orc, 3, 1, 2, 7, inc, ext, 0.0625))
+
+
 def py_pins():
     """(pin, oracle function) pairs of the python oracles."""
     from oracle import gp, mlp
-    return [(pyo_self_pair_fix, gp.self_pair_fix), (pyo_mlp_offsets, mlp.offsets)]
+    return [(pyo_self_pair_fix, gp.self_pair_fix), (pyo_mlp_offsets, mlp.offsets),
+            (pyo_box_muller, gp.box_muller), (pyo_incumbents, gp.incumbents)]
 
 
 ALL = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

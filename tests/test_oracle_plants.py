@@ -4,6 +4,8 @@ The oracle is rebuilt with a -DPLANT_* define that introduces one plausible
 error (dropped term, wrong comparison, wrong log base, missing centring, ...);
 the named pin must then fail. This shows the pins constrain the oracle.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -97,6 +99,82 @@ PY_PLANTS = [
     (pins.pyo_mlp_offsets, _off_extent_minus_one),
     (pins.pyo_mlp_offsets, _off_yx_swapped),
 ]
+
+
+def _bm_no_plus_one(words):
+    w = np.asarray(words, np.uint64)
+    top = (w >> np.uint64(40)).astype(np.float64)
+    z = np.empty(6)
+    for i in range(3):
+        u1 = max(top[2 * i], 1.0) * 2.0 ** -24  # planted: u1 without the + 1
+        u2 = top[2 * i + 1] * 2.0 ** -24
+        rad = math.sqrt(-2.0 * math.log(u1))
+        z[2 * i], z[2 * i + 1] = rad * math.cos(2 * math.pi * u2), rad * math.sin(2 * math.pi * u2)
+    return z
+
+
+def _bm_no_two(words):
+    w = np.asarray(words, np.uint64)
+    top = (w >> np.uint64(40)).astype(np.float64)
+    z = np.empty(6)
+    for i in range(3):
+        u1 = (top[2 * i] + 1.0) * 2.0 ** -24
+        u2 = top[2 * i + 1] * 2.0 ** -24
+        rad = math.sqrt(-math.log(u1))  # planted: missing factor 2
+        z[2 * i], z[2 * i + 1] = rad * math.cos(2 * math.pi * u2), rad * math.sin(2 * math.pi * u2)
+    return z
+
+
+def _bm_swapped(words):
+    w = np.asarray(words, np.uint64)
+    top = (w >> np.uint64(40)).astype(np.float64)
+    z = np.empty(6)
+    for i in range(3):
+        u1 = (top[2 * i] + 1.0) * 2.0 ** -24
+        u2 = top[2 * i + 1] * 2.0 ** -24
+        rad = math.sqrt(-2.0 * math.log(u1))
+        z[2 * i], z[2 * i + 1] = rad * math.sin(2 * math.pi * u2), rad * math.cos(2 * math.pi * u2)
+    return z
+
+
+def _inc_later_on_ties(thetas, values, count=2):
+    return sorted(range(len(values)), key=lambda i: (-values[i], -i))[:count]
+
+
+def _inc_smallest(thetas, values, count=2):
+    return sorted(range(len(values)), key=lambda i: (values[i], i))[:count]
+
+
+PY_PLANTS += [
+    (pins.pyo_box_muller, _bm_no_plus_one),
+    (pins.pyo_box_muller, _bm_no_two),
+    (pins.pyo_box_muller, _bm_swapped),
+    (pins.pyo_incumbents, _inc_later_on_ties),
+    (pins.pyo_incumbents, _inc_smallest),
+]
+
+
+def _lt_relative_to_box_origin(orc, seed, rp, rnd, j, theta_inc, ext, scale):
+    from oracle import gp
+    w = np.concatenate([orc.philox([j, rp, 2 + rnd, 2], [seed, gp.ROUND_KEY]),
+                        orc.philox([j, rp, 2 + rnd, 3], [seed, gp.ROUND_KEY])])
+    ext = np.asarray(ext, np.float64)
+    return np.clip(scale * ext * gp.box_muller(w), 0.0, ext - 1.0)  # planted: incumbent dropped
+
+
+def _lt_unit_spread(orc, seed, rp, rnd, j, theta_inc, ext, scale):
+    from oracle import gp
+    w = np.concatenate([orc.philox([j, rp, 2 + rnd, 2], [seed, gp.ROUND_KEY]),
+                        orc.philox([j, rp, 2 + rnd, 3], [seed, gp.ROUND_KEY])])
+    ext = np.asarray(ext, np.float64)
+    return np.clip(np.asarray(theta_inc) + scale * gp.box_muller(w), 0.0, ext - 1.0)  # planted
+
+
+@pytest.mark.parametrize("planted", [_lt_relative_to_box_origin, _lt_unit_spread],
+                         ids=lambda v: v.__name__)
+def test_local_theta_plant_is_caught(orc, planted):
+    with pytest.raises(AssertionError):
+        pins.pyo_local_theta(planted, orc)
 
 
 @pytest.mark.parametrize("pin,planted", PY_PLANTS, ids=lambda v: v.__name__)
