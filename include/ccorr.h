@@ -404,12 +404,28 @@ typedef struct {
     int32_t k;          /* KSG neighbours (-1: ceil(3n/100)) */
     int32_t bins;       /* histogram bins, 2..16 */
     uint64_t seed;
+    int32_t local_picks; /* local proposals per round from the second, 0 <= local_picks < per_round */
+    float local_scale;   /* their spread per axis as a fraction of the region extent, (0, 1] */
 } cc_bos_params;
 
 /*
+ * Local proposals (a project reading of how the acquisition is searched; the
+ * paper names a global optimiser): with local_picks = L > 0, from the second
+ * round on the first L proposals of a round are not taken from the pool but
+ * perturb the two best samples so far (largest objective value, the earlier
+ * sample on ties; proposal j uses incumbent j mod 2): theta_d = clip(theta_inc,d
+ * + local_scale * extent_d * z_d, 0, extent_d - 1), z six standard normals by
+ * Box-Muller from Philox blocks {j, r, 2 + t, 2} and {j, r, 2 + t, 3} (key
+ * {seed, 0xB0517D}): for i = 0..2, u1 = (top 24 bits of word 2i + 1) / 2^24,
+ * u2 = top 24 bits of word 2i+1 / 2^24, z_2i = sqrt(-2 ln u1) cos(2 pi u2),
+ * z_2i+1 = ... sin. They are rounded, evaluated and reduced like every
+ * proposal, but the GP is conditioned on the round's R - L pool proposals only
+ * (all R in the first round). L = 0 is the plain reading.
+ *
  * Create the sampling state for n_rp region pairs (rp_a[i], rp_b[i]) of one
- * field (host arrays). Device memory: pool * (6 + 2 + per_round * rounds) * 4
- * bytes per region pair, plus small arrays.
+ * field (host arrays). Device memory: pool * (6 + 2 + S) * 4 bytes per region
+ * pair with S = per_round + (rounds - 1) (per_round - local_picks) GP
+ * observations, plus per_round * rounds * 28 bytes of sample history.
  */
 cc_status cc_bos_create(cc_ctx* ctx, int32_t field_id, const int32_t* rp_a, const int32_t* rp_b,
                         int n_rp, const cc_bos_params* params, cc_bos** out);
@@ -452,13 +468,22 @@ cc_status cc_bos_results(cc_ctx* ctx, cc_bos* bos, cc_rp_result* out);
 
 /*
  * Inspect region pair rp (host outputs, each may be NULL): pool [pool][6],
- * posterior mean and variance [pool], observed pool entries and objective
- * values [n_obs], the last round's point pairs [per_round] and measure values
- * [4][per_round]; *n_obs = observations so far.
+ * posterior mean and variance [pool], the GP's observed pool entries and
+ * objective values [n_obs], the last round's point pairs [per_round] and
+ * measure values [4][per_round]; *n_obs = GP observations so far.
  */
 cc_status cc_bos_inspect(cc_ctx* ctx, cc_bos* bos, int rp, float* pool, float* mu, float* var,
                          int32_t* obs, float* y, uint32_t* pa, uint32_t* pb, float* vals,
                          int32_t* n_obs);
+
+/*
+ * Every sample evaluated so far for region pair rp, in order (round-major,
+ * proposal j within a round): theta (host float [n][6], the continuous
+ * position that was rounded, or NULL) and the objective measure's value
+ * (host float [n], or NULL); *n_samples = rounds run x per_round.
+ */
+cc_status cc_bos_samples(cc_ctx* ctx, cc_bos* bos, int rp, float* theta, float* y,
+                         int32_t* n_samples);
 
 /* Release the sampling state. */
 cc_status cc_bos_destroy(cc_ctx* ctx, cc_bos* bos);

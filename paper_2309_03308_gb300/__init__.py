@@ -247,14 +247,15 @@ class Context:
 
     def bos_create(self, fid: int, rp_a, rp_b, pool=2048, per_round=32, rounds=30,
                    shortlist=128, kappa=0.5, objective=CC_MI_KSG, k=10, bins=16, seed=3,
-                   field_b: int | None = None):
+                   field_b: int | None = None, local_picks=0, local_scale=0.0625):
         """Batched BOS state over region pairs (rp_a[i], rp_b[i]) of field fid;
         with field_b, the second point of each pair is read from that field
-        (regions rp_b[i] belong to it): the inter-variable matrix."""
+        (regions rp_b[i] belong to it): the inter-variable matrix. local_picks
+        proposals per round (from the second) perturb the two best samples."""
         a = np.ascontiguousarray(rp_a, np.int32)
         b = np.ascontiguousarray(rp_b, np.int32)
         prm = _lib.cc_bos_params(pool, per_round, rounds, shortlist, kappa, objective, k, bins,
-                                 seed)
+                                 seed, local_picks, local_scale)
         h = ctypes.c_void_p()
         fb = fid if field_b is None else field_b
         self._check(self.lib.cc_bos_create2(self.h, fid, fb, a.ctypes.data, b.ctypes.data,
@@ -301,6 +302,16 @@ class Bos:
             ctypes.byref(n)))
         s = n.value
         return dict(pool=pool, mu=mu, var=var, obs=obs[:s], y=y[:s], pa=pa, pb=pb, vals=vals)
+
+    def samples(self, rp: int):
+        """Every evaluated sample of region pair rp in order: (theta [n][6], objective [n])."""
+        R, T = self.prm.per_round, self.prm.rounds
+        theta = np.empty((R * T, 6), np.float32)
+        y = np.empty(R * T, np.float32)
+        n = ctypes.c_int32()
+        self.ctx._check(self.ctx.lib.cc_bos_samples(self.ctx.h, self.h, rp, theta.ctypes.data,
+                                                    y.ctypes.data, ctypes.byref(n)))
+        return theta[:n.value], y[:n.value]
 
     def close(self):
         if self.h:

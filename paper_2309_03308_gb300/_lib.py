@@ -52,7 +52,8 @@ class cc_bos_params(ctypes.Structure):
     _fields_ = [("pool", ctypes.c_int32), ("per_round", ctypes.c_int32),
                 ("rounds", ctypes.c_int32), ("shortlist", ctypes.c_int32),
                 ("kappa", ctypes.c_float), ("objective", ctypes.c_int32), ("k", ctypes.c_int32),
-                ("bins", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("bins", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("local_picks", ctypes.c_int32), ("local_scale", ctypes.c_float)]
 
 
 _P = ctypes.c_void_p
@@ -95,6 +96,7 @@ SIGNATURES = {
     "cc_bos_run": (_S, [_P, _P, _I, _I]),
     "cc_bos_results": (_S, [_P, _P, _P]),
     "cc_bos_inspect": (_S, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I32)]),
+    "cc_bos_samples": (_S, [_P, _P, _I, _P, _P, ctypes.POINTER(_I32)]),
     "cc_bos_destroy": (_S, [_P, _P]),
     "cc_sur_create": (_S, [_P, _I, _U64, ctypes.POINTER(_P)]),
     "cc_sur_set_params": (_S, [_P, _P, _P]),

@@ -50,6 +50,9 @@ constexpr int kBosThreads = 256;
 
 struct BosDev {
     int n_rp, Q, R, T, M;
+    int L;        // local proposals per round from the second round on (0: none)
+    float lscale; // their spread per axis as a fraction of the region extent
+    int S;        // GP observations provisioned: R + (T - 1) (R - L)
     float kappa;
     uint64_t seed;
     int objective, k, bins;
@@ -65,6 +68,10 @@ struct BosDev {
     float* y;            // [n_rp][R*T]
     float* beta;         // [n_rp][R*T]
     float* hyp;          // [n_rp][4]: prior mean, signal var, noise var
+    float* theta;        // [n_rp][R*T][6] every evaluated proposal's position, in order
+    float* yall;         // [n_rp][R*T] its objective value
+    float* inc_val;      // [n_rp][2] the two best objective values so far
+    int* inc_idx;        // [n_rp][2] their sample indices (into theta)
     const float* prior;  // [n_rp][Q] or null
     int* picks;          // [n_rp][R]
     uint32_t* pa;        // [n_rp*R]
@@ -95,6 +102,13 @@ struct BosDev {
     double fix_over_n;  // 1 / (2^40 n): fixed-point sum -> mean
     double logn;
 };
+
+// GP observations before round r (round 0 conditions all R proposals, later
+// rounds the R - L pool proposals) and new ones in round r
+__host__ __device__ __forceinline__ int obs_before(int r, int R, int L) {
+    return r == 0 ? 0 : R + (r - 1) * (R - L);
+}
+__host__ __device__ __forceinline__ int obs_new(int r, int R, int L) { return r == 0 ? R : R - L; }
 
 __device__ __forceinline__ unsigned okey32(float v) {
     const unsigned b = __float_as_uint(v + 0.0f);
@@ -154,7 +168,8 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
         }
         return;
     }
-    const int s = r * R;
+    const int s = obs_before(r, R, d.L), L = d.L;
+    if (tid < L) picks[tid] = -1;  // local proposals: positions made by k_bos_round_pairs
     unsigned long long* key = reinterpret_cast<unsigned long long*>(bs);
     int* SL = reinterpret_cast<int*>(key + Q);
     float* cov = reinterpret_cast<float*>(SL + M);
@@ -207,7 +222,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    const float* Vr = d.V + (int64_t)rp * (R * d.T) * Q;
+    const float* Vr = d.V + (int64_t)rp * d.S * Q;  // d.S GP observation rows per region pair
     // 16 gathered rows per barrier; per row a thread reads its 2 x per
     // operands once and updates its per x per block (per <= 8)
     for (int t0 = 0; t0 < s; t0 += 16) {
@@ -255,9 +270,9 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
         }
     }
     __syncthreads();
-    // greedy picks with the kriging-believer update
+    // greedy picks with the kriging-believer update (the R - L pool proposals)
     float* col = rowbuf;
-    for (int j = 0; j < R; ++j) {
+    for (int j = 0; j < R - L; ++j) {
         float bv = -CUDART_INF_F;
         int bi = 0x7fffffff;
         for (int i = tid; i < M; i += blockDim.x) {
@@ -289,7 +304,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
                     red_i[0] = red_i[w];
                 }
             const int c = red_i[0];
-            picks[j] = SL[c];
+            picks[L + j] = SL[c];
             atomicOr(&sel[SL[c] >> 5], 1u << (SL[c] & 31));
         }
         __syncthreads();
@@ -304,13 +319,50 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
 }
 
 // ---------------------------------------------------------------------------
-// probabilistic reparameterization of proposal j: blocks {j, rp, 2 + r, 0/1}
+// probabilistic reparameterization of proposal j: blocks {j, rp, 2 + r, 0/1}.
+// A local proposal (pick -1) first gets its position from incumbent j mod 2
+// (the only one when a single sample exists): theta_d = clip(theta_inc,d +
+// lscale ext_d z_d, 0, ext_d - 1) with six Box-Muller normals from blocks
+// {j, rp, 2 + r, 2/3}: for i = 0..2, u1 = (top 24 bits of w[2i] + 1) 2^-24,
+// u2 = top 24 bits of w[2i+1] 2^-24, z = sqrt(-2 ln u1) (cos, sin)(2 pi u2).
 __global__ void k_bos_round_pairs(BosDev d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n_rp * d.R) return;
     const int rp = i / d.R, j = i % d.R, r = *d.round;
     const int c = d.picks[rp * d.R + j];
-    const float* th = d.pool + ((int64_t)rp * d.Q + c) * 6;
+    const int* bx = d.box + rp * 12;
+    float th[6];
+    if (c >= 0) {
+#pragma unroll
+        for (int a = 0; a < 6; ++a) th[a] = d.pool[((int64_t)rp * d.Q + c) * 6 + a];
+    } else {
+        const int ninc = min(2, r * d.R);
+        const int src = max(d.inc_idx[rp * 2 + j % ninc], 0);  // set after every round
+        const float* ti = d.theta + ((int64_t)rp * d.R * d.T + src) * 6;
+        uint64_t w0[4] = {(uint64_t)j, (uint64_t)rp, (uint64_t)(2 + r), 2};
+        uint64_t w1[4] = {(uint64_t)j, (uint64_t)rp, (uint64_t)(2 + r), 3};
+        philox4x64_10(w0, d.seed, kRoundKey);
+        philox4x64_10(w1, d.seed, kRoundKey);
+        const uint64_t w[8] = {w0[0], w0[1], w0[2], w0[3], w1[0], w1[1], w1[2], w1[3]};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float u1 = (float)((w[2 * q] >> 40) + 1) * 5.9604644775390625e-8f;  // 2^-24
+            const float u2 = (float)(w[2 * q + 1] >> 40) * 5.9604644775390625e-8f;
+            const float rad = sqrtf(-2.f * logf(u1));
+            float sn, cs;
+            sincospif(2.f * u2, &sn, &cs);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int a = 2 * q + h;
+                const int ext = bx[a < 3 ? 3 + a : 6 + 3 + (a - 3)];
+                const float z = h ? rad * sn : rad * cs;
+                th[a] = fminf(fmaxf(fmaf(d.lscale * (float)ext, z, ti[a]), 0.f), (float)(ext - 1));
+            }
+        }
+    }
+    float* hist = d.theta + ((int64_t)rp * d.R * d.T + (int64_t)r * d.R + j) * 6;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) hist[a] = th[a];
     uint64_t w0[4] = {(uint64_t)j, (uint64_t)rp, (uint64_t)(2 + r), 0};
     uint64_t w1[4] = {(uint64_t)j, (uint64_t)rp, (uint64_t)(2 + r), 1};
     philox4x64_10(w0, d.seed, kRoundKey);
@@ -322,7 +374,6 @@ __global__ void k_bos_round_pairs(BosDev d) {
         const float f = floorf(th[a]);
         v[a] = (int)f + (u24(w[a]) < __fsub_rn(th[a], f) ? 1 : 0);
     }
-    const int* bx = d.box + rp * 12;
     if (d.self[rp]) {  // a self pair never pairs a point with itself
         if (v[0] == v[3] && v[1] == v[4] && v[2] == v[5]) {
             const int np = bx[3] * bx[4] * bx[5];
@@ -434,6 +485,32 @@ __global__ void k_bos_extremes(BosDev d) {
         b.count++;
     }
     d.best[i] = b;
+    if (m == d.objective) {
+        // the objective's value of every sample, and the two best so far (the
+        // earlier sample on ties: strictly greater values replace)
+        const int r = *d.round;
+        float v0 = r ? d.inc_val[rp * 2] : -CUDART_INF_F;
+        float v1 = r ? d.inc_val[rp * 2 + 1] : -CUDART_INF_F;
+        int i0 = r ? d.inc_idx[rp * 2] : -1, i1 = r ? d.inc_idx[rp * 2 + 1] : -1;
+        for (int j = 0; j < d.R; ++j) {
+            const float v = d.vals[(int64_t)m * per + rp * d.R + j];
+            const int idx = r * d.R + j;
+            d.yall[(int64_t)rp * d.R * d.T + idx] = v;
+            if (v > v0) {
+                v1 = v0;
+                i1 = i0;
+                v0 = v;
+                i0 = idx;
+            } else if (v > v1) {
+                v1 = v;
+                i1 = idx;
+            }
+        }
+        d.inc_val[rp * 2] = v0;
+        d.inc_val[rp * 2 + 1] = v1;
+        d.inc_idx[rp * 2] = i0;
+        d.inc_idx[rp * 2 + 1] = i1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -441,8 +518,10 @@ __global__ void k_bos_extremes(BosDev d) {
 __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     extern __shared__ __align__(16) unsigned char cs[];
     const int rp = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
-    const int r = *d.round, R = d.R, Q = d.Q, S = R * d.T;
-    const int s = r * R;
+    const int r = *d.round, R = d.R, Q = d.Q, S = d.S;
+    // the round's GP observations: all R proposals in round 0, the R - L pool
+    // proposals (after the local ones) later; nn <= R, matrices use stride nn
+    const int s = obs_before(r, R, d.L), nn = obs_new(r, R, d.L), j0 = r == 0 ? 0 : d.L;
     float* G = reinterpret_cast<float*>(cs);               // 32 rows x 32 of V[:, P] (0-padded)
     double* Lf = reinterpret_cast<double*>(G + 32 * 32);   // R x R (fp64 Cholesky)
     float* covP = reinterpret_cast<float*>(Lf + R * R);    // R x R
@@ -453,13 +532,13 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     float* yv = pp + R * 6;                       // R
     float* mP = yv + R;                           // R prior at picks
     float* hyp = mP + R;                          // 4
-    const int* P = d.picks + rp * R;
+    const int* P = d.picks + rp * R + j0;
     const int per = d.n_rp * R;
     float* Vr = d.V + (int64_t)rp * S * Q;
     float* mu = d.mu + (int64_t)rp * Q;
     float* var = d.var + (int64_t)rp * Q;
-    if (tid < R) {
-        yv[tid] = d.vals[(int64_t)d.objective * per + rp * R + tid];
+    if (tid < nn) {
+        yv[tid] = d.vals[(int64_t)d.objective * per + rp * R + j0 + tid];
 #pragma unroll
         for (int a = 0; a < 6; ++a) pp[tid * 6 + a] = d.pool[((int64_t)rp * Q + P[tid]) * 6 + a];
     }
@@ -484,7 +563,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
             var[c] = sf2;
         }
     }
-    if (tid < R) mP[tid] = d.prior ? d.prior[(int64_t)rp * Q + P[tid]] : m0;
+    if (tid < nn) mP[tid] = d.prior ? d.prior[(int64_t)rp * Q + P[tid]] : m0;
     float inv_ell[6];
     inv_ell_of(d, rp, inv_ell);
     // covP = V[:, P]^T V[:, P] and gb = V[:, P]^T beta over the s old rows
@@ -493,7 +572,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     auto gather = [&](int t0) {  // G[t][j] = V[t0 + t][P[j]], zero beyond s and R
         for (int e = tid; e < 32 * 32; e += blockDim.x) {
             const int t = t0 + (e >> 5), j = e & 31;
-            G[e] = (t < s && j < R) ? Vr[(int64_t)t * Q + P[j]] : 0.f;
+            G[e] = (t < s && j < nn) ? Vr[(int64_t)t * Q + P[j]] : 0.f;
         }
     };
     for (int t0 = 0; t0 < s; t0 += 32) {
@@ -501,53 +580,53 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
         __syncthreads();
         for (int q = 0; q < 4; ++q) {
             const int e = tid + q * blockDim.x;
-            if (e < R * R) {
-                const int i = e / R, j = e % R;
+            if (e < nn * nn) {
+                const int i = e / nn, j = e % nn;
                 float a = cacc[q];
                 for (int t = 0; t < 32; ++t) a = fmaf(G[t * 32 + i], G[t * 32 + j], a);
                 cacc[q] = a;
             }
         }
-        if (tid < R)
+        if (tid < nn)
             for (int t = 0; t < 32 && t0 + t < s; ++t)
                 gacc = fmaf(G[t * 32 + tid], d.beta[(int64_t)rp * S + t0 + t], gacc);
         __syncthreads();
     }
     for (int q = 0; q < 4; ++q) {
         const int e = tid + q * blockDim.x;
-        if (e < R * R) {
-            const int i = e / R, j = e % R;
+        if (e < nn * nn) {
+            const int i = e / nn, j = e % nn;
             covP[e] = matern52(pp + i * 6, pp + j * 6, inv_ell, sf2) - cacc[q] + (i == j ? sn2 : 0.f);
         }
     }
-    if (tid < R) gb[tid] = gacc;
+    if (tid < nn) gb[tid] = gacc;
     __syncthreads();
     // Cholesky of covP (fp64, warp 0: lane = row)
     if (tid < 32) {
-        for (int j = 0; j < R; ++j) {
+        for (int j = 0; j < nn; ++j) {
             if (lane == j) {
-                double sum = covP[j * R + j];
-                for (int q = 0; q < j; ++q) sum -= Lf[j * R + q] * Lf[j * R + q];
-                Lf[j * R + j] = sqrt(fmax(sum, 1e-12 * (double)sf2));
+                double sum = covP[j * nn + j];
+                for (int q = 0; q < j; ++q) sum -= Lf[j * nn + q] * Lf[j * nn + q];
+                Lf[j * nn + j] = sqrt(fmax(sum, 1e-12 * (double)sf2));
             }
             __syncwarp();
-            if (lane > j && lane < R) {
-                double sum = covP[lane * R + j];
-                for (int q = 0; q < j; ++q) sum -= Lf[lane * R + q] * Lf[j * R + q];
-                Lf[lane * R + j] = sum / Lf[j * R + j];
+            if (lane > j && lane < nn) {
+                double sum = covP[lane * nn + j];
+                for (int q = 0; q < j; ++q) sum -= Lf[lane * nn + q] * Lf[j * nn + q];
+                Lf[lane * nn + j] = sum / Lf[j * nn + j];
             }
             __syncwarp();
         }
-        for (int e = lane; e < R * R; e += 32) {
-            const int i = e / R, j = e % R;
+        for (int e = lane; e < nn * nn; e += 32) {
+            const int i = e / nn, j = e % nn;
             L[e] = j <= i ? (float)Lf[e] : 0.f;
         }
         __syncwarp();
         if (lane == 0) {  // beta2 = L22^-1 (y - m_P - V[:, P]^T beta1)
-            for (int i = 0; i < R; ++i) {
+            for (int i = 0; i < nn; ++i) {
                 double v = (double)yv[i] - mP[i] - gb[i];
-                for (int q = 0; q < i; ++q) v -= Lf[i * R + q] * (double)b2[q];
-                b2[i] = (float)(v / Lf[i * R + i]);
+                for (int q = 0; q < i; ++q) v -= Lf[i * nn + q] * (double)b2[q];
+                b2[i] = (float)(v / Lf[i * nn + i]);
             }
         }
     }
@@ -605,11 +684,11 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
             float dv = 0.f, dm = 0.f;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                if (i < R) {
+                if (i < nn) {
                     float x = matern52(pp + i * 6, pcl, inv_ell, sf2) - w[i];
 #pragma unroll
-                    for (int q = 0; q < i; ++q) x = fmaf(-L[i * R + q], w[q], x);
-                    x /= L[i * R + i];
+                    for (int q = 0; q < i; ++q) x = fmaf(-L[i * nn + q], w[q], x);
+                    x /= L[i * nn + i];
                     w[i] = x;
                     Vr[(int64_t)(s + i) * Q + c] = x;
                     dv = fmaf(x, x, dv);
@@ -622,7 +701,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
         finish(cA, wA);
         finish(cB, wB);
     }
-    if (tid < R) {
+    if (tid < nn) {
         d.obs[(int64_t)rp * S + s + tid] = P[tid];
         d.y[(int64_t)rp * S + s + tid] = yv[tid];
         d.beta[(int64_t)rp * S + s + tid] = b2[tid];
@@ -645,7 +724,7 @@ struct cc_bos {
     int field = -1, field_b = -1;
     uint64_t field_version = ~0ull, field_b_version = ~0ull;
     DevMem box, self, pool, V, mu, var, sel, obs, y, beta, hyp, prior, picks, pa, pb, vals, best,
-        counters;
+        counters, theta, yall, inc_val, inc_idx;
     int eval_warps = 8, eval_blocks_per_sm = 4;
     bool tuned = false;
     cudaGraph_t graph = nullptr;
@@ -837,6 +916,10 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
                      "a multiple of 16 in [16, 128], per_round * rounds + shortlist <= pool");
     if (prm->objective < CC_PEARSON || prm->objective > CC_MI_KSG)
         return bfail(ctx, CC_ERR_INVALID_ARG, "unknown objective measure");
+    if (prm->local_picks < 0 || prm->local_picks >= R ||
+        !(prm->local_scale > 0.f && prm->local_scale <= 1.f))
+        return bfail(ctx, CC_ERR_INVALID_ARG,
+                     "need 0 <= local_picks < per_round and 0 < local_scale <= 1");
     const int k = prm->k == -1 ? (3 * f.n + 99) / 100 : prm->k;
     if (k < 1 || k > f.n - 1 || k > 32 || prm->bins < 2 || prm->bins > 16)
         return bfail(ctx, CC_ERR_INVALID_ARG, "k in [1, min(n-1, 32)], bins in [2, 16]");
@@ -873,6 +956,9 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
     d.R = R;
     d.T = T;
     d.M = M;
+    d.L = prm->local_picks;
+    d.lscale = prm->local_scale;
+    d.S = R + (T - 1) * (R - d.L);
     d.kappa = prm->kappa;
     d.seed = prm->seed;
     d.objective = prm->objective;
@@ -882,7 +968,7 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
     d.n_pad = f.n_pad;
     d.X = f.X;
     d.Y = f.Y;
-    const int64_t S = (int64_t)R * T;
+    const int64_t S = d.S, RT = (int64_t)R * T;
     BK(b->box.alloc(box.size() * 4));
     BK(b->self.alloc(self.size() * 4));
     BK(b->pool.alloc((size_t)n_rp * Q * 6 * 4));
@@ -900,6 +986,10 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
     BK(b->vals.alloc((size_t)4 * n_rp * R * 4));
     BK(b->best.alloc((size_t)4 * n_rp * sizeof(Partial)));
     BK(b->counters.alloc(16));
+    BK(b->theta.alloc((size_t)n_rp * RT * 6 * 4));
+    BK(b->yall.alloc((size_t)n_rp * RT * 4));
+    BK(b->inc_val.alloc((size_t)n_rp * 2 * 4));
+    BK(b->inc_idx.alloc((size_t)n_rp * 2 * 4));
     cudaStream_t st = ctx->stream;
     BK(cudaMemcpyAsync(b->box.p, box.data(), box.size() * 4, cudaMemcpyHostToDevice, st));
     BK(cudaMemcpyAsync(b->self.p, self.data(), self.size() * 4, cudaMemcpyHostToDevice, st));
@@ -917,6 +1007,10 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
     d.y = b->y.as<float>();
     d.beta = b->beta.as<float>();
     d.hyp = b->hyp.as<float>();
+    d.theta = b->theta.as<float>();
+    d.yall = b->yall.as<float>();
+    d.inc_val = b->inc_val.as<float>();
+    d.inc_idx = b->inc_idx.as<int>();
     d.prior = nullptr;
     d.picks = b->picks.as<int>();
     d.pa = b->pa.as<uint32_t>();
@@ -1093,7 +1187,7 @@ cc_status cc_bos_inspect(cc_ctx* ctx, cc_bos* b, int rp, float* pool, float* mu,
                          int32_t* n_obs) {
     if (!ctx || !b || rp < 0 || rp >= b->d.n_rp) return CC_ERR_INVALID_ARG;
     const BosDev& d = b->d;
-    const int64_t S = (int64_t)d.R * d.T, s = (int64_t)b->rounds_done * d.R;
+    const int64_t S = d.S, s = obs_before(b->rounds_done, d.R, d.L);
     cudaStream_t st = ctx->stream;
     if (pool) BK(cudaMemcpyAsync(pool, d.pool + (int64_t)rp * d.Q * 6, d.Q * 24, cudaMemcpyDeviceToHost, st));
     if (mu) BK(cudaMemcpyAsync(mu, d.mu + (int64_t)rp * d.Q, d.Q * 4, cudaMemcpyDeviceToHost, st));
@@ -1107,6 +1201,20 @@ cc_status cc_bos_inspect(cc_ctx* ctx, cc_bos* b, int rp, float* pool, float* mu,
             BK(cudaMemcpyAsync(vals + m * d.R, d.vals + (int64_t)m * d.n_rp * d.R + rp * d.R,
                                d.R * 4, cudaMemcpyDeviceToHost, st));
     if (n_obs) *n_obs = (int32_t)s;
+    BK(cudaStreamSynchronize(st));
+    return CC_OK;
+}
+
+cc_status cc_bos_samples(cc_ctx* ctx, cc_bos* b, int rp, float* theta, float* y,
+                         int32_t* n_samples) {
+    if (!ctx || !b || rp < 0 || rp >= b->d.n_rp) return CC_ERR_INVALID_ARG;
+    const BosDev& d = b->d;
+    const int64_t RT = (int64_t)d.R * d.T, n = (int64_t)b->rounds_done * d.R;
+    cudaStream_t st = ctx->stream;
+    if (theta && n)
+        BK(cudaMemcpyAsync(theta, d.theta + rp * RT * 6, n * 24, cudaMemcpyDeviceToHost, st));
+    if (y && n) BK(cudaMemcpyAsync(y, d.yall + rp * RT, n * 4, cudaMemcpyDeviceToHost, st));
+    if (n_samples) *n_samples = (int32_t)n;
     BK(cudaStreamSynchronize(st));
     return CC_OK;
 }

@@ -213,3 +213,130 @@ def test_two_field_segment_extremes(orc):
                 assert abs(ref[out[s]["argmax"]] - seg.max()) < 1e-5
                 assert abs(out[s]["min"] - seg.min()) < 1e-5
     ctx.close()
+
+
+LOCAL, LSCALE = 3, 0.0625
+
+
+@pytest.fixture(scope="module")
+def setup_local():
+    """The batched search with LOCAL local proposals per round (from the second)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_03308_gb300 import Context, build
+    build.build()
+    F = gen.field(31, X, Y, Z, N)
+    ctx = Context(0)
+    fid = ctx.load_field(F)
+    rids = ctx.partition_regular(fid, 8, 8, 3)
+    boxes = [ctx.region_info(r)[1] for r in rids]
+    pairs = [(0, 7), (3, 3), (5, 20)]
+    bos = ctx.bos_create(fid, [rids[a] for a, _ in pairs], [rids[b] for _, b in pairs], pool=Q,
+                         per_round=R, rounds=T, shortlist=M, kappa=KAPPA, k=K, bins=BINS,
+                         seed=SEED, local_picks=LOCAL, local_scale=LSCALE)
+    bos.run(T)
+    out = ([bos.inspect(i) for i in range(len(pairs))], [bos.samples(i) for i in range(len(pairs))],
+           bos.results())
+    yield (F, boxes, pairs) + out
+    bos.close()
+    ctx.close()
+
+
+def test_local_proposals_against_oracle(setup_local, orc):
+    """Every sample replayed through the oracle: round 0 takes the first R pool
+    entries; later rounds start with LOCAL proposals around the two best
+    samples so far (the oracle's incumbents of the replayed values, its FP64
+    perturbation within fp32 rounding) followed by pool proposals, which alone
+    are the GP's observations; rounding, values and running extremes exact."""
+    F, boxes, pairs, states, samples, res = setup_local
+    for rp, (pair, st, (theta, yall)) in enumerate(zip(pairs, states, samples)):
+        ba, bb = boxes[pair[0]], boxes[pair[1]]
+        ea, eb = ext_of(ba), ext_of(bb)
+        ext = np.array(ea + eb, np.float64)
+        pool = st["pool"]
+        assert theta.shape == (R * T, 6) and yall.shape == (R * T,)
+        assert np.array_equal(theta[:R], pool[:R])
+        pa, pb = [], []
+        for i in range(R * T):
+            v = ogp.bernoulli_voxels(orc, SEED, rp, i // R, i % R, theta[i])
+            if pair[0] == pair[1]:
+                v = ogp.self_pair_fix(v, ea)
+            a, b = point_ids(ba, bb, v)
+            pa.append(a)
+            pb.append(b)
+        pa, pb = np.array(pa, np.uint32), np.array(pb, np.uint32)
+        vals = {m: orc.eval_pairs(F, m, pa, pb, k=K, bins=BINS) for m in range(4)}
+        assert np.abs(yall - vals[oracle.MI_KSG]).max() < 1e-5
+        gp_obs = []
+        for rnd in range(T):
+            for j in range(R):
+                i = rnd * R + j
+                if rnd > 0 and j < LOCAL:
+                    # incumbents among the samples before this round, on the GPU's values
+                    inc = ogp.incumbents(theta[:rnd * R], list(yall[:rnd * R]))
+                    want = ogp.local_theta(orc, SEED, rp, rnd, j, theta[inc[j % len(inc)]], ext,
+                                           LSCALE)
+                    assert np.abs(theta[i] - want).max() < 1e-4, (rnd, j, theta[i], want)
+                else:
+                    c = int(st["obs"][len(gp_obs)])
+                    assert np.array_equal(theta[i], pool[c])
+                    gp_obs.append(c)
+        assert len(gp_obs) == len(st["obs"]) == R + (T - 1) * (R - LOCAL)
+        assert np.abs(st["y"] - vals[oracle.MI_KSG][[i for i in range(R * T)
+                                                     if i < R or i % R >= LOCAL]]).max() < 1e-5
+        for m in range(4):  # running extremes over every sample, local ones included
+            assert abs(res[m][rp]["max"] - vals[m].max()) < 1e-5
+            assert abs(res[m][rp]["min"] - vals[m].min()) < 1e-5
+            assert res[m][rp]["count"] == R * T
+        # the GP posterior holds the pool observations only
+        y = np.asarray(st["y"], np.float64)
+        m0 = float(np.mean(y[:R]))
+        sf2 = max(float(np.mean((y[:R] - m0) ** 2)), 1e-12)
+        g = ogp.GP(0.25 * ext, sf2, 1e-4 * sf2)
+        # every pool proposal of a round is a valid UCB / kriging-believer choice
+        # of the posterior on the GP observations before that round
+        tol = 2e-3 * np.sqrt(sf2) + 1e-6
+        pool64 = pool.astype(np.float64)
+        for rnd in range(1, T):
+            s0 = R + (rnd - 1) * (R - LOCAL)
+            obs = st["obs"][:s0]
+            mu_r, var_r = g.posterior(pool64[obs], y[:s0], np.full(s0, m0), pool64,
+                                      np.full(Q, m0))
+            ucb = mu_r + KAPPA * np.sqrt(np.maximum(var_r, 0))
+            sel = np.zeros(Q, bool)
+            sel[obs] = True
+            sl = ogp.shortlist(ucb, sel, M)
+            picks = list(st["obs"][s0:s0 + R - LOCAL])
+            assert all(ucb[p] >= ucb[sl[-1]] - tol for p in picks), rnd
+            cand = np.array(list(sl) + [p for p in picks if p not in set(sl.tolist())])
+            cov = g.posterior_cov(pool64[obs], pool64[cand])
+            taken = np.zeros(len(cand), bool)
+            for p in picks:
+                i = int(np.nonzero(cand == p)[0][0])
+                bu = mu_r[cand] + KAPPA * np.sqrt(np.maximum(np.diag(cov), 0))
+                bu[taken] = -np.inf
+                assert bu[i] >= bu.max() - tol, (rnd, p, bu[i], bu.max())
+                taken[i] = True
+                col = cov[:, i].copy()
+                cov -= np.outer(col, col) / (col[i] + g.sn2)
+        mu, var = g.posterior(pool64[st["obs"]], y, np.full(len(y), m0), pool64,
+                              np.full(Q, m0))
+        assert np.abs(st["mu"] - mu).max() < 5e-3 * np.sqrt(sf2) + 1e-6
+        assert np.abs(st["var"] - var).max() < 5e-3 * sf2 + 1e-9
+
+
+def test_local_picks_argument_checks():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_03308_gb300 import CCError, Context
+    F = gen.field(31, X, Y, Z, N)
+    ctx = Context(0)
+    fid = ctx.load_field(F)
+    rids = ctx.partition_regular(fid, 8, 8, 3)
+    for kw in (dict(local_picks=R), dict(local_picks=-1), dict(local_picks=2, local_scale=0.0)):
+        with pytest.raises(CCError):
+            ctx.bos_create(fid, [rids[0]], [rids[1]], pool=Q, per_round=R, rounds=T, shortlist=M,
+                           **kw)
+    ctx.close()
