@@ -877,7 +877,8 @@ def run_context(args, cc, dev, stream, rank, sur=None):
             rp_b.append(rids[j])
     n_rp, R, T = len(rp_a), cfg["per_round"], cfg["rounds"]
     kw = dict(pool=2048, per_round=R, rounds=T, shortlist=128, kappa=0.5,
-              objective=pg.CC_MI_KSG, k=cfg["k"], bins=cfg["bins"], seed=cfg["seed"] + rank)
+              objective=pg.CC_MI_KSG, k=cfg["k"], bins=cfg["bins"], seed=cfg["seed"] + rank,
+              local_picks=R // 4, local_scale=0.0625)
 
     def timed(use_graph, objective=pg.CC_MI_KSG):
         warm = cc.bos_create(fid, rp_a, rp_b, **dict(kw, objective=objective))
@@ -940,7 +941,7 @@ def run_context(args, cc, dev, stream, rank, sur=None):
                        "surrogate_prior_wins": float(np.mean(sbest > ksg_best)),
                        "surrogate_prior_ties": float(np.mean(sbest == ksg_best))}
     out = {"workload": cfg["name"], "region_pairs": n_rp, "rounds": T, "per_round": R,
-           "pool": kw["pool"], "shortlist": kw["shortlist"],
+           "pool": kw["pool"], "shortlist": kw["shortlist"], "local_picks": kw["local_picks"],
            "bos_ms_graph": ms_graph, "bos_ms_direct": ms_direct,
            "bos_round_ms": ms_graph / T,
            "samples_per_s": n_rp * R * T / (ms_graph * 1e-3),
@@ -1053,8 +1054,8 @@ def bos_vs_random(cc, dev, fid, rp_a, rp_b, kw, count=256, local_picks=8, local_
           for i in range(count)]
     exact_s = time.perf_counter() - t0
     found, times = {}, {}
-    for name, extra in (("bos_plain", {}), ("bos_local", dict(local_picks=local_picks,
-                                                              local_scale=local_scale))):
+    for name, extra in (("bos_plain", dict(local_picks=0)),
+                        ("bos_local", dict(local_picks=local_picks, local_scale=local_scale))):
         bo = cc.bos_create(fid, a, b, **dict(kw, objective=pg.CC_PEARSON, **extra))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1141,7 +1142,7 @@ def run_mean_tree_experiment(cc, fid, rids, rp_a, rp_b, kw):
     pos = {r: k for k, r in enumerate(rids)}
     ia, ib = [pos[rp_a[i]] for i in sel], [pos[rp_b[i]] for i in sel]
     bx, by, bz = cfg["region"]
-    kwm = dict(kw, pool=256, per_round=10, rounds=10, shortlist=16)
+    kwm = dict(kw, pool=256, per_round=10, rounds=10, shortlist=16, local_picks=2)
     out = {"region_pairs": len(sel), "samples": 100, "runs": 10}
     t0 = time.perf_counter()
     for name, objective, m in (("pearson", pg.CC_PEARSON, 0), ("ksg", pg.CC_MI_KSG, 3)):
