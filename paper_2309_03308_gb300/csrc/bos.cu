@@ -53,6 +53,7 @@ struct BosDev {
     int L;        // local proposals per round from the second round on (0: none)
     float lscale; // their spread per axis as a fraction of the region extent
     int S;        // GP observations provisioned: R + (T - 1) (R - L)
+    int Sp;       // S rounded up to 8: the stride of one pool entry's column of V
     float kappa;
     uint64_t seed;
     int objective, k, bins;
@@ -60,7 +61,8 @@ struct BosDev {
     const int* box;      // [n_rp][12]: a.x0 y0 z0 ext_x ext_y ext_z, b likewise
     const int* self;     // [n_rp]
     float* pool;         // [n_rp][Q][6]
-    float* V;            // [n_rp][R*T][Q]
+    float* V;            // [n_rp][Q][Sp] pool-major: column c (observations 0..) contiguous,
+                         // zero beyond the rows written so far
     float* mu;           // [n_rp][Q]
     float* var;          // [n_rp][Q]
     unsigned* sel;       // [n_rp][Q/32]
@@ -222,13 +224,14 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    const float* Vr = d.V + (int64_t)rp * d.S * Q;  // d.S GP observation rows per region pair
+    const int Sp = d.Sp;
+    const float* Vr = d.V + (int64_t)rp * Q * Sp;  // pool-major columns of Sp rows
     // 16 gathered rows per barrier; per row a thread reads its 2 x per
     // operands once and updates its per x per block (per <= 8)
     for (int t0 = 0; t0 < s; t0 += 16) {
         for (int e = tid; e < 16 * M; e += blockDim.x) {
             const int t = t0 + e / M, i = e % M;
-            rowbuf[e] = t < s ? Vr[(int64_t)t * Q + SL[i]] : 0.f;
+            rowbuf[e] = t < s ? Vr[(int64_t)SL[i] * Sp + t] : 0.f;
         }
         __syncthreads();
         if (per == 8) {  // shortlist of 128: the operands are two aligned float4 each
@@ -534,7 +537,8 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     float* hyp = mP + R;                          // 4
     const int* P = d.picks + rp * R + j0;
     const int per = d.n_rp * R;
-    float* Vr = d.V + (int64_t)rp * S * Q;
+    const int Sp = d.Sp;
+    float* Vr = d.V + (int64_t)rp * Q * Sp;  // pool-major columns of Sp rows
     float* mu = d.mu + (int64_t)rp * Q;
     float* var = d.var + (int64_t)rp * Q;
     if (tid < nn) {
@@ -572,7 +576,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     auto gather = [&](int t0) {  // G[t][j] = V[t0 + t][P[j]], zero beyond s and R
         for (int e = tid; e < 32 * 32; e += blockDim.x) {
             const int t = t0 + (e >> 5), j = e & 31;
-            G[e] = (t < s && j < nn) ? Vr[(int64_t)t * Q + P[j]] : 0.f;
+            G[e] = (t < s && j < nn) ? Vr[(int64_t)P[j] * Sp + t] : 0.f;
         }
     };
     for (int t0 = 0; t0 < s; t0 += 32) {
@@ -632,13 +636,17 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     }
     __syncthreads();
     // new rows: V2 = L22^-1 (K(P, pool) - V[:, P]^T V), then mu, var updates.
-    // W = V[:, P]^T V over panels of 2 x 256 pool columns: a thread keeps the
-    // 32 x 2 block of W for its columns c and c + 256 in registers; per old row
-    // t it reads G[t][0..31] as eight broadcast float4 and two values of V
-    // (64 FMAs per 8 shared + 2 global loads), loading eight rows at a time.
+    // W = V[:, P]^T V over panels of 2 x 256 pool entries: a thread keeps the
+    // nn x 2 block of W for its entries c and c + 256 in registers (groups of
+    // four picks beyond nn are skipped); V is pool-major, so per step it reads
+    // eight observations of each of its two columns as two aligned float4
+    // (rows at and beyond s are zero, as are G's) and G's eight rows as
+    // broadcast float4.
     constexpr int kPanel = 2 * kBosThreads;
     for (int c0 = 0; c0 < Q; c0 += kPanel) {
         const int cA = c0 + tid, cB = c0 + kBosThreads + tid;
+        const float* colA = Vr + (int64_t)min(cA, Q - 1) * Sp;
+        const float* colB = Vr + (int64_t)min(cB, Q - 1) * Sp;
         float wA[32], wB[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) wA[i] = wB[i] = 0.f;
@@ -647,30 +655,29 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
             gather(t0);
             __syncthreads();
             const int tn = min(32, s - t0);
-            // eight rows per step: their 16 loads of V are in flight together
             for (int tb = 0; tb < tn; tb += 8) {
-                float vA[8], vB[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int64_t row = (int64_t)(t0 + tb + u) * Q;
-                    const bool ok = tb + u < tn;
-                    vA[u] = ok && cA < Q ? __ldcs(Vr + row + cA) : 0.f;
-                    vB[u] = ok && cB < Q ? __ldcs(Vr + row + cB) : 0.f;
-                }
+                const float4 a0 = __ldcs(reinterpret_cast<const float4*>(colA + t0 + tb));
+                const float4 a1 = __ldcs(reinterpret_cast<const float4*>(colA + t0 + tb + 4));
+                const float4 b0 = __ldcs(reinterpret_cast<const float4*>(colB + t0 + tb));
+                const float4 b1 = __ldcs(reinterpret_cast<const float4*>(colB + t0 + tb + 4));
+                const float vA[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float vB[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const float4* g4 = reinterpret_cast<const float4*>(G + (tb + u) * 32);
 #pragma unroll
                     for (int i4 = 0; i4 < 8; ++i4) {
-                        const float4 g = g4[i4];
-                        wA[4 * i4 + 0] = fmaf(g.x, vA[u], wA[4 * i4 + 0]);
-                        wA[4 * i4 + 1] = fmaf(g.y, vA[u], wA[4 * i4 + 1]);
-                        wA[4 * i4 + 2] = fmaf(g.z, vA[u], wA[4 * i4 + 2]);
-                        wA[4 * i4 + 3] = fmaf(g.w, vA[u], wA[4 * i4 + 3]);
-                        wB[4 * i4 + 0] = fmaf(g.x, vB[u], wB[4 * i4 + 0]);
-                        wB[4 * i4 + 1] = fmaf(g.y, vB[u], wB[4 * i4 + 1]);
-                        wB[4 * i4 + 2] = fmaf(g.z, vB[u], wB[4 * i4 + 2]);
-                        wB[4 * i4 + 3] = fmaf(g.w, vB[u], wB[4 * i4 + 3]);
+                        if (4 * i4 < nn) {  // uniform over the block
+                            const float4 g = g4[i4];
+                            wA[4 * i4 + 0] = fmaf(g.x, vA[u], wA[4 * i4 + 0]);
+                            wA[4 * i4 + 1] = fmaf(g.y, vA[u], wA[4 * i4 + 1]);
+                            wA[4 * i4 + 2] = fmaf(g.z, vA[u], wA[4 * i4 + 2]);
+                            wA[4 * i4 + 3] = fmaf(g.w, vA[u], wA[4 * i4 + 3]);
+                            wB[4 * i4 + 0] = fmaf(g.x, vB[u], wB[4 * i4 + 0]);
+                            wB[4 * i4 + 1] = fmaf(g.y, vB[u], wB[4 * i4 + 1]);
+                            wB[4 * i4 + 2] = fmaf(g.z, vB[u], wB[4 * i4 + 2]);
+                            wB[4 * i4 + 3] = fmaf(g.w, vB[u], wB[4 * i4 + 3]);
+                        }
                     }
                 }
             }
@@ -690,7 +697,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
                     for (int q = 0; q < i; ++q) x = fmaf(-L[i * nn + q], w[q], x);
                     x /= L[i * nn + i];
                     w[i] = x;
-                    Vr[(int64_t)(s + i) * Q + c] = x;
+                    Vr[(int64_t)c * Sp + s + i] = x;
                     dv = fmaf(x, x, dv);
                     dm = fmaf(x, b2[i], dm);
                 }
@@ -959,6 +966,7 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
     d.L = prm->local_picks;
     d.lscale = prm->local_scale;
     d.S = R + (T - 1) * (R - d.L);
+    d.Sp = (d.S + 7) / 8 * 8;
     d.kappa = prm->kappa;
     d.seed = prm->seed;
     d.objective = prm->objective;
@@ -972,7 +980,7 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
     BK(b->box.alloc(box.size() * 4));
     BK(b->self.alloc(self.size() * 4));
     BK(b->pool.alloc((size_t)n_rp * Q * 6 * 4));
-    BK(b->V.alloc((size_t)n_rp * S * Q * 4));
+    BK(b->V.alloc((size_t)n_rp * Q * d.Sp * 4));
     BK(b->mu.alloc((size_t)n_rp * Q * 4));
     BK(b->var.alloc((size_t)n_rp * Q * 4));
     BK(b->sel.alloc((size_t)n_rp * (Q / 32) * 4));
@@ -996,6 +1004,7 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
     BK(cudaMemsetAsync(b->sel.p, 0, b->sel.bytes, st));
     BK(cudaMemsetAsync(b->counters.p, 0, 16, st));
     BK(cudaMemsetAsync(b->beta.p, 0, b->beta.bytes, st));
+    BK(cudaMemsetAsync(b->V.p, 0, b->V.bytes, st));  // rows not yet written read as zero
     d.box = b->box.as<int>();
     d.self = b->self.as<int>();
     d.pool = b->pool.as<float>();
