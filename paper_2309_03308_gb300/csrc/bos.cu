@@ -47,6 +47,7 @@ double digamma_int_host(int m);
 
 constexpr uint64_t kPoolKey = 0xB05B05ull, kRoundKey = 0xB0517Dull;
 constexpr int kBosThreads = 256;
+constexpr int kGRows = 512;  // rows of V[:, P] the conditioning keeps in shared memory
 
 struct BosDev {
     int n_rp, Q, R, T, M;
@@ -177,8 +178,8 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
     float* cov = reinterpret_cast<float*>(SL + M);
     float* pos = cov + M * M;
     float* msl = pos + M * 6;
-    float* rowbuf = msl + M;         // 16 rows x M
-    float* red_v = rowbuf + 16 * M;  // per-warp argmax
+    float* rowbuf = msl + M;         // 2 x 16 rows x M (double-buffered batches)
+    float* red_v = rowbuf + 32 * M;  // per-warp argmax
     int* red_i = reinterpret_cast<int*>(red_v + 32);
     const float* mu = d.mu + (int64_t)rp * Q;
     const float* var = d.var + (int64_t)rp * Q;
@@ -226,18 +227,39 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
     const int Sp = d.Sp;
     const float* Vr = d.V + (int64_t)rp * Q * Sp;  // pool-major columns of Sp rows
-    // 16 gathered rows per barrier; per row a thread reads its 2 x per
-    // operands once and updates its per x per block (per <= 8)
-    for (int t0 = 0; t0 < s; t0 += 16) {
-        for (int e = tid; e < 16 * M; e += blockDim.x) {
-            const int t = t0 + e / M, i = e % M;
-            rowbuf[e] = t < s ? Vr[(int64_t)SL[i] * Sp + t] : 0.f;
+    // 16 gathered rows per barrier, double-buffered: the next batch's values
+    // (M / 16 per thread) are loaded into registers while the current batch is
+    // multiplied, then stored into the other half of rowbuf; per row a thread
+    // reads its 2 x per operands once and updates its per x per block (per <= 8)
+    const int vals_per_thread = 16 * M / kBosThreads;  // M / 16 <= 8
+    float nxt[8];
+    auto load_batch = [&](int t0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < vals_per_thread) {
+                const int e = tid + q * kBosThreads, t = t0 + e / M, i = e % M;
+                nxt[q] = t < s ? Vr[(int64_t)SL[i] * Sp + t] : 0.f;
+            }
         }
-        __syncthreads();
+    };
+    auto store_batch = [&](float* buf) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < vals_per_thread) buf[tid + q * kBosThreads] = nxt[q];
+    };
+    if (s > 0) {
+        load_batch(0);
+        store_batch(rowbuf);
+    }
+    __syncthreads();
+    for (int t0 = 0, bi = 0; t0 < s; t0 += 16, bi ^= 1) {
+        const float* cur = rowbuf + bi * 16 * M;
+        const bool more = t0 + 16 < s;
+        if (more) load_batch(t0 + 16);
         if (per == 8) {  // shortlist of 128: the operands are two aligned float4 each
             for (int t = 0; t < 16; ++t) {
-                const float4* ra = reinterpret_cast<const float4*>(rowbuf + t * M + ti * 8);
-                const float4* rb = reinterpret_cast<const float4*>(rowbuf + t * M + tj * 8);
+                const float4* ra = reinterpret_cast<const float4*>(cur + t * M + ti * 8);
+                const float4* rb = reinterpret_cast<const float4*>(cur + t * M + tj * 8);
                 const float4 a0 = ra[0], a1 = ra[1], b0 = rb[0], b1 = rb[1];
                 const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                 const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
@@ -251,8 +273,8 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
                 float a[8], b[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    a[i] = i < per ? rowbuf[t * M + ti * per + i] : 0.f;
-                    b[i] = i < per ? rowbuf[t * M + tj * per + i] : 0.f;
+                    a[i] = i < per ? cur[t * M + ti * per + i] : 0.f;
+                    b[i] = i < per ? cur[t * M + tj * per + i] : 0.f;
                 }
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
@@ -260,6 +282,8 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
                     for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
             }
         }
+        // the other half was last read in the previous batch, before its barrier
+        if (more) store_batch(rowbuf + (bi ^ 1) * 16 * M);
         __syncthreads();
     }
 #pragma unroll
@@ -525,8 +549,8 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     // the round's GP observations: all R proposals in round 0, the R - L pool
     // proposals (after the local ones) later; nn <= R, matrices use stride nn
     const int s = obs_before(r, R, d.L), nn = obs_new(r, R, d.L), j0 = r == 0 ? 0 : d.L;
-    float* G = reinterpret_cast<float*>(cs);               // 32 rows x 32 of V[:, P] (0-padded)
-    double* Lf = reinterpret_cast<double*>(G + 32 * 32);   // R x R (fp64 Cholesky)
+    float* G = reinterpret_cast<float*>(cs);                 // kGRows x 32 of V[:, P] (0-padded)
+    double* Lf = reinterpret_cast<double*>(G + kGRows * 32);  // R x R (fp64 Cholesky)
     float* covP = reinterpret_cast<float*>(Lf + R * R);    // R x R
     float* L = covP + R * R;                               // R x R fp32 copy
     float* gb = L + R * R;                        // R: V[:, P]^T beta
@@ -570,31 +594,35 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     if (tid < nn) mP[tid] = d.prior ? d.prior[(int64_t)rp * Q + P[tid]] : m0;
     float inv_ell[6];
     inv_ell_of(d, rp, inv_ell);
-    // covP = V[:, P]^T V[:, P] and gb = V[:, P]^T beta over the s old rows
+    // covP = V[:, P]^T V[:, P] and gb = V[:, P]^T beta over the s old rows.
+    // G holds up to kGRows rows of V[:, P] at a time (most rounds: all of them)
     float cacc[4] = {0.f, 0.f, 0.f, 0.f};  // entries tid, tid+256, ... of R x R
     float gacc = 0.f;
-    auto gather = [&](int t0) {  // G[t][j] = V[t0 + t][P[j]], zero beyond s and R
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+    // G[t][j] = V[t0 + t][P[j]] for t < rows rounded up to 8, zero beyond s and nn
+    auto gather = [&](int t0, int rows) {
+        const int rp8 = (rows + 7) & ~7;
+        for (int e = tid; e < rp8 * 32; e += blockDim.x) {
             const int t = t0 + (e >> 5), j = e & 31;
             G[e] = (t < s && j < nn) ? Vr[(int64_t)P[j] * Sp + t] : 0.f;
         }
     };
-    for (int t0 = 0; t0 < s; t0 += 32) {
-        gather(t0);
+    for (int t0 = 0; t0 < s; t0 += kGRows) {
+        const int rows = min(kGRows, s - t0);
+        __syncthreads();
+        gather(t0, rows);
         __syncthreads();
         for (int q = 0; q < 4; ++q) {
             const int e = tid + q * blockDim.x;
             if (e < nn * nn) {
                 const int i = e / nn, j = e % nn;
                 float a = cacc[q];
-                for (int t = 0; t < 32; ++t) a = fmaf(G[t * 32 + i], G[t * 32 + j], a);
+                for (int t = 0; t < rows; ++t) a = fmaf(G[t * 32 + i], G[t * 32 + j], a);
                 cacc[q] = a;
             }
         }
         if (tid < nn)
-            for (int t = 0; t < 32 && t0 + t < s; ++t)
+            for (int t = 0; t < rows; ++t)
                 gacc = fmaf(G[t * 32 + tid], d.beta[(int64_t)rp * S + t0 + t], gacc);
-        __syncthreads();
     }
     for (int q = 0; q < 4; ++q) {
         const int e = tid + q * blockDim.x;
@@ -638,11 +666,13 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     // new rows: V2 = L22^-1 (K(P, pool) - V[:, P]^T V), then mu, var updates.
     // W = V[:, P]^T V over panels of 2 x 256 pool entries: a thread keeps the
     // nn x 2 block of W for its entries c and c + 256 in registers (groups of
-    // four picks beyond nn are skipped); V is pool-major, so per step it reads
-    // eight observations of each of its two columns as two aligned float4
-    // (rows at and beyond s are zero, as are G's) and G's eight rows as
-    // broadcast float4.
+    // four picks beyond nn are skipped); V is pool-major, so a step reads eight
+    // observations of each of its two columns as two aligned float4 (rows at
+    // and beyond s are zero, as are G's), the next step's loads issued before
+    // this step's FMAs, and G's eight rows as broadcast float4 from shared
+    // memory (G stays resident while s <= kGRows).
     constexpr int kPanel = 2 * kBosThreads;
+    const bool resident = s <= kGRows;
     for (int c0 = 0; c0 < Q; c0 += kPanel) {
         const int cA = c0 + tid, cB = c0 + kBosThreads + tid;
         const float* colA = Vr + (int64_t)min(cA, Q - 1) * Sp;
@@ -650,16 +680,29 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
         float wA[32], wB[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) wA[i] = wB[i] = 0.f;
-        for (int t0 = 0; t0 < s; t0 += 32) {
-            __syncthreads();
-            gather(t0);
-            __syncthreads();
-            const int tn = min(32, s - t0);
-            for (int tb = 0; tb < tn; tb += 8) {
-                const float4 a0 = __ldcs(reinterpret_cast<const float4*>(colA + t0 + tb));
-                const float4 a1 = __ldcs(reinterpret_cast<const float4*>(colA + t0 + tb + 4));
-                const float4 b0 = __ldcs(reinterpret_cast<const float4*>(colB + t0 + tb));
-                const float4 b1 = __ldcs(reinterpret_cast<const float4*>(colB + t0 + tb + 4));
+        float4 na0, na1, nb0, nb1;  // the next step's rows of the two columns
+        if (s > 0) {
+            na0 = __ldcs(reinterpret_cast<const float4*>(colA));
+            na1 = __ldcs(reinterpret_cast<const float4*>(colA + 4));
+            nb0 = __ldcs(reinterpret_cast<const float4*>(colB));
+            nb1 = __ldcs(reinterpret_cast<const float4*>(colB + 4));
+        }
+        for (int t0 = 0; t0 < s; t0 += kGRows) {
+            const int rows = min(kGRows, s - t0);
+            if (!resident) {  // uniform: every thread takes the same branch
+                __syncthreads();
+                gather(t0, rows);
+                __syncthreads();
+            }
+            for (int tb = 0; tb < rows; tb += 8) {
+                const float4 a0 = na0, a1 = na1, b0 = nb0, b1 = nb1;
+                const int tn = t0 + tb + 8;  // the next step's first row
+                if (tn < s) {
+                    na0 = __ldcs(reinterpret_cast<const float4*>(colA + tn));
+                    na1 = __ldcs(reinterpret_cast<const float4*>(colA + tn + 4));
+                    nb0 = __ldcs(reinterpret_cast<const float4*>(colB + tn));
+                    nb1 = __ldcs(reinterpret_cast<const float4*>(colB + tn + 4));
+                }
                 const float vA[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                 const float vB[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -766,11 +809,12 @@ cc_status bfail(cc_ctx* c, cc_status s, const char* fmt, ...) {
 
 size_t propose_smem(const BosDev& d) {
     const int M = d.M;
-    return (size_t)d.Q * 8 + M * 4 + (size_t)M * M * 4 + M * 6 * 4 + M * 4 + 16 * M * 4 + 32 * 8;
+    return (size_t)d.Q * 8 + M * 4 + (size_t)M * M * 4 + M * 6 * 4 + M * 4 + 32 * M * 4 + 32 * 8;
 }
 size_t condition_smem(const BosDev& d) {
     const int R = d.R;
-    return 32 * 32 * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 + R * 6 * 4 + 2 * R * 4 + 16;
+    return (size_t)kGRows * 32 * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 + R * 6 * 4 +
+           2 * R * 4 + 16;
 }
 size_t eval_smem(const BosDev& d, int warps) {
     const int pl = (d.n + 2) & ~1;
