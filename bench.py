@@ -656,6 +656,12 @@ def run_one_to_all(args, cc, dev, stream, n):
     return res
 
 
+# Surrogate training: 8192 pairs per step with the learning rate scaled by the
+# square root of the batch ratio from 4096 / 2e-3 (same held-out correlation
+# for both networks, 1.4x the samples per second of batch 4096)
+SUR_BATCH, SUR_LR = 8192, 2.8e-3
+
+
 def run_surrogate(args, cc, dev, stream, rank):
     """Learned surrogate: train on exact KSG values, screen a focus region pair."""
     import torch
@@ -679,8 +685,8 @@ def run_surrogate(args, cc, dev, stream, rank):
     sur = Surrogate(cc, cfg["n"], seed=5)
     epochs = 3
     t0 = time.perf_counter()
-    losses = sur.train(ft, pa[:n_fit], pb[:n_fit], tgt[:n_fit], epochs=epochs, batch=4096,
-                       lr=2e-3, seed=6)
+    losses = sur.train(ft, pa[:n_fit], pb[:n_fit], tgt[:n_fit], epochs=epochs, batch=SUR_BATCH,
+                       lr=SUR_LR, seed=6)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     held = sur.predict(ft, pa[n_fit:], pb[n_fit:], out=torch.empty(n_train - n_fit, device=dev))
@@ -709,7 +715,8 @@ def run_surrogate(args, cc, dev, stream, rank):
     exact_top = cc.eval_pairs(fe, fe, Params(pg.CC_MI_KSG, k=cfg["k"]), A[ia], B[ib])
     rpa, rpb = cc.sample_pairs(ra, rb, 33, K)
     exact_rand = cc.eval_pairs(fe, fe, Params(pg.CC_MI_KSG, k=cfg["k"]), rpa, rpb)
-    out = {"workload": cfg["name"], "train_pairs": n_fit, "epochs": epochs,
+    out = {"workload": cfg["name"], "train_pairs": n_fit, "epochs": epochs, "batch": SUR_BATCH,
+           "lr": SUR_LR,
            "label_s": label_s, "train_s": train_s,
            "train_samples_per_s": epochs * n_fit / train_s,
            "train_loss_per_epoch": [float(x) for x in losses],
@@ -816,8 +823,8 @@ def pearson_surrogate(cc, dev, ft_field, fe, regions):
     sur = Surrogate(cc, cfg["n"], seed=8)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = sur.train(ft, pa[:n_fit], pb[:n_fit], tgt[:n_fit], epochs=3, batch=4096, lr=2e-3,
-                       seed=9)
+    losses = sur.train(ft, pa[:n_fit], pb[:n_fit], tgt[:n_fit], epochs=3, batch=SUR_BATCH,
+                       lr=SUR_LR, seed=9)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     held = sur.predict(ft, pa[n_fit:], pb[n_fit:], out=torch.empty(n_train - n_fit, device=dev))
