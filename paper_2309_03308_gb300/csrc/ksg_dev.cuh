@@ -217,8 +217,8 @@ __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
     __syncwarp();
 }
 
-// One sample (x-sorted position ti) of a staged pair: eps and the two counts;
-// returns psi[n_x] + psi[n_y] from the fixed-point table.
+// The walk state of one sample of a staged pair (ksg_begin, ksg_step,
+// ksg_finish below; ksg_sample runs them in order).
 //
 // The walk runs along one axis (W: that axis's sorted (value, other value)
 // entries), from the sample's position s outwards on both sides at once.
@@ -233,9 +233,20 @@ __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
 // value; every position not passed then has a distance not below it, so the
 // list's last entry is eps exactly.
 template <int KMAX>
-__device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n, int n_pad, int k,
-                                                int ti, const long long* __restrict__ psi,
-                                                int* cx_out, int* cy_out, float* eps_out) {
+struct KsgWalk {
+    float top[KMAX];    // the KMAX smallest distances offered so far, ascending
+    const float2* W;    // walk axis order
+    const float2* O;    // other axis order (sorted in .x)
+    float pv, ov;       // the sample's value on the walk / other axis
+    int s, L, R;        // the sample's walk position; next unvisited positions
+    bool on_y;          // the walk runs along y
+};
+
+// Start the walk of sample ti (x-sorted position) of a staged pair: choose
+// the axis, visit the first k positions and sort them.
+template <int KMAX>
+__device__ __forceinline__ void ksg_begin(KsgWalk<KMAX>& w, const unsigned char* slot, int n,
+                                          int n_pad, int k, int ti) {
     constexpr int pad = ksg_pad(KMAX);
     constexpr int P1 = (KMAX + 1) / 2, NP1 = 2 * P1;
     const float2* XO = reinterpret_cast<const float2*>(slot) + pad;
@@ -243,72 +254,97 @@ __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n
     const uint16_t* upos = reinterpret_cast<const uint16_t*>(YO + n_pad + pad);
     const float2 zi = XO[ti];
     const int ui = upos[ti];
-    // walk along the axis with the wider local spacing
-    const int h = 4;
+    // walk along the axis with the wider local spacing (span of the 8
+    // neighbours on each side in sorted order)
+    const int h = 8;
     const float span_x = __fsub_rn(XO[min(ti + h, n - 1)].x, XO[max(ti - h, 0)].x);
     const float span_y = __fsub_rn(YO[min(ui + h, n - 1)].x, YO[max(ui - h, 0)].x);
-    const bool on_y = span_y > span_x;
-    const float2* W = on_y ? YO : XO;
-    const float2* O = on_y ? XO : YO;  // other axis order (sorted in .x)
-    const int s = on_y ? ui : ti;
-    const float pv = on_y ? zi.y : zi.x, ov = on_y ? zi.x : zi.y;
+    w.on_y = span_y > span_x;
+    w.W = w.on_y ? YO : XO;
+    w.O = w.on_y ? XO : YO;
+    w.s = w.on_y ? ui : ti;
+    w.pv = w.on_y ? zi.y : zi.x;
+    w.ov = w.on_y ? zi.x : zi.y;
     // the first k positions, alternating left / right; unused slots are -inf
-    float top[KMAX];
+    float c[NP1];
+#pragma unroll
+    for (int t = 0; t < P1; ++t) {
+        const float2 l = w.W[w.s - 1 - t], r = w.W[w.s + 1 + t];
+        const float dl = fmaxf(__fsub_rn(w.pv, l.x), fabsf(__fsub_rn(w.ov, l.y)));
+        const float dr = fmaxf(__fsub_rn(r.x, w.pv), fabsf(__fsub_rn(w.ov, r.y)));
+        c[2 * t] = 2 * t < k ? dl : -CUDART_INF_F;
+        c[2 * t + 1] = 2 * t + 1 < k ? dr : -CUDART_INF_F;
+    }
+    sort_small<NP1>(c);
+#pragma unroll
+    for (int m = 0; m < KMAX; ++m) w.top[m] = c[m + NP1 - KMAX];
+    w.L = w.s - (k + 1) / 2 - 1;
+    w.R = w.s + k / 2 + 1;
+}
+
+// One walk step; returns false (and changes nothing) once the walk has ended.
+template <int KMAX>
+__device__ __forceinline__ bool ksg_step(KsgWalk<KMAX>& w) {
+    // a side is open while its next axis distance is below the k-th value;
+    // a step offers two positions per open side, or four from the only open
+    // side (a walk near either end of the sorted order then takes half the
+    // steps). Offered positions: L, L-1 (or R+2, R+3 when the left side is
+    // closed) and R, R+1 (or L-2, L-3 when the right side is closed); an
+    // open left side has L >= 0 and an open right side R <= n - 1, so every
+    // index stays within the sentinels.
+    const float2* W = w.W;
+    const int L = w.L, R = w.R;
+    const float pv = w.pv, ov = w.ov;
+    const float kth = w.top[KMAX - 1];
+    const bool lo = __fsub_rn(pv, W[L].x) < kth;
+    const bool ro = __fsub_rn(W[R].x, pv) < kth;
+    if (!(lo || ro)) return false;
+    const float2 z0 = W[lo ? L : R + 2], z1 = W[lo ? L - 1 : R + 3];
+    const float2 z2 = W[ro ? R : L - 2], z3 = W[ro ? R + 1 : L - 3];
+    const float a0 = fabsf(__fsub_rn(pv, z0.x)), a1 = fabsf(__fsub_rn(pv, z1.x));
+    const float a2 = fabsf(__fsub_rn(pv, z2.x)), a3 = fabsf(__fsub_rn(pv, z3.x));
+    const float d0 = fmaxf(a0, fabsf(__fsub_rn(ov, z0.y)));
+    const float d1 = fmaxf(a1, fabsf(__fsub_rn(ov, z1.y)));
+    const float d2 = fmaxf(a2, fabsf(__fsub_rn(ov, z2.y)));
+    const float d3 = fmaxf(a3, fabsf(__fsub_rn(ov, z3.y)));
+    // positions are passed in order of axis distance on each side, so the
+    // passed ones of z0, z1 and of z2, z3 are prefixes
+    const int c01 = (int)(a0 < kth) + (int)(a1 < kth);
+    const int c23 = (int)(a2 < kth) + (int)(a3 < kth);
+    w.L = L - (lo ? c01 + (ro ? 0 : c23) : 0);
+    w.R = R + (ro ? c23 + (lo ? 0 : c01) : 0);
+    topk_merge4<KMAX>(w.top, d0, d1, d2, d3);
+    return true;
+}
+
+// The counts of a finished walk; returns psi[n_x] + psi[n_y] from the
+// fixed-point table.
+template <int KMAX>
+__device__ __forceinline__ long long ksg_finish(const KsgWalk<KMAX>& w, int n,
+                                                const long long* __restrict__ psi, int* cx_out,
+                                                int* cy_out, float* eps_out) {
+    const float2* W = w.W;
+    const float2* O = w.O;
+    const float pv = w.pv, ov = w.ov, eps = w.top[KMAX - 1];
+    const int s = w.s;
+    // walk axis: the passed window (L, R), trimmed to axis distance < eps.
+    // Along each side the axis distance falls towards s, so the positions to
+    // trim are a prefix of the side; almost always fewer than eight, found
+    // by lifting over 4, 2, 1, with a position-by-position continuation
+    // beyond seven.
+    int L = max(w.L, -1), R = min(w.R, n);
     {
-        float c[NP1];
-#pragma unroll
-        for (int t = 0; t < P1; ++t) {
-            const float2 l = W[s - 1 - t], r = W[s + 1 + t];
-            const float dl = fmaxf(__fsub_rn(pv, l.x), fabsf(__fsub_rn(ov, l.y)));
-            const float dr = fmaxf(__fsub_rn(r.x, pv), fabsf(__fsub_rn(ov, r.y)));
-            c[2 * t] = 2 * t < k ? dl : -CUDART_INF_F;
-            c[2 * t + 1] = 2 * t + 1 < k ? dr : -CUDART_INF_F;
-        }
-        sort_small<NP1>(c);
-#pragma unroll
-        for (int m = 0; m < KMAX; ++m) top[m] = c[m + NP1 - KMAX];
-    }
-    int L = s - (k + 1) / 2 - 1, R = s + k / 2 + 1;
-    while (true) {
-        // a side is open while its next axis distance is below the k-th
-        // value; a step offers two positions per open side, or four from
-        // the only open side (a walk near either end of the sorted order
-        // then takes half the steps). Offered positions: L, L-1 (or R+2,
-        // R+3 when the left side is closed) and R, R+1 (or L-2, L-3 when
-        // the right side is closed); an open left side has L >= 0 and an
-        // open right side R <= n - 1, so every index stays within the
-        // sentinels.
-        const float kth = top[KMAX - 1];
-        const bool lo = __fsub_rn(pv, W[L].x) < kth;
-        const bool ro = __fsub_rn(W[R].x, pv) < kth;
-        if (!(lo || ro)) break;
-        const float2 z0 = W[lo ? L : R + 2], z1 = W[lo ? L - 1 : R + 3];
-        const float2 z2 = W[ro ? R : L - 2], z3 = W[ro ? R + 1 : L - 3];
-        const float a0 = fabsf(__fsub_rn(pv, z0.x)), a1 = fabsf(__fsub_rn(pv, z1.x));
-        const float a2 = fabsf(__fsub_rn(pv, z2.x)), a3 = fabsf(__fsub_rn(pv, z3.x));
-        const float d0 = fmaxf(a0, fabsf(__fsub_rn(ov, z0.y)));
-        const float d1 = fmaxf(a1, fabsf(__fsub_rn(ov, z1.y)));
-        const float d2 = fmaxf(a2, fabsf(__fsub_rn(ov, z2.y)));
-        const float d3 = fmaxf(a3, fabsf(__fsub_rn(ov, z3.y)));
-        // positions are passed in order of axis distance on each side, so
-        // the passed ones of z0, z1 and of z2, z3 are prefixes
-        const int c01 = (int)(a0 < kth) + (int)(a1 < kth);
-        const int c23 = (int)(a2 < kth) + (int)(a3 < kth);
-        L -= lo ? c01 + (ro ? 0 : c23) : 0;
-        R += ro ? c23 + (lo ? 0 : c01) : 0;
-        topk_merge4<KMAX>(top, d0, d1, d2, d3);
-    }
-    const float eps = top[KMAX - 1];
-    // walk axis: the passed window (L, R), trimmed to axis distance < eps
-    L = max(L, -1);
-    R = min(R, n);
-    {  // trim both ends at once by branch-free binary lifting over the window
         const int wl = s - 1 - L, wr = R - 1 - s;
         int tl = 0, tr = 0;
-        for (int step = 1 << (31 - __clz(max(wl, wr) | 1)); step > 0; step >>= 1) {
+#pragma unroll
+        for (int step = 4; step > 0; step >>= 1) {
             if (tl + step <= wl && !(__fsub_rn(pv, W[L + tl + step].x) < eps)) tl += step;
             if (tr + step <= wr && !(__fsub_rn(W[R - tr - step].x, pv) < eps)) tr += step;
         }
+        if (tl == 7)
+            while (tl < wl && !(__fsub_rn(pv, W[L + tl + 1].x) < eps)) ++tl;
+        if (tr == 7)
+            while (tr < wr && !(__fsub_rn(W[R - tr - 1].x, pv) < eps)) ++tr;
         L += tl;
         R -= tr;
     }
@@ -323,14 +359,27 @@ __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n
         if (jb < n && __fsub_rn(O[jb].x, ov) < eps) b += step;
     }
     const int c_oth = max(b - a, 1);
-    const int cx = on_y ? c_oth : c_walk;
-    const int cy = on_y ? c_walk : c_oth;
+    const int cx = w.on_y ? c_oth : c_walk;
+    const int cy = w.on_y ? c_walk : c_oth;
     if (cx_out) {
         *cx_out = cx;
         *cy_out = cy;
         *eps_out = eps;
     }
     return psi[cx] + psi[cy];
+}
+
+// One sample (x-sorted position ti) of a staged pair: eps and the two counts;
+// returns psi[n_x] + psi[n_y] from the fixed-point table.
+template <int KMAX>
+__device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n, int n_pad, int k,
+                                                int ti, const long long* __restrict__ psi,
+                                                int* cx_out, int* cy_out, float* eps_out) {
+    KsgWalk<KMAX> w;
+    ksg_begin<KMAX>(w, slot, n, n_pad, k, ti);
+    while (ksg_step<KMAX>(w)) {
+    }
+    return ksg_finish<KMAX>(w, n, psi, cx_out, cy_out, eps_out);
 }
 
 }  // namespace cc
