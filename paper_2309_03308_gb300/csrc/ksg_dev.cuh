@@ -134,8 +134,11 @@ __host__ __device__ constexpr int ksg_kmax(int k) {
 }
 
 // sentinel entries on each side of a staged sorted array: the first walk
-// step reads up to ceil(KMAX/2) positions out, a later step two more
-__host__ __device__ constexpr int ksg_pad(int kmax) { return (kmax + 1) / 2 + 2; }
+// step reads up to ceil(KMAX/2) positions out, a later step two more, and
+// the window trim reads up to seven positions past the sample
+__host__ __device__ constexpr int ksg_pad(int kmax) {
+    return (kmax + 1) / 2 + 2 > 7 ? (kmax + 1) / 2 + 2 : 7;
+}
 
 __host__ __device__ constexpr size_t ksg_slot_bytes(int n_pad, int kmax) {
     return (size_t)(n_pad + 2 * ksg_pad(kmax)) * 2 * sizeof(float2) +
@@ -331,15 +334,19 @@ __device__ __forceinline__ long long ksg_finish(const KsgWalk<KMAX>& w, int n,
     // Along each side the axis distance falls towards s, so the positions to
     // trim are a prefix of the side; almost always fewer than eight, found
     // by lifting over 4, 2, 1, with a position-by-position continuation
-    // beyond seven.
+    // beyond seven. The lifting needs no window bound: for eps > 0 the
+    // sample's own position and everything past it (sentinels included)
+    // fail the trim test, and the probes stay within seven positions of the
+    // window, inside the sentinels (for eps = 0 the count is 1 whatever the
+    // trim finds).
     int L = max(w.L, -1), R = min(w.R, n);
     {
         const int wl = s - 1 - L, wr = R - 1 - s;
         int tl = 0, tr = 0;
 #pragma unroll
         for (int step = 4; step > 0; step >>= 1) {
-            if (tl + step <= wl && !(__fsub_rn(pv, W[L + tl + step].x) < eps)) tl += step;
-            if (tr + step <= wr && !(__fsub_rn(W[R - tr - step].x, pv) < eps)) tr += step;
+            if (!(__fsub_rn(pv, W[L + tl + step].x) < eps)) tl += step;
+            if (!(__fsub_rn(W[R - tr - step].x, pv) < eps)) tr += step;
         }
         if (tl == 7)
             while (tl < wl && !(__fsub_rn(pv, W[L + tl + 1].x) < eps)) ++tl;
@@ -350,14 +357,21 @@ __device__ __forceinline__ long long ksg_finish(const KsgWalk<KMAX>& w, int n,
     }
     const int c_walk = eps > 0.f ? R - L - 1 : 1;
     // other axis: [a, b) with a = first j with fl(ov - O[j].x) < eps,
-    // b = first j with fl(O[j].x - ov) >= eps; both found by one branch-free
-    // binary search over power-of-two steps (a and b interleaved)
+    // b = first j with fl(O[j].x - ov) >= eps (fl32 differences are monotone
+    // along the sorted order). Both by one branch-free search (a and b
+    // interleaved) that halves a range of the same length for every lane:
+    // the answer lies in [base, base + len], a probe at base + half - 1
+    // either moves base up by half or leaves it, and len shrinks by half, so
+    // no probe leaves [0, n) and the loop count is the same for all lanes.
     int a = 0, b = 0;
-    for (int step = 1 << (31 - __clz(n)); step > 0; step >>= 1) {
-        const int ja = a + step - 1, jb = b + step - 1;
-        if (ja < n && !(__fsub_rn(ov, O[ja].x) < eps)) a += step;
-        if (jb < n && __fsub_rn(O[jb].x, ov) < eps) b += step;
+    for (int len = n; len > 1;) {
+        const int half = len >> 1;
+        if (!(__fsub_rn(ov, O[a + half - 1].x) < eps)) a += half;
+        if (__fsub_rn(O[b + half - 1].x, ov) < eps) b += half;
+        len -= half;
     }
+    a += !(__fsub_rn(ov, O[a].x) < eps) ? 1 : 0;
+    b += __fsub_rn(O[b].x, ov) < eps ? 1 : 0;
     const int c_oth = max(b - a, 1);
     const int cx = w.on_y ? c_oth : c_walk;
     const int cy = w.on_y ? c_walk : c_oth;
