@@ -204,6 +204,13 @@ struct SideState {
     unsigned long long best;  // (key of best value, inverted pair index)
     float thr[2];             // second-pass threshold, bound
 };
+// C[m][n] = sum_k A[m sam + k sak] B[n sbn + k sbk] on the tensor cores
+// (tc_mm.cu): BF16 (flag 1) or FP32 operands, N <= 256; with kc < K the z-th
+// K slice writes part[z][M][N]; B's row b_ones (>= 0) reads as 1.
+cudaError_t launch_tc_mm(const void* A, int a_bf16, int64_t sam, int64_t sak, const void* B,
+                         int b_bf16, int64_t sbn, int64_t sbk, int64_t b_ones, float* C,
+                         int64_t ldc, int M, int N, int64_t K, int64_t kc, float* part,
+                         int* status, cudaStream_t st);
 cudaError_t launch_sur_screen_tc(const float* Ea, const float* Ua, const float* Eb,
                                  const void* wb, const float* w, int64_t oW3, int64_t ow4,
                                  int64_t ob4, const uint32_t* pts_a, const uint32_t* pts_b,

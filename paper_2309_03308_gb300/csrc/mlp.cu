@@ -20,6 +20,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "device.cuh"
@@ -28,6 +29,28 @@
 namespace cc {
 
 constexpr int kH1 = 128, kE = 64, kH3 = 128, kHeadIn = 3 * kE + 3;
+// row strides of the BF16 GEMM operands padded to 16 bytes (the tensor-core
+// GEMM then reads whole 16-byte chunks): encoder inputs and W1 rows of n
+// values, head inputs and W3 rows of 195
+constexpr int kHeadInP = 200;
+__host__ __device__ inline int ldz(int n) { return (n + 7) & ~7; }
+
+// padded BF16 copies of W1 [128][ldz(n)] and W3 [128][kHeadInP], written
+// wherever the BF16 weight vector is written
+struct PadW {
+    __nv_bfloat16* p;
+    int64_t oW1, oW3;
+    int n;
+};
+__device__ __forceinline__ void pad_store(const PadW& pw, int64_t i, __nv_bfloat16 v) {
+    if (i >= pw.oW1 && i < pw.oW1 + (int64_t)kH1 * pw.n) {
+        const int64_t j = i - pw.oW1;
+        pw.p[(j / pw.n) * ldz(pw.n) + j % pw.n] = v;
+    } else if (i >= pw.oW3 && i < pw.oW3 + (int64_t)kH3 * kHeadIn) {
+        const int64_t j = i - pw.oW3;
+        pw.p[(int64_t)kH1 * ldz(pw.n) + (j / kHeadIn) * kHeadInP + j % kHeadIn] = v;
+    }
+}
 
 struct SurOff {
     int64_t W1, b1, W2, b2, W3, b3, w4, b4, total;
@@ -119,14 +142,34 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// C = the sum of S dense partials [S][M][N]: slice z adds into accumulator
+// z mod 8 and the eight are added in order (a fixed order, so the result does
+// not depend on timing; eight loads in flight per thread). With bias, column
+// N - 1 goes to bias[m] and C receives columns 0 .. N - 2.
 __global__ void k_mm_reduce(const float* __restrict__ part, int S, int M, int N,
-                            float* __restrict__ C, int64_t ldc, int accumulate) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)M * N;
+                            float* __restrict__ C, int64_t ldc, int accumulate,
+                            float* __restrict__ bias) {
+    const int64_t MN = (int64_t)M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN;
          e += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int z = 0; z < S; ++z) s += part[(int64_t)z * M * N + e];
-        float* c = C + (e / N) * ldc + e % N;
-        *c = accumulate ? *c + s : s;
+        float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int z = 0;
+        for (; z + 8 <= S; z += 8) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] += part[(int64_t)(z + j) * MN + e];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (z + j < S) a[j] += part[(int64_t)(z + j) * MN + e];
+        const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+        const int64_t m = e / N;
+        const int n = (int)(e % N);
+        if (bias && n == N - 1) {
+            bias[m] = accumulate ? bias[m] + s : s;
+        } else {
+            float* c = C + m * ldc + n;
+            *c = accumulate ? *c + s : s;
+        }
     }
 }
 
@@ -152,21 +195,94 @@ static cudaError_t mm(const TA* A, int64_t sam, int64_t sak, const TB* B, int64_
         note_launch();
         const int64_t MN = (int64_t)M * N;
         k_mm_reduce<<<(unsigned)std::min<int64_t>((MN + 255) / 256, 1024), 256, 0, st>>>(
-            ws->as<float>(), S, M, N, C, ldc, acc);
+            ws->as<float>(), S, M, N, C, ldc, acc, nullptr);
     }
     return cudaGetLastError();
+}
+
+// The same product on the tensor cores (tc_mm.cu) when N <= 256 and the
+// operands are 16-byte aligned along a unit-stride dimension, with the
+// arguments in mm's order; weight gradients (few output tiles, K = the
+// batch) split K into slices of at least 128 and sum the slices' partials in
+// slice order. Otherwise (e.g. encoders of more than 256 members) k_mm.
+__global__ void k_sur_colsum(const float* __restrict__ A, int64_t rows, int cols,
+                             float* __restrict__ out);
+
+template <class TA, class TB>
+static cudaError_t tmm(int* status, const TA* A, int64_t sam, int64_t sak, const TB* B,
+                       int64_t sbk, int64_t sbn, float* C, int64_t ldc, int M, int N, int K,
+                       cudaStream_t st, DevMem* ws = nullptr, float* bias = nullptr) {
+    // bias (weight gradients): bias[m] = sum_k A(m, k), A an FP32 [K][M] matrix,
+    // computed as one more output column against an all-ones row of B
+    const int NB = N + (bias ? 1 : 0);
+    auto fallback = [&]() -> cudaError_t {
+        cudaError_t e = mm(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, 0, st, ws);
+        if (e != cudaSuccess || !bias) return e;
+        note_launch();
+        k_sur_colsum<<<M, 256, 0, st>>>(reinterpret_cast<const float*>(A), K, M, bias);
+        return cudaGetLastError();
+    };
+    if (NB > 256) return fallback();
+    constexpr int abf = std::is_same<TA, __nv_bfloat16>::value;
+    constexpr int bbf = std::is_same<TB, __nv_bfloat16>::value;
+    if (bias && (abf || sam != 1 || sak != M)) return cudaErrorInvalidValue;
+    const int64_t mt = (M + 127) / 128;
+    const int sms = sm_count();
+    int64_t kc = ((int64_t)K + 63) / 64 * 64, S = 1;
+    if (ws && 2 * mt < sms && K >= 1024) {
+        S = std::max<int64_t>(1, std::min<int64_t>(sms / mt, K / 128));
+        kc = ((K + S - 1) / S + 63) / 64 * 64;
+        S = (K + kc - 1) / kc;
+    }
+    if (S == 1 && !bias) {
+        const cudaError_t e = launch_tc_mm(A, abf, sam, sak, B, bbf, sbn, sbk, -1, C, ldc, M, N, K,
+                                           kc, nullptr, status, st);
+        return e == cudaErrorNotSupported ? fallback() : e;
+    }
+    if (!ws) return cudaErrorInvalidValue;
+    cudaError_t e = ws->ensure(sizeof(float) * (size_t)S * M * NB);
+    if (e != cudaSuccess) return e;
+    e = launch_tc_mm(A, abf, sam, sak, B, bbf, sbn, sbk, bias ? N : -1, nullptr, NB, M, NB, K, kc,
+                     ws->as<float>(), status, st);
+    if (e == cudaErrorNotSupported) return fallback();
+    if (e != cudaSuccess) return e;
+    note_launch();
+    const int64_t MN = (int64_t)M * NB;
+    k_mm_reduce<<<(unsigned)std::min<int64_t>((MN + 127) / 128, 4096), 128, 0, st>>>(
+        ws->as<float>(), (int)S, M, NB, C, ldc, 0, bias);
+    return cudaGetLastError();
+}
+
+// Gradients of the output layer: partial sums over a chunk of 64 rows per
+// block, part[i][h] = sum_b H3[b][h] dy[b] (h < 128) and part[i][128] =
+// sum_b dy[b] (b4); k_mm_reduce adds the chunks into w4 and b4 (adjacent).
+__global__ void k_sur_w4_grad(const __nv_bfloat16* __restrict__ H3, const float* __restrict__ dy,
+                              int64_t B, float* __restrict__ part) {
+    const int64_t b0 = (int64_t)blockIdx.x * 64, b1 = min(B, b0 + 64);
+    const int h = threadIdx.x;
+    float* out = part + (int64_t)blockIdx.x * (kH3 + 1);
+    if (h < kH3) {
+        float s = 0.f;
+        for (int64_t b = b0; b < b1; ++b) s = fmaf(__bfloat162float(H3[b * kH3 + h]), dy[b], s);
+        out[h] = s;
+    } else if (h < kH3 + 32) {
+        float s = 0.f;
+        for (int64_t b = b0 + (h - kH3); b < b1; b += 32) s += dy[b];
+        s = warp_sum_f32(s);
+        if (h == kH3) out[kH3] = s;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // encoder inputs: row r of X0 = z-scores of point pts[r] (bf16)
 __global__ void k_sur_gather_z(const float* __restrict__ zhat, int n, int n_pad, float scale,
-                               const uint32_t* __restrict__ pts, int64_t rows,
+                               const uint32_t* __restrict__ pts, int64_t rows, int ldx,
                                __nv_bfloat16* __restrict__ X0) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / n;
         const int k = (int)(e % n);
-        X0[e] = __float2bfloat16_rn(zhat[(int64_t)pts[r] * n_pad + k] * scale);
+        X0[r * ldx + k] = __float2bfloat16_rn(zhat[(int64_t)pts[r] * n_pad + k] * scale);
     }
 }
 
@@ -211,7 +327,7 @@ __global__ void k_sur_head_input(const float* __restrict__ Ef, const float* __re
                                         : (q / ((int64_t)X * Y)) - (p / ((int64_t)X * Y));
             v = (float)dp / (float)(a == 0 ? X : a == 1 ? Y : Z);
         }
-        X3[e] = __float2bfloat16_rn(v);
+        X3[b * kHeadInP + c] = __float2bfloat16_rn(v);
     }
 }
 
@@ -282,7 +398,7 @@ __global__ void k_sur_split(const float* __restrict__ dX3, const float* __restri
 
 __global__ void k_sur_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                            float* __restrict__ v, int64_t P, float lr, float c1, float c2,
-                           __nv_bfloat16* __restrict__ wb) {
+                           __nv_bfloat16* __restrict__ wb, PadW pw) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -292,7 +408,9 @@ __global__ void k_sur_adam(float* __restrict__ w, const float* __restrict__ g, f
         v[i] = vi;
         const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
         w[i] = wi;
-        wb[i] = __float2bfloat16_rn(wi);
+        const __nv_bfloat16 h = __float2bfloat16_rn(wi);
+        wb[i] = h;
+        pad_store(pw, i, h);
     }
 }
 
@@ -311,10 +429,14 @@ __global__ void k_sur_add_bias(float* __restrict__ A, const float* __restrict__ 
         A[e] += bias[e % cols];
 }
 
-__global__ void k_sur_cast(const float* __restrict__ w, int64_t P, __nv_bfloat16* __restrict__ wb) {
+__global__ void k_sur_cast(const float* __restrict__ w, int64_t P, __nv_bfloat16* __restrict__ wb,
+                           PadW pw) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-         i += (int64_t)gridDim.x * blockDim.x)
-        wb[i] = __float2bfloat16_rn(w[i]);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(w[i]);
+        wb[i] = h;
+        pad_store(pw, i, h);
+    }
 }
 
 // training batch: rows 0..B-1 = first points, B..2B-1 = second points; each
@@ -364,6 +486,7 @@ struct cc_sur {
     int n = 0;
     SurOff off{1};
     DevMem w, wb, g, m, v;
+    DevMem wp;  // padded BF16 W1 and W3 (PadW)
     int64_t step = 0;
     float tmean = 0.f, tsd = 1.f;
     // batch scratch
@@ -407,12 +530,12 @@ cc_status ensure_batch(cc_ctx* ctx, cc_sur* s, int64_t B) {
     const int n = s->n;
     SK(s->pts.alloc(8 * B));
     SK(s->tb.alloc(4 * B));
-    SK(s->X0.alloc(2 * 2 * B * n));
+    SK(s->X0.alloc(2 * 2 * B * ldz(n)));
     SK(s->A1.alloc(4 * 2 * B * kH1));
     SK(s->H1.alloc(2 * 2 * B * kH1));
     SK(s->Ef.alloc(4 * 2 * B * kE));
     SK(s->E.alloc(4 * 2 * B * kE));
-    SK(s->X3.alloc(2 * B * kHeadIn));
+    SK(s->X3.alloc(2 * B * kHeadInP));
     SK(s->A3.alloc(4 * B * kH3));
     SK(s->H3.alloc(2 * B * kH3));
     SK(s->y.alloc(4 * B));
@@ -429,6 +552,10 @@ cc_status ensure_batch(cc_ctx* ctx, cc_sur* s, int64_t B) {
 
 typedef __nv_bfloat16 bf16;
 
+PadW padw(cc_sur* s) { return PadW{s->wp.as<bf16>(), s->off.W1, s->off.W3, s->n}; }
+const bf16* w1p(cc_sur* s) { return s->wp.as<bf16>(); }
+const bf16* w3p(cc_sur* s) { return s->wp.as<bf16>() + (int64_t)kH1 * ldz(s->n); }
+
 // forward over a batch whose point list (2B entries) is in s->pts; with t,
 // also the loss (sum of squares into s->loss) and dy
 cc_status forward(cc_ctx* ctx, cc_sur* s, const Field& f, int64_t B, const float* t) {
@@ -440,19 +567,19 @@ cc_status forward(cc_ctx* ctx, cc_sur* s, const Field& f, int64_t B, const float
     note_launch(5);
     k_sur_gather_z<<<grid1(2 * B * n), 256, 0, st>>>(f.zhat.as<float>(), n, f.n_pad,
                                                      sqrtf((float)(n - 1)), s->pts.as<uint32_t>(),
-                                                     2 * B, s->X0.as<bf16>());
-    SK(mm(s->X0.as<bf16>(), n, 1, wb + o.W1, 1, n, s->A1.as<float>(), kH1, (int)(2 * B), kH1, n,
-          0, st));
+                                                     2 * B, ldz(n), s->X0.as<bf16>());
+    SK(tmm(ctx->status.as<int>(), s->X0.as<bf16>(), ldz(n), 1, w1p(s), 1, ldz(n), s->A1.as<float>(),
+           kH1, (int)(2 * B), kH1, n, st));
     k_sur_bias_gelu<<<grid1(2 * B * kH1), 256, 0, st>>>(s->A1.as<float>(), w + o.b1, 2 * B, kH1,
                                                         s->H1.as<bf16>());
-    SK(mm(s->H1.as<bf16>(), kH1, 1, wb + o.W2, 1, kH1, s->Ef.as<float>(), kE, (int)(2 * B), kE,
-          kH1, 0, st));
+    SK(tmm(ctx->status.as<int>(), s->H1.as<bf16>(), kH1, 1, wb + o.W2, 1, kH1, s->Ef.as<float>(), kE,
+           (int)(2 * B), kE, kH1, st));
     const uint32_t* pts = s->pts.as<uint32_t>();
     k_sur_head_input<<<grid1(B * kHeadIn), 256, 0, st>>>(s->Ef.as<float>(), w + o.b2, pts,
                                                          pts + B, f.X, f.Y, f.Z, B,
                                                          s->X3.as<bf16>(), s->E.as<float>());
-    SK(mm(s->X3.as<bf16>(), kHeadIn, 1, wb + o.W3, 1, kHeadIn, s->A3.as<float>(), kH3, (int)B, kH3,
-          kHeadIn, 0, st));
+    SK(tmm(ctx->status.as<int>(), s->X3.as<bf16>(), kHeadInP, 1, w3p(s), 1, kHeadInP,
+           s->A3.as<float>(), kH3, (int)B, kH3, kHeadIn, st));
     k_sur_bias_gelu<<<grid1(B * kH3), 256, 0, st>>>(s->A3.as<float>(), w + o.b3, B, kH3,
                                                     s->H3.as<bf16>());
     if (t) SK(cudaMemsetAsync(s->loss.p, 0, 8, st));
@@ -470,34 +597,36 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
     const SurOff& o = s->off;
     const bf16* wb = s->wb.as<bf16>();
     float* g = s->g.as<float>();
-    // head output layer
-    SK(mm(s->H3.as<bf16>(), 1, kH3, s->dy.as<float>(), 1, 0, g + o.w4, 1, kH3, 1, (int)B, 0, st,
-          &s->ws));
-    note_launch(5);
-    k_sur_colsum<<<1, 256, 0, st>>>(s->dy.as<float>(), B, 1, g + o.b4);
+    // head output layer: w4 and b4 (adjacent) from per-chunk partial sums
+    {
+        const int64_t nb = (B + 63) / 64;
+        SK(s->ws.ensure(sizeof(float) * (size_t)nb * (kH3 + 1)));
+        note_launch(3);  // with the head's GELU backward
+        k_sur_w4_grad<<<(unsigned)nb, kH3 + 32, 0, st>>>(s->H3.as<bf16>(), s->dy.as<float>(), B,
+                                                         s->ws.as<float>());
+        k_mm_reduce<<<2, 128, 0, st>>>(s->ws.as<float>(), (int)nb, 1, kH3 + 1, g + o.w4, kH3 + 1,
+                                       0, nullptr);
+    }
     k_sur_gelu_bwd<<<grid1(B * kH3), 256, 0, st>>>(s->A3.as<float>(), s->dy.as<float>(),
                                                    s->w.as<float>() + o.w4, nullptr, B, kH3,
                                                    s->dA3.as<float>());
-    SK(mm(s->dA3.as<float>(), 1, kH3, s->X3.as<bf16>(), kHeadIn, 1, g + o.W3, kHeadIn, kH3, kHeadIn,
-          (int)B, 0, st, &s->ws));
-    k_sur_colsum<<<kH3, 256, 0, st>>>(s->dA3.as<float>(), B, kH3, g + o.b3);
-    SK(mm(s->dA3.as<float>(), kH3, 1, wb + o.W3, kHeadIn, 1, s->dX3.as<float>(), kHeadIn, (int)B,
-          kHeadIn, kH3, 0, st));
+    SK(tmm(ctx->status.as<int>(), s->dA3.as<float>(), 1, kH3, s->X3.as<bf16>(), kHeadInP, 1,
+           g + o.W3, kHeadIn, kH3, kHeadIn, (int)B, st, &s->ws, g + o.b3));
+    SK(tmm(ctx->status.as<int>(), s->dA3.as<float>(), kH3, 1, w3p(s), kHeadInP, 1,
+           s->dX3.as<float>(), kHeadIn, (int)B, kHeadIn, kH3, st));
     k_sur_split<<<grid1(B * kE), 256, 0, st>>>(s->dX3.as<float>(), s->E.as<float>(), B,
                                                s->dE.as<float>());
     // encoder
-    SK(mm(s->dE.as<float>(), 1, kE, s->H1.as<bf16>(), kH1, 1, g + o.W2, kH1, kE, kH1, (int)(2 * B),
-          0, st, &s->ws));
-    note_launch(3);
-    k_sur_colsum<<<kE, 256, 0, st>>>(s->dE.as<float>(), 2 * B, kE, g + o.b2);
-    SK(mm(s->dE.as<float>(), kE, 1, wb + o.W2, kH1, 1, s->dH1.as<float>(), kH1, (int)(2 * B), kH1,
-          kE, 0, st));
+    SK(tmm(ctx->status.as<int>(), s->dE.as<float>(), 1, kE, s->H1.as<bf16>(), kH1, 1, g + o.W2,
+           kH1, kE, kH1, (int)(2 * B), st, &s->ws, g + o.b2));
+    note_launch(2);
+    SK(tmm(ctx->status.as<int>(), s->dE.as<float>(), kE, 1, wb + o.W2, kH1, 1, s->dH1.as<float>(),
+           kH1, (int)(2 * B), kH1, kE, st));
     k_sur_gelu_bwd<<<grid1(2 * B * kH1), 256, 0, st>>>(s->A1.as<float>(), nullptr, nullptr,
                                                        s->dH1.as<float>(), 2 * B, kH1,
                                                        s->dA1.as<float>());
-    SK(mm(s->dA1.as<float>(), 1, kH1, s->X0.as<bf16>(), n, 1, g + o.W1, n, kH1, n, (int)(2 * B), 0,
-          st, &s->ws));
-    k_sur_colsum<<<kH1, 256, 0, st>>>(s->dA1.as<float>(), 2 * B, kH1, g + o.b1);
+    SK(tmm(ctx->status.as<int>(), s->dA1.as<float>(), 1, kH1, s->X0.as<bf16>(), ldz(n), 1, g + o.W1,
+           n, kH1, n, (int)(2 * B), st, &s->ws, g + o.b1));
     SK(cudaGetLastError());
     return CC_OK;
 }
@@ -552,8 +681,9 @@ cc_status screen_predict(cc_ctx* ctx, cc_sur* s, int32_t region_a, int32_t regio
         note_launch(2);
         k_sur_gather_z<<<grid1(np * n), 256, 0, st>>>(f->zhat.as<float>(), n, f->n_pad,
                                                       sqrtf((float)(n - 1)),
-                                                      rg.pts.as<uint32_t>(), np, s->X0.as<bf16>());
-        SK(mm(s->X0.as<bf16>(), n, 1, s->wb.as<bf16>() + o.W1, 1, n, s->A1.as<float>(), kH1,
+                                                      rg.pts.as<uint32_t>(), np, ldz(n),
+                                                      s->X0.as<bf16>());
+        SK(mm(s->X0.as<bf16>(), ldz(n), 1, s->wb.as<bf16>() + o.W1, 1, n, s->A1.as<float>(), kH1,
               (int)np, kH1, n, 0, st));
         k_sur_bias_gelu<<<grid1(np * kH1), 256, 0, st>>>(s->A1.as<float>(), w + o.b1, np, kH1,
                                                          s->H1.as<bf16>());
@@ -594,6 +724,8 @@ cc_status cc_sur_create(cc_ctx* ctx, int n_members, uint64_t seed, cc_sur** out)
     const int64_t P = s->off.total;
     SK(s->w.alloc(4 * P));
     SK(s->wb.alloc(2 * P));
+    SK(s->wp.alloc(2 * ((size_t)kH1 * ldz(n_members) + (size_t)kH3 * kHeadInP)));
+    SK(cudaMemsetAsync(s->wp.p, 0, s->wp.bytes, ctx->stream));
     SK(s->g.alloc(4 * P));
     SK(s->m.alloc(4 * P));
     SK(s->v.alloc(4 * P));
@@ -630,7 +762,8 @@ cc_status cc_sur_set_params(cc_ctx* ctx, cc_sur* s, const float* params) {
     SK(cudaMemsetAsync(s->m.p, 0, 4 * P, ctx->stream));
     SK(cudaMemsetAsync(s->v.p, 0, 4 * P, ctx->stream));
     note_launch();
-    k_sur_cast<<<grid1(P), 256, 0, ctx->stream>>>(s->w.as<float>(), P, s->wb.as<bf16>());
+    k_sur_cast<<<grid1(P), 256, 0, ctx->stream>>>(s->w.as<float>(), P, s->wb.as<bf16>(),
+                                                  padw(s));
     SK(cudaGetLastError());
     SK(cudaStreamSynchronize(ctx->stream));
     s->step = 0;
@@ -755,7 +888,7 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
             k_sur_adam<<<grid1(s->off.total), 256, 0, st>>>(s->w.as<float>(), s->g.as<float>(),
                                                             s->m.as<float>(), s->v.as<float>(),
                                                             s->off.total, lr, c1, c2,
-                                                            s->wb.as<bf16>());
+                                                            s->wb.as<bf16>(), padw(s));
             SK(cudaGetLastError());
             if (epoch_loss && (k % 64 == 63 || k == steps - 1)) {
                 double l = 0;

@@ -61,6 +61,28 @@ def test_gradients_match_oracle(env):
     sur.close()
 
 
+def test_large_batch_predictions_match_oracle(env):
+    # more pairs than one prediction chunk (65,536), so the encoder products
+    # run over many more row tiles than the GPU has SMs
+    from paper_2309_03308_gb300 import Surrogate
+    ctx, F, fid = env
+    rng = np.random.default_rng(8)
+    P = X * Y * Z
+    pa = rng.integers(0, P, 70000).astype(np.uint32)
+    pb = rng.integers(0, P, 70000).astype(np.uint32)
+    w = mlp.init(N, 9)
+    sur = Surrogate(ctx, N)
+    sur.set_params(w.astype(np.float32))
+    sur.set_target_scale(0.0, 1.0)
+    y = sur.predict(fid, pa, pb)
+    zi, zj = mlp.zscore(F, pa), mlp.zscore(F, pb)
+    ref, _ = mlp.forward(w.astype(np.float32).astype(np.float64), zi, zj,
+                         mlp.offsets(X, Y, Z, pa, pb), N)
+    err = np.abs(y - ref)
+    assert err.max() < 3e-2 * max(1.0, np.abs(ref).max()), (err.max(), int(err.argmax()))
+    sur.close()
+
+
 def test_training_and_screen(env, orc):
     from paper_2309_03308_gb300 import CC_MI_KSG, Params, Surrogate
     ctx, F, fid = env
