@@ -48,6 +48,7 @@ double digamma_int_host(int m);
 constexpr uint64_t kPoolKey = 0xB05B05ull, kRoundKey = 0xB0517Dull;
 constexpr int kBosThreads = 256;
 constexpr int kGRows = 512;  // rows of V[:, P] the conditioning keeps in shared memory
+constexpr int kEvalChunk = 8;  // KSG candidates per work-queue pull
 
 struct BosDev {
     int n_rp, Q, R, T, M;
@@ -82,7 +83,7 @@ struct BosDev {
     float* vals;         // [4][n_rp*R]
     Partial* best;       // [4][n_rp], argmax/argmin = (pa << 32) | pb
     int* round;
-    int* queue;
+    int* queue;          // [2]: next item of the non-KSG measures, next KSG chunk
     int* status;
     // field planes
     const float* zhat;  // planes of the field of the first regions ...
@@ -155,6 +156,68 @@ __global__ void k_bos_pool(BosDev d) {
     }
 }
 
+// Warp-wide descending sort of 256 unique 64-bit keys, eight per lane in
+// blocked order (lane l holds positions 8l .. 8l + 7): a bitonic sorter whose
+// stages at distance >= 8 exchange across lanes. An element takes its
+// partner's key only when the partner is strictly larger (it keeps the
+// maximum) or strictly smaller (it keeps the minimum), so equal keys stay.
+__device__ __forceinline__ void warp_sort256_desc(unsigned long long (&k)[8], int lane) {
+    const int g0 = lane * 8;
+#pragma unroll
+    for (int size = 2; size <= 256; size <<= 1) {
+#pragma unroll
+        for (int d = size >> 1; d > 0; d >>= 1) {
+            if (d >= 8) {
+                const bool keep_max = ((g0 & d) == 0) == ((g0 & size) == 0);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, k[e], d / 8);
+                    k[e] = (keep_max ? o > k[e] : o < k[e]) ? o : k[e];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int e2 = e ^ d;
+                    if (e2 > e) {
+                        const bool desc = ((g0 + e) & size) == 0;
+                        const unsigned long long a = k[e], b = k[e2];
+                        const bool swap = desc ? b > a : b < a;
+                        k[e] = swap ? b : a;
+                        k[e2] = swap ? a : b;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Descending order of a bitonic sequence of 128 keys, four per lane in
+// blocked order: the bitonic merger.
+__device__ __forceinline__ void warp_merge128_desc(unsigned long long (&k)[4], int lane) {
+    const int g0 = lane * 4;
+#pragma unroll
+    for (int d = 64; d > 0; d >>= 1) {
+        if (d >= 4) {
+            const bool keep_max = (g0 & d) == 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, k[e], d / 4);
+                k[e] = (keep_max ? o > k[e] : o < k[e]) ? o : k[e];
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int e2 = e ^ d;
+                if (e2 > e) {
+                    const unsigned long long a = k[e], b = k[e2];
+                    k[e] = a > b ? a : b;
+                    k[e2] = a > b ? b : a;
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // propose: one CTA per region pair. Dynamic smem: Q keys (8 B), M shortlist
 // ids, M x M covariance, M x 6 positions, M means, a row buffer.
@@ -179,8 +242,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
     float* pos = cov + M * M;
     float* msl = pos + M * 6;
     float* rowbuf = msl + M;         // 2 x 16 rows x M (double-buffered batches)
-    float* red_v = rowbuf + 32 * M;  // per-warp argmax
-    int* red_i = reinterpret_cast<int*>(red_v + 32);
+    float* red_v = rowbuf + 32 * M;  // 32 scalars
     const float* mu = d.mu + (int64_t)rp * Q;
     const float* var = d.var + (int64_t)rp * Q;
     const float kappa = d.kappa, sf2 = d.hyp[rp * 4 + 1], sn2 = d.hyp[rp * 4 + 2];
@@ -191,18 +253,40 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
                        : ((unsigned long long)okey32(u) << 32) | (0xffffffffull - (unsigned)c);
     }
     __syncthreads();
-    for (int size = 2; size <= Q; size <<= 1) {  // bitonic sort, descending
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = tid; i < Q; i += blockDim.x) {
-                const int p = i ^ stride;
-                if (p > i) {
-                    const bool desc = (i & size) == 0;
-                    const unsigned long long a = key[i], b = key[p];
-                    if ((a < b) == desc) {
-                        key[i] = b;
-                        key[p] = a;
-                    }
+    // the M largest keys, in descending order: each warp sorts 256-key
+    // segments of the pool in registers (eight keys per lane) and keeps each
+    // segment's top 128 in place; a tree of pairwise merges (the top 128 of
+    // two descending lists: the elementwise maximum against the other list
+    // reversed is bitonic and holds them, a bitonic merger orders it) leaves
+    // the 128 largest in segment 0. Keys are unique apart from the zero keys
+    // of taken entries, so the shortlist and its order are those of a full
+    // descending sort.
+    {
+        const int warp = tid >> 5, lane = tid & 31, nseg = Q / 256;
+        for (int sg = warp; sg < nseg; sg += kBosThreads / 32) {
+            unsigned long long k8[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) k8[e] = key[sg * 256 + lane * 8 + e];
+            warp_sort256_desc(k8, lane);
+            if (lane < 16) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) key[sg * 256 + lane * 8 + e] = k8[e];
+            }
+        }
+        __syncthreads();
+        for (int w = 1; w < nseg; w <<= 1) {
+            for (int m = warp; m * 2 * w < nseg; m += kBosThreads / 32) {
+                const int sa = m * 2 * w * 256, sb = sa + w * 256;
+                unsigned long long k4[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const unsigned long long a = key[sa + lane * 4 + e],
+                                             b = key[sb + 127 - lane * 4 - e];
+                    k4[e] = a > b ? a : b;
                 }
+                warp_merge128_desc(k4, lane);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) key[sa + lane * 4 + e] = k4[e];
             }
             __syncthreads();
         }
@@ -297,14 +381,34 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
         }
     }
     __syncthreads();
-    // greedy picks with the kriging-believer update (the R - L pool proposals)
-    float* col = rowbuf;
+    // greedy picks with the kriging-believer update (the R - L pool
+    // proposals), by warp 0 alone. The UCB needs only the diagonal of the
+    // updated covariance, and the column of pick j is cov0[:, c_j] minus the
+    // terms of the earlier picks, col_p col_p[c_j] / (col_p[c_p] + noise): the
+    // same operations in the same order as subtracting every rank-one update
+    // from the whole matrix, on j + 1 columns instead of M. cov0 is exactly
+    // symmetric (both triangles are the same products), so column c is read
+    // as row c.
+    if (tid >= 32) return;
+    const int lane = tid;
+    float* colbuf = rowbuf;  // [R - L][M]: the picks' columns
+    float* invb = red_v;     // [R - L]: 1 / (col_p[c_p] + noise)
+    float dg[4];
+    bool tk[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        dg[q] = i < M ? cov[i * M + i] : 0.f;
+        tk[q] = i >= M;
+    }
     for (int j = 0; j < R - L; ++j) {
         float bv = -CUDART_INF_F;
         int bi = 0x7fffffff;
-        for (int i = tid; i < M; i += blockDim.x) {
-            if (SL[i] < 0) continue;  // taken this round
-            const float u = msl[i] + kappa * sqrtf(fmaxf(cov[i * M + i], 0.f));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            if (tk[q]) continue;
+            const float u = msl[i] + kappa * sqrtf(fmaxf(dg[q], 0.f));
             if (u > bv || (u == bv && i < bi)) {
                 bv = u;
                 bi = i;
@@ -319,29 +423,31 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
                 bi = oi;
             }
         }
-        if ((tid & 31) == 0) {
-            red_v[tid >> 5] = bv;
-            red_i[tid >> 5] = bi;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (red_v[w] > red_v[0] || (red_v[w] == red_v[0] && red_i[w] < red_i[0])) {
-                    red_v[0] = red_v[w];
-                    red_i[0] = red_i[w];
-                }
-            const int c = red_i[0];
+        const int c = bi;
+        if (lane == 0) {
             picks[L + j] = SL[c];
             atomicOr(&sel[SL[c] >> 5], 1u << (SL[c] & 31));
         }
-        __syncthreads();
-        const int c = red_i[0];
-        for (int i = tid; i < M; i += blockDim.x) col[i] = cov[i * M + c];
-        __syncthreads();
-        const float inv = 1.f / (col[c] + sn2);
-        for (int e = tid; e < M * M; e += blockDim.x) cov[e] -= col[e / M] * col[e % M] * inv;
-        if (tid == 0) SL[c] = -1 - SL[c];
-        __syncthreads();
+        float x[4], xc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            float v = i < M ? cov[c * M + i] : 0.f;
+            for (int p = 0; p < j; ++p) v -= colbuf[p * M + i] * colbuf[p * M + c] * invb[p];
+            x[q] = v;
+            if (q == (c >> 5)) xc = v;
+        }
+        xc = __shfl_sync(0xffffffffu, xc, c & 31);
+        const float inv = 1.f / (xc + sn2);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            if (i < M) colbuf[j * M + i] = x[q];
+            dg[q] -= x[q] * x[q] * inv;
+            tk[q] = tk[q] || i == c;
+        }
+        if (lane == 0) invb[j] = inv;
+        __syncwarp();
     }
 }
 
@@ -416,6 +522,12 @@ __global__ void k_bos_round_pairs(BosDev d) {
 }
 
 // ---------------------------------------------------------------------------
+// KSG candidates of the evaluation are walked as a sample stream (two staging
+// slots per warp) for 32 <= n <= 256, one candidate per warp otherwise
+__host__ __device__ __forceinline__ bool eval_stream(int n, int n_pad) {
+    return n >= 32 && n_pad <= 256;
+}
+
 // evaluate: persistent work queue over (measure, pair) items, KSG first.
 template <int KMAX>
 __global__ void k_bos_eval(BosDev d, int warps_per_block) {
@@ -425,9 +537,11 @@ __global__ void k_bos_eval(BosDev d, int warps_per_block) {
     long long* psi = reinterpret_cast<long long*>(es);
     long long* clogc = psi + ((n + 2) & ~1);
     const size_t slot = ksg_slot_bytes(n_pad, KMAX);
+    const bool stream = eval_stream(n, n_pad);
+    const int slots = stream ? 2 : 1;
     unsigned char* wbase = reinterpret_cast<unsigned char*>(clogc + ((n + 2) & ~1)) +
-                           (size_t)warp * (slot + 256 * sizeof(int));
-    int* hist = reinterpret_cast<int*>(wbase + slot);
+                           (size_t)warp * (slots * slot + 256 * sizeof(int));
+    int* hist = reinterpret_cast<int*>(wbase + slots * slot);
     for (int i = threadIdx.x; i <= n; i += blockDim.x) {
         psi[i] = d.psi_fix[i];
         clogc[i] = d.clogc_fix[i];
@@ -435,9 +549,61 @@ __global__ void k_bos_eval(BosDev d, int warps_per_block) {
     for (int c = lane; c < B * B; c += 32) hist[c] = 0;
     __syncthreads();
     const int per = d.n_rp * d.R, total = 4 * per;
+    // KSG first (the longest measure): for 32 <= n <= 256 a warp takes chunks of
+    // kEvalChunk consecutive candidates and walks their samples as one
+    // stream, 32 per round, with two staging slots (a round spans at most two
+    // candidates; a candidate's slot is restaged for the one two places
+    // later, whose first sample lies beyond the round that ends it)
+    if (stream) {
+        while (true) {
+            int c0 = 0;
+            if (lane == 0) c0 = atomicAdd(d.queue + 1, kEvalChunk);
+            c0 = __shfl_sync(0xffffffffu, c0, 0);
+            if (c0 >= per) break;
+            const int c1 = min(per, c0 + kEvalChunk);
+            int tr = c0, tir = 0, staged = c0;
+            long long acc[2] = {0, 0};
+            while (tr < c1) {
+                const int t_last = min(c1 - 1, tr + (tir + 31 >= n ? 1 : 0));
+                for (; staged <= t_last; ++staged) {  // warp-uniform
+                    const int64_t ra = (int64_t)d.pa[staged] * n_pad,
+                                  rb = (int64_t)d.pb[staged] * n_pad;
+                    ksg_stage<KMAX>(wbase + (staged & 1) * slot, n, n_pad, d.sorted + ra,
+                                    d.perm + ra, d.fvals + ra, d.sorted_b + rb, d.perm_b + rb,
+                                    d.fvals_b + rb);
+                }
+                int ti = tir + lane, tt = tr;
+                if (ti >= n) {
+                    ti -= n;
+                    ++tt;
+                }
+                if (tt < c1) {
+                    const long long v = ksg_sample<KMAX>(wbase + (tt & 1) * slot, n, n_pad, d.k,
+                                                         ti, psi, nullptr, nullptr, nullptr);
+                    if (tt & 1) acc[1] += v;
+                    else acc[0] += v;
+                }
+                if (tir + 32 >= n) {  // candidate tr ends in this round
+                    const long long sum = warp_sum_i64((tr & 1) ? acc[1] : acc[0]);
+                    if (lane == 0)
+                        d.vals[(int64_t)CC_MI_KSG * per + tr] =
+                            (float)(d.psi_nk - (double)sum * d.fix_over_n);
+                    if (tr & 1) acc[1] = 0;
+                    else acc[0] = 0;
+                }
+                __syncwarp();
+                tir += 32;
+                if (tir >= n) {
+                    tir -= n;
+                    ++tr;
+                }
+            }
+        }
+    }
+    const int first = stream ? per : 0;  // the items left to the queue below
     while (true) {
         int item = 0;
-        if (lane == 0) item = atomicAdd(d.queue, 1);
+        if (lane == 0) item = first + atomicAdd(d.queue, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total) break;
         const int measure = 3 - item / per, t = item % per;
@@ -559,6 +725,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     float* yv = pp + R * 6;                       // R
     float* mP = yv + R;                           // R prior at picks
     float* hyp = mP + R;                          // 4
+    float* Linv = hyp + 4;                        // R: 1 / L22[i][i]
     const int* P = d.picks + rp * R + j0;
     const int per = d.n_rp * R;
     const int Sp = d.Sp;
@@ -633,33 +800,43 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     }
     if (tid < nn) gb[tid] = gacc;
     __syncthreads();
-    // Cholesky of covP (fp64, warp 0: lane = row)
+    // Cholesky of covP (fp64, warp 0, lane i owns row i), right-looking: at
+    // step j the pivot's reciprocal square root scales column j and the
+    // trailing rows subtract their column-j products, so each entry sees
+    // the same subtractions in the same order as the column-by-column form
+    // while all rows work at once (this GPU's FP64 pipe is narrow).
     if (tid < 32) {
+        for (int e = lane; e < nn * nn; e += 32) Lf[e] = (double)covP[e];
+        __syncwarp();
         for (int j = 0; j < nn; ++j) {
+            const double x = fmax(Lf[j * nn + j], 1e-12 * (double)sf2);
+            const double rj = rsqrt(x);
+            const bool below = lane > j && lane < nn;
+            const double lij = below ? Lf[lane * nn + j] * rj : 0.0;
+            __syncwarp();  // column j is read before it is overwritten
             if (lane == j) {
-                double sum = covP[j * nn + j];
-                for (int q = 0; q < j; ++q) sum -= Lf[j * nn + q] * Lf[j * nn + q];
-                Lf[j * nn + j] = sqrt(fmax(sum, 1e-12 * (double)sf2));
+                Lf[j * nn + j] = x * rj;
+                Linv[j] = (float)rj;
+            } else if (below) {
+                Lf[lane * nn + j] = lij;
             }
             __syncwarp();
-            if (lane > j && lane < nn) {
-                double sum = covP[lane * nn + j];
-                for (int q = 0; q < j; ++q) sum -= Lf[lane * nn + q] * Lf[j * nn + q];
-                Lf[lane * nn + j] = sum / Lf[j * nn + j];
-            }
+            if (below)
+                for (int q = j + 1; q <= lane; ++q) Lf[lane * nn + q] -= lij * Lf[q * nn + j];
             __syncwarp();
         }
         for (int e = lane; e < nn * nn; e += 32) {
             const int i = e / nn, j = e % nn;
             L[e] = j <= i ? (float)Lf[e] : 0.f;
         }
-        __syncwarp();
-        if (lane == 0) {  // beta2 = L22^-1 (y - m_P - V[:, P]^T beta1)
-            for (int i = 0; i < nn; ++i) {
-                double v = (double)yv[i] - mP[i] - gb[i];
-                for (int q = 0; q < i; ++q) v -= Lf[i * nn + q] * (double)b2[q];
-                b2[i] = (float)(v / Lf[i * nn + i]);
-            }
+        // beta2 = L22^-1 (y - m_P - V[:, P]^T beta1), forward substitution
+        // by columns: lane q keeps its right-hand side
+        double v = lane < nn ? (double)yv[lane] - mP[lane] - gb[lane] : 0.0;
+        for (int i = 0; i < nn; ++i) {
+            const double vi = __shfl_sync(0xffffffffu, v, i);
+            const float bi = (float)(vi / Lf[i * nn + i]);
+            if (lane == i) b2[i] = bi;
+            if (lane > i && lane < nn) v -= Lf[lane * nn + i] * (double)bi;
         }
     }
     __syncthreads();
@@ -738,7 +915,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
                     float x = matern52(pp + i * 6, pcl, inv_ell, sf2) - w[i];
 #pragma unroll
                     for (int q = 0; q < i; ++q) x = fmaf(-L[i * nn + q], w[q], x);
-                    x /= L[i * nn + i];
+                    x *= Linv[i];
                     w[i] = x;
                     Vr[(int64_t)c * Sp + s + i] = x;
                     dv = fmaf(x, x, dv);
@@ -760,7 +937,8 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
 
 __global__ void k_bos_advance(BosDev d) {
     *d.round += 1;
-    *d.queue = 0;
+    d.queue[0] = 0;
+    d.queue[1] = 0;
 }
 
 }  // namespace cc
@@ -814,11 +992,12 @@ size_t propose_smem(const BosDev& d) {
 size_t condition_smem(const BosDev& d) {
     const int R = d.R;
     return (size_t)kGRows * 32 * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 + R * 6 * 4 +
-           2 * R * 4 + 16;
+           2 * R * 4 + 16 + R * 4;
 }
 size_t eval_smem(const BosDev& d, int warps) {
     const int pl = (d.n + 2) & ~1;
-    return 2 * pl * 8 + (size_t)warps * (ksg_slot_bytes(d.n_pad, ksg_kmax(d.k)) + 256 * 4);
+    const int slots = eval_stream(d.n, d.n_pad) ? 2 : 1;
+    return 2 * pl * 8 + (size_t)warps * (slots * ksg_slot_bytes(d.n_pad, ksg_kmax(d.k)) + 256 * 4);
 }
 
 // set_attr: raise the kernel's dynamic shared-memory limit first (not while
@@ -1175,7 +1354,7 @@ cc_status cc_bos_run(cc_ctx* ctx, cc_bos* b, int rounds, int use_graph) {
             for (auto& sh : shapes) {
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; ++rep) {
-                    BK(cudaMemsetAsync(b->d.queue, 0, 4, st));
+                    BK(cudaMemsetAsync(b->d.queue, 0, 8, st));
                     BK(cudaEventRecord(e0, st));
                     BK(launch_eval(b->d, sh[0], cc::sm_count() * sh[1], true, st));
                     BK(cudaEventRecord(e1, st));
@@ -1190,7 +1369,7 @@ cc_status cc_bos_run(cc_ctx* ctx, cc_bos* b, int rounds, int use_graph) {
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            BK(cudaMemsetAsync(b->d.queue, 0, 4, st));
+            BK(cudaMemsetAsync(b->d.queue, 0, 8, st));
             tune_store(key, w, bps);
         }
         b->eval_warps = w;
