@@ -40,6 +40,7 @@
 
 #include "internal.cuh"
 #include "ksg_dev.cuh"
+#include "tc_dev.cuh"
 
 namespace cc {
 
@@ -156,6 +157,22 @@ __global__ void k_bos_pool(BosDev d) {
     }
 }
 
+// Bytes of the propose kernel's first shared region: the pool keys, the two
+// 16 KB operand tiles of the shortlist product, or the picks' columns
+// (32 x 128 floats), whichever is largest.
+__host__ __device__ constexpr size_t propose_region0(int Q) {
+    return (size_t)Q * 8 > 32768 ? (size_t)Q * 8 : 32768;
+}
+
+// D (TMEM) (+)= A B^T, TF32 operands from shared-memory descriptors
+__device__ __forceinline__ void bos_mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                             uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
 // Warp-wide descending sort of 256 unique 64-bit keys, eight per lane in
 // blocked order (lane l holds positions 8l .. 8l + 7): a bitonic sorter whose
 // stages at distance >= 8 exchange across lanes. An element takes its
@@ -236,13 +253,19 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
     }
     const int s = obs_before(r, R, d.L), L = d.L;
     if (tid < L) picks[tid] = -1;  // local proposals: positions made by k_bos_round_pairs
-    unsigned long long* key = reinterpret_cast<unsigned long long*>(bs);
-    int* SL = reinterpret_cast<int*>(key + Q);
+    // shared memory: region0 (1024-byte aligned) holds the pool keys, then the
+    // product's operand tiles, then the picks' columns
+    unsigned char* region0 = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(bs) + 1023) & ~uintptr_t(1023));
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(region0);
+    int* SL = reinterpret_cast<int*>(region0 + propose_region0(Q));
     float* cov = reinterpret_cast<float*>(SL + M);
     float* pos = cov + M * M;
     float* msl = pos + M * 6;
-    float* rowbuf = msl + M;         // 2 x 16 rows x M (double-buffered batches)
-    float* red_v = rowbuf + 32 * M;  // 32 scalars
+    float* red_v = msl + M;  // 32 scalars
+    uint64_t* bar = reinterpret_cast<uint64_t*>(red_v + 32);  // 2 mbarriers
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const float* mu = d.mu + (int64_t)rp * Q;
     const float* var = d.var + (int64_t)rp * Q;
     const float kappa = d.kappa, sf2 = d.hyp[rp * 4 + 1], sn2 = d.hyp[rp * 4 + 2];
@@ -301,86 +324,124 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
         for (int a = 0; a < 6; ++a) pos[i * 6 + a] = d.pool[((int64_t)rp * Q + c) * 6 + a];
     }
     __syncthreads();
-    // posterior covariance among the shortlist: K(SL, SL) - V[:, SL]^T V[:, SL]
-    const int ti = tid >> 4, tj = tid & 15;  // 16 x 16 threads, (M/16)^2 entries each
-    const int per = M / 16;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    // posterior covariance among the shortlist: K(SL, SL) - X^T X with
+    // X = V[:, SL] (s observations x M entries), on the tensor cores: per
+    // K step three TF32 products X_hi X_hi + X_hi X_lo + X_lo X_hi, where
+    // X_hi keeps the first 11 significant bits of X and X_lo = X - X_hi
+    // exactly (the dropped X_lo X_lo term and the 11-bit reading of X_lo are
+    // below 2^-20 relative), FP32 accumulation in TMEM. The operand tiles
+    // are 128 rows (entries, zero beyond M) x 32 observations, K-major with
+    // the 128-byte swizzle; A and B are the same tiles. One stage: the next
+    // block's loads are issued while the MMAs of the current one run.
     const int Sp = d.Sp;
     const float* Vr = d.V + (int64_t)rp * Q * Sp;  // pool-major columns of Sp rows
-    // 16 gathered rows per barrier, double-buffered: the next batch's values
-    // (M / 16 per thread) are loaded into registers while the current batch is
-    // multiplied, then stored into the other half of rowbuf; per row a thread
-    // reads its 2 x per operands once and updates its per x per block (per <= 8)
-    const int vals_per_thread = 16 * M / kBosThreads;  // M / 16 <= 8
-    float nxt[8];
-    auto load_batch = [&](int t0) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (q < vals_per_thread) {
-                const int e = tid + q * kBosThreads, t = t0 + e / M, i = e % M;
-                nxt[q] = t < s ? Vr[(int64_t)SL[i] * Sp + t] : 0.f;
-            }
-        }
-    };
-    auto store_batch = [&](float* buf) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (q < vals_per_thread) buf[tid + q * kBosThreads] = nxt[q];
-    };
-    if (s > 0) {
-        load_batch(0);
-        store_batch(rowbuf);
+    const int warp = tid >> 5, lane = tid & 31;
+    unsigned char* Xh = region0;
+    unsigned char* Xl = region0 + 128 * 128;
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc::smem_u32(tslot)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc::tc_fence_before();
     __syncthreads();
-    for (int t0 = 0, bi = 0; t0 < s; t0 += 16, bi ^= 1) {
-        const float* cur = rowbuf + bi * 16 * M;
-        const bool more = t0 + 16 < s;
-        if (more) load_batch(t0 + 16);
-        if (per == 8) {  // shortlist of 128: the operands are two aligned float4 each
-            for (int t = 0; t < 16; ++t) {
-                const float4* ra = reinterpret_cast<const float4*>(cur + t * M + ti * 8);
-                const float4* rb = reinterpret_cast<const float4*>(cur + t * M + tj * 8);
-                const float4 a0 = ra[0], a1 = ra[1], b0 = rb[0], b1 = rb[1];
-                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int srow = tid >> 1, sc0 = (tid & 1) * 4;  // staging unit: row, four 16-byte chunks
+    const float* src = Vr + (int64_t)(srow < M ? SL[srow] : 0) * Sp;
+    float4 nx[4];
+    auto load_blk = [&](int t0) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-            }
-        } else {
-            for (int t = 0; t < 16; ++t) {
-                float a[8], b[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    a[i] = i < per ? cur[t * M + ti * per + i] : 0.f;
-                    b[i] = i < per ? cur[t * M + tj * per + i] : 0.f;
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-            }
+        for (int q = 0; q < 4; ++q) {
+            const int t = t0 + 4 * (sc0 + q);  // rows at and beyond s read as zero in V
+            nx[q] = (srow < M && t < s) ? __ldcs(reinterpret_cast<const float4*>(src + t))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        // the other half was last read in the previous batch, before its barrier
-        if (more) store_batch(rowbuf + (bi ^ 1) * 16 * M);
+    };
+    auto split = [](float x, float& hi) {
+        hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+        return x - hi;
+    };
+    const int nkb = (s + 31) / 32;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(M >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);  // FP32 += TF32 x TF32, K-major
+    load_blk(0);
+    for (int kb = 0; kb < nkb; ++kb) {
+        if (kb > 0 && !*abort_flag && !tc::mbar_wait(&bar[0], (kb - 1) & 1, abort_flag)) {
+            *abort_flag = 1;
+            set_status(d.status, DEV_TIMEOUT);
+        }
+        __syncthreads();  // the previous block's MMAs have read the tiles
+        if (*abort_flag) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float4 h, l;
+            l.x = split(nx[q].x, h.x);
+            l.y = split(nx[q].y, h.y);
+            l.z = split(nx[q].z, h.z);
+            l.w = split(nx[q].w, h.w);
+            const uint32_t off = (uint32_t)(srow * 128 + (((sc0 + q) ^ (srow & 7)) << 4));
+            *reinterpret_cast<float4*>(Xh + off) = h;
+            *reinterpret_cast<float4*>(Xl + off) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-    }
+        if (tid == 0) {
+            tc::tc_fence_after();
+            const uint32_t bh = tc::smem_u32(Xh), bl = tc::smem_u32(Xl);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        if (i >= per) break;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (j >= per) break;
-            const int a = ti * per + i, b = tj * per + j;
-            cov[a * M + b] = matern52(pos + a * 6, pos + b * 6, inv_ell, sf2) - acc[i][j];
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t dh = tc::sdesc(bh + k * 32), dl = tc::sdesc(bl + k * 32);
+                bos_mma_tf32(tmem, dh, dh, idesc, (kb | k) != 0);
+                bos_mma_tf32(tmem, dh, dl, idesc, 1);
+                bos_mma_tf32(tmem, dl, dh, idesc, 1);
+            }
+            tc::mma_commit(&bar[0]);
         }
+        if (kb + 1 < nkb) load_blk(32 * (kb + 1));
+    }
+    if (!*abort_flag && !tc::mbar_wait(&bar[0], (nkb - 1) & 1, abort_flag)) {
+        *abort_flag = 1;
+        set_status(d.status, DEV_TIMEOUT);
     }
     __syncthreads();
+    const bool ok = !*abort_flag;
+    if (ok) {
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows) and 64 columns;
+        // column c of the covariance goes to cov[c M + row] (lanes write
+        // consecutive words), so row c of cov is column c
+        tc::tc_fence_after();
+        const int row = 32 * (warp & 3) + lane, cb = 64 * (warp >> 2);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cb;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc::tmem_ld32(taddr + 32 * h, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int col = cb + 32 * h + i;
+                if (row < M && col < M)
+                    cov[col * M + row] = matern52(pos + row * 6, pos + col * 6, inv_ell, sf2) - v[i];
+            }
+        }
+    } else if (tid == 0) {  // every issued MMA completes before TMEM is released
+        tc::mma_commit(&bar[1]);
+        tc::mbar_wait(&bar[1], 0, nullptr);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    }
+    if (!ok) return;
     // greedy picks with the kriging-believer update (the R - L pool
     // proposals), by warp 0 alone. The UCB needs only the diagonal of the
     // updated covariance, and the column of pick j is cov0[:, c_j] minus the
@@ -390,8 +451,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_propose(BosDev d) {
     // symmetric (both triangles are the same products), so column c is read
     // as row c.
     if (tid >= 32) return;
-    const int lane = tid;
-    float* colbuf = rowbuf;  // [R - L][M]: the picks' columns
+    float* colbuf = reinterpret_cast<float*>(region0);  // [R - L][M]: the picks' columns
     float* invb = red_v;     // [R - L]: 1 / (col_p[c_p] + noise)
     float dg[4];
     bool tk[4];
@@ -987,7 +1047,8 @@ cc_status bfail(cc_ctx* c, cc_status s, const char* fmt, ...) {
 
 size_t propose_smem(const BosDev& d) {
     const int M = d.M;
-    return (size_t)d.Q * 8 + M * 4 + (size_t)M * M * 4 + M * 6 * 4 + M * 4 + 32 * M * 4 + 32 * 8;
+    return 1024 + propose_region0(d.Q) + M * 4 + (size_t)M * M * 4 + M * 6 * 4 + M * 4 + 32 * 4 +
+           16 + 16;
 }
 size_t condition_smem(const BosDev& d) {
     const int R = d.R;
