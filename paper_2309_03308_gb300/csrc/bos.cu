@@ -775,7 +775,11 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     // the round's GP observations: all R proposals in round 0, the R - L pool
     // proposals (after the local ones) later; nn <= R, matrices use stride nn
     const int s = obs_before(r, R, d.L), nn = obs_new(r, R, d.L), j0 = r == 0 ? 0 : d.L;
-    float* G = reinterpret_cast<float*>(cs);                 // kGRows x 32 of V[:, P] (0-padded)
+    // G (kGRows x 32 of V[:, P], 0-padded) is 1024-byte aligned: the operand
+    // tiles of the product below reuse its space
+    unsigned char* cs_al = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(cs) + 1023) & ~uintptr_t(1023));
+    float* G = reinterpret_cast<float*>(cs_al);
     double* Lf = reinterpret_cast<double*>(G + kGRows * 32);  // R x R (fp64 Cholesky)
     float* covP = reinterpret_cast<float*>(Lf + R * R);    // R x R
     float* L = covP + R * R;                               // R x R fp32 copy
@@ -786,6 +790,9 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     float* mP = yv + R;                           // R prior at picks
     float* hyp = mP + R;                          // 4
     float* Linv = hyp + 4;                        // R: 1 / L22[i][i]
+    uint64_t* cbar = reinterpret_cast<uint64_t*>(Linv + R + (R & 1));  // 6 mbarriers
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(cbar + 6);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int* P = d.picks + rp * R + j0;
     const int per = d.n_rp * R;
     const int Sp = d.Sp;
@@ -900,93 +907,197 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
         }
     }
     __syncthreads();
-    // new rows: V2 = L22^-1 (K(P, pool) - V[:, P]^T V), then mu, var updates.
-    // W = V[:, P]^T V over panels of 2 x 256 pool entries: a thread keeps the
-    // nn x 2 block of W for its entries c and c + 256 in registers (groups of
-    // four picks beyond nn are skipped); V is pool-major, so a step reads eight
-    // observations of each of its two columns as two aligned float4 (rows at
-    // and beyond s are zero, as are G's), the next step's loads issued before
-    // this step's FMAs, and G's eight rows as broadcast float4 from shared
-    // memory (G stays resident while s <= kGRows).
-    constexpr int kPanel = 2 * kBosThreads;
-    const bool resident = s <= kGRows;
-    for (int c0 = 0; c0 < Q; c0 += kPanel) {
-        const int cA = c0 + tid, cB = c0 + kBosThreads + tid;
-        const float* colA = Vr + (int64_t)min(cA, Q - 1) * Sp;
-        const float* colB = Vr + (int64_t)min(cB, Q - 1) * Sp;
-        float wA[32], wB[32];
+    // new rows: V2 = L22^-1 (K(P, pool) - W) with W = V[:, P]^T V, then the
+    // mean and variance updates of every pool entry (finish below).
+    auto finish = [&](int c, float (&w)[32]) {
+        const float* pc = d.pool + ((int64_t)rp * Q + c) * 6;
+        float pcl[6];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) wA[i] = wB[i] = 0.f;
-        float4 na0, na1, nb0, nb1;  // the next step's rows of the two columns
-        if (s > 0) {
-            na0 = __ldcs(reinterpret_cast<const float4*>(colA));
-            na1 = __ldcs(reinterpret_cast<const float4*>(colA + 4));
-            nb0 = __ldcs(reinterpret_cast<const float4*>(colB));
-            nb1 = __ldcs(reinterpret_cast<const float4*>(colB + 4));
-        }
-        for (int t0 = 0; t0 < s; t0 += kGRows) {
-            const int rows = min(kGRows, s - t0);
-            if (!resident) {  // uniform: every thread takes the same branch
-                __syncthreads();
-                gather(t0, rows);
-                __syncthreads();
+        for (int a = 0; a < 6; ++a) pcl[a] = pc[a];
+        float dv = 0.f, dm = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (i < nn) {
+                float x = matern52(pp + i * 6, pcl, inv_ell, sf2) - w[i];
+#pragma unroll
+                for (int q = 0; q < i; ++q) x = fmaf(-L[i * nn + q], w[q], x);
+                x *= Linv[i];
+                w[i] = x;
+                Vr[(int64_t)c * Sp + s + i] = x;
+                dv = fmaf(x, x, dv);
+                dm = fmaf(x, b2[i], dm);
             }
-            for (int tb = 0; tb < rows; tb += 8) {
-                const float4 a0 = na0, a1 = na1, b0 = nb0, b1 = nb1;
-                const int tn = t0 + tb + 8;  // the next step's first row
-                if (tn < s) {
-                    na0 = __ldcs(reinterpret_cast<const float4*>(colA + tn));
-                    na1 = __ldcs(reinterpret_cast<const float4*>(colA + tn + 4));
-                    nb0 = __ldcs(reinterpret_cast<const float4*>(colB + tn));
-                    nb1 = __ldcs(reinterpret_cast<const float4*>(colB + tn + 4));
+        }
+        var[c] -= dv;
+        mu[c] += dm;
+    };
+    if (s == 0) {  // round 0: no earlier observations, W = 0
+        for (int c = tid; c < Q; c += blockDim.x) {
+            float w[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) w[i] = 0.f;
+            finish(c, w);
+        }
+    } else {
+        // W^T (Q x 32) = V^T G on the tensor cores, per tile of 128 pool
+        // entries (the MMA's M) and the picks padded to 32 (N), K = the s
+        // observations in blocks of 32: three TF32 products per K step
+        // (hi x hi + hi x lo + lo x hi, x = hi + lo with hi the first 11
+        // significant bits), FP32 accumulation in TMEM. Warps 4-7 stage the
+        // operand tiles (K-major, 128-byte swizzle, one stage; the next
+        // block's loads are in flight while the MMAs run) and lane 0 of warp
+        // 4 issues the MMAs into one of two TMEM accumulators; warps 0-3 read
+        // a finished tile's accumulator (TMEM lane = pool entry) and run its
+        // entries' finish while the next tile is multiplied. Every wait is
+        // bounded; on timeout the block records DEV_TIMEOUT, the roles leave
+        // their loops, issued MMAs are drained and TMEM is freed.
+        unsigned char* Ah = cs_al;         // 128 x 128 B
+        unsigned char* Al = Ah + 16384;
+        unsigned char* Bh = Al + 16384;    // 32 x 128 B
+        unsigned char* Bl = Bh + 4096;
+        uint64_t* sfree = &cbar[0];   // the stage's MMAs have completed
+        uint64_t* afull = &cbar[1];   // [2] accumulator b holds a finished tile
+        uint64_t* aempty = &cbar[3];  // [2] accumulator b has been read
+        uint64_t* drain = &cbar[5];
+        const int warp = tid >> 5, ntile = Q / 128, nkb = (s + 31) / 32;
+        __syncthreads();  // G is no longer read: its space becomes the stage
+        if (tid == 0) {
+            tc::mbar_init(sfree, 1);
+            tc::mbar_init(&afull[0], 1);
+            tc::mbar_init(&afull[1], 1);
+            tc::mbar_init(&aempty[0], 4);
+            tc::mbar_init(&aempty[1], 4);
+            tc::mbar_init(drain, 1);
+            *abort_flag = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             tc::smem_u32(tslot)),
+                         "r"(64));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+        tc::tc_fence_after();
+        const uint32_t tmem = *tslot;
+        auto fail = [&]() {
+            *abort_flag = 1;
+            set_status(d.status, DEV_TIMEOUT);
+        };
+        if (warp >= 4) {  // producers
+            const int pt = tid - 128;
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(32 >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);  // FP32 += TF32 x TF32, K-major
+            float4 na[8], nb[2];
+            // block (m, kb): A unit q: row (pt + 128 q) >> 3 of tile m, chunk & 7;
+            // B unit q: pick (pt + 128 q) >> 3, chunk & 7; rows >= s read as 0
+            auto load = [&](int m, int kb) {
+                const int t0 = 32 * kb;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int u = pt + 128 * q, t = t0 + 4 * (u & 7);
+                    const float* src = Vr + (int64_t)(128 * m + (u >> 3)) * Sp + t;
+                    na[q] = t < s ? __ldcs(reinterpret_cast<const float4*>(src))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                const float vA[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float vB[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float4* g4 = reinterpret_cast<const float4*>(G + (tb + u) * 32);
+                for (int q = 0; q < 2; ++q) {
+                    const int u = pt + 128 * q, j = u >> 3, t = t0 + 4 * (u & 7);
+                    nb[q] = (j < nn && t < s)
+                                ? __ldcg(reinterpret_cast<const float4*>(Vr + (int64_t)P[j] * Sp + t))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            };
+            auto put = [&](unsigned char* hi, unsigned char* lo, int u, float4 v) {
+                float4 h, l;
+                h.x = __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
+                h.y = __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
+                h.z = __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
+                h.w = __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
+                l.x = v.x - h.x;
+                l.y = v.y - h.y;
+                l.z = v.z - h.z;
+                l.w = v.w - h.w;
+                const int row = u >> 3, ch = u & 7;
+                const uint32_t off = (uint32_t)(row * 128 + ((ch ^ (row & 7)) << 4));
+                *reinterpret_cast<float4*>(hi + off) = h;
+                *reinterpret_cast<float4*>(lo + off) = l;
+            };
+            auto pbar = []() { asm volatile("bar.sync 1, 128;" ::: "memory"); };
+            load(0, 0);
+            int it = 0;
+            for (int m = 0; m < ntile; ++m) {
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    if (pt == 0 && it > 0 && !*abort_flag &&
+                        !tc::mbar_wait(sfree, (it - 1) & 1, abort_flag))
+                        fail();
+                    pbar();  // the stage is free (or the block gave up)
+                    if (*abort_flag) break;
 #pragma unroll
-                    for (int i4 = 0; i4 < 8; ++i4) {
-                        if (4 * i4 < nn) {  // uniform over the block
-                            const float4 g = g4[i4];
-                            wA[4 * i4 + 0] = fmaf(g.x, vA[u], wA[4 * i4 + 0]);
-                            wA[4 * i4 + 1] = fmaf(g.y, vA[u], wA[4 * i4 + 1]);
-                            wA[4 * i4 + 2] = fmaf(g.z, vA[u], wA[4 * i4 + 2]);
-                            wA[4 * i4 + 3] = fmaf(g.w, vA[u], wA[4 * i4 + 3]);
-                            wB[4 * i4 + 0] = fmaf(g.x, vB[u], wB[4 * i4 + 0]);
-                            wB[4 * i4 + 1] = fmaf(g.y, vB[u], wB[4 * i4 + 1]);
-                            wB[4 * i4 + 2] = fmaf(g.z, vB[u], wB[4 * i4 + 2]);
-                            wB[4 * i4 + 3] = fmaf(g.w, vB[u], wB[4 * i4 + 3]);
+                    for (int q = 0; q < 8; ++q) put(Ah, Al, pt + 128 * q, na[q]);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) put(Bh, Bl, pt + 128 * q, nb[q]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    pbar();  // the stage is written
+                    if (pt == 0) {
+                        const int b = m & 1;
+                        if (kb == 0 && m >= 2 && !tc::mbar_wait(&aempty[b], ((m - 2) >> 1) & 1,
+                                                                 abort_flag))
+                            fail();
+                        if (!*abort_flag) {
+                            tc::tc_fence_after();
+                            const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al),
+                                           bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
+                            const uint32_t dt = tmem + 32 * b;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const uint64_t dah = tc::sdesc(ah + k * 32), dal = tc::sdesc(al + k * 32),
+                                               dbh = tc::sdesc(bh + k * 32), dbl = tc::sdesc(bl + k * 32);
+                                bos_mma_tf32(dt, dah, dbh, idesc, (kb | k) != 0);
+                                bos_mma_tf32(dt, dah, dbl, idesc, 1);
+                                bos_mma_tf32(dt, dal, dbh, idesc, 1);
+                            }
+                            tc::mma_commit(sfree);
+                            if (kb == nkb - 1) tc::mma_commit(&afull[b]);
                         }
                     }
+                    const int nm = kb + 1 < nkb ? m : m + 1, nk = kb + 1 < nkb ? kb + 1 : 0;
+                    if (nm < ntile) load(nm, nk);
                 }
+                if (*abort_flag) break;
+            }
+        } else {  // epilogue warps: TMEM lanes 32 warp .. + 31 = pool entries of the tile
+            for (int m = 0; m < ntile; ++m) {
+                const int b = m & 1;
+                int ok = 1;
+                if (lane == 0) ok = tc::mbar_wait(&afull[b], (m >> 1) & 1, abort_flag) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) fail();
+                    break;
+                }
+                tc::tc_fence_after();
+                float w[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * b, w);
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&aempty[b]);
+                finish(128 * m + 32 * warp + lane, w);
             }
         }
-        auto finish = [&](int c, float (&w)[32]) {
-            if (c >= Q) return;
-            const float* pc = d.pool + ((int64_t)rp * Q + c) * 6;
-            float pcl[6];
-#pragma unroll
-            for (int a = 0; a < 6; ++a) pcl[a] = pc[a];
-            float dv = 0.f, dm = 0.f;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                if (i < nn) {
-                    float x = matern52(pp + i * 6, pcl, inv_ell, sf2) - w[i];
-#pragma unroll
-                    for (int q = 0; q < i; ++q) x = fmaf(-L[i * nn + q], w[q], x);
-                    x *= Linv[i];
-                    w[i] = x;
-                    Vr[(int64_t)c * Sp + s + i] = x;
-                    dv = fmaf(x, x, dv);
-                    dm = fmaf(x, b2[i], dm);
-                }
-            }
-            var[c] -= dv;
-            mu[c] += dm;
-        };
-        finish(cA, wA);
-        finish(cB, wB);
+        __syncthreads();
+        if (*abort_flag && tid == 128) {  // every issued MMA completes before TMEM is released
+            tc::mma_commit(drain);
+            tc::mbar_wait(drain, 0, nullptr);
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tc::tc_fence_after();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                         "r"(64));
+        }
     }
     if (tid < nn) {
         d.obs[(int64_t)rp * S + s + tid] = P[tid];
@@ -1052,8 +1163,8 @@ size_t propose_smem(const BosDev& d) {
 }
 size_t condition_smem(const BosDev& d) {
     const int R = d.R;
-    return (size_t)kGRows * 32 * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 + R * 6 * 4 +
-           2 * R * 4 + 16 + R * 4;
+    return 1024 + (size_t)kGRows * 32 * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 +
+           R * 6 * 4 + 2 * R * 4 + 16 + (R + 1) * 4 + 6 * 8 + 16;
 }
 size_t eval_smem(const BosDev& d, int warps) {
     const int pl = (d.n + 2) & ~1;
