@@ -19,6 +19,12 @@
 //              L22 = chol(posterior cov(P, P) + noise): mean and variance of all
 //              pool entries then update as mu += V2^T beta2, var -= colsum(V2^2).
 //
+// The two contractions of the GP, the shortlist's V[:, SL]^T V[:, SL] and the
+// conditioning's V[:, P]^T V, run on the tensor cores in TF32 with each FP32
+// operand split exactly into a TF32 head and tail (three products per K step,
+// FP32 accumulation in TMEM), which keeps FP32-level accuracy in the
+// posterior's cancellation K - V^T V.
+//
 // Matern nu = 5/2 kernel with ARD length scales 0.25 x extent (voxels); the
 // signal variance is the variance of the first round's objective values, the
 // noise variance 1e-4 of it, the prior mean their mean (or a supplied value

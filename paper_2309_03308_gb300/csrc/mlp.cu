@@ -396,9 +396,22 @@ __global__ void k_sur_split(const float* __restrict__ dX3, const float* __restri
     }
 }
 
+// One training step's values, read from device memory by the kernels of a
+// step that is replayed from a CUDA graph (cursor = the step's index).
+struct SurStep {
+    int64_t start;  // first position of the batch in the epoch's order
+    uint64_t step;  // the optimiser's step count before the step (swap stream)
+    float c1, c2;   // Adam's bias corrections after the step
+};
+
 __global__ void k_sur_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                            float* __restrict__ v, int64_t P, float lr, float c1, float c2,
-                           __nv_bfloat16* __restrict__ wb, PadW pw) {
+                           __nv_bfloat16* __restrict__ wb, PadW pw, const SurStep* __restrict__ sp,
+                           const int* __restrict__ cursor) {
+    if (sp) {
+        c1 = sp[*cursor].c1;
+        c2 = sp[*cursor].c2;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -444,7 +457,13 @@ __global__ void k_sur_cast(const float* __restrict__ w, int64_t P, __nv_bfloat16
 __global__ void k_sur_batch(const uint32_t* __restrict__ pa, const uint32_t* __restrict__ pb,
                             const float* __restrict__ tgt, const int64_t* __restrict__ order,
                             int64_t start, int64_t B, uint64_t seed, uint64_t step, int swap,
-                            uint32_t* __restrict__ pts, float* __restrict__ tb) {
+                            uint32_t* __restrict__ pts, float* __restrict__ tb,
+                            const SurStep* __restrict__ sp = nullptr,
+                            const int* __restrict__ cursor = nullptr) {
+    if (sp) {
+        start = sp[*cursor].start;
+        step = sp[*cursor].step;
+    }
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
          b += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = order ? order[start + b] : start + b;
@@ -463,6 +482,8 @@ __global__ void k_sur_batch(const uint32_t* __restrict__ pa, const uint32_t* __r
         tb[b] = tgt ? tgt[s] : 0.f;
     }
 }
+
+__global__ void k_sur_next(int* cursor) { *cursor += 1; }
 
 // linear pair index a * nb + b -> point ids of the pair
 __global__ void k_sur_ids_to_pairs(const uint32_t* __restrict__ ids, int64_t count,
@@ -494,6 +515,7 @@ struct cc_sur {
     DevMem pts, tb, X0, A1, H1, Ef, E, X3, A3, H3, y, dy, dA3, dX3, dE, dH1, dA1, loss;
     DevMem order;
     DevMem ws;  // split-K partials of the weight-gradient GEMMs
+    DevMem steps;  // per-step values of a training epoch, then the step cursor
 };
 
 namespace {
@@ -870,26 +892,77 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         return z ^ (z >> 31);
     };
-    for (int ep = 0; ep < epochs; ++ep) {
+    // Each step's kernels read the step's batch offset, swap stream and Adam
+    // corrections from a device table (one entry per step of the epoch); the
+    // first step runs directly, the second is captured into a CUDA graph
+    // (every buffer is sized by then) and the graph is replayed for the rest,
+    // so the GPU runs a step's ~25 launches back to back.
+    SK(s->steps.ensure(sizeof(SurStep) * (size_t)steps + 16));
+    SurStep* dsteps = s->steps.as<SurStep>();
+    int* cursor = reinterpret_cast<int*>(dsteps + steps);
+    std::vector<SurStep> hsteps((size_t)steps);
+    cudaGraphExec_t exec = nullptr;
+    int graph_kernels = 0;
+    auto body = [&]() -> cc_status {
+        cc_status r2;
+        note_launch();
+        k_sur_batch<<<grid1(B), 256, 0, st>>>(da, db, dt, s->order.as<int64_t>(), 0, B, seed, 0,
+                                              1, s->pts.as<uint32_t>(), s->tb.as<float>(), dsteps,
+                                              cursor);
+        if ((r2 = forward(ctx, s, *f, B, s->tb.as<float>()))) return r2;
+        if ((r2 = backward(ctx, s, B))) return r2;
+        note_launch(2);
+        k_sur_adam<<<grid1(s->off.total), 256, 0, st>>>(s->w.as<float>(), s->g.as<float>(),
+                                                        s->m.as<float>(), s->v.as<float>(),
+                                                        s->off.total, lr, 1.f, 1.f,
+                                                        s->wb.as<bf16>(), padw(s), dsteps, cursor);
+        k_sur_next<<<1, 1, 0, st>>>(cursor);
+        SK(cudaGetLastError());
+        return CC_OK;
+    };
+    cc_status res = CC_OK;
+    for (int ep = 0; ep < epochs && res == CC_OK; ++ep) {
         for (int64_t i = 0; i < n_pairs; ++i) order[i] = i;
         for (int64_t i = n_pairs - 1; i > 0; --i) std::swap(order[i], order[next() % (i + 1)]);
         SK(cudaMemcpyAsync(s->order.p, order.data(), 8 * n_pairs, cudaMemcpyHostToDevice, st));
+        for (int64_t k = 0; k < steps; ++k) {
+            const int64_t t = s->step + k + 1;
+            hsteps[k] = SurStep{k * B, (uint64_t)(s->step + k), 1.f - powf(0.9f, (float)t),
+                                1.f - powf(0.999f, (float)t)};
+        }
+        SK(cudaMemcpyAsync(dsteps, hsteps.data(), sizeof(SurStep) * (size_t)steps,
+                           cudaMemcpyHostToDevice, st));
+        SK(cudaMemsetAsync(cursor, 0, sizeof(int), st));
         double sum = 0;
         for (int64_t k = 0; k < steps; ++k) {
-            note_launch();
-            k_sur_batch<<<grid1(B), 256, 0, st>>>(da, db, dt, s->order.as<int64_t>(), k * B, B,
-                                                  seed, (uint64_t)s->step, 1,
-                                                  s->pts.as<uint32_t>(), s->tb.as<float>());
-            if ((r = forward(ctx, s, *f, B, s->tb.as<float>()))) return r;
-            if ((r = backward(ctx, s, B))) return r;
-            s->step++;
-            const float c1 = 1.f - powf(0.9f, (float)s->step), c2 = 1.f - powf(0.999f, (float)s->step);
-            note_launch();
-            k_sur_adam<<<grid1(s->off.total), 256, 0, st>>>(s->w.as<float>(), s->g.as<float>(),
-                                                            s->m.as<float>(), s->v.as<float>(),
-                                                            s->off.total, lr, c1, c2,
-                                                            s->wb.as<bf16>(), padw(s));
-            SK(cudaGetLastError());
+            if (exec) {
+                note_launch(graph_kernels);
+                SK(cudaGraphLaunch(exec, st));
+            } else if (k == 0 || steps < 3) {
+                if ((res = body())) break;
+            } else {
+                uint64_t before = 0, after = 0;
+                cc_launch_count(&before);
+                SK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+                const cc_status rb = body();
+                cudaGraph_t g = nullptr;
+                const cudaError_t ec = cudaStreamEndCapture(st, &g);
+                cc_launch_count(&after);
+                graph_kernels = (int)(after - before);
+                note_launch(-graph_kernels);
+                if (rb != CC_OK || ec != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    cudaGetLastError();
+                    res = rb != CC_OK ? rb : sfail(ctx, CC_ERR_CUDA, "step capture: %s",
+                                                   cudaGetErrorString(ec));
+                    break;
+                }
+                const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+                cudaGraphDestroy(g);
+                SK(ei);
+                note_launch(graph_kernels);
+                SK(cudaGraphLaunch(exec, st));
+            }
             if (epoch_loss && (k % 64 == 63 || k == steps - 1)) {
                 double l = 0;
                 SK(cudaMemcpyAsync(&l, s->loss.p, 8, cudaMemcpyDeviceToHost, st));
@@ -897,8 +970,11 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
                 sum += l / B;
             }
         }
+        s->step += steps;
         if (epoch_loss) epoch_loss[ep] = (float)(sum / ((steps + 63) / 64));
     }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (res) return res;
     SK(cudaStreamSynchronize(st));
     return CC_OK;
 }
