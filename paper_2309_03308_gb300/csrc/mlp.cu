@@ -144,24 +144,26 @@ __global__ void __launch_bounds__(256)
 
 // C = the sum of S dense partials [S][M][N]: slice z adds into accumulator
 // z mod 8 and the eight are added in order (a fixed order, so the result does
-// not depend on timing; eight loads in flight per thread). With bias, column
-// N - 1 goes to bias[m] and C receives columns 0 .. N - 2.
-__global__ void k_mm_reduce(const float* __restrict__ part, int S, int M, int N,
-                            float* __restrict__ C, int64_t ldc, int accumulate,
-                            float* __restrict__ bias) {
+// not depend on timing). A block of 256 threads takes 32 outputs: warp j sums
+// the slices z = j mod 8 of its lane's output, so every output's eight
+// accumulators are summed in parallel. With bias, column N - 1 goes to
+// bias[m] and C receives columns 0 .. N - 2.
+constexpr int kReduceOuts = 32;  // outputs per block of k_mm_reduce (256 threads)
+__global__ void __launch_bounds__(256)
+    k_mm_reduce(const float* __restrict__ part, int S, int M, int N, float* __restrict__ C,
+                int64_t ldc, int accumulate, float* __restrict__ bias) {
+    __shared__ float red[8][kReduceOuts + 1];
     const int64_t MN = (int64_t)M * N;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        int z = 0;
-        for (; z + 8 <= S; z += 8) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) a[j] += part[(int64_t)(z + j) * MN + e];
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (z + j < S) a[j] += part[(int64_t)(z + j) * MN + e];
-        const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * kReduceOuts + lane;
+    float a = 0.f;
+    if (e < MN)
+        for (int z = j; z < S; z += 8) a += part[(int64_t)z * MN + e];
+    red[j][lane] = a;
+    __syncthreads();
+    if (j == 0 && e < MN) {
+        const float s = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                        ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
         const int64_t m = e / N;
         const int n = (int)(e % N);
         if (bias && n == N - 1) {
@@ -172,6 +174,7 @@ __global__ void k_mm_reduce(const float* __restrict__ part, int S, int M, int N,
         }
     }
 }
+inline unsigned reduce_blocks(int64_t MN) { return (unsigned)((MN + kReduceOuts - 1) / kReduceOuts); }
 
 template <class TA, class TB>
 static cudaError_t mm(const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk, int64_t sbn,
@@ -194,8 +197,8 @@ static cudaError_t mm(const TA* A, int64_t sam, int64_t sak, const TB* B, int64_
     if (S > 1) {
         note_launch();
         const int64_t MN = (int64_t)M * N;
-        k_mm_reduce<<<(unsigned)std::min<int64_t>((MN + 255) / 256, 1024), 256, 0, st>>>(
-            ws->as<float>(), S, M, N, C, ldc, acc, nullptr);
+        k_mm_reduce<<<reduce_blocks(MN), 256, 0, st>>>(ws->as<float>(), S, M, N, C, ldc, acc,
+                                                        nullptr);
     }
     return cudaGetLastError();
 }
@@ -248,8 +251,8 @@ static cudaError_t tmm(int* status, const TA* A, int64_t sam, int64_t sak, const
     if (e != cudaSuccess) return e;
     note_launch();
     const int64_t MN = (int64_t)M * NB;
-    k_mm_reduce<<<(unsigned)std::min<int64_t>((MN + 127) / 128, 4096), 128, 0, st>>>(
-        ws->as<float>(), (int)S, M, NB, C, ldc, 0, bias);
+    k_mm_reduce<<<reduce_blocks(MN), 256, 0, st>>>(ws->as<float>(), (int)S, M, NB, C, ldc, 0,
+                                                    bias);
     return cudaGetLastError();
 }
 
@@ -626,8 +629,9 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
         note_launch(3);  // with the head's GELU backward
         k_sur_w4_grad<<<(unsigned)nb, kH3 + 32, 0, st>>>(s->H3.as<bf16>(), s->dy.as<float>(), B,
                                                          s->ws.as<float>());
-        k_mm_reduce<<<2, 128, 0, st>>>(s->ws.as<float>(), (int)nb, 1, kH3 + 1, g + o.w4, kH3 + 1,
-                                       0, nullptr);
+        k_mm_reduce<<<reduce_blocks(kH3 + 1), 256, 0, st>>>(s->ws.as<float>(), (int)nb, 1,
+                                                             kH3 + 1, g + o.w4, kH3 + 1, 0,
+                                                             nullptr);
     }
     k_sur_gelu_bwd<<<grid1(B * kH3), 256, 0, st>>>(s->A3.as<float>(), s->dy.as<float>(),
                                                    s->w.as<float>() + o.w4, nullptr, B, kH3,
