@@ -56,6 +56,10 @@ constexpr uint64_t kPoolKey = 0xB05B05ull, kRoundKey = 0xB0517Dull;
 constexpr int kBosThreads = 256;
 constexpr int kGRows = 512;  // rows of V[:, P] the conditioning keeps in shared memory
 constexpr int kEvalChunk = 8;  // KSG candidates per work-queue pull
+// the conditioning's first shared region: G (kGRows x 32 floats), later the
+// product's operand stage (40 KB) and its two-block load ring (40 KB)
+constexpr size_t kCondRegion0 = 81920;
+static_assert(kCondRegion0 >= (size_t)kGRows * 32 * 4, "G fits the first region");
 
 struct BosDev {
     int n_rp, Q, R, T, M;
@@ -168,6 +172,13 @@ __global__ void k_bos_pool(BosDev d) {
 // (32 x 128 floats), whichever is largest.
 __host__ __device__ constexpr size_t propose_region0(int Q) {
     return (size_t)Q * 8 > 32768 ? (size_t)Q * 8 : 32768;
+}
+
+// 16-byte global -> shared copy through L2 (cp.async)
+__device__ __forceinline__ void bos_cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(smem)),
+                 "l"(gmem)
+                 : "memory");
 }
 
 // D (TMEM) (+)= A B^T, TF32 operands from shared-memory descriptors
@@ -786,7 +797,7 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
     unsigned char* cs_al = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(cs) + 1023) & ~uintptr_t(1023));
     float* G = reinterpret_cast<float*>(cs_al);
-    double* Lf = reinterpret_cast<double*>(G + kGRows * 32);  // R x R (fp64 Cholesky)
+    double* Lf = reinterpret_cast<double*>(cs_al + kCondRegion0);  // R x R (fp64 Cholesky)
     float* covP = reinterpret_cast<float*>(Lf + R * R);    // R x R
     float* L = covP + R * R;                               // R x R fp32 copy
     float* gb = L + R * R;                        // R: V[:, P]^T beta
@@ -995,25 +1006,39 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
             const int pt = tid - 128;
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(32 >> 3) << 17) |
                                    ((uint32_t)(128 >> 4) << 24);  // FP32 += TF32 x TF32, K-major
-            float4 na[8], nb[2];
-            // block (m, kb): A unit q: row (pt + 128 q) >> 3 of tile m, chunk & 7;
-            // B unit q: pick (pt + 128 q) >> 3, chunk & 7; rows >= s read as 0
-            auto load = [&](int m, int kb) {
-                const int t0 = 32 * kb;
+            // block it = (m, kb): A unit q: row (pt + 128 q) >> 3 of tile m, chunk
+            // & 7; B unit q: pick (pt + 128 q) >> 3, chunk & 7; rows >= s read as 0.
+            // Each producer copies its own ten 16-byte units of a block into a
+            // two-block ring (cp.async, [slot][unit][thread]) two blocks ahead
+            // of the one it converts, and converts only its own units, so the
+            // ring needs no barrier.
+            float4* ring = reinterpret_cast<float4*>(Bl + 4096);  // [2][10][128]
+            auto issue = [&](int itn) {
+                const int mn = itn / nkb, kbn = itn - mn * nkb;
+                if (mn < ntile) {
+                    const int t0 = 32 * kbn, sl = itn & 1;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int u = pt + 128 * q, t = t0 + 4 * (u & 7);
-                    const float* src = Vr + (int64_t)(128 * m + (u >> 3)) * Sp + t;
-                    na[q] = t < s ? __ldcs(reinterpret_cast<const float4*>(src))
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                    for (int q = 0; q < 8; ++q) {
+                        const int u = pt + 128 * q, t = t0 + 4 * (u & 7);
+                        if (t < s)
+                            bos_cp_async16(&ring[(sl * 10 + q) * 128 + pt],
+                                           Vr + (int64_t)(128 * mn + (u >> 3)) * Sp + t);
+                    }
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int u = pt + 128 * q, j = u >> 3, t = t0 + 4 * (u & 7);
-                    nb[q] = (j < nn && t < s)
-                                ? __ldcg(reinterpret_cast<const float4*>(Vr + (int64_t)P[j] * Sp + t))
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int q = 0; q < 2; ++q) {
+                        const int u = pt + 128 * q, j = u >> 3, t = t0 + 4 * (u & 7);
+                        if (j < nn && t < s)
+                            bos_cp_async16(&ring[(sl * 10 + 8 + q) * 128 + pt],
+                                           Vr + (int64_t)P[j] * Sp + t);
+                    }
                 }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            auto unit = [&](int itn, int q) {  // this thread's unit q of block itn
+                const int kbn = itn % nkb, u = pt + 128 * (q < 8 ? q : q - 8);
+                const int t = 32 * kbn + 4 * (u & 7);
+                const bool ok = q < 8 ? t < s : ((u >> 3) < nn && t < s);
+                return ok ? ring[((itn & 1) * 10 + q) * 128 + pt] : make_float4(0.f, 0.f, 0.f, 0.f);
             };
             auto put = [&](unsigned char* hi, unsigned char* lo, int u, float4 v) {
                 float4 h, l;
@@ -1031,19 +1056,21 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
                 *reinterpret_cast<float4*>(lo + off) = l;
             };
             auto pbar = []() { asm volatile("bar.sync 1, 128;" ::: "memory"); };
-            load(0, 0);
+            issue(0);
+            issue(1);
             int it = 0;
             for (int m = 0; m < ntile; ++m) {
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");  // block it has landed
                     if (pt == 0 && it > 0 && !*abort_flag &&
                         !tc::mbar_wait(sfree, (it - 1) & 1, abort_flag))
                         fail();
                     pbar();  // the stage is free (or the block gave up)
                     if (*abort_flag) break;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) put(Ah, Al, pt + 128 * q, na[q]);
+                    for (int q = 0; q < 8; ++q) put(Ah, Al, pt + 128 * q, unit(it, q));
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) put(Bh, Bl, pt + 128 * q, nb[q]);
+                    for (int q = 0; q < 2; ++q) put(Bh, Bl, pt + 128 * q, unit(it, 8 + q));
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     pbar();  // the stage is written
                     if (pt == 0) {
@@ -1068,11 +1095,11 @@ __global__ void __launch_bounds__(kBosThreads) k_bos_condition(BosDev d) {
                             if (kb == nkb - 1) tc::mma_commit(&afull[b]);
                         }
                     }
-                    const int nm = kb + 1 < nkb ? m : m + 1, nk = kb + 1 < nkb ? kb + 1 : 0;
-                    if (nm < ntile) load(nm, nk);
+                    issue(it + 2);  // into the slot of block it, just converted
                 }
                 if (*abort_flag) break;
             }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the block
         } else {  // epilogue warps: TMEM lanes 32 warp .. + 31 = pool entries of the tile
             for (int m = 0; m < ntile; ++m) {
                 const int b = m & 1;
@@ -1169,8 +1196,8 @@ size_t propose_smem(const BosDev& d) {
 }
 size_t condition_smem(const BosDev& d) {
     const int R = d.R;
-    return 1024 + (size_t)kGRows * 32 * 4 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 +
-           R * 6 * 4 + 2 * R * 4 + 16 + (R + 1) * 4 + 6 * 8 + 16;
+    return 1024 + kCondRegion0 + R * R * 4 + R * R * 8 + R * R * 4 + 2 * R * 4 + R * 6 * 4 +
+           2 * R * 4 + 16 + (R + 1) * 4 + 6 * 8 + 16;
 }
 size_t eval_smem(const BosDev& d, int warps) {
     const int pl = (d.n + 2) & ~1;
