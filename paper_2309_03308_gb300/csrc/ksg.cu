@@ -17,16 +17,16 @@
 //
 //   eps_i: walk outward from i along ONE axis, over that axis's sorted order,
 //   on both sides at once; every visited j offers d_ij. The first k
-//   positions are taken unconditionally and sorted by a fixed network; each
-//   later step offers the next two positions of each side to a sorted register
-//   list of the k smallest (four values merged at once: sorted, folded into
-//   the list's top four, bitonic merger) and passes the positions whose axis
-//   distance was below the list's k-th value. When both next axis distances
-//   are not below the k-th value no unvisited j can enter, so the walk stops
-//   with the exact k-th smallest. The walk length is about the number of
-//   samples within eps_i along the axis, large where that axis is locally
-//   dense; each lane walks along the axis whose local spacing (8-neighbour
-//   span in sorted order) is wider. Sentinels (+-inf) around the staged arrays
+//   positions are taken unconditionally and sorted by a fixed network; the
+//   first step offers the next four positions of each side, every later step
+//   the next two, to a sorted register list of the k smallest (the new values
+//   sorted, folded into the list's top entries, bitonic merger) and passes
+//   the positions whose axis distance was below the list's k-th value. When
+//   both next axis distances are not below the k-th value no unvisited j can
+//   enter, so the walk stops with the exact k-th smallest. The walk length is
+//   about the number of samples within eps_i along the axis, so each lane
+//   walks along the axis on which the ~0.8 sqrt(k n) sorted positions nearest
+//   to the sample span the wider range. Sentinels (+-inf) around the staged arrays
 //   keep the step free of bounds checks, and all lanes run the same code on
 //   lane-selected arrays.
 //
@@ -45,7 +45,7 @@ namespace cc {
 
 double digamma_int_host(int m);
 
-constexpr int kKsgWarps = 4;
+constexpr int kKsgWarps = 8;
 // The pair-batch form holds one staged pair per warp in shared memory; for
 // large n the slot, not the register file, limits the warps an SM can run,
 // so a block takes as many warps as leave room for two blocks per SM.
@@ -290,7 +290,8 @@ static cudaError_t ksg_launch(const Field& fa, const Field& fb, int k, const int
                                                  (int)smem2);
             if (e != cudaSuccess) return e;
         }
-        const int64_t want_warps = (int64_t)sms * 16 * kKsgWarps;
+        // about 32 blocks' worth of warps per SM, so the last pairs spread thinly
+        const int64_t want_warps = (int64_t)sms * 32 * kKsgWarps;
         const int64_t per_warp = (N + want_warps - 1) / want_warps;
         const int64_t warps = (N + per_warp - 1) / per_warp;
         const int64_t blocks = (warps + kKsgWarps - 1) / kKsgWarps;

@@ -133,9 +133,10 @@ __host__ __device__ constexpr int ksg_kmax(int k) {
            : k <= 16 ? 16 : 32;
 }
 
-// sentinel entries on each side of a staged sorted array: the first walk
-// step reads up to ceil(KMAX/2) positions out, a later step two more, and
-// the window trim reads up to seven positions past the sample
+// sentinel entries on each side of a staged sorted array: the walk's start
+// reads up to ceil(KMAX/2) positions out, a step up to seven positions past
+// the next position of an open side, and the window trim up to seven
+// positions past the sample
 __host__ __device__ constexpr int ksg_pad(int kmax) {
     return (kmax + 1) / 2 + 2 > 7 ? (kmax + 1) / 2 + 2 : 7;
 }
@@ -227,9 +228,10 @@ __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
 // entries), from the sample's position s outwards on both sides at once.
 // L / R are the next unvisited positions on each side. The first k
 // positions (ceil(k/2) left, floor(k/2) right) are visited unconditionally
-// and sorted; every later step offers the next two positions of each side
-// and advances a side past the positions whose axis distance was below the
-// k-th smallest value before the step. A position that is offered but not
+// and sorted; the first step offers the next four positions of each side
+// (ksg_step8), every later step the next two (ksg_step), and a step advances
+// a side past the positions whose axis distance was below the k-th smallest
+// value before the step. A position that is offered but not
 // passed has a Chebyshev distance not below that value, so it cannot change
 // the list (and it is offered again only under the same condition). The
 // walk ends when both next axis distances are not below the k-th smallest
@@ -257,12 +259,23 @@ __device__ __forceinline__ void ksg_begin(KsgWalk<KMAX>& w, const unsigned char*
     const uint16_t* upos = reinterpret_cast<const uint16_t*>(YO + n_pad + pad);
     const float2 zi = XO[ti];
     const int ui = upos[ti];
-    // walk along the axis with the wider local spacing (span of the 8
-    // neighbours on each side in sorted order)
-    const int h = 8;
-    const float span_x = __fsub_rn(XO[min(ti + h, n - 1)].x, XO[max(ti - h, 0)].x);
-    const float span_y = __fsub_rn(YO[min(ui + h, n - 1)].x, YO[max(ui - h, 0)].x);
-    w.on_y = span_y > span_x;
+    // Walk along the axis on which fewer samples lie within eps. The walk
+    // visits about as many positions as its axis has samples closer than
+    // eps, typically sqrt(k n) of them, so each axis is scored by the radius
+    // around the sample that holds m ~ 0.8 sqrt(k n) sorted positions: for
+    // two placements of a window of m + 1 consecutive positions that
+    // contains the sample (clipped to the sorted order), the larger of the
+    // window's two end distances; the smaller over the placements estimates
+    // the radius of the m nearest positions, and the axis with the larger
+    // radius is walked. (A wrong choice costs steps, never exactness.)
+    const int m = min((int)(0.8f * sqrtf((float)(k * n)) + 0.5f), n - 1);
+    auto window = [&](const float2* A, int r, float v, int j) {
+        const int lo = min(max(r - j, 0), n - 1 - m);
+        return fmaxf(__fsub_rn(v, A[lo].x), __fsub_rn(A[lo + m].x, v));
+    };
+    const float rad_x = fminf(window(XO, ti, zi.x, m >> 2), window(XO, ti, zi.x, (3 * m) >> 2));
+    const float rad_y = fminf(window(YO, ui, zi.y, m >> 2), window(YO, ui, zi.y, (3 * m) >> 2));
+    w.on_y = rad_y > rad_x;
     w.W = w.on_y ? YO : XO;
     w.O = w.on_y ? XO : YO;
     w.s = w.on_y ? ui : ti;
@@ -317,6 +330,56 @@ __device__ __forceinline__ bool ksg_step(KsgWalk<KMAX>& w) {
     w.L = L - (lo ? c01 + (ro ? 0 : c23) : 0);
     w.R = R + (ro ? c23 + (lo ? 0 : c01) : 0);
     topk_merge4<KMAX>(w.top, d0, d1, d2, d3);
+    return true;
+}
+
+// The KMAX smallest of the sorted list t and eight new values, sorted (as
+// topk_merge4, with a sorting network of eight).
+template <int KMAX>
+__device__ __forceinline__ void topk_merge8(float (&t)[KMAX], float (&c)[8]) {
+    sort_small<8>(c);
+    if constexpr (KMAX >= 8) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[KMAX - 1 - j] = fminf(t[KMAX - 1 - j], c[j]);
+        bitonic_merge<KMAX>(t);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) topk_insert<KMAX>(t, c[j]);
+    }
+}
+
+// The first step after ksg_begin: as ksg_step, with four positions per open
+// side, or eight from the only open side. Almost every walk takes at least
+// two steps, so this merges the first two into one with one sorting network
+// of eight. An open left side has L >= 0 and an open right side R <= n - 1,
+// so every index stays within seven positions of the sorted order, inside
+// the sentinels.
+template <int KMAX>
+__device__ __forceinline__ bool ksg_step8(KsgWalk<KMAX>& w) {
+    const float2* W = w.W;
+    const int L = w.L, R = w.R;
+    const float pv = w.pv, ov = w.ov;
+    const float kth = w.top[KMAX - 1];
+    const bool lo = __fsub_rn(pv, W[L].x) < kth;
+    const bool ro = __fsub_rn(W[R].x, pv) < kth;
+    if (!(lo || ro)) return false;
+    float c[8];
+    int cl = 0, cr = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        // left offers L - j (or R + 4 + j when closed), right R + j (or L - 4 - j)
+        const float2 zl = W[lo ? L - j : R + 4 + j];
+        const float2 zr = W[ro ? R + j : L - 4 - j];
+        const float al = fabsf(__fsub_rn(pv, zl.x)), ar = fabsf(__fsub_rn(pv, zr.x));
+        c[j] = fmaxf(al, fabsf(__fsub_rn(ov, zl.y)));
+        c[4 + j] = fmaxf(ar, fabsf(__fsub_rn(ov, zr.y)));
+        cl += (int)(al < kth);
+        cr += (int)(ar < kth);
+    }
+    // passed positions are prefixes of each side (axis distance grows outwards)
+    w.L = L - (lo ? cl + (ro ? 0 : cr) : 0);
+    w.R = R + (ro ? cr + (lo ? 0 : cl) : 0);
+    topk_merge8<KMAX>(w.top, c);
     return true;
 }
 
@@ -391,8 +454,9 @@ __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n
                                                 int* cx_out, int* cy_out, float* eps_out) {
     KsgWalk<KMAX> w;
     ksg_begin<KMAX>(w, slot, n, n_pad, k, ti);
-    while (ksg_step<KMAX>(w)) {
-    }
+    if (ksg_step8<KMAX>(w))
+        while (ksg_step<KMAX>(w)) {
+        }
     return ksg_finish<KMAX>(w, n, psi, cx_out, cy_out, eps_out);
 }
 
