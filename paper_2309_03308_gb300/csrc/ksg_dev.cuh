@@ -168,12 +168,16 @@ __device__ __forceinline__ void ksg_stage(unsigned char* slot, int n, int n_pad,
     float2* YO = XO + n_pad + 2 * pad;
     uint16_t* upos = reinterpret_cast<uint16_t*>(YO + n_pad + pad);
     uint16_t* invq = upos + n_pad;
+    // -inf before position 0; +inf from position n up to n_pad + pad - 1
+    // (the counting search of ksg_finish probes up to position n_pad - 1)
+    const float2 lo = make_float2(-CUDART_INF_F, 0.f), hi = make_float2(CUDART_INF_F, 0.f);
     if (lane < pad) {
-        const float2 lo = make_float2(-CUDART_INF_F, 0.f), hi = make_float2(CUDART_INF_F, 0.f);
         XO[lane - pad] = lo;
         YO[lane - pad] = lo;
-        XO[n + lane] = hi;
-        YO[n + lane] = hi;
+    }
+    for (int j = n + lane; j < n_pad + pad; j += 32) {
+        XO[j] = hi;
+        YO[j] = hi;
     }
     // y side: invq (inverse argsort of q) and YO = (y sorted, x of that member)
     for (int base = 0; base < n; base += 32 * IT) {
@@ -383,6 +387,14 @@ __device__ __forceinline__ bool ksg_step8(KsgWalk<KMAX>& w) {
     return true;
 }
 
+// One level of the counting search of ksg_finish: the probes at offset
+// H - 1 from the lower bound a and the upper bound b.
+template <int H>
+__device__ __forceinline__ void ksg_probe2(const float2* O, int& a, int& b, float ov, float eps) {
+    if (!(__fsub_rn(ov, O[a + (H - 1)].x) < eps)) a += H;
+    if (__fsub_rn(O[b + (H - 1)].x, ov) < eps) b += H;
+}
+
 // The counts of a finished walk; returns psi[n_x] + psi[n_y] from the
 // fixed-point table.
 template <int KMAX>
@@ -421,17 +433,25 @@ __device__ __forceinline__ long long ksg_finish(const KsgWalk<KMAX>& w, int n,
     const int c_walk = eps > 0.f ? R - L - 1 : 1;
     // other axis: [a, b) with a = first j with fl(ov - O[j].x) < eps,
     // b = first j with fl(O[j].x - ov) >= eps (fl32 differences are monotone
-    // along the sorted order). Both by one branch-free search (a and b
-    // interleaved) that halves a range of the same length for every lane:
-    // the answer lies in [base, base + len], a probe at base + half - 1
-    // either moves base up by half or leaves it, and len shrinks by half, so
-    // no probe leaves [0, n) and the loop count is the same for all lanes.
+    // along the sorted order; the +inf entries from position n on satisfy
+    // both tests, so a, b <= n). Both by one branch-free search (a and b
+    // interleaved) over a range of 2^L >= n positions: the answer lies in
+    // [base, base + len], a probe at base + len / 2 - 1 either moves base up
+    // by len / 2 or leaves it, and len halves. L is the same for every lane,
+    // so the probes are unrolled with constant offsets from the entry point
+    // that L selects, and no probe passes position 2^L - 1 <= n_pad - 1.
     int a = 0, b = 0;
-    for (int len = n; len > 1;) {
-        const int half = len >> 1;
-        if (!(__fsub_rn(ov, O[a + half - 1].x) < eps)) a += half;
-        if (__fsub_rn(O[b + half - 1].x, ov) < eps) b += half;
-        len -= half;
+    switch (32 - __clz(n - 1)) {  // L = ceil(log2 n), 1 <= L <= 10 for 2 <= n <= 1024
+        case 10: ksg_probe2<512>(O, a, b, ov, eps); [[fallthrough]];
+        case 9: ksg_probe2<256>(O, a, b, ov, eps); [[fallthrough]];
+        case 8: ksg_probe2<128>(O, a, b, ov, eps); [[fallthrough]];
+        case 7: ksg_probe2<64>(O, a, b, ov, eps); [[fallthrough]];
+        case 6: ksg_probe2<32>(O, a, b, ov, eps); [[fallthrough]];
+        case 5: ksg_probe2<16>(O, a, b, ov, eps); [[fallthrough]];
+        case 4: ksg_probe2<8>(O, a, b, ov, eps); [[fallthrough]];
+        case 3: ksg_probe2<4>(O, a, b, ov, eps); [[fallthrough]];
+        case 2: ksg_probe2<2>(O, a, b, ov, eps); [[fallthrough]];
+        default: ksg_probe2<1>(O, a, b, ov, eps);
     }
     a += !(__fsub_rn(ov, O[a].x) < eps) ? 1 : 0;
     b += __fsub_rn(O[b].x, ov) < eps ? 1 : 0;
