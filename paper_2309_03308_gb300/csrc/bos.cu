@@ -1211,8 +1211,7 @@ template <int KMAX>
 cudaError_t eval_launch(const BosDev& d, int warps, int blocks, bool set_attr, cudaStream_t st) {
     const size_t smem = eval_smem(d, warps);
     if (set_attr) {
-        cudaError_t e = cudaFuncSetAttribute(
-            k_bos_eval<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = raise_smem_limit(k_bos_eval<KMAX>, smem);
         if (e != cudaSuccess) return e;
     }
     note_launch();
@@ -1222,8 +1221,7 @@ cudaError_t eval_launch(const BosDev& d, int warps, int blocks, bool set_attr, c
 
 template <int KMAX>
 cudaError_t eval_attr(const BosDev& d, int warps) {
-    return cudaFuncSetAttribute(k_bos_eval<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)eval_smem(d, warps));
+    return raise_smem_limit(k_bos_eval<KMAX>, eval_smem(d, warps));
 }
 
 cudaError_t set_eval_attr(const BosDev& d, int warps) {
@@ -1460,10 +1458,8 @@ cc_status cc_bos_create2(cc_ctx* ctx, int32_t field_id, int32_t field_b_id, cons
     note_launch();
     k_bos_pool<<<(unsigned)(((int64_t)n_rp * Q + 255) / 256), 256, 0, st>>>(d);
     BK(cudaGetLastError());
-    BK(cudaFuncSetAttribute(k_bos_propose, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)propose_smem(d)));
-    BK(cudaFuncSetAttribute(k_bos_condition, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)condition_smem(d)));
+    BK(raise_smem_limit(k_bos_propose, propose_smem(d)));
+    BK(raise_smem_limit(k_bos_condition, condition_smem(d)));
     BK(cudaStreamSynchronize(st));
     *out = guard.release();
     return CC_OK;

@@ -138,6 +138,19 @@ void note_launch(int kernels = 1);
 // Streaming multiprocessors of the current device (grid sizes scale with it).
 int sm_count();
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`, never lowering it: launches captured into a CUDA graph keep
+// their own sizes, so a later call with a smaller size must leave the limit
+// where an earlier capture needs it.
+template <class Kernel>
+cudaError_t raise_smem_limit(Kernel* kernel, size_t bytes) {
+    cudaFuncAttributes a{};
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // Kernel launchers (defined in the .cu files), all on `st`.
 // in: member-major [n][in_stride] (P points used), vals: point-major [P][n_pad]
 cudaError_t launch_ingest(const float* in, int n, int64_t P, int64_t in_stride, int n_pad,

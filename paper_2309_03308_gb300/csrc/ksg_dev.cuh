@@ -292,8 +292,13 @@ __device__ __forceinline__ void ksg_begin(KsgWalk<KMAX>& w, const unsigned char*
         const float2 l = w.W[w.s - 1 - t], r = w.W[w.s + 1 + t];
         const float dl = fmaxf(__fsub_rn(w.pv, l.x), fabsf(__fsub_rn(w.ov, l.y)));
         const float dr = fmaxf(__fsub_rn(r.x, w.pv), fabsf(__fsub_rn(w.ov, r.y)));
-        c[2 * t] = 2 * t < k ? dl : -CUDART_INF_F;
-        c[2 * t + 1] = 2 * t + 1 < k ? dr : -CUDART_INF_F;
+        c[2 * t] = dl;
+        c[2 * t + 1] = dr;
+    }
+    if (k < NP1) {  // the same for every lane
+#pragma unroll
+        for (int t = 0; t < NP1; ++t)
+            if (t >= k) c[t] = -CUDART_INF_F;
     }
     sort_small<NP1>(c);
 #pragma unroll
@@ -316,11 +321,12 @@ __device__ __forceinline__ bool ksg_step(KsgWalk<KMAX>& w) {
     const int L = w.L, R = w.R;
     const float pv = w.pv, ov = w.ov;
     const float kth = w.top[KMAX - 1];
-    const bool lo = __fsub_rn(pv, W[L].x) < kth;
-    const bool ro = __fsub_rn(W[R].x, pv) < kth;
+    const float2 wl = W[L], wr = W[R];
+    const bool lo = __fsub_rn(pv, wl.x) < kth;
+    const bool ro = __fsub_rn(wr.x, pv) < kth;
     if (!(lo || ro)) return false;
-    const float2 z0 = W[lo ? L : R + 2], z1 = W[lo ? L - 1 : R + 3];
-    const float2 z2 = W[ro ? R : L - 2], z3 = W[ro ? R + 1 : L - 3];
+    const float2 z0 = lo ? wl : W[R + 2], z1 = W[lo ? L - 1 : R + 3];
+    const float2 z2 = ro ? wr : W[L - 2], z3 = W[ro ? R + 1 : L - 3];
     const float a0 = fabsf(__fsub_rn(pv, z0.x)), a1 = fabsf(__fsub_rn(pv, z1.x));
     const float a2 = fabsf(__fsub_rn(pv, z2.x)), a3 = fabsf(__fsub_rn(pv, z3.x));
     const float d0 = fmaxf(a0, fabsf(__fsub_rn(ov, z0.y)));
@@ -364,16 +370,17 @@ __device__ __forceinline__ bool ksg_step8(KsgWalk<KMAX>& w) {
     const int L = w.L, R = w.R;
     const float pv = w.pv, ov = w.ov;
     const float kth = w.top[KMAX - 1];
-    const bool lo = __fsub_rn(pv, W[L].x) < kth;
-    const bool ro = __fsub_rn(W[R].x, pv) < kth;
+    const float2 wl = W[L], wr = W[R];
+    const bool lo = __fsub_rn(pv, wl.x) < kth;
+    const bool ro = __fsub_rn(wr.x, pv) < kth;
     if (!(lo || ro)) return false;
     float c[8];
     int cl = 0, cr = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         // left offers L - j (or R + 4 + j when closed), right R + j (or L - 4 - j)
-        const float2 zl = W[lo ? L - j : R + 4 + j];
-        const float2 zr = W[ro ? R + j : L - 4 - j];
+        const float2 zl = j == 0 && lo ? wl : W[lo ? L - j : R + 4 + j];
+        const float2 zr = j == 0 && ro ? wr : W[ro ? R + j : L - 4 - j];
         const float al = fabsf(__fsub_rn(pv, zl.x)), ar = fabsf(__fsub_rn(pv, zr.x));
         c[j] = fmaxf(al, fabsf(__fsub_rn(ov, zl.y)));
         c[4 + j] = fmaxf(ar, fabsf(__fsub_rn(ov, zr.y)));

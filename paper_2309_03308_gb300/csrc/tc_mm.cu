@@ -403,8 +403,9 @@ cudaError_t launch_tc_mm(const void* A, int a_bf16, int64_t sam, int64_t sak, co
     if (!kern || (b_ones >= 0 && (bm & MM_ALONG_K) != 0)) return cudaErrorNotSupported;
     const int np = (N + 15) / 16 * 16;
     const size_t smem = tc::mm_smem_bytes(np);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    // never lowered: the training step's launches are captured into a graph
+    // with their own sizes
+    cudaError_t e = raise_smem_limit(kern, smem);
     if (e != cudaSuccess) return e;
     const int64_t slices = (K + kc - 1) / kc;
     // the output: part (dense [slices][M][ldc] partials) whenever it is given,
