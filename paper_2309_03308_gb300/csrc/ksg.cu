@@ -113,8 +113,10 @@ __global__ void __launch_bounds__(kMaxPairWarps * 32)
             if (!((valid >> sl) & 1u)) continue;
             int cx, cy;
             float eps;
-            const long long v = ksg_sample<KMAX>(wbase + sl * slot_bytes, n, n_pad, k, ti, psi,
-                                                 nx_out ? &cx : nullptr, &cy, &eps);
+            // pair-batch form (n > 256 or n < 32): long walks take eight
+            // positions in every step
+            const long long v = ksg_sample<KMAX, true>(wbase + sl * slot_bytes, n, n_pad, k, ti,
+                                                       psi, nx_out ? &cx : nullptr, &cy, &eps);
 #pragma unroll
             for (int u = 0; u < kMaxGroup; ++u)
                 if (u == sl) acc[u] += v;

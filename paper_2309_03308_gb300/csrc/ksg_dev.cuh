@@ -474,16 +474,21 @@ __device__ __forceinline__ long long ksg_finish(const KsgWalk<KMAX>& w, int n,
 }
 
 // One sample (x-sorted position ti) of a staged pair: eps and the two counts;
-// returns psi[n_x] + psi[n_y] from the fixed-point table.
-template <int KMAX>
+// returns psi[n_x] + psi[n_y] from the fixed-point table. kLong: every step
+// offers eight positions (long walks, n > 256); otherwise only the first.
+template <int KMAX, bool kLong = false>
 __device__ __forceinline__ long long ksg_sample(const unsigned char* slot, int n, int n_pad, int k,
                                                 int ti, const long long* __restrict__ psi,
                                                 int* cx_out, int* cy_out, float* eps_out) {
     KsgWalk<KMAX> w;
     ksg_begin<KMAX>(w, slot, n, n_pad, k, ti);
-    if (ksg_step8<KMAX>(w))
+    if constexpr (kLong) {
+        while (ksg_step8<KMAX>(w)) {
+        }
+    } else if (ksg_step8<KMAX>(w)) {
         while (ksg_step<KMAX>(w)) {
         }
+    }
     return ksg_finish<KMAX>(w, n, psi, cx_out, cy_out, eps_out);
 }
 
