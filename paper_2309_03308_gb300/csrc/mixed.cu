@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(256)
     if (nchunks) N = min(N, (int64_t)*nchunks * 32);
     unsigned lo[NS], hi[NS];
     bool on[NS];
+    bool any = false;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const Select* sel = sv.sel[s];
@@ -243,7 +244,12 @@ __global__ void __launch_bounds__(256)
         on[s] = !(thr && (sel->threshold == 0u || sel->overflow));
         lo[s] = thr ? okey(*thr) : sel->threshold;
         hi[s] = thr ? sel->threshold : 0u;
+        // second pass: an empty window [lo, hi) takes nothing (the usual case:
+        // the first pass's threshold lies below the best value minus the bound)
+        if (thr && lo[s] >= hi[s]) on[s] = false;
+        any = any || on[s];
     }
+    if (!any) return;  // the same for every thread
     const int lane = threadIdx.x & 31;
     auto offer = [&](int s, float w, int64_t idx) {
         const float x = sv.sign[s] * w;
