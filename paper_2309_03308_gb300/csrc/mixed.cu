@@ -324,10 +324,11 @@ __device__ __forceinline__ float dot2_warp(const float (&x)[R], const float* __r
 }
 
 // One warp per chunk, one lane per pair: lane j evaluates (a, 32 * chunk + j)
-// with a sequential Dot2 over the members. The 32 column rows are read 32
-// members at a time, coalesced, into a transposed shared-memory tile (rows
-// padded to 33 words), and row a's member is broadcast from the lane that
-// holds it, so a chunk costs one pass over its rows and no reductions.
+// with a sequential Dot2 over the members. Lane j reads its own column row
+// as aligned float4s (rows are n_pad >= 32 R floats, 16-byte aligned), two
+// 32-member slices in flight at a time, and row a's member is broadcast from
+// the lane that holds it, so a chunk costs two memory round trips, no shared
+// memory and no reductions.
 // The chunks of one side (blockIdx.y) of the refinement: candidate ids,
 // where this pass's ids start (null: 0) and end, the sign of the side, and
 // where the refined values, pair ids and the best key go.
@@ -358,9 +359,7 @@ __global__ void __launch_bounds__(256)
     float* __restrict__ vals = rs.vals;
     unsigned long long* __restrict__ pair_ids = rs.pair_ids;
     unsigned long long* __restrict__ best = rs.best;
-    __shared__ float tile[8][32][33];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float (*T)[33] = tile[wib];
     const unsigned count = min(*count_p, cap);
     const unsigned start = start_p ? min(*start_p, cap) : 0u;
     for (int64_t w = start + (int64_t)blockIdx.x * 8 + wib; w < count;
@@ -377,36 +376,40 @@ __global__ void __launch_bounds__(256)
         }
         const int64_t b = chunk * 32 + lane;
         const bool ok = b < nb && (!self || b > a);
-        const int64_t row = ok ? (int64_t)pts_b[b] * n_pad : -1;
+        // a lane without a pair reads a valid row and discards its value
+        const float4* yrow = reinterpret_cast<const float4*>(
+            plane_b + (int64_t)pts_b[ok ? b : 0] * n_pad);
         float s = 0.f, c = 0.f;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (r * 32 < n) {  // warp-uniform
-                // all 32 loads of the slice are issued before the tile is
-                // written, so they are in flight together
-                float v[32];
-                const int k = r * 32 + lane;
+        for (int r0 = 0; r0 < R; r0 += 2) {
+            if (r0 * 32 < n) {  // warp-uniform
+                // the float4s of slices r0 and r0 + 1 that hold members below n
+                float4 q[16];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t rj = __shfl_sync(0xffffffffu, row, j);
-                    v[j] = rj >= 0 && k < n ? __ldg(plane_b + rj + k) : 0.f;
+                for (int u = 0; u < 16; ++u) {
+                    const int m0 = r0 * 32 + 4 * u;
+                    q[u] = (r0 + u / 8 < R && m0 < n) ? __ldg(yrow + r0 * 8 + u)
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                __syncwarp();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) T[j][lane] = v[j];
-                __syncwarp();
-                const int kn = min(32, n - r * 32);
+                for (int u = 0; u < 16; ++u) {
+                    const int r = r0 + u / 8;
+                    if (r < R) {
+                        const float yq[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
-                for (int kk = 0; kk < 32; ++kk) {
-                    if (kk < kn) {
-                        const float xv = __shfl_sync(0xffffffffu, x[r], kk);
-                        const float yv = T[lane][kk];
-                        const float p = __fmul_rn(xv, yv);
-                        const float pe = fmaf(xv, yv, -p);  // TwoProduct error, exact
-                        float t, q;
-                        two_sum(s, p, t, q);
-                        s = t;
-                        c = __fadd_rn(c, __fadd_rn(q, pe));
+                        for (int e = 0; e < 4; ++e) {
+                            const int kk = 4 * (u % 8) + e;  // member r * 32 + kk
+                            if (r * 32 + kk < n) {
+                                const float xv = __shfl_sync(0xffffffffu, x[r], kk);
+                                const float yv = yq[e];
+                                const float p = __fmul_rn(xv, yv);
+                                const float pe = fmaf(xv, yv, -p);  // TwoProduct error, exact
+                                float t, qq;
+                                two_sum(s, p, t, qq);
+                                s = t;
+                                c = __fadd_rn(c, __fadd_rn(qq, pe));
+                            }
+                        }
                     }
                 }
             }
@@ -517,11 +520,14 @@ __global__ void k_second_threshold(SideState* ss, int nsides, const unsigned* em
 //                  that are larger (binary search; keys are unique), and
 //                  entries placed below topk are written out.
 constexpr int kTopChunk = 1024, kTopMax = 8192;
+// keys per thread of k_topk_chunks: 512 threads a chunk, so each SM
+// sub-partition holds four warps to hide the exchange latencies
+constexpr int kTopE = 2;
 
-template <int D>
-__device__ __forceinline__ void sort_regs(unsigned long long (&key)[8], int i0, int size) {
+template <int D, int E>
+__device__ __forceinline__ void sort_regs(unsigned long long (&key)[E], int i0, int size) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < E; ++e) {
         constexpr int dd = D;
         const int e2 = e ^ dd;
         if (e2 > e) {
@@ -534,12 +540,12 @@ __device__ __forceinline__ void sort_regs(unsigned long long (&key)[8], int i0, 
     }
 }
 
-__global__ void __launch_bounds__(kTopChunk / 8)
+__global__ void __launch_bounds__(kTopChunk / kTopE)
     k_topk_chunks(const float* __restrict__ vals, const unsigned long long* __restrict__ pids,
                   const uint32_t* __restrict__ sel_idx, const unsigned* __restrict__ count_p,
                   unsigned cap, unsigned long long* __restrict__ sorted) {
     __shared__ unsigned long long skey[kTopChunk];
-    constexpr int E = 8;
+    constexpr int E = kTopE;
     const int t = threadIdx.x, c0 = blockIdx.x * kTopChunk;
     const unsigned count = min(min(*count_p, cap), (unsigned)kTopMax);
     if ((unsigned)c0 >= count) return;  // block-uniform: an empty chunk is never read
@@ -557,7 +563,7 @@ __global__ void __launch_bounds__(kTopChunk / 8)
     }
     for (int size = 2; size <= kTopChunk; size <<= 1) {
         for (int d = size >> 1; d > 0; d >>= 1) {
-            if (d >= 256) {  // partner in another warp
+            if (d >= 32 * E) {  // partner in another warp
                 __syncthreads();
 #pragma unroll
                 for (int e = 0; e < E; ++e) skey[t * E + e] = key[e];
@@ -578,11 +584,11 @@ __global__ void __launch_bounds__(kTopChunk / 8)
                     key[e] = (keep_max ? o > key[e] : o < key[e]) ? o : key[e];
                 }
             } else if (d == 4) {
-                sort_regs<4>(key, t * E, size);
+                if constexpr (E > 4) sort_regs<4, E>(key, t * E, size);
             } else if (d == 2) {
-                sort_regs<2>(key, t * E, size);
+                if constexpr (E > 2) sort_regs<2, E>(key, t * E, size);
             } else {
-                sort_regs<1>(key, t * E, size);
+                sort_regs<1, E>(key, t * E, size);
             }
         }
     }
@@ -756,7 +762,7 @@ cudaError_t launch_sort_top(const float* vals, const unsigned long long* pids,
                             unsigned long long* scratch, cudaStream_t st) {
     if (topk < 0 || topk > kTopMax) return cudaErrorInvalidValue;
     note_launch(2);
-    k_topk_chunks<<<kTopMax / kTopChunk, kTopChunk / 8, 0, st>>>(vals, pids, sel_idx, count, cap,
+    k_topk_chunks<<<kTopMax / kTopChunk, kTopChunk / kTopE, 0, st>>>(vals, pids, sel_idx, count, cap,
                                                                  scratch);
     k_topk_rank<<<kTopMax / 256, 256, 0, st>>>(scratch, count, cap, sign, topk, out_vals,
                                                out_ids);
