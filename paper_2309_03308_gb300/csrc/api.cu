@@ -78,10 +78,9 @@ Region* get_region(cc_ctx* ctx, int32_t id) {
 }
 
 // Device status word: read, reset, map to cc_status.
-cc_status take_status(cc_ctx* ctx) {
-    int s = 0;
-    CK(cudaMemcpyAsync(&s, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+// the library status of a device status word already read back (clears the
+// device word when it holds an error)
+cc_status status_value(cc_ctx* ctx, int s) {
     if (s == DEV_OK) return CC_OK;
     CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), ctx->stream));
     switch (s) {
@@ -90,6 +89,13 @@ cc_status take_status(cc_ctx* ctx) {
         case DEV_TIMEOUT: return fail(ctx, CC_ERR_TIMEOUT, "device-side wait timed out");
     }
     return fail(ctx, CC_ERR_CUDA, "device status %d", s);
+}
+
+cc_status take_status(cc_ctx* ctx) {
+    int s = 0;
+    CK(cudaMemcpyAsync(&s, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return status_value(ctx, s);
 }
 
 // fixed-point tables (2^40 scale) of psi(m) and m ln m for m = 0..n
@@ -944,9 +950,14 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
     } while (0)
     auto enqueue = [&]() -> cudaError_t {
         EK(cudaMemsetAsync(hist, 0, 4 * 2 * 4096 + sizeof(SideState) * 2 + sizeof(Select), st));
+        // the tensor-core kernel builds the first-level selection histogram
+        // when its epilogue has slack (K of 8 or more 128-byte blocks: the
+        // contraction, not the epilogue, bounds it); with short K the epilogue
+        // is the bound and a separate pass is faster
+        const bool hist_fused = qa->kbytes / 128 >= 8;
         EK(launch_tc_chunk_extremes(fp8, fp8 || exact, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad,
                                     qa->kbytes, self, qa->inv.as<float>(), qb->inv.as<float>(), cmax,
-                                    cmin, ctx->status.as<int>(), st));
+                                    cmin, hist_fused ? hist : nullptr, ctx->status.as<int>(), st));
         // relative error of the approximate values beyond the quantization error:
         // FP32 accumulation (2^-12, conservative), or for exact integer ranks the
         // two fp32 scalings of the epilogue (2^-22 covers them)
@@ -956,8 +967,8 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
         // the second compaction appends the chunks in [r* - B, first threshold)
         // after the first pass's, unless the first pass took every chunk or
         // overflowed.
-        EK(launch_select_top2(cmax, cmin, N, (unsigned)std::max(topk, 256), 256u, hist, ss, cids,
-                              cap, st));
+        EK(launch_select_top2(cmax, cmin, N, (unsigned)std::max(topk, 256), 256u, hist,
+                              hist_fused, ss, cids, cap, st));
         EK(launch_refine_chunks2(plane_a, plane_b, fa.n_pad, fa.n, ra->pts.as<uint32_t>(), na,
                                  rb->pts.as<uint32_t>(), nb, self, na_pad, cids, cap, ss, true,
                                  rvals, rpids, fp8, st));
@@ -977,14 +988,28 @@ extern "C" cc_status cc_all_pairs_topk(cc_ctx* ctx, int32_t region_a, int32_t re
     };
 #undef EK
     CK(run_cached_graph(ctx, ctx->topk_graphs, key, enqueue));
+    // the side records and the top list land in pinned memory (asynchronous
+    // copies, one wait) and are copied out on the host
     SideState hout[2];
-    CK(cudaMemcpyAsync(hout, ss, sizeof hout, cudaMemcpyDeviceToHost, st));
+    const size_t o_hv = 256, o_hi = o_hv + 4 * (size_t)topk;
+    CK(ctx->host_out.ensure(o_hi + 8 * (size_t)topk));
+    unsigned char* hb = ctx->host_out.as<unsigned char>();
+    static_assert(sizeof(SideState) * 2 + sizeof(int) <= 256, "landing area");
+    CK(cudaMemcpyAsync(hb, ss, sizeof hout, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hb + sizeof hout, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (topk > 0) {
-        CK(cudaMemcpyAsync(vals, tvals, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(ids, tids, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hb + o_hv, tvals, 4 * (size_t)topk, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hb + o_hi, tids, 8 * (size_t)topk, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
-    if ((s = take_status(ctx))) return s;
+    memcpy(hout, hb, sizeof hout);
+    int dev_status = 0;
+    memcpy(&dev_status, hb + sizeof hout, sizeof(int));
+    if (topk > 0) {
+        memcpy(vals, hb + o_hv, 4 * (size_t)topk);
+        memcpy(ids, hb + o_hi, 8 * (size_t)topk);
+    }
+    if ((s = status_value(ctx, dev_status))) return s;
     cc_mixed_info inf{};
     float ext_val[2] = {-INFINITY, -INFINITY};
     uint64_t ext_id[2] = {~0ull, ~0ull};
@@ -1042,7 +1067,7 @@ extern "C" cc_status cc_all_pairs_approx(cc_ctx* ctx, int32_t region_a, int32_t 
     const bool exact = rank_exact(sp, fp8, fa.n);
     CK(launch_tc_chunk_extremes(fp8, fp8 || exact, qa->q.p, na, na_pad, qb->q.p, nb, nb_pad,
                                 qa->kbytes, self, qa->inv.as<float>(), qb->inv.as<float>(), dmax,
-                                dmin, ctx->status.as<int>(), st));
+                                dmin, nullptr, ctx->status.as<int>(), st));
     CK(cudaMemcpyAsync(demax, qa->emax.p, 4, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(demax + 1, qb->emax.p, 4, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpy2DAsync(cmax, sizeof(float) * na, dmax, sizeof(float) * na_pad,

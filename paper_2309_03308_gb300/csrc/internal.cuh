@@ -48,6 +48,33 @@ struct DevMem {
     }
 };
 
+// Pinned host memory, grow-only (device-to-host copies of small results
+// land here asynchronously and are copied out after one stream wait).
+struct HostMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    HostMem() = default;
+    HostMem(const HostMem&) = delete;
+    HostMem& operator=(const HostMem&) = delete;
+    ~HostMem() {
+        if (p) cudaFreeHost(p);
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMallocHost(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        else p = nullptr;
+        return e;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
 // Per-point planes of one field, point-major [P][n_pad].
 struct Field {
     int X = 0, Y = 0, Z = 0, n = 0, n_pad = 0;
@@ -109,6 +136,7 @@ struct cc_ctx {
     // scratch
     cc::DevMem pair_a, pair_b, vals_out, partials, rp_out, ksg_nx, ksg_ny, ksg_eps, mixed;
     cc::DevMem approx;  // chunk extremes exported by cc_all_pairs_approx
+    cc::HostMem host_out;  // pinned landing area of cc_all_pairs_topk's results
     std::map<int, std::unique_ptr<cc::DevMem>> psi_fix;   // n -> int64 [n+1]
     std::map<int, std::unique_ptr<cc::DevMem>> clogc_fix; // n -> int64 [n+1]
     // host-to-device copies of an update overlap its ingest: a second stream
@@ -233,7 +261,8 @@ cudaError_t launch_sur_screen_tc(const float* Ea, const float* Ua, const float* 
 cudaError_t launch_tc_chunk_extremes(bool fp8, bool scaled, const void* qa, int64_t na,
                                      int64_t na_pad, const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
                                      int self, const float* inv_sa, const float* inv_sb,
-                                     float* cmax, float* cmin, int* status, cudaStream_t st);
+                                     float* cmax, float* cmin, unsigned* hist0, int* status,
+                                     cudaStream_t st);
 cudaError_t launch_quantize(bool fp8, const float* plane, int n_pad, int n, const uint32_t* pts,
                             int64_t np, int64_t np_pad, int kbytes, void* q, float* inv_scale,
                             unsigned* emax_bits, cudaStream_t st);
@@ -245,10 +274,11 @@ cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned wa
                               cudaStream_t st, const unsigned* nchunks = nullptr);
 // Both extreme sides at once: keys of +v0 (side 0) and -v1 (side 1); side s
 // selects at least want_s chunk ids into out + s * cap using ss[s].sel; hist
-// holds 2 x 4096 zeroed bins.
+// holds 2 x 4096 bins, zeroed, or with hist0_built the first-level (11-bit)
+// histograms that launch_tc_chunk_extremes added.
 cudaError_t launch_select_top2(const float* v0, const float* v1, int64_t N, unsigned want0,
-                               unsigned want1, unsigned* hist, SideState* ss, uint32_t* out,
-                               unsigned cap, cudaStream_t st);
+                               unsigned want1, unsigned* hist, bool hist0_built, SideState* ss,
+                               uint32_t* out, unsigned cap, cudaStream_t st);
 // second compaction of both sides (keys in [thr_s, first threshold))
 cudaError_t launch_compact_second2(const float* v0, const float* v1, int64_t N, SideState* ss,
                                    uint32_t* out, unsigned cap, cudaStream_t st);

@@ -123,9 +123,11 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // 3a. two-pass histogram select on order-preserving keys of sign * value,
 // for NS = 1 or 2 value arrays at once (the maximum and the minimum side of a
-// region pair share every pass). Pass `level` 0 bins the top 12 bits, pass 1
-// the next 12 among keys whose top 12 bits equal sel->prefix. Values of -inf
-// (empty chunks) are skipped. N is a multiple of 4 (read as float4).
+// region pair share every pass). Pass `level` 0 bins the top 32 - shift bits
+// (shift 20: 12 bits; 21: 11 bits, the histogram the tensor-core kernel
+// builds), pass 1 the next 12 among keys whose top bits equal sel->prefix.
+// Values of -inf (empty chunks) are skipped. N is a multiple of 4 (read as
+// float4).
 struct SideVals {
     const float* v[2];
     float sign[2];
@@ -135,7 +137,7 @@ struct SideVals {
 
 template <int NS>
 __global__ void __launch_bounds__(256)
-    k_hist12(SideVals sv, int64_t N, int level, unsigned* __restrict__ hist,
+    k_hist12(SideVals sv, int64_t N, int level, int shift, unsigned* __restrict__ hist,
              const unsigned* __restrict__ nchunks) {
     __shared__ unsigned h[NS][4096];
     if (nchunks) N = min(N, (int64_t)*nchunks * 32);
@@ -156,8 +158,8 @@ __global__ void __launch_bounds__(256)
                 const float x = sv.sign[s] * w[j];
                 if (!(x > -CUDART_INF_F)) continue;
                 const unsigned k = okey(x);
-                if (level == 0) atomicAdd(&h[s][k >> 20], 1u);
-                else if ((k >> 20) == prefix[s]) atomicAdd(&h[s][(k >> 8) & 0xfffu], 1u);
+                if (level == 0) atomicAdd(&h[s][k >> shift], 1u);
+                else if ((k >> shift) == prefix[s]) atomicAdd(&h[s][(k >> (shift - 12)) & 0xfffu], 1u);
             }
         }
     }
@@ -169,8 +171,8 @@ __global__ void __launch_bounds__(256)
             const float x = sv.sign[s] * sv.v[s][i];
             if (!(x > -CUDART_INF_F)) continue;
             const unsigned k = okey(x);
-            if (level == 0) atomicAdd(&h[s][k >> 20], 1u);
-            else if ((k >> 20) == prefix[s]) atomicAdd(&h[s][(k >> 8) & 0xfffu], 1u);
+            if (level == 0) atomicAdd(&h[s][k >> shift], 1u);
+            else if ((k >> shift) == prefix[s]) atomicAdd(&h[s][(k >> (shift - 12)) & 0xfffu], 1u);
         }
     }
     __syncthreads();
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(256)
 
 // One block per side: scan the side's 4096 bins from the top until `want`
 // keys are covered.
-__global__ void k_pick_bin(unsigned* __restrict__ hist_all, int level, unsigned want0,
+__global__ void k_pick_bin(unsigned* __restrict__ hist_all, int level, int shift, unsigned want0,
                            unsigned want1, SideVals sv) {
     __shared__ unsigned part[1024];
     unsigned* hist = hist_all + 4096 * blockIdx.x;
@@ -216,7 +218,7 @@ __global__ void k_pick_bin(unsigned* __restrict__ hist_all, int level, unsigned 
             sel->prefix = (unsigned)bin;
             sel->need = target - acc;
         } else {
-            sel->threshold = (sel->prefix << 20) | ((unsigned)bin << 8);
+            sel->threshold = (sel->prefix << shift) | ((unsigned)bin << (shift - 12));
         }
         if (part[t] < target) sel->threshold = 0u;  // fewer keys than wanted: take all
     }
@@ -671,10 +673,10 @@ cudaError_t launch_select_top(const float* v, int64_t N, float sign, unsigned wa
     sv.sign[0] = sv.sign[1] = sign;
     sv.sel[0] = sv.sel[1] = sel;
     note_launch(5);
-    k_hist12<1><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 0, hist, nchunks);
-    k_pick_bin<<<1, 1024, 0, st>>>(hist, 0, want, want, sv);
-    k_hist12<1><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 1, hist, nchunks);
-    k_pick_bin<<<1, 1024, 0, st>>>(hist, 1, want, want, sv);
+    k_hist12<1><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 0, 20, hist, nchunks);
+    k_pick_bin<<<1, 1024, 0, st>>>(hist, 0, 20, want, want, sv);
+    k_hist12<1><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 1, 20, hist, nchunks);
+    k_pick_bin<<<1, 1024, 0, st>>>(hist, 1, 20, want, want, sv);
     k_compact<1><<<grid_for(N, 256 * 8), 256, 0, st>>>(sv, N, out, cap, nchunks);
     return cudaGetLastError();
 }
@@ -691,15 +693,19 @@ static SideVals two_sides(const float* v0, const float* v1, SideState* ss) {
 }
 
 cudaError_t launch_select_top2(const float* v0, const float* v1, int64_t N, unsigned want0,
-                               unsigned want1, unsigned* hist, SideState* ss, uint32_t* out,
-                               unsigned cap, cudaStream_t st) {
+                               unsigned want1, unsigned* hist, bool hist0_built, SideState* ss,
+                               uint32_t* out, unsigned cap, cudaStream_t st) {
     if (N % 4) return cudaErrorInvalidValue;
     const SideVals sv = two_sides(v0, v1, ss);
-    note_launch(5);
-    k_hist12<2><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 0, hist, nullptr);
-    k_pick_bin<<<2, 1024, 0, st>>>(hist, 0, want0, want1, sv);
-    k_hist12<2><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 1, hist, nullptr);
-    k_pick_bin<<<2, 1024, 0, st>>>(hist, 1, want0, want1, sv);
+    // the first-level histogram: built by the tensor-core kernel (11 bits), or
+    // here (12 bits)
+    const int shift = hist0_built ? 21 : 20;
+    note_launch(hist0_built ? 4 : 5);
+    if (!hist0_built)
+        k_hist12<2><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 0, shift, hist, nullptr);
+    k_pick_bin<<<2, 1024, 0, st>>>(hist, 0, shift, want0, want1, sv);
+    k_hist12<2><<<grid_for(N, 256 * 16), 256, 0, st>>>(sv, N, 1, shift, hist, nullptr);
+    k_pick_bin<<<2, 1024, 0, st>>>(hist, 1, shift, want0, want1, sv);
     k_compact<2><<<grid_for(N, 256 * 8), 256, 0, st>>>(sv, N, out, cap, nullptr);
     return cudaGetLastError();
 }

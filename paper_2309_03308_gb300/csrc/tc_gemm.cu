@@ -35,6 +35,15 @@ constexpr int A_BYTES = TM * 128, B_BYTES = TN * 128, STAGE_BYTES = A_BYTES + B_
 constexpr int THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
 constexpr int EPI = 256;      // epilogue threads
 constexpr int TMEM_COLS = 512;  // two 256-column fp32 accumulators
+// first-level histogram of the candidate selection: the top 11 bits of the
+// order-preserving key (the selection's second level resolves 12 more)
+constexpr int HIST_SHIFT = 21, HIST_BINS = 1 << (32 - HIST_SHIFT);
+
+// order-preserving unsigned key of a float (-0 and +0 map to one key)
+__device__ __forceinline__ unsigned order_key(float v) {
+    const unsigned b = __float_as_uint(v + 0.0f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
 
 // Instruction descriptor: FP32 accumulator, A/B BF16 (kind::f16) or E4M3
 // (kind::f8f6f4), both K-major, N = 256, M = 128.
@@ -65,7 +74,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         int64_t nb, int tiles_m, int tiles_n, int self,
                         const float* __restrict__ inv_sa, const float* __restrict__ inv_sb,
                         float* __restrict__ cmax, float* __restrict__ cmin, int64_t na_pad,
-                        int* status) {
+                        unsigned* __restrict__ hist0, int* status) {
     extern __shared__ unsigned char tc_smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -77,8 +86,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* colscale = reinterpret_cast<float*>(tmem_slot + 4);
+    // first-level selection histograms of the two extreme sides (HIST_BINS
+    // bins each, keys order_key(max) and order_key(-min)), flushed to hist0 at
+    // the end
+    unsigned* hsh = reinterpret_cast<unsigned*>(colscale + 2 * TN);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (hist0)
+        for (int i = threadIdx.x; i < 2 * HIST_BINS; i += THREADS) hsh[i] = 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -252,6 +267,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (mx > -CUDART_INF_F) mx = mx * rs;
                         if (mn < CUDART_INF_F) mn = mn * rs;
                     }
+                    if (hist0) {  // lanes with the same bin add once
+                        const unsigned b0 =
+                            mx > -CUDART_INF_F ? order_key(mx) >> HIST_SHIFT : 0xffffffffu;
+                        const unsigned b1 =
+                            mn < CUDART_INF_F ? order_key(-mn) >> HIST_SHIFT : 0xffffffffu;
+                        const unsigned g0 = __match_any_sync(0xffffffffu, b0);
+                        if (b0 != 0xffffffffu && lane == __ffs(g0) - 1)
+                            atomicAdd(&hsh[b0], (unsigned)__popc(g0));
+                        const unsigned g1 = __match_any_sync(0xffffffffu, b1);
+                        if (b1 != 0xffffffffu && lane == __ffs(g1) - 1)
+                            atomicAdd(&hsh[HIST_BINS + b1], (unsigned)__popc(g1));
+                    }
                     const int64_t chunk = (n0 >> 5) + c;
                     if (row < na_pad) {
                         cmax[chunk * na_pad + row] = mx;
@@ -277,9 +304,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS));
     }
+    if (hist0)  // side s's bins at hist0 + 4096 s
+        for (int i = threadIdx.x; i < 2 * HIST_BINS; i += THREADS)
+            if (hsh[i]) atomicAdd(&hist0[(i / HIST_BINS) * 4096 + i % HIST_BINS], hsh[i]);
 }
 
-constexpr size_t smem_bytes() { return 1024 + STAGES * STAGE_BYTES + 256 + 16 + 2 * TN * 4; }
+constexpr size_t smem_bytes() {
+    return 1024 + STAGES * STAGE_BYTES + 256 + 16 + 2 * TN * 4 + 2 * HIST_BINS * 4;
+}
 
 }  // namespace tc
 
@@ -313,17 +345,22 @@ static cudaError_t make_map(CUtensorMap* m, const void* base, bool fp8, int64_t 
 }
 
 // qa: [na_pad][kbytes] operand A (rows padded to 256), qb likewise; kbytes a
-// multiple of 128. Writes cmax/cmin [nb_pad/32][na_pad].
+// multiple of 128. Writes cmax/cmin [nb_pad/32][na_pad]; with hist0, also
+// adds the first-level selection histograms of both sides (bins of the top 11
+// key bits; side s at hist0 + 4096 s, which the caller zeroes).
 cudaError_t launch_tc_chunk_extremes(bool fp8, bool scaled, const void* qa, int64_t na, int64_t na_pad,
                                      const void* qb, int64_t nb, int64_t nb_pad, int64_t kbytes,
                                      int self, const float* inv_sa, const float* inv_sb,
-                                     float* cmax, float* cmin, int* status, cudaStream_t st) {
+                                     float* cmax, float* cmin, unsigned* hist0, int* status,
+                                     cudaStream_t st) {
     if (kbytes % 128 || na_pad % 256 || nb_pad % 256) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     cudaError_t e = make_map(&ma, qa, fp8, na_pad, kbytes, tc::TM);
     if (e == cudaSuccess) e = make_map(&mb, qb, fp8, nb_pad, kbytes, tc::TN);
     if (e != cudaSuccess) return e;
-    const int tiles_m = (int)((na + tc::TM - 1) / tc::TM);
+    // every padded row is covered (rows past na hold -inf / +inf), so the
+    // selection passes never read an extreme this call did not write
+    const int tiles_m = (int)(na_pad / tc::TM);
     const int tiles_n = (int)((nb + tc::TN - 1) / tc::TN);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -339,7 +376,8 @@ cudaError_t launch_tc_chunk_extremes(bool fp8, bool scaled, const void* qa, int6
     if (e != cudaSuccess) return e;
     note_launch();
     kern<<<grid, tc::THREADS, smem, st>>>(ma, mb, (int)(kbytes / 128), na, nb, tiles_m, tiles_n,
-                                          self, inv_sa, inv_sb, cmax, cmin, na_pad, status);
+                                          self, inv_sa, inv_sb, cmax, cmin, na_pad, hist0,
+                                          status);
     return cudaGetLastError();
 }
 
