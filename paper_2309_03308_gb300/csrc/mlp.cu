@@ -335,23 +335,32 @@ __global__ void k_sur_head_input(const float* __restrict__ Ef, const float* __re
 }
 
 // y = w4 . h3 + b4; loss terms and dy = 2 (y - t) / B (one warp per row)
+// with t, also the head's GELU backward dA3[b][h] = (dy[b] w4[h]) gelu'(A3[b][h])
 __global__ void k_sur_out(const __nv_bfloat16* __restrict__ H3, const float* __restrict__ w4,
                           const float* __restrict__ b4, const float* __restrict__ t, int64_t B,
                           float tmean, float tinv, float* __restrict__ y, float* __restrict__ dy,
-                          double* __restrict__ loss) {
+                          double* __restrict__ loss, const float* __restrict__ A3,
+                          float* __restrict__ dA3) {
     const int lane = threadIdx.x & 31;
     for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B;
          b += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         float s = 0.f;
         for (int h = lane; h < kH3; h += 32) s = fmaf(__bfloat162float(H3[b * kH3 + h]), w4[h], s);
         s = warp_sum_f32(s) + b4[0];
+        float d = 0.f;
         if (lane == 0) {
             y[b] = s;
             if (t) {
                 const float r = s - (t[b] - tmean) * tinv;
-                dy[b] = 2.f * r / (float)B;
+                d = 2.f * r / (float)B;
+                dy[b] = d;
                 atomicAdd(loss, (double)r * r);
             }
+        }
+        if (t) {
+            d = __shfl_sync(0xffffffffu, d, 0);
+            for (int h = lane; h < kH3; h += 32)
+                dA3[b * kH3 + h] = (d * w4[h]) * gelu_grad(A3[b * kH3 + h]);
         }
     }
 }
@@ -608,9 +617,11 @@ cc_status forward(cc_ctx* ctx, cc_sur* s, const Field& f, int64_t B, const float
     k_sur_bias_gelu<<<grid1(B * kH3), 256, 0, st>>>(s->A3.as<float>(), w + o.b3, B, kH3,
                                                     s->H3.as<bf16>());
     if (t) SK(cudaMemsetAsync(s->loss.p, 0, 8, st));
+    // with targets, also the head's GELU backward dA3 = (dy w4) gelu'(A3)
     k_sur_out<<<grid1(B * 32), 256, 0, st>>>(s->H3.as<bf16>(), w + o.w4, w + o.b4, t, B, s->tmean,
                                              1.f / s->tsd, s->y.as<float>(), s->dy.as<float>(),
-                                             s->loss.as<double>());
+                                             s->loss.as<double>(), s->A3.as<float>(),
+                                             s->dA3.as<float>());
     SK(cudaGetLastError());
     return CC_OK;
 }
@@ -626,16 +637,13 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
     {
         const int64_t nb = (B + 63) / 64;
         SK(s->ws.ensure(sizeof(float) * (size_t)nb * (kH3 + 1)));
-        note_launch(3);  // with the head's GELU backward
+        note_launch(2);
         k_sur_w4_grad<<<(unsigned)nb, kH3 + 32, 0, st>>>(s->H3.as<bf16>(), s->dy.as<float>(), B,
                                                          s->ws.as<float>());
         k_mm_reduce<<<reduce_blocks(kH3 + 1), 256, 0, st>>>(s->ws.as<float>(), (int)nb, 1,
                                                              kH3 + 1, g + o.w4, kH3 + 1, 0,
                                                              nullptr);
     }
-    k_sur_gelu_bwd<<<grid1(B * kH3), 256, 0, st>>>(s->A3.as<float>(), s->dy.as<float>(),
-                                                   s->w.as<float>() + o.w4, nullptr, B, kH3,
-                                                   s->dA3.as<float>());
     SK(tmm(ctx->status.as<int>(), s->dA3.as<float>(), 1, kH3, s->X3.as<bf16>(), kHeadInP, 1,
            g + o.W3, kHeadIn, kH3, kHeadIn, (int)B, st, &s->ws, g + o.b3));
     SK(tmm(ctx->status.as<int>(), s->dA3.as<float>(), kH3, 1, w3p(s), kHeadInP, 1,
