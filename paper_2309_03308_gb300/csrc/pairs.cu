@@ -116,7 +116,10 @@ __device__ __forceinline__ long long hist_slices(const uint32_t* __restrict__ ba
 // reads four members' bins as one 32-bit word per side; the sample whose
 // atomic increment found its cell empty owns the cell and, once the counts
 // are complete, adds that cell's c ln c and clears it, so every occupied cell
-// is summed once and no sweep over the B^2 cells is needed.
+// is summed once and no sweep over the B^2 cells is needed. A warp keeps the
+// fixed-point sums of 32 consecutive pairs of its own, one per lane, and
+// converts them to MI together: the FP64 steps (GB300's FP64 pipe is narrow)
+// then run once per 32 pairs instead of once per pair on one lane.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_hist_pairs(const uint8_t* __restrict__ bins_a, const long long* __restrict__ hm_a,
                  int64_t Pa, const uint8_t* __restrict__ bins_b,
@@ -133,6 +136,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     __syncthreads();
     const int64_t w0 = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
+    long long dk = 0;   // this lane's pending pair: fixed-point sum difference
+    int64_t tk = -1;    // and its index
+    int slot = 0;       // lane that takes the next pair
+    auto flush = [&]() {
+        if (tk >= 0) out[tk] = (float)(logn + (double)dk * fix_over_n);
+        tk = -1;
+        slot = 0;
+    };
     for (int64_t t = w0; t < N; t += stride) {
         const uint32_t p = pa[t], q = pb[t];
         if (p >= Pa || q >= Pb) {
@@ -172,11 +183,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             s = hist_slices(ba, bb, n, B, h, clogc, lane);
         }
         s = warp_sum_u64_redux(s);  // c ln c >= 0: the fixed-point sums are non-negative
-        if (lane == 0) {
-            const long long d = s - hm_a[p] - hm_b[q];
-            out[t] = (float)(logn + (double)d * fix_over_n);
+        if (lane == slot) {
+            dk = s - hm_a[p] - hm_b[q];
+            tk = t;
         }
+        if (++slot == 32) flush();
     }
+    flush();
 }
 
 cudaError_t launch_hist_pairs(const uint8_t* bins_a, const int64_t* hm_a, int64_t Pa,
