@@ -250,3 +250,26 @@ def test_focus_full_size_bf16_certified_against_oracle(cc, orc):
     listed = set((ia * len(B) + ib).tolist())
     assert all(int(x) in listed for x in (sa[above] * len(B) + sb[above]))
     cc.free_field(fid)
+
+
+def test_partial_row_tile_after_larger_call(cc, orc):
+    """A region of 100 points pads to 256 rows, two row tiles of 128 of which
+    only the first holds real points. Every padded row's chunk extremes must be
+    written by the call itself: here an earlier call on 256 points that
+    include the column region (so its extremes reach 1) used the same scratch
+    layout just before, and a stale row left in place would take candidate
+    slots from the real chunks. The second call's extremes, certificate and
+    top list are checked against the FP64 oracle."""
+    from paper_2309_03308_gb300 import CC_BF16, CC_PEARSON, Params
+    F = gen.field(2, 352, 256, 20, 100, box=(64, 64, 0, 96, 96, 20))  # 32 x 32 x 20 points
+    fid = cc.load_field(F)
+    rb, rbig, rsmall = cc.define_regions(
+        fid, [(0, 0, 0, 32, 32, 20), (0, 0, 0, 16, 16, 1), (20, 20, 10, 30, 30, 11)])
+    prm = Params(CC_PEARSON, precision=CC_BF16)
+    res0, _, _, cert0 = cc.all_pairs_topk(rbig, rb, prm, topk=4096)
+    assert res0["max"] > 0.999 and cert0["certified_max"] == 1  # a point paired with itself
+    res, ids, vals, cert = cc.all_pairs_topk(rsmall, rb, prm, topk=4096)
+    full = all_values(orc, oracle.PEARSON, np.ascontiguousarray(F[:, 10:11, 20:30, 20:30]), F)
+    check(res, ids, vals, cert, full, 100 * 20480, 4096)
+    assert np.all(ids < full.size)  # every listed pair has a real row
+    cc.free_field(fid)
