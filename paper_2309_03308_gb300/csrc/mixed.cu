@@ -36,56 +36,65 @@ __device__ __forceinline__ float okey_inv(unsigned o) {
 }
 
 // ---------------------------------------------------------------------------
-// 1. quantization: one warp per region point.
+// 1. quantization: one warp per region point. The error norms' maximum goes
+// to emax_bits with one atomic per block (8 warps), not per warp: 20,480
+// atomics on one address serialised and took most of the launch.
 template <bool FP8>
 __global__ void __launch_bounds__(256)
     k_quantize(const float* __restrict__ plane, int n_pad, int n, const uint32_t* __restrict__ pts,
                int64_t np, int64_t np_pad, int kbytes, unsigned char* __restrict__ q,
                float* __restrict__ inv_scale, unsigned* __restrict__ emax_bits) {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (r >= np_pad) return;
+    __shared__ unsigned block_max[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 8 + warp;
     const int kelems = FP8 ? kbytes : kbytes / 2;
     unsigned char* qrow = q + r * kbytes;
-    if (r >= np) {
+    unsigned my_max = 0u;  // bits of this warp's error norm (non-negative floats order as bits)
+    if (r < np_pad && r >= np) {  // warp-uniform: a padding row
         for (int b = lane * 4; b < kbytes; b += 128) *reinterpret_cast<uint32_t*>(qrow + b) = 0;
         if (FP8 && lane == 0) inv_scale[r] = 0.f;
-        return;
-    }
-    const float* z = plane + (int64_t)pts[r] * n_pad;
-    float amax = 0.f;
-    if (FP8) {
-        for (int k = lane; k < n; k += 32) amax = fmaxf(amax, fabsf(z[k]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    }
-    const float s = FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f;
-    float err = 0.f;
-    for (int k = lane * 2; k < kelems; k += 64) {
-        const float z0 = k < n ? z[k] : 0.f, z1 = k + 1 < n ? z[k + 1] : 0.f;
-        float d0, d1;
+    } else if (r < np) {  // warp-uniform
+        const float* z = plane + (int64_t)pts[r] * n_pad;
+        float amax = 0.f;
         if (FP8) {
-            const __nv_fp8x2_storage_t v =
-                __nv_cvt_float2_to_fp8x2(make_float2(z0 * s, z1 * s), __NV_SATFINITE, __NV_E4M3);
-            *reinterpret_cast<__nv_fp8x2_storage_t*>(qrow + k) = v;
-            const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(v, __NV_E4M3);
-            const float2 back = __half22float2(*reinterpret_cast<const __half2*>(&hr));
-            d0 = back.x / s - z0;
-            d1 = back.y / s - z1;
-        } else {
-            const __nv_bfloat162 v = __floats2bfloat162_rn(z0, z1);
-            *reinterpret_cast<__nv_bfloat162*>(qrow + 2 * k) = v;
-            const float2 back = __bfloat1622float2(v);
-            d0 = back.x - z0;
-            d1 = back.y - z1;
+            for (int k = lane; k < n; k += 32) amax = fmaxf(amax, fabsf(z[k]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         }
-        err = fmaf(d0, d0, fmaf(d1, d1, err));
-    }
-    err = warp_sum_f32(err);
-    if (lane == 0) {
-        if (FP8) inv_scale[r] = 1.f / s;
+        const float s = FP8 ? (amax > 0.f ? 448.f / amax : 1.f) : 1.f;
+        float err = 0.f;
+        for (int k = lane * 2; k < kelems; k += 64) {
+            const float z0 = k < n ? z[k] : 0.f, z1 = k + 1 < n ? z[k + 1] : 0.f;
+            float d0, d1;
+            if (FP8) {
+                const __nv_fp8x2_storage_t v = __nv_cvt_float2_to_fp8x2(
+                    make_float2(z0 * s, z1 * s), __NV_SATFINITE, __NV_E4M3);
+                *reinterpret_cast<__nv_fp8x2_storage_t*>(qrow + k) = v;
+                const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(v, __NV_E4M3);
+                const float2 back = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+                d0 = back.x / s - z0;
+                d1 = back.y / s - z1;
+            } else {
+                const __nv_bfloat162 v = __floats2bfloat162_rn(z0, z1);
+                *reinterpret_cast<__nv_bfloat162*>(qrow + 2 * k) = v;
+                const float2 back = __bfloat1622float2(v);
+                d0 = back.x - z0;
+                d1 = back.y - z1;
+            }
+            err = fmaf(d0, d0, fmaf(d1, d1, err));
+        }
+        err = warp_sum_f32(err);
+        if (FP8 && lane == 0) inv_scale[r] = 1.f / s;
         // small relative margin for the fp32 accumulation of the error norm
-        atomicMax(emax_bits, __float_as_uint(sqrtf(err) * 1.001f));
+        my_max = __float_as_uint(sqrtf(err) * 1.001f);
+    }
+    if (lane == 0) block_max[warp] = my_max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned m = 0u;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, block_max[w]);
+        if (m) atomicMax(emax_bits, m);
     }
 }
 
@@ -368,7 +377,11 @@ __global__ void __launch_bounds__(256)
          w += (int64_t)gridDim.x * 8) {
         const uint32_t id = ids[w];
         const int64_t chunk = id / na_pad, a = id % na_pad;
-        if (a >= na) continue;  // warp-uniform
+        if (a >= na) {  // warp-uniform: a padded row holds no pair (its slots say so)
+            vals[w * 32 + lane] = -CUDART_INF_F;
+            pair_ids[w * 32 + lane] = ~0ull;
+            continue;
+        }
         float x[R];
         const float* xa = plane_a + (int64_t)pts_a[a] * n_pad;
 #pragma unroll
@@ -460,7 +473,11 @@ __global__ void __launch_bounds__(256)
          w += (int64_t)gridDim.x * 8) {
         const uint32_t id = ids[w];
         const int64_t chunk = id / na_pad, a = id % na_pad;
-        if (a >= na) continue;  // warp-uniform
+        if (a >= na) {  // warp-uniform: a padded row holds no pair (its slots say so)
+            vals[w * 32 + lane] = -CUDART_INF_F;
+            pair_ids[w * 32 + lane] = ~0ull;
+            continue;
+        }
         float x[R];
         const float* xa = plane_a + (int64_t)pts_a[a] * n_pad;
 #pragma unroll
