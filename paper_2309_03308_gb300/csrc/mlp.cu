@@ -334,14 +334,16 @@ __global__ void k_sur_head_input(const float* __restrict__ Ef, const float* __re
     }
 }
 
-// y = w4 . h3 + b4; loss terms and dy = 2 (y - t) / B (one warp per row)
+// y = w4 . h3 + b4; loss terms and dy = 2 (y - t) / B (one warp per row, 256 threads)
 // with t, also the head's GELU backward dA3[b][h] = (dy[b] w4[h]) gelu'(A3[b][h])
 __global__ void k_sur_out(const __nv_bfloat16* __restrict__ H3, const float* __restrict__ w4,
                           const float* __restrict__ b4, const float* __restrict__ t, int64_t B,
                           float tmean, float tinv, float* __restrict__ y, float* __restrict__ dy,
                           double* __restrict__ loss, const float* __restrict__ A3,
                           float* __restrict__ dA3) {
+    __shared__ double block_loss[8];  // 256 threads
     const int lane = threadIdx.x & 31;
+    double wloss = 0.0;  // this warp's rows' squared residuals (lane 0)
     for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B;
          b += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         float s = 0.f;
@@ -354,13 +356,22 @@ __global__ void k_sur_out(const __nv_bfloat16* __restrict__ H3, const float* __r
                 const float r = s - (t[b] - tmean) * tinv;
                 d = 2.f * r / (float)B;
                 dy[b] = d;
-                atomicAdd(loss, (double)r * r);
+                wloss += (double)r * r;
             }
         }
         if (t) {
             d = __shfl_sync(0xffffffffu, d, 0);
             for (int h = lane; h < kH3; h += 32)
                 dA3[b * kH3 + h] = (d * w4[h]) * gelu_grad(A3[b * kH3 + h]);
+        }
+    }
+    if (t) {  // one atomic per block on the loss (one address for every row)
+        if (lane == 0) block_loss[threadIdx.x >> 5] = wloss;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double l = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) l += block_loss[w];
+            atomicAdd(loss, l);
         }
     }
 }
