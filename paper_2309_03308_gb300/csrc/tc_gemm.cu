@@ -12,7 +12,9 @@
 // max and min of the approximate correlations (FP8, and BF16 integer ranks:
 // rescaled by the two per-point inverse scales). No per-pair value is stored:
 // the chunk extremes select the candidates that are re-evaluated exactly
-// afterwards.
+// afterwards. Optionally the epilogue also counts both sides' extremes into
+// the selection's first-level histogram (top 11 bits of their order-preserving
+// keys, in shared memory, added to global memory once per CTA).
 //
 // Warp roles (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0  TMA producer        warp 1  TMEM allocation + MMA issuer
