@@ -176,6 +176,45 @@ __global__ void __launch_bounds__(256)
 }
 inline unsigned reduce_blocks(int64_t MN) { return (unsigned)((MN + kReduceOuts - 1) / kReduceOuts); }
 
+// Up to four k_mm_reduce problems in one launch (a training step's weight
+// gradients, each from its own partials): block b belongs to the segment
+// whose range of reduce_blocks holds b, and reduces its 32 outputs in the
+// same order as k_mm_reduce (accumulate = 0).
+struct ReduceSeg {
+    const float* part = nullptr;
+    int S = 0, M = 0, N = 0;
+    float* C = nullptr;
+    int64_t ldc = 0;
+    float* bias = nullptr;
+    unsigned blocks = 0;  // reduce_blocks(M N); 0: nothing to reduce
+};
+struct ReduceSegs {
+    ReduceSeg s[4];
+};
+__global__ void __launch_bounds__(256) k_mm_reduce_multi(ReduceSegs segs) {
+    __shared__ float red[8][kReduceOuts + 1];
+    unsigned blk = blockIdx.x;
+    int q = 0;
+    while (q < 3 && blk >= segs.s[q].blocks) blk -= segs.s[q++].blocks;  // block-uniform
+    const ReduceSeg g = segs.s[q];
+    const int64_t MN = (int64_t)g.M * g.N;
+    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blk * kReduceOuts + lane;
+    float a = 0.f;
+    if (e < MN)
+        for (int z = j; z < g.S; z += 8) a += g.part[(int64_t)z * MN + e];
+    red[j][lane] = a;
+    __syncthreads();
+    if (j == 0 && e < MN) {
+        const float sum = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                          ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+        const int64_t m = e / g.N;
+        const int n = (int)(e % g.N);
+        if (g.bias && n == g.N - 1) g.bias[m] = sum;
+        else g.C[m * g.ldc + n] = sum;
+    }
+}
+
 template <class TA, class TB>
 static cudaError_t mm(const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk, int64_t sbn,
                       float* C, int64_t ldc, int M, int N, int K, int acc, cudaStream_t st,
@@ -214,9 +253,13 @@ __global__ void k_sur_colsum(const float* __restrict__ A, int64_t rows, int cols
 template <class TA, class TB>
 static cudaError_t tmm(int* status, const TA* A, int64_t sam, int64_t sak, const TB* B,
                        int64_t sbk, int64_t sbn, float* C, int64_t ldc, int M, int N, int K,
-                       cudaStream_t st, DevMem* ws = nullptr, float* bias = nullptr) {
+                       cudaStream_t st, DevMem* ws = nullptr, float* bias = nullptr,
+                       ReduceSeg* defer = nullptr) {
     // bias (weight gradients): bias[m] = sum_k A(m, k), A an FP32 [K][M] matrix,
-    // computed as one more output column against an all-ones row of B
+    // computed as one more output column against an all-ones row of B.
+    // defer: the split-K partials' reduction is described in *defer for one
+    // later k_mm_reduce_multi launch instead of launched here (blocks 0: none)
+    if (defer) *defer = ReduceSeg{};
     const int NB = N + (bias ? 1 : 0);
     auto fallback = [&]() -> cudaError_t {
         cudaError_t e = mm(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, 0, st, ws);
@@ -249,8 +292,12 @@ static cudaError_t tmm(int* status, const TA* A, int64_t sam, int64_t sak, const
                      ws->as<float>(), status, st);
     if (e == cudaErrorNotSupported) return fallback();
     if (e != cudaSuccess) return e;
-    note_launch();
     const int64_t MN = (int64_t)M * NB;
+    if (defer) {
+        *defer = ReduceSeg{ws->as<float>(), (int)S, M, NB, C, ldc, bias, reduce_blocks(MN)};
+        return cudaSuccess;
+    }
+    note_launch();
     k_mm_reduce<<<reduce_blocks(MN), 256, 0, st>>>(ws->as<float>(), (int)S, M, NB, C, ldc, 0,
                                                     bias);
     return cudaGetLastError();
@@ -537,7 +584,8 @@ struct cc_sur {
     int64_t cap = 0;
     DevMem pts, tb, X0, A1, H1, Ef, E, X3, A3, H3, y, dy, dA3, dX3, dE, dH1, dA1, loss;
     DevMem order;
-    DevMem ws;  // split-K partials of the weight-gradient GEMMs
+    DevMem ws;  // split-K partials of the weight-gradient GEMMs: w4 / b4 chunks,
+    DevMem ws3, ws2, ws1;  // W3 / b3, W2 / b2, W1 / b1 (reduced together at the end)
     DevMem steps;  // per-step values of a training epoch, then the step cursor
 };
 
@@ -644,26 +692,27 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
     const SurOff& o = s->off;
     const bf16* wb = s->wb.as<bf16>();
     float* g = s->g.as<float>();
+    // the weight gradients' partials are summed by one launch at the end
+    ReduceSegs segs;
     // head output layer: w4 and b4 (adjacent) from per-chunk partial sums
     {
         const int64_t nb = (B + 63) / 64;
         SK(s->ws.ensure(sizeof(float) * (size_t)nb * (kH3 + 1)));
-        note_launch(2);
+        note_launch();
         k_sur_w4_grad<<<(unsigned)nb, kH3 + 32, 0, st>>>(s->H3.as<bf16>(), s->dy.as<float>(), B,
                                                          s->ws.as<float>());
-        k_mm_reduce<<<reduce_blocks(kH3 + 1), 256, 0, st>>>(s->ws.as<float>(), (int)nb, 1,
-                                                             kH3 + 1, g + o.w4, kH3 + 1, 0,
-                                                             nullptr);
+        segs.s[0] = ReduceSeg{s->ws.as<float>(), (int)nb, 1, kH3 + 1, g + o.w4, kH3 + 1, nullptr,
+                              reduce_blocks(kH3 + 1)};
     }
     SK(tmm(ctx->status.as<int>(), s->dA3.as<float>(), 1, kH3, s->X3.as<bf16>(), kHeadInP, 1,
-           g + o.W3, kHeadIn, kH3, kHeadIn, (int)B, st, &s->ws, g + o.b3));
+           g + o.W3, kHeadIn, kH3, kHeadIn, (int)B, st, &s->ws3, g + o.b3, &segs.s[1]));
     SK(tmm(ctx->status.as<int>(), s->dA3.as<float>(), kH3, 1, w3p(s), kHeadInP, 1,
            s->dX3.as<float>(), kHeadIn, (int)B, kHeadIn, kH3, st));
     k_sur_split<<<grid1(B * kE), 256, 0, st>>>(s->dX3.as<float>(), s->E.as<float>(), B,
                                                s->dE.as<float>());
     // encoder
     SK(tmm(ctx->status.as<int>(), s->dE.as<float>(), 1, kE, s->H1.as<bf16>(), kH1, 1, g + o.W2,
-           kH1, kE, kH1, (int)(2 * B), st, &s->ws, g + o.b2));
+           kH1, kE, kH1, (int)(2 * B), st, &s->ws2, g + o.b2, &segs.s[2]));
     note_launch(2);
     SK(tmm(ctx->status.as<int>(), s->dE.as<float>(), kE, 1, wb + o.W2, kH1, 1, s->dH1.as<float>(),
            kH1, (int)(2 * B), kH1, kE, st));
@@ -671,7 +720,13 @@ cc_status backward(cc_ctx* ctx, cc_sur* s, int64_t B) {
                                                        s->dH1.as<float>(), 2 * B, kH1,
                                                        s->dA1.as<float>());
     SK(tmm(ctx->status.as<int>(), s->dA1.as<float>(), 1, kH1, s->X0.as<bf16>(), ldz(n), 1, g + o.W1,
-           n, kH1, n, (int)(2 * B), st, &s->ws, g + o.b1));
+           n, kH1, n, (int)(2 * B), st, &s->ws1, g + o.b1, &segs.s[3]));
+    unsigned blocks = 0;
+    for (const ReduceSeg& r : segs.s) blocks += r.blocks;
+    if (blocks) {
+        note_launch();
+        k_mm_reduce_multi<<<blocks, 256, 0, st>>>(segs);
+    }
     SK(cudaGetLastError());
     return CC_OK;
 }
