@@ -20,6 +20,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -584,6 +585,8 @@ struct cc_sur {
     int64_t cap = 0;
     DevMem pts, tb, X0, A1, H1, Ef, E, X3, A3, H3, y, dy, dA3, dX3, dE, dH1, dA1, loss;
     DevMem order;
+    HostMem order_h[2];  // pinned epoch permutations (the next one is built while a step runs)
+    HostMem loss_h;      // pinned landing area of the periodic loss reads
     DevMem ws;  // split-K partials of the weight-gradient GEMMs: w4 / b4 chunks,
     DevMem ws3, ws2, ws1;  // W3 / b3, W2 / b2, W1 / b1 (reduced together at the end)
     DevMem steps;  // per-step values of a training epoch, then the step cursor
@@ -959,9 +962,15 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
     cc_status r = ensure_batch(ctx, s, B);
     if (r) return r;
     const int64_t steps = n_pairs / B;
-    // per-epoch shuffle: a seeded permutation (host Fisher-Yates on SplitMix64)
-    std::vector<int64_t> order(n_pairs);
+    // per-epoch shuffle: a seeded permutation (host Fisher-Yates on SplitMix64).
+    // Epoch e + 1's permutation is built by a second host thread into the
+    // other of two pinned buffers while epoch e's steps run on the GPU (the
+    // generator is used by one thread at a time, in epoch order, so every
+    // permutation is the one a sequential loop would draw); an event per
+    // buffer marks when its copy to the device has been done.
     SK(s->order.ensure(8 * n_pairs));
+    SK(s->order_h[0].ensure(8 * n_pairs));
+    SK(s->order_h[1].ensure(8 * n_pairs));
     uint64_t rs = seed ^ 0xA0761D6478BD642Full;
     auto next = [&]() {
         rs += 0x9E3779B97F4A7C15ull;
@@ -970,6 +979,32 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         return z ^ (z >> 31);
     };
+    auto shuffle_into = [&](int64_t* order) {
+        for (int64_t i = 0; i < n_pairs; ++i) order[i] = i;
+        for (int64_t i = n_pairs - 1; i > 0; --i) std::swap(order[i], order[next() % (i + 1)]);
+    };
+    struct Worker {  // joined on every way out of this function
+        std::thread t;
+        void join() {
+            if (t.joinable()) t.join();
+        }
+        ~Worker() { join(); }
+    } worker;
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        bool used[2] = {false, false};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } copied;
+    for (int b = 0; b < 2; ++b)
+        SK(cudaEventCreateWithFlags(&copied.e[b], cudaEventDisableTiming));
+    // loss reads every 64 steps land in pinned memory without a host wait
+    const int64_t reads = (steps + 63) / 64;
+    SK(s->loss_h.ensure(sizeof(double) * (size_t)std::max<int64_t>(1, reads * epochs)));
+    double* loss_h = s->loss_h.as<double>();
+    if (epochs > 0) worker.t = std::thread(shuffle_into, s->order_h[0].as<int64_t>());
     // Each step's kernels read the step's batch offset, swap stream and Adam
     // corrections from a device table (one entry per step of the epoch); the
     // first step runs directly, the second is captured into a CUDA graph
@@ -1000,9 +1035,15 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
     };
     cc_status res = CC_OK;
     for (int ep = 0; ep < epochs && res == CC_OK; ++ep) {
-        for (int64_t i = 0; i < n_pairs; ++i) order[i] = i;
-        for (int64_t i = n_pairs - 1; i > 0; --i) std::swap(order[i], order[next() % (i + 1)]);
-        SK(cudaMemcpyAsync(s->order.p, order.data(), 8 * n_pairs, cudaMemcpyHostToDevice, st));
+        const int b = ep & 1;
+        worker.join();  // this epoch's permutation is complete
+        SK(cudaMemcpyAsync(s->order.p, s->order_h[b].p, 8 * n_pairs, cudaMemcpyHostToDevice, st));
+        SK(cudaEventRecord(copied.e[b], st));
+        copied.used[b] = true;
+        if (ep + 1 < epochs) {  // the next one, into the other buffer once its copy is done
+            if (copied.used[b ^ 1]) SK(cudaEventSynchronize(copied.e[b ^ 1]));
+            worker.t = std::thread(shuffle_into, s->order_h[b ^ 1].as<int64_t>());
+        }
         for (int64_t k = 0; k < steps; ++k) {
             const int64_t t = s->step + k + 1;
             hsteps[k] = SurStep{k * B, (uint64_t)(s->step + k), 1.f - powf(0.9f, (float)t),
@@ -1011,7 +1052,6 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
         SK(cudaMemcpyAsync(dsteps, hsteps.data(), sizeof(SurStep) * (size_t)steps,
                            cudaMemcpyHostToDevice, st));
         SK(cudaMemsetAsync(cursor, 0, sizeof(int), st));
-        double sum = 0;
         for (int64_t k = 0; k < steps; ++k) {
             if (exec) {
                 note_launch(graph_kernels);
@@ -1041,19 +1081,22 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
                 note_launch(graph_kernels);
                 SK(cudaGraphLaunch(exec, st));
             }
-            if (epoch_loss && (k % 64 == 63 || k == steps - 1)) {
-                double l = 0;
-                SK(cudaMemcpyAsync(&l, s->loss.p, 8, cudaMemcpyDeviceToHost, st));
-                SK(cudaStreamSynchronize(st));
-                sum += l / B;
-            }
+            if (epoch_loss && (k % 64 == 63 || k == steps - 1))  // read k / 64 of the epoch
+                SK(cudaMemcpyAsync(loss_h + ep * reads + k / 64, s->loss.p, 8,
+                                   cudaMemcpyDeviceToHost, st));
         }
         s->step += steps;
-        if (epoch_loss) epoch_loss[ep] = (float)(sum / ((steps + 63) / 64));
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (res) return res;
     SK(cudaStreamSynchronize(st));
+    if (epoch_loss) {  // the mean of each epoch's loss reads, in read order
+        for (int ep = 0; ep < epochs; ++ep) {
+            double sum = 0;
+            for (int64_t j = 0; j < reads; ++j) sum += loss_h[ep * reads + j] / B;
+            epoch_loss[ep] = (float)(sum / reads);
+        }
+    }
     return CC_OK;
 }
 
