@@ -137,6 +137,9 @@ struct cc_ctx {
     cc::DevMem pair_a, pair_b, vals_out, partials, rp_out, ksg_nx, ksg_ny, ksg_eps, mixed;
     cc::DevMem approx;  // chunk extremes exported by cc_all_pairs_approx
     cc::HostMem host_out;  // pinned landing area of cc_all_pairs_topk's results
+    // surrogate training: pinned epoch permutations (the next one is drawn
+    // while an epoch runs) and the periodic loss reads
+    cc::HostMem sur_order[2], sur_loss;
     std::map<int, std::unique_ptr<cc::DevMem>> psi_fix;   // n -> int64 [n+1]
     std::map<int, std::unique_ptr<cc::DevMem>> clogc_fix; // n -> int64 [n+1]
     // host-to-device copies of an update overlap its ingest: a second stream

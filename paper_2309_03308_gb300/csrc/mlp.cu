@@ -585,8 +585,6 @@ struct cc_sur {
     int64_t cap = 0;
     DevMem pts, tb, X0, A1, H1, Ef, E, X3, A3, H3, y, dy, dA3, dX3, dE, dH1, dA1, loss;
     DevMem order;
-    HostMem order_h[2];  // pinned epoch permutations (the next one is built while a step runs)
-    HostMem loss_h;      // pinned landing area of the periodic loss reads
     DevMem ws;  // split-K partials of the weight-gradient GEMMs: w4 / b4 chunks,
     DevMem ws3, ws2, ws1;  // W3 / b3, W2 / b2, W1 / b1 (reduced together at the end)
     DevMem steps;  // per-step values of a training epoch, then the step cursor
@@ -945,22 +943,7 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
         db = hb.as<uint32_t>();
         dt = ht.as<float>();
     }
-    // target standardization from the training targets
-    {
-        std::vector<float> h(n_pairs);
-        SK(cudaMemcpyAsync(h.data(), dt, 4 * n_pairs, cudaMemcpyDeviceToHost, st));
-        SK(cudaStreamSynchronize(st));
-        double m = 0, v = 0;
-        for (float x : h) m += x;
-        m /= n_pairs;
-        for (float x : h) v += (x - m) * (x - m);
-        v /= n_pairs;
-        s->tmean = (float)m;
-        s->tsd = (float)std::max(sqrt(v), 1e-6);
-    }
     const int64_t B = std::min<int64_t>(batch, n_pairs);
-    cc_status r = ensure_batch(ctx, s, B);
-    if (r) return r;
     const int64_t steps = n_pairs / B;
     // per-epoch shuffle: a seeded permutation (host Fisher-Yates on SplitMix64).
     // Epoch e + 1's permutation is built by a second host thread into the
@@ -969,8 +952,9 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
     // permutation is the one a sequential loop would draw); an event per
     // buffer marks when its copy to the device has been done.
     SK(s->order.ensure(8 * n_pairs));
-    SK(s->order_h[0].ensure(8 * n_pairs));
-    SK(s->order_h[1].ensure(8 * n_pairs));
+    HostMem* order_h = ctx->sur_order;  // pinned, kept by the context for later calls
+    SK(order_h[0].ensure(8 * n_pairs));
+    SK(order_h[1].ensure(8 * n_pairs));
     uint64_t rs = seed ^ 0xA0761D6478BD642Full;
     auto next = [&]() {
         rs += 0x9E3779B97F4A7C15ull;
@@ -1002,9 +986,25 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
         SK(cudaEventCreateWithFlags(&copied.e[b], cudaEventDisableTiming));
     // loss reads every 64 steps land in pinned memory without a host wait
     const int64_t reads = (steps + 63) / 64;
-    SK(s->loss_h.ensure(sizeof(double) * (size_t)std::max<int64_t>(1, reads * epochs)));
-    double* loss_h = s->loss_h.as<double>();
-    if (epochs > 0) worker.t = std::thread(shuffle_into, s->order_h[0].as<int64_t>());
+    SK(ctx->sur_loss.ensure(sizeof(double) * (size_t)std::max<int64_t>(1, reads * epochs)));
+    double* loss_h = ctx->sur_loss.as<double>();
+    // the first permutation is drawn while the targets are standardized
+    if (epochs > 0) worker.t = std::thread(shuffle_into, order_h[0].as<int64_t>());
+    // target standardization from the training targets
+    {
+        std::vector<float> h(n_pairs);
+        SK(cudaMemcpyAsync(h.data(), dt, 4 * n_pairs, cudaMemcpyDeviceToHost, st));
+        SK(cudaStreamSynchronize(st));
+        double m = 0, v = 0;
+        for (float x : h) m += x;
+        m /= n_pairs;
+        for (float x : h) v += (x - m) * (x - m);
+        v /= n_pairs;
+        s->tmean = (float)m;
+        s->tsd = (float)std::max(sqrt(v), 1e-6);
+    }
+    cc_status r = ensure_batch(ctx, s, B);
+    if (r) return r;
     // Each step's kernels read the step's batch offset, swap stream and Adam
     // corrections from a device table (one entry per step of the epoch); the
     // first step runs directly, the second is captured into a CUDA graph
@@ -1037,12 +1037,12 @@ cc_status cc_sur_train(cc_ctx* ctx, cc_sur* s, int32_t field_id, const uint32_t*
     for (int ep = 0; ep < epochs && res == CC_OK; ++ep) {
         const int b = ep & 1;
         worker.join();  // this epoch's permutation is complete
-        SK(cudaMemcpyAsync(s->order.p, s->order_h[b].p, 8 * n_pairs, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(s->order.p, order_h[b].p, 8 * n_pairs, cudaMemcpyHostToDevice, st));
         SK(cudaEventRecord(copied.e[b], st));
         copied.used[b] = true;
         if (ep + 1 < epochs) {  // the next one, into the other buffer once its copy is done
             if (copied.used[b ^ 1]) SK(cudaEventSynchronize(copied.e[b ^ 1]));
-            worker.t = std::thread(shuffle_into, s->order_h[b ^ 1].as<int64_t>());
+            worker.t = std::thread(shuffle_into, order_h[b ^ 1].as<int64_t>());
         }
         for (int64_t k = 0; k < steps; ++k) {
             const int64_t t = s->step + k + 1;
