@@ -19,7 +19,8 @@
 //   on both sides at once; every visited j offers d_ij. The first k
 //   positions are taken unconditionally and sorted by a fixed network; the
 //   first step offers the next four positions of each side, every later step
-//   the next two, to a sorted register list of the k smallest (the new values
+//   the next two (four again in the pair-batch form, whose walks are long),
+//   to a sorted register list of the k smallest (the new values
 //   sorted, folded into the list's top entries, bitonic merger) and passes
 //   the positions whose axis distance was below the list's k-th value. When
 //   both next axis distances are not below the k-th value no unvisited j can
