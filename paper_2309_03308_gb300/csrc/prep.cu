@@ -79,7 +79,12 @@ cudaError_t launch_ingest(const float* in, int n, int64_t P, int64_t in_stride, 
 //                 FP64 reciprocal square root is shared with rhat's
 //   sorted, perm  ascending order, stable: a warp bitonic sort of the unique
 //                 64-bit keys (order-preserving bits of v + 0.0f, member index),
-//                 so -0.0 and +0.0 tie and equal values keep member order
+//                 so -0.0 and +0.0 tie and equal values keep member order. For
+//                 n_pad <= 128 the warp first sorts 32-bit keys (the top 25
+//                 order bits, the 7-bit member index): the same order whenever
+//                 no two members share those 25 bits (values within 2^7 ulp of
+//                 each other, ties included), which the warp checks on adjacent
+//                 sorted keys, taking the 64-bit sort otherwise
 //   rank2         2 * average rank (ties averaged): for a run of equal values
 //                 at sorted positions a..b, every member gets a + b + 2
 //                 (= 2L + E + 1 with L values below and E equal)
@@ -105,6 +110,42 @@ __device__ __forceinline__ float pow2_scale(float m) {
     int ex;
     frexpf(m, &ex);  // m = f * 2^ex, f in [0.5, 1)
     return ldexpf(1.f, min(1 - ex, 126));  // below 2^-126 (subnormal m): 2^126
+}
+
+// Ascending warp bitonic sort of 32 * E unique keys, lane l holding positions
+// l*E .. l*E+E-1. Exchange across lanes: the element takes its partner's key
+// when (partner < own) equals "this element keeps the minimum", one
+// comparison; the keep-minimum flag depends on the lane only, since
+// e < E <= d leaves the bits d and size of g0 + e to g0.
+template <int E, class K>
+__device__ __forceinline__ void warp_bitonic(K (&key)[E], int g0) {
+    constexpr int NP = 32 * E;
+#pragma unroll
+    for (int size = 2; size <= NP; size <<= 1) {
+#pragma unroll
+        for (int d = size >> 1; d > 0; d >>= 1) {
+            if (d >= E) {
+                const bool keep_min = ((g0 & d) == 0) == ((g0 & size) == 0);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const K o = __shfl_xor_sync(0xffffffffu, key[e], d / E);
+                    key[e] = ((o < key[e]) == keep_min) ? o : key[e];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int e2 = e ^ d;
+                    if (e2 > e) {
+                        const bool asc = ((g0 + e) & size) == 0;
+                        const bool swap = (key[e2] < key[e]) == asc;
+                        const K a = key[e], b = key[e2];
+                        key[e] = swap ? b : a;
+                        key[e2] = swap ? a : b;
+                    }
+                }
+            }
+        }
+    }
 }
 
 template <int E>
@@ -179,37 +220,34 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
         warp_sum_ff(ss_h, ss_l);
     }
 
-    // bitonic sort, ascending, over NP keys (unique: the member index is in
-    // the low word). Exchange across lanes: the element takes its partner's
-    // key when (partner < own) equals "this element keeps the minimum", one
-    // 64-bit comparison; the keep-minimum flag depends on the lane only, since
-    // e < E <= d leaves the bits d and size of g0 + e to g0.
+    // ascending sort of the unique 64-bit keys
+    bool sorted32 = false;
+    if constexpr (NP <= 128) {
+        unsigned k32[E];
 #pragma unroll
-    for (int size = 2; size <= NP; size <<= 1) {
+        for (int e = 0; e < E; ++e)
+            k32[e] = ((unsigned)(key[e] >> 32) & 0xffffff80u) | (unsigned)(g0 + e);
+        warp_bitonic<E>(k32, g0);
+        // the 64-bit keys' order unless two real members share the top 25
+        // bits; such members are adjacent in it
+        const unsigned next = __shfl_down_sync(0xffffffffu, k32[0], 1);
+        bool clash = false;
 #pragma unroll
-        for (int d = size >> 1; d > 0; d >>= 1) {
-            if (d >= E) {
-                const bool keep_min = ((g0 & d) == 0) == ((g0 & size) == 0);
+        for (int e = 0; e < E; ++e) {
+            const unsigned nk = e + 1 < E ? k32[e + 1] : next;
+            clash |= g0 + e + 1 < n && (nk >> 7) == (k32[e] >> 7);
+        }
+        if (!__any_sync(0xffffffffu, clash)) {  // the sorted 64-bit keys, rebuilt
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[e], d / E);
-                    key[e] = ((o < key[e]) == keep_min) ? o : key[e];
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int e2 = e ^ d;
-                    if (e2 > e) {
-                        const bool asc = ((g0 + e) & size) == 0;
-                        const bool swap = (key[e2] < key[e]) == asc;
-                        const unsigned long long a = key[e], b = key[e2];
-                        key[e] = swap ? b : a;
-                        key[e2] = swap ? a : b;
-                    }
-                }
+            for (int e = 0; e < E; ++e) {
+                const unsigned m = k32[e] & 0x7fu;
+                const unsigned hi = g0 + e < n ? order_bits(vals[row + m]) : 0xffffffffu;
+                key[e] = ((unsigned long long)hi << 32) | m;
             }
+            sorted32 = true;
         }
     }
+    if (!sorted32) warp_bitonic<E>(key, g0);
 
     // sorted values, permutation, and runs of equal values
     float sv[E];
