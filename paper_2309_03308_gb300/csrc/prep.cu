@@ -148,8 +148,14 @@ __device__ __forceinline__ void warp_bitonic(K (&key)[E], int g0) {
     }
 }
 
+// resident blocks per SM the register allocation must allow (E = 4: the
+// n <= 128 workloads, 9 blocks of 4 warps at <= 56 registers)
+__host__ __device__ constexpr int prep_min_blocks(int E) {
+    return E == 1 ? 12 : E == 2 ? 10 : E == 4 ? 9 : E == 8 ? 6 : E == 16 ? 4 : 3;
+}
+
 template <int E>
-__global__ void __launch_bounds__(kPrepWarps * 32)
+__global__ void __launch_bounds__(kPrepWarps * 32, prep_min_blocks(E))
     k_point_prep(const float* __restrict__ vals, int64_t p_begin, int64_t P, int n, float nf,
                  float* __restrict__ sorted,
                  uint16_t* __restrict__ perm, int16_t* __restrict__ rank2,
@@ -303,51 +309,60 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
         build(pb.B[0], pb.bins[0] + row, pb.hmarg[0]);
         if (pb.count > 1) build(pb.B[1], pb.bins[1] + row, pb.hmarg[1]);
     }
-    // run start a: prefix max of (start ? g : 0); run end b: suffix min of (end ? g : NP)
-    const float prev_last = __shfl_up_sync(0xffffffffu, sv[E - 1], 1);
-    const float next_first = __shfl_down_sync(0xffffffffu, sv[0], 1);
-    int a[E], b[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int g = g0 + e;
-        const float pv = e > 0 ? sv[e - 1] : prev_last;
-        const bool start = g == 0 || g >= n || !(pv == sv[e]);
-        a[e] = start ? g : 0;
-        if (e > 0) a[e] = max(a[e], a[e - 1]);
-    }
-#pragma unroll
-    for (int e = E - 1; e >= 0; --e) {
-        const int g = g0 + e;
-        const float nv = e < E - 1 ? sv[e + 1] : next_first;
-        const bool end = g >= n - 1 || !(nv == sv[e]);
-        b[e] = end ? g : NP;
-        if (e < E - 1) b[e] = min(b[e], b[e + 1]);
-    }
-    int carry_a = a[E - 1], carry_b = b[0];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int ta = __shfl_up_sync(0xffffffffu, carry_a, o);
-        const int tb = __shfl_down_sync(0xffffffffu, carry_b, o);
-        if (lane >= o) carry_a = max(carry_a, ta);
-        if (lane + o < 32) carry_b = min(carry_b, tb);
-    }
-    const int before_a = __shfl_up_sync(0xffffffffu, carry_a, 1);
-    const int after_b = __shfl_down_sync(0xffffffffu, carry_b, 1);
-    long long c2 = 0;
     int r2[E];
+    long long c2 = 0;
+    if (sorted32) {
+        // every value is distinct: the member at sorted position g has
+        // rank2 = 2g + 2, and the centred ranks 2g + 1 - n square-sum to
+        // n (n^2 - 1) / 3
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int g = g0 + e;
-        const int aa = lane > 0 ? max(a[e], before_a) : a[e];
-        const int bb = lane < 31 ? min(b[e], after_b) : b[e];
-        r2[e] = aa + bb + 2;
-        if (g < n) {
-            const long long c = r2[e] - (n + 1);
-            c2 += c * c;
+        for (int e = 0; e < E; ++e) r2[e] = 2 * (g0 + e) + 2;
+        c2 = (long long)n * ((long long)n * n - 1) / 3;
+    } else {
+        // run start a: prefix max of (start ? g : 0); run end b: suffix min of (end ? g : NP)
+        const float prev_last = __shfl_up_sync(0xffffffffu, sv[E - 1], 1);
+        const float next_first = __shfl_down_sync(0xffffffffu, sv[0], 1);
+        int a[E], b[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int g = g0 + e;
+            const float pv = e > 0 ? sv[e - 1] : prev_last;
+            const bool start = g == 0 || g >= n || !(pv == sv[e]);
+            a[e] = start ? g : 0;
+            if (e > 0) a[e] = max(a[e], a[e - 1]);
         }
+#pragma unroll
+        for (int e = E - 1; e >= 0; --e) {
+            const int g = g0 + e;
+            const float nv = e < E - 1 ? sv[e + 1] : next_first;
+            const bool end = g >= n - 1 || !(nv == sv[e]);
+            b[e] = end ? g : NP;
+            if (e < E - 1) b[e] = min(b[e], b[e + 1]);
+        }
+        int carry_a = a[E - 1], carry_b = b[0];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ta = __shfl_up_sync(0xffffffffu, carry_a, o);
+            const int tb = __shfl_down_sync(0xffffffffu, carry_b, o);
+            if (lane >= o) carry_a = max(carry_a, ta);
+            if (lane + o < 32) carry_b = min(carry_b, tb);
+        }
+        const int before_a = __shfl_up_sync(0xffffffffu, carry_a, 1);
+        const int after_b = __shfl_down_sync(0xffffffffu, carry_b, 1);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int g = g0 + e;
+            const int aa = lane > 0 ? max(a[e], before_a) : a[e];
+            const int bb = lane < 31 ? min(b[e], after_b) : b[e];
+            r2[e] = aa + bb + 2;
+            if (g < n) {
+                const long long c = r2[e] - (n + 1);
+                c2 += c * c;
+            }
+        }
+        // each c^2 <= n^2 <= 2^20 and n <= 1024 values: the sum fits 32 bits
+        c2 = (long long)__reduce_add_sync(0xffffffffu, (unsigned)c2);
     }
-    // each c^2 <= n^2 <= 2^20 and n <= 1024 values: the sum fits 32 bits
-    c2 = (long long)__reduce_add_sync(0xffffffffu, (unsigned)c2);
     // FP64 finalisation, one instruction stream for both norms: lane 0 the
     // sum of squared deviations, lane 1 the sum of squared centred ranks
     const double ss_s = (double)ss_h + (double)ss_l;  // in units of (vscale dscale)^2
