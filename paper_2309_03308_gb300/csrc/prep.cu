@@ -76,7 +76,7 @@ cudaError_t launch_ingest(const float* in, int n, int64_t P, int64_t in_stride, 
 //                 few instructions: this GPU's FP64 rate is a small fraction of
 //                 its FP32 rate)
 //   zhat          (v - mean) / sqrt(ss) rounded to fp32 (0 when ss == 0); the
-//                 FP64 reciprocal square root is shared with rhat's
+//                 scale 1 / sqrt(ss) by a float-float Newton step (ff_rsqrt)
 //   sorted, perm  ascending order, stable: a warp bitonic sort of the unique
 //                 64-bit keys (order-preserving bits of v + 0.0f, member index),
 //                 so -0.0 and +0.0 tie and equal values keep member order. For
@@ -97,6 +97,25 @@ __device__ __forceinline__ unsigned order_bits(float v) {
 }
 __device__ __forceinline__ float unorder_bits(unsigned o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// 1 / sqrt(h + l) rounded to fp32, for a float-float h + l with h > 0 and
+// |l| <= ulp(h) / 2: the hardware estimate y (relative error e0 ~ 2^-22) and
+// one Newton step y (1 + e / 2 + 3 e^2 / 8) on the residual e = 1 - (h + l) y^2,
+// which is formed from exact FMA products (absolute error ~2^-44). The value
+// before the final rounding is within ~2^-43 of 1 / sqrt(h + l), so the result
+// is the correctly rounded one except within that distance of a rounding
+// boundary. FP32 pipe only: a warp-wide FP64 instruction holds GB300's narrow
+// FP64 pipe for many cycles.
+__device__ __forceinline__ float ff_rsqrt(float h, float l) {
+    const float y = rsqrtf(h);
+    const float yy = __fmul_rn(y, y);
+    const float yy_l = fmaf(y, y, -yy);  // y^2 = yy + yy_l exactly
+    float e = fmaf(-h, yy, 1.0f);        // 1 - h yy, the product exact
+    e = fmaf(-h, yy_l, e);
+    e = fmaf(-l, yy, e);
+    const float t = fmaf(0.375f * e, e, 0.5f * e);
+    return fmaf(y, t, y);
 }
 
 // warp maximum of non-negative floats: their bit patterns order as integers
@@ -363,14 +382,13 @@ __global__ void __launch_bounds__(kPrepWarps * 32, prep_min_blocks(E))
         // each c^2 <= n^2 <= 2^20 and n <= 1024 values: the sum fits 32 bits
         c2 = (long long)__reduce_add_sync(0xffffffffu, (unsigned)c2);
     }
-    // FP64 finalisation, one instruction stream for both norms: lane 0 the
-    // sum of squared deviations, lane 1 the sum of squared centred ranks
-    const double ss_s = (double)ss_h + (double)ss_l;  // in units of (vscale dscale)^2
-    const double x = lane == 0 ? ss_s : (double)c2;
-    const double r = x > 0.0 ? rsqrt(x) : 0.0;
-    const float inv = (float)__shfl_sync(0xffffffffu, r, 0);
-    const float rinv = (float)__shfl_sync(0xffffffffu, r, 1);
-    if (lane == 0) {  // undo the power-of-two scalings (exact reciprocals)
+    // the two norms' reciprocal square roots on the FP32 pipe (the sums are
+    // the same on every lane; c2 < 2^29 splits exactly into two floats)
+    const float inv = ss_h > 0.f ? ff_rsqrt(ss_h, ss_l) : 0.f;
+    const float c2h = (float)c2;
+    const float rinv = c2 > 0 ? ff_rsqrt(c2h, (float)(c2 - (long long)c2h)) : 0.f;
+    if (lane == 0) {  // FP64 statistics; undo the power-of-two scalings (exact reciprocals)
+        const double ss_s = (double)ss_h + (double)ss_l;  // in units of (vscale dscale)^2
         const double rv = (double)__frcp_rn(vscale), rs = rv * (double)__frcp_rn(dscale);
         mean_out[p] = ((double)mean_h + (double)mean_l) * rv;
         ss_out[p] = ss_s * (rs * rs);
