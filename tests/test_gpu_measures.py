@@ -76,6 +76,55 @@ def test_planes_with_ties(cc, orc):
     assert np.all(z == 0)
 
 
+def _near_equal_rows(n, rng):
+    """Member vectors whose values sit a fixed number of ulps apart (1, 127,
+    128, 129) around 1 and -1, subnormals around zero with both signed zeros,
+    one 1-ulp pair in random data, and random rows, each row permuted."""
+    one = np.float32(1.0).view(np.int32)
+    rows = []
+    for step in (1, 127, 128, 129):
+        rows.append((one + step * np.arange(n, dtype=np.int32)).view(np.float32))
+    rows.append(-(one + np.arange(n, dtype=np.int32)).view(np.float32))
+    sub = (np.arange(n, dtype=np.int32) - n // 2).astype(np.float32) * np.float32(2.0 ** -149)
+    sub[0], sub[1] = np.float32(-0.0), np.float32(0.0)
+    rows.append(sub)
+    r = rng.standard_normal(n).astype(np.float32)
+    r[1] = (r[0].view(np.int32) + 1).view(np.float32)
+    rows.append(r)
+    for _ in range(9):
+        rows.append(rng.standard_normal(n).astype(np.float32))
+    return np.stack([rng.permutation(x) for x in rows], axis=1)  # [n][rows]
+
+
+@pytest.mark.parametrize("n", [32, 100, 128])
+def test_planes_near_equal_values(cc, orc, n):
+    """Values closer than the sort's first-pass key resolution (2^7 ulp), but
+    distinct, next to rows that it separates: ranks, sorted values and bins
+    bit-exact, z-scores within a few fp32 roundings, KSG counts bit-exact."""
+    rng = np.random.default_rng(17 + n)
+    F = _near_equal_rows(n, rng).reshape(n, 1, 4, 4)
+    fid = cc.load_field(F)
+    pts = np.arange(16, dtype=np.uint32)
+    assert np.array_equal(cc.get_plane(fid, 0, pts, n), orc.rank2(F, pts))
+    for B in (8, 16):
+        assert np.array_equal(cc.get_plane(fid, 1, pts, n, bins=B), orc.bins(F, pts, B))
+    srt = cc.get_plane(fid, 2, pts, n)
+    assert np.array_equal(srt, np.sort(F.reshape(n, -1).T, axis=1))
+    z = cc.get_plane(fid, 3, pts, n).astype(np.float64)
+    V = F.reshape(n, -1).T.astype(np.float64)
+    d = V - V.mean(axis=1, keepdims=True)
+    ss = (d * d).sum(axis=1, keepdims=True)
+    ref = np.divide(d, np.sqrt(ss), out=np.zeros_like(d), where=ss > 0)
+    assert np.all(np.abs(z - ref) <= 4 * 2.0 ** -24 * np.abs(ref).max(axis=1, keepdims=True))
+    pa, pb = np.meshgrid(pts, pts, indexing="ij")
+    pa, pb = pa.ravel(), pb.ravel()
+    out, nx, ny, eps = cc.ksg_counts(fid, fid, 3, pa, pb, n)
+    ref_v, rnx, rny, reps = orc.eval_pairs(F, oracle.MI_KSG, pa, pb, k=3, want_ksg=True)
+    assert np.array_equal(eps, reps)
+    assert np.array_equal(nx, rnx) and np.array_equal(ny, rny)
+    cc.free_field(fid)
+
+
 def test_update_field_rebuilds_every_plane(cc, orc):
     """After cc_update_field the planes, including the bin planes of the bin
     counts already in use (rebuilt in the per-point pass) and of a new bin
